@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Throughput of QAOA Max-Cut edge-network contraction on GB300.
+
+One step = one evaluation of <C>(gamma, beta) and its gradient for one
+graph: every per-edge <Z_u Z_v> light-cone network is contracted (forward
+pass) and swept backwards (adjoint), and the per-edge scalars are reduced to
+<C> and d<C>/d(gamma, beta) in FP64 - all in one launch of the executor.
+The planner (host) runs once before timing, as the paper excludes ordering
+time.  `value` is edge networks per second with inputs resident in device
+memory; `e2e` is the same through the host-pointer C call (pinned inputs
+copied in, results copied out, every step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference   # the FP64 CPU oracle on the same metric
+
+With N > 1 (torchrun) every rank contracts its own seeded graph of the
+same family (independent problems, weak scaling) and no collective touches
+the data path.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import WORKLOADS  # noqa: E402
+
+DEFAULT_WORKLOAD = "qaoa_p1_n50_d3"
+METRIC = "edge-<ZZ> networks/s (value + gradient)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--dtype", default=None, help="override the workload's element type")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_config(w, networks, want_grad, dtype):
+    return {
+        "workload": w.name,
+        "graph": f"{w.d}-regular, n={w.n}, configuration model seed {w.graph_seed}",
+        "p": w.p,
+        "networks_per_step": networks,
+        "ordering": w.ordering,
+        "form": ("diagonal ZZ (hyperedges)" if w.diag else "rank-4 ZZ") +
+                (", light cone" if w.lightcone else ", full network"),
+        "want_grad": want_grad,
+        "dtype": dtype,
+        "l2": "flushed between timed steps (256 MiB write outside the events)",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def oracle_networks_per_s(w, edges, g, b, want_grad, seconds):
+    """The FP64 oracle (O-TN, forward-mode gradient) on a bounded sample."""
+    from oracle import tensornet as tn
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        for e in edges:
+            if want_grad:
+                tn.edge_value_grad(w.n, edges, g, b, e, lightcone=w.lightcone, dense=not w.diag)
+            else:
+                tn.edge_value(w.n, edges, g, b, e, lightcone=w.lightcone, dense=not w.diag)
+            done += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                return done / el, done, el
+
+
+def run_reference(args):
+    """The oracle as the reference arm: same metric, rank 0 only."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    edges = w.graph()
+    g, b = w.angles()
+    want_grad = True
+    sample = edges[:min(len(edges), 25)]
+    for _ in range(args.warmup):
+        oracle_networks_per_s(w, edges, g, b, want_grad, 0.0)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        from oracle import tensornet as tn
+        for e in sample:
+            tn.edge_value_grad(w.n, edges, g, b, e, lightcone=w.lightcone, dense=not w.diag)
+        times.append(time.perf_counter() - t0)
+    per_step = sum(times) / len(times)
+    value = len(sample) / per_step
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": "networks/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "config": workload_config(w, len(sample), want_grad, "c128"),
+        "cpu_baseline": {"value": value, "unit": "networks/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(sample)} of {len(edges)} edge networks per step, "
+                                   "FP64 tensor-network oracle with forward-mode gradient"},
+        "e2e": {"value": value, "unit": "networks/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_1709_03636_gb300 as q
+    from paper_1709_03636_gb300 import _lib
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    base = WORKLOADS[args.workload]
+    dtype = args.dtype or base.dtype
+    want_grad = True
+    # rank r contracts graph seed (seed + r): independent problems
+    from dataclasses import replace
+    w = replace(base, graph_seed=base.graph_seed + rank)
+    edges = w.graph()
+    g, b = w.angles()
+    circ = q.Circuit.qaoa(w.n, edges, w.p)
+    batch = q.Batch(circ, lightcone=w.lightcone, diag=w.diag, ordering=w.ordering)
+    stats = batch.stats()
+    n_nets = stats["n_networks"]
+    engine = q.Engine(local, arena_bytes=1 << 30)
+    batch.prepare(engine, dtype, want_grad=want_grad)
+    batch.prepare(engine, dtype, want_grad=False)
+    P = 2 * w.p
+    params = torch.tensor(g + b, dtype=torch.float64, device=dev)
+    out = torch.zeros(1 + P + n_nets, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def device_step(grad):
+        q.qaoa_expectation_device(engine, batch, params, out, dtype, want_grad=grad,
+                                  stream=stream)
+
+    def timed(fn, steps):
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            fn()
+            e.record(stream)
+            evs.append((s, e))
+        torch.cuda.synchronize()
+        return [s.elapsed_time(e) for s, e in evs]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        device_step(True)
+        device_step(False)
+    barrier()
+    with ClockSampler(local) as clocks:
+        wall0 = time.perf_counter()
+        step_ms = timed(lambda: device_step(True), args.steps)
+        wall = time.perf_counter() - wall0
+    launches = args.steps * engine.last_launches
+    barrier()
+    fwd_ms = timed(lambda: device_step(False), args.steps)
+    barrier()
+
+    # end to end through the host-pointer call: pinned params in, results out
+    h_gam = torch.tensor(g, dtype=torch.float64).pin_memory()
+    h_bet = torch.tensor(b, dtype=torch.float64).pin_memory()
+    h_C = torch.zeros(1, dtype=torch.float64).pin_memory()
+    h_edge = torch.zeros(n_nets, dtype=torch.float64).pin_memory()
+    h_grad = torch.zeros(P, dtype=torch.float64).pin_memory()
+    vp = lambda t: q.ctypes.c_void_p(t.data_ptr())  # noqa: E731
+
+    def e2e_step():
+        _lib.check(_lib.lib.qtc_qaoa_expectation(
+            engine.ptr, batch.ptr, q.ctypes.cast(vp(h_gam), q.ctypes.POINTER(q.ctypes.c_double)),
+            q.ctypes.cast(vp(h_bet), q.ctypes.POINTER(q.ctypes.c_double)),
+            q.DTYPES[dtype], 1, q.ctypes.c_void_p(stream.cuda_stream),
+            q.ctypes.cast(vp(h_C), q.ctypes.POINTER(q.ctypes.c_double)),
+            q.ctypes.cast(vp(h_edge), q.ctypes.POINTER(q.ctypes.c_double)),
+            q.ctypes.cast(vp(h_grad), q.ctypes.POINTER(q.ctypes.c_double))))
+
+    for _ in range(args.warmup):
+        e2e_step()
+    barrier()
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_times.append(time.perf_counter() - t0)
+    barrier()
+
+    ms = sum(step_ms) / len(step_ms)
+    e2e_s = sum(e2e_times) / len(e2e_times)
+    fwd = sum(fwd_ms) / len(fwd_ms)
+    if world > 1:
+        t = torch.tensor([ms, e2e_s, fwd], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, e2e_s, fwd = t.tolist()
+    value = world * n_nets / (ms * 1e-3)
+    elem = 16 if dtype == "c128" else 8
+    alg_bytes = (stats["bytes_c64"] + stats["grad_bytes_c64"]) * elem / 8
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "networks/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+        "data": "synthetic", "config": workload_config(w, n_nets, want_grad, dtype),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "smem_exec_kernel", "peak_kind": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "e2e": {"value": world * n_nets / e2e_s, "unit": "networks/s",
+                "h2d_bytes_per_step": 8 * P, "d2h_bytes_per_step": 8 * (1 + P + n_nets)},
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+        "forward_only": {"value": world * n_nets / (fwd * 1e-3), "unit": "networks/s",
+                         "ms_per_step": fwd},
+        "grad_fwd_ratio": ms / fwd,
+        "timed_wall_s": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, done, el = oracle_networks_per_s(w, edges, g, b, want_grad, 10.0)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": "networks/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} edge networks of {w.name} with gradient in {el:.1f} s "
+                      "(FP64 tensor-network oracle, numpy einsum, one thread)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * qtc.h — C ABI of the GB300 tensor-network contraction engine for quantum
+ * circuits (QAOA Max-Cut), after "qTorch: The quantum tensor contraction
+ * handler" (arXiv 1709.03636).
+ *
+ * The problem (Section 1): given a circuit and an initial state, compute an
+ * expectation value <psi|M|psi> (Section 3.3) or an amplitude.  The pipeline
+ * follows Sections 2-3: circuit -> closed tensor network -> contraction
+ * ordering (Algorithm 1 "LG" or Algorithm 2 "Stoch") -> a sequence of
+ * pairwise contractions (Eq. 1) -> scalar.
+ *
+ * Conventions for every call:
+ *  - All functions return a qtc_status; none aborts.  On failure the
+ *    thread-local message from qtc_last_error() says why.
+ *  - Host arrays passed in are copied before the call returns; the caller
+ *    keeps ownership.  Output pointers are owned by the caller.
+ *  - "device" pointers are CUDA global-memory addresses on the engine's
+ *    device; "host" pointers are ordinary (pageable or pinned) host memory.
+ *  - Device memory is never allocated by the library: every device buffer it
+ *    uses lives in the arena the caller hands to qtc_engine_create.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls with host outputs synchronise that stream before they
+ *    return; calls with device outputs are asynchronous on it.
+ *  - Handles are not thread-safe; use one engine per host thread.
+ */
+#ifndef QTC_H
+#define QTC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum qtc_status {
+  QTC_OK = 0,
+  QTC_ERR_INVALID = 1,     /* bad argument, graph, observable or handle      */
+  QTC_ERR_ARENA = 2,       /* the plan needs more arena than was given        */
+  QTC_ERR_TIMEOUT = 3,     /* a bounded device-side wait expired              */
+  QTC_ERR_CUDA = 4,        /* a CUDA runtime call failed                      */
+  QTC_ERR_UNSUPPORTED = 5  /* valid request this build does not implement     */
+} qtc_status;
+
+/* Element type of the contraction.  C128 = complex double; C64 = complex
+ * float with FP32 accumulation; SPLIT_BF16 = C64, except that contraction
+ * steps large enough to be dense GEMMs run on the tensor cores with each
+ * FP32 operand split into two BF16 parts (hi + lo) and the three products
+ * hi*hi + hi*lo + lo*hi accumulated in FP32. */
+typedef enum qtc_dtype { QTC_C128 = 0, QTC_C64 = 1, QTC_SPLIT_BF16 = 2 } qtc_dtype;
+
+/* Gates (Section 2: nodes of the network).  Angles follow
+ * RX(t) = exp(-i t X/2), RZ(t) = exp(-i t Z/2), ZZ(t) = exp(-i t Z(x)Z/2);
+ * the QAOA phase gate of Section 4.1 is ZZ(gamma) and the mixer
+ * exp(-i beta X) is RX(2 beta). */
+typedef enum qtc_gate {
+  QTC_GATE_H = 0, QTC_GATE_X = 1, QTC_GATE_Y = 2, QTC_GATE_Z = 3,
+  QTC_GATE_RX = 4, QTC_GATE_RZ = 5, QTC_GATE_ZZ = 6, QTC_GATE_CNOT = 7
+} qtc_gate;
+
+/* Observables (Section 3.3: <psi|M|psi> for a Pauli string M, or the
+ * amplitude <x|psi> of one basis state). */
+typedef enum qtc_obs_kind {
+  QTC_OBS_ZZ = 0,         /* Z_u Z_v                                        */
+  QTC_OBS_IDENTITY = 1,   /* the identity: <psi|psi> = 1 (needs lightcone=0) */
+  QTC_OBS_PAULI = 2,      /* pauli[q] in {'I','X','Y','Z'} for q = 0..n-1    */
+  QTC_OBS_AMPLITUDE = 3   /* <x|psi>, x given by bits[q] in {0,1}            */
+} qtc_obs_kind;
+
+typedef struct qtc_observable {
+  int kind;               /* qtc_obs_kind                                   */
+  int u, v;               /* qubits of QTC_OBS_ZZ                           */
+  const char* pauli;      /* QTC_OBS_PAULI: n characters, host              */
+  const uint8_t* bits;    /* QTC_OBS_AMPLITUDE: n bytes, host               */
+} qtc_observable;
+
+/* Contraction ordering (Section 3.1). */
+typedef enum qtc_order_kind {
+  QTC_ORDER_STOCH = 0,    /* Algorithm 2: random wire, rank-growth threshold */
+  QTC_ORDER_LG = 1        /* Algorithm 1: elimination ordering of the line
+                             graph, found by min-fill with random restarts   */
+} qtc_order_kind;
+
+typedef struct qtc_plan_opts {
+  int kind;               /* qtc_order_kind                                 */
+  uint64_t seed;          /* SplitMix64 seed of the random choices          */
+  int max_rejections;     /* Stoch: MaxRejections (<= 0 means 10)           */
+  int restarts;           /* LG: number of randomised min-fill runs (<=0: 8)*/
+  double budget_ms;       /* LG: stop restarting after this long (<=0: none)*/
+} qtc_plan_opts;
+
+typedef struct qtc_plan_info {
+  int n_tensors;          /* leaves of the network                          */
+  int n_labels;           /* distinct indices (wires / hyperedges)          */
+  int n_steps;            /* pairwise contractions (Eq. 1)                  */
+  int max_rank;           /* largest intermediate rank (width + 1 bound)    */
+  double cmacs;           /* complex multiply-adds: sum of 2^(b+x+y+z)      */
+  double bytes_c64;       /* algorithmic bytes: sum 8*(|A|+|B|+|C|)         */
+  double lg_width;        /* LG: width of the line-graph elimination order  */
+} qtc_plan_info;
+
+typedef struct qtc_batch_info {
+  int n_networks;
+  int n_params;
+  int max_rank;           /* over all networks                              */
+  int n_steps_total;
+  double cmacs;           /* forward, all networks                          */
+  double bytes_c64;       /* forward algorithmic bytes, all networks        */
+  int n_smem_networks;    /* networks executed entirely in shared memory    */
+  int n_global_networks;  /* networks with steps executed from global memory*/
+  double grad_cmacs;      /* adjoint sweep only: two contractions per step  */
+  double grad_bytes_c64;  /* adjoint sweep only, algorithmic bytes          */
+} qtc_batch_info;
+
+typedef struct qtc_engine qtc_engine;
+typedef struct qtc_circuit qtc_circuit;
+typedef struct qtc_network qtc_network;
+typedef struct qtc_plan qtc_plan;
+typedef struct qtc_batch qtc_batch;
+
+/* Last error message of the calling thread ("" if none).  Valid until the
+ * next failing call on this thread. */
+const char* qtc_last_error(void);
+
+/* ---- engine -------------------------------------------------------------
+ * An engine binds one CUDA device and one caller-owned device arena
+ * [arena, arena + arena_bytes), 256-byte aligned.  Plans, intermediates,
+ * counters and results are carved from it; the library never calls
+ * cudaMalloc.  The arena must stay valid until qtc_engine_destroy. */
+qtc_status qtc_engine_create(int device, void* arena, size_t arena_bytes,
+                             qtc_engine** out);
+void qtc_engine_destroy(qtc_engine* e);
+/* Forget every prepared program, making the whole arena free again. */
+qtc_status qtc_engine_reset(qtc_engine* e);
+
+/* ---- circuits (Section 2, Section 4.1) ---------------------------------
+ * A circuit has n qubits starting in |0>, a list of gates, and n_params
+ * real parameters.  A gate's angle is coeff * params[slot] + constant
+ * (slot = -1: constant only). */
+qtc_status qtc_circuit_create(int n, int n_params, qtc_circuit** out);
+qtc_status qtc_circuit_add_gate(qtc_circuit* c, int gate, const int32_t* qubits,
+                                int slot, double coeff, double constant);
+/* QAOA Max-Cut circuit of Section 4.1 on the graph with m edges
+ * edges[2i], edges[2i+1] (host): H on every qubit, then for k = 1..p the
+ * phase gates ZZ(gamma_k) on every edge and RX(2 beta_k) on every qubit.
+ * Parameters: slot k-1 = gamma_k, slot p+k-1 = beta_k.  The edge list is
+ * kept as the default set of ZZ observables of qtc_batch_create. */
+qtc_status qtc_circuit_qaoa(int n, const int32_t* edges, int m, int p,
+                            qtc_circuit** out);
+void qtc_circuit_destroy(qtc_circuit* c);
+
+/* ---- networks (Section 2) ----------------------------------------------
+ * Builds the closed network of <psi|M|psi> as a ket network, its complex
+ * conjugate (bra) and the observable between them, with bond dimension 2
+ * (Section 2 uses dimension-4 superoperator wires; fusing each ket/bra wire
+ * pair gives that form back).  lightcone != 0 keeps only the gates in the
+ * reverse light cone of the observable.  diag_mode != 0 attaches diagonal
+ * gates (ZZ, RZ, Z) to the wire they act on, so one index may be shared by
+ * more than two tensors; diag_mode = 0 gives every gate its own input and
+ * output wires (rank-4 ZZ tensors).  A leading H on |0> is folded into the
+ * state |+>. */
+qtc_status qtc_network_build(const qtc_circuit* c, const qtc_observable* obs,
+                             int lightcone, int diag_mode, qtc_network** out);
+/* Leaves of a network, for inspection.  counts: host, 2 ints
+ * (n_leaves, n_labels).  Each array may be NULL; otherwise it holds n_leaves
+ * entries (labels: 4 per leaf, unused slots -1), host:
+ * kind (LeafKind code, see device_program.h), conj (1 = bra side, values
+ * complex-conjugated), slot/coeff/constant (angle = coeff*params[slot] +
+ * constant), labels in storage order (label k = bit k of the element index). */
+qtc_status qtc_network_leaves(const qtc_network* n, int32_t* counts, int32_t* kind,
+                              int32_t* conj, int32_t* slot, double* coeff,
+                              double* constant, int32_t* labels);
+void qtc_network_destroy(qtc_network* n);
+
+/* ---- plans (Section 3.1, Algorithms 1 and 2) ---------------------------- */
+qtc_status qtc_plan_create(const qtc_network* n, const qtc_plan_opts* opts,
+                           qtc_plan** out);
+qtc_status qtc_plan_stats(const qtc_plan* p, qtc_plan_info* info);
+/* Writes the contraction tree: for step s, operands (lhs[s], rhs[s]) are
+ * tensor ids (0..n_tensors-1 leaves, n_tensors+t the result of step t).
+ * Arrays hold n_steps entries (host). */
+qtc_status qtc_plan_steps(const qtc_plan* p, int32_t* lhs, int32_t* rhs);
+void qtc_plan_destroy(qtc_plan* p);
+
+/* Contract one network on the GPU (Eq. 1 applied step by step).
+ * params: host, n_params values.  out_re_im: host, 2 doubles (the scalar
+ * <psi|M|psi> or <x|psi>).  grad_re_im: host, nullable, 2*n_params doubles:
+ * d(scalar)/d(params[k]) as (re, im) pairs, by the adjoint sweep. */
+qtc_status qtc_contract(qtc_engine* e, const qtc_plan* p, const double* params,
+                        int dtype, void* stream, double* out_re_im,
+                        double* grad_re_im);
+
+/* ---- QAOA batches (all edge networks of one graph) ---------------------
+ * One <Z_u Z_v> network per observable edge obs_edges[2i], [2i+1] (host;
+ * NULL = the circuit's QAOA edges), each with its own plan. */
+qtc_status qtc_batch_create(const qtc_circuit* c, const int32_t* obs_edges,
+                            int m, int lightcone, int diag_mode,
+                            const qtc_plan_opts* opts, qtc_batch** out);
+qtc_status qtc_batch_stats(const qtc_batch* b, qtc_batch_info* info);
+void qtc_batch_destroy(qtc_batch* b);
+
+/* Upload the batch's device program for (dtype, want_grad) into the arena.
+ * Optional: the expectation calls below prepare on first use. */
+qtc_status qtc_batch_prepare(qtc_engine* e, qtc_batch* b, int dtype,
+                             int want_grad, void* stream);
+
+/* <C> = sum_i (1 - <Z_u Z_v>_i)/2 over the batch's edges (Eqs. for the
+ * Max-Cut objective and its clauses, Section 4.1), and its gradient.
+ * gammas, betas: host, p values each.  C_out: host, 1 double.
+ * per_edge_out: host, nullable, m doubles <Z_u Z_v>_i.
+ * grad_out: host, nullable (needs want_grad), 2p doubles
+ * d<C>/d(gamma_1..p, beta_1..p).  Synchronises `stream`. */
+qtc_status qtc_qaoa_expectation(qtc_engine* e, qtc_batch* b,
+                                const double* gammas, const double* betas,
+                                int dtype, int want_grad, void* stream,
+                                double* C_out, double* per_edge_out,
+                                double* grad_out);
+
+/* Same computation with device-resident inputs and outputs, asynchronous
+ * on `stream` (no host synchronisation; capturable in a CUDA graph once the
+ * batch is prepared).  params_dev: device, 2p doubles (gammas then betas).
+ * out_dev: device, 1 + 2p + m doubles: [<C>, d<C>/dtheta (2p, zeros when
+ * want_grad = 0), <Z_u Z_v> per edge (m)]. */
+qtc_status qtc_qaoa_expectation_device(qtc_engine* e, qtc_batch* b,
+                                       const double* params_dev, int dtype,
+                                       int want_grad, void* stream,
+                                       double* out_dev);
+
+/* Number of kernel launches the last expectation or contract call on this
+ * engine issued (for launch accounting). */
+int qtc_engine_last_launches(const qtc_engine* e);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QTC_H */

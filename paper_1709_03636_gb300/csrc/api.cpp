@@ -1,0 +1,632 @@
+// C ABI of the engine (declared in include/qtc.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <thread>
+
+#include <cuda_runtime.h>
+
+#include "exec_launch.h"
+#include "qtc_internal.h"
+
+namespace qtc {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+[[noreturn]] void fail(qtc_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  throw Error{s, buf};
+}
+
+static void cuda_check(cudaError_t err, const char* what) {
+  if (err != cudaSuccess)
+    fail(QTC_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(err), cudaGetErrorString(err));
+}
+
+template <typename F>
+static qtc_status guarded(F&& f) {
+  try {
+    f();
+    return QTC_OK;
+  } catch (const Error& e) {
+    set_last_error(e.msg);
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host out of memory");
+    return QTC_ERR_INVALID;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return QTC_ERR_INVALID;
+  }
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    cuda_check(cudaGetDevice(&prev), "cudaGetDevice");
+    if (prev != dev) cuda_check(cudaSetDevice(dev), "cudaSetDevice");
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != prev && prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// A batch's program resident in one engine's arena.
+struct Prepared {
+  const void* engine = nullptr;
+  uint64_t generation = 0;
+  int dtype = 0;
+  int want_grad = 0;
+  ProgramDev prog{};
+  int grid = 0, block = 0;
+  size_t smem = 0;
+};
+
+}  // namespace qtc
+
+using namespace qtc;
+
+struct qtc_engine {
+  int device = 0;
+  char* arena = nullptr;
+  size_t bytes = 0;
+  size_t used = 0;
+  uint64_t generation = 1;
+  int sm_count = 0;
+  size_t smem_optin = 0;
+  int last_launches = 0;
+
+  char* alloc(size_t n) {
+    size_t at = (used + 255) & ~size_t(255);
+    if (at + n > bytes)
+      fail(QTC_ERR_ARENA, "arena of %zu bytes is too small: need %zu more at offset %zu", bytes,
+           n, at);
+    used = at + n;
+    return arena + at;
+  }
+};
+
+struct qtc_circuit {
+  Circuit c;
+};
+struct qtc_network {
+  Network net;
+};
+struct qtc_batch {
+  Circuit circuit;
+  std::vector<Plan> plans;
+  std::vector<std::pair<int, int>> obs_edges;
+  std::vector<double> weights;
+  int qaoa_reduce = 1;
+  std::vector<Prepared> prepared;
+};
+struct qtc_plan {
+  Plan plan;
+  std::unique_ptr<qtc_batch> single;  // one-network batch for qtc_contract
+};
+
+extern "C" const char* qtc_last_error(void) { return g_last_error.c_str(); }
+
+// ---- engine ------------------------------------------------------------------
+
+extern "C" qtc_status qtc_engine_create(int device, void* arena, size_t arena_bytes,
+                                        qtc_engine** out) {
+  return guarded([&] {
+    if (!out) fail(QTC_ERR_INVALID, "null output handle");
+    if (!arena || ((uintptr_t)arena & 255)) fail(QTC_ERR_INVALID, "arena must be 256-byte aligned");
+    int count = 0;
+    cuda_check(cudaGetDeviceCount(&count), "cudaGetDeviceCount");
+    if (device < 0 || device >= count) fail(QTC_ERR_INVALID, "device %d of %d", device, count);
+    auto e = std::make_unique<qtc_engine>();
+    e->device = device;
+    e->arena = (char*)arena;
+    e->bytes = arena_bytes;
+    int v = 0;
+    cuda_check(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device), "SM count");
+    e->sm_count = v;
+    cuda_check(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device),
+               "shared memory limit");
+    e->smem_optin = (size_t)v;
+    *out = e.release();
+  });
+}
+
+extern "C" void qtc_engine_destroy(qtc_engine* e) { delete e; }
+
+extern "C" qtc_status qtc_engine_reset(qtc_engine* e) {
+  return guarded([&] {
+    if (!e) fail(QTC_ERR_INVALID, "null engine");
+    e->used = 0;
+    e->generation += 1;
+  });
+}
+
+extern "C" int qtc_engine_last_launches(const qtc_engine* e) { return e ? e->last_launches : 0; }
+
+// ---- circuits ------------------------------------------------------------------
+
+extern "C" qtc_status qtc_circuit_create(int n, int n_params, qtc_circuit** out) {
+  return guarded([&] {
+    if (!out) fail(QTC_ERR_INVALID, "null output handle");
+    if (n <= 0 || n > 4096) fail(QTC_ERR_INVALID, "qubit count %d", n);
+    if (n_params < 0 || n_params > 64) fail(QTC_ERR_INVALID, "parameter count %d (max 64)", n_params);
+    auto c = std::make_unique<qtc_circuit>();
+    c->c.n = n;
+    c->c.n_params = n_params;
+    *out = c.release();
+  });
+}
+
+static void add_gate(Circuit& c, int kind, const int32_t* qubits, int slot, double coeff,
+                     double constant) {
+  Gate g{};
+  g.kind = kind;
+  g.slot = slot;
+  g.coeff = coeff;
+  g.constant = constant;
+  switch (kind) {
+    case QTC_GATE_H: case QTC_GATE_X: case QTC_GATE_Y: case QTC_GATE_Z:
+    case QTC_GATE_RX: case QTC_GATE_RZ:
+      g.nq = 1;
+      break;
+    case QTC_GATE_ZZ: case QTC_GATE_CNOT:
+      g.nq = 2;
+      break;
+    default:
+      fail(QTC_ERR_INVALID, "unknown gate kind %d", kind);
+  }
+  if (!qubits) fail(QTC_ERR_INVALID, "null qubit list");
+  for (int k = 0; k < g.nq; ++k) {
+    if (qubits[k] < 0 || qubits[k] >= c.n) fail(QTC_ERR_INVALID, "qubit %d out of range", qubits[k]);
+    g.q[k] = qubits[k];
+  }
+  if (g.nq == 2 && g.q[0] == g.q[1]) fail(QTC_ERR_INVALID, "two-qubit gate on one qubit");
+  const bool parametric = kind == QTC_GATE_RX || kind == QTC_GATE_RZ || kind == QTC_GATE_ZZ;
+  if (slot >= 0 && (!parametric || slot >= c.n_params))
+    fail(QTC_ERR_INVALID, "parameter slot %d invalid for gate kind %d", slot, kind);
+  if (slot < -1) fail(QTC_ERR_INVALID, "parameter slot %d", slot);
+  if (!std::isfinite(coeff) || !std::isfinite(constant)) fail(QTC_ERR_INVALID, "non-finite angle");
+  c.gates.push_back(g);
+}
+
+extern "C" qtc_status qtc_circuit_add_gate(qtc_circuit* c, int gate, const int32_t* qubits,
+                                           int slot, double coeff, double constant) {
+  return guarded([&] {
+    if (!c) fail(QTC_ERR_INVALID, "null circuit");
+    add_gate(c->c, gate, qubits, slot, coeff, constant);
+  });
+}
+
+extern "C" qtc_status qtc_circuit_qaoa(int n, const int32_t* edges, int m, int p,
+                                       qtc_circuit** out) {
+  return guarded([&] {
+    if (!out) fail(QTC_ERR_INVALID, "null output handle");
+    if (n <= 1 || n > 4096) fail(QTC_ERR_INVALID, "qubit count %d", n);
+    if (p <= 0 || 2 * p > 64) fail(QTC_ERR_INVALID, "depth p = %d (1..32)", p);
+    if (m <= 0 || !edges) fail(QTC_ERR_INVALID, "empty edge list");
+    auto c = std::make_unique<qtc_circuit>();
+    Circuit& cc = c->c;
+    cc.n = n;
+    cc.n_params = 2 * p;
+    cc.p = p;
+    std::vector<std::pair<int, int>> seen;
+    for (int i = 0; i < m; ++i) {
+      int a = edges[2 * i], b = edges[2 * i + 1];
+      if (a < 0 || a >= n || b < 0 || b >= n || a == b)
+        fail(QTC_ERR_INVALID, "edge %d = (%d, %d) invalid", i, a, b);
+      std::pair<int, int> key(std::min(a, b), std::max(a, b));
+      if (std::find(seen.begin(), seen.end(), key) != seen.end())
+        fail(QTC_ERR_INVALID, "edge (%d, %d) repeated", a, b);
+      seen.push_back(key);
+      cc.edges.push_back({a, b});
+    }
+    for (int q = 0; q < n; ++q) add_gate(cc, QTC_GATE_H, &q, -1, 0, 0);
+    for (int k = 0; k < p; ++k) {
+      for (auto& e : cc.edges) {
+        int32_t qs[2] = {e.first, e.second};
+        add_gate(cc, QTC_GATE_ZZ, qs, k, 1.0, 0.0);        // exp(-i gamma_k ZZ/2)
+      }
+      for (int q = 0; q < n; ++q) add_gate(cc, QTC_GATE_RX, &q, p + k, 2.0, 0.0);  // RX(2 beta_k)
+    }
+    *out = c.release();
+  });
+}
+
+extern "C" void qtc_circuit_destroy(qtc_circuit* c) { delete c; }
+
+// ---- networks and plans ----------------------------------------------------------
+
+extern "C" qtc_status qtc_network_build(const qtc_circuit* c, const qtc_observable* obs,
+                                        int lightcone, int diag_mode, qtc_network** out) {
+  return guarded([&] {
+    if (!c || !obs || !out) fail(QTC_ERR_INVALID, "null argument");
+    auto n = std::make_unique<qtc_network>();
+    n->net = build_network(c->c, *obs, lightcone != 0, diag_mode != 0);
+    *out = n.release();
+  });
+}
+
+extern "C" qtc_status qtc_network_leaves(const qtc_network* n, int32_t* counts, int32_t* kind,
+                                         int32_t* conj, int32_t* slot, double* coeff,
+                                         double* constant, int32_t* labels) {
+  return guarded([&] {
+    if (!n) fail(QTC_ERR_INVALID, "null network");
+    const Network& net = n->net;
+    if (counts) {
+      counts[0] = (int32_t)net.leaves.size();
+      counts[1] = net.n_labels;
+    }
+    for (size_t i = 0; i < net.leaves.size(); ++i) {
+      const Leaf& l = net.leaves[i];
+      if (kind) kind[i] = l.spec.kind;
+      if (conj) conj[i] = l.spec.conj;
+      if (slot) slot[i] = l.spec.slot;
+      if (coeff) coeff[i] = l.spec.coeff;
+      if (constant) constant[i] = l.spec.constant;
+      if (labels)
+        for (int k = 0; k < 4; ++k)
+          labels[4 * i + k] = k < (int)l.labels.size() ? l.labels[k] : -1;
+    }
+  });
+}
+
+extern "C" void qtc_network_destroy(qtc_network* n) { delete n; }
+
+static qtc_plan_opts default_opts() {
+  qtc_plan_opts o{};
+  o.kind = QTC_ORDER_LG;
+  o.seed = 0;
+  o.max_rejections = 10;
+  o.restarts = 8;
+  o.budget_ms = 0;
+  return o;
+}
+
+extern "C" qtc_status qtc_plan_create(const qtc_network* n, const qtc_plan_opts* opts,
+                                      qtc_plan** out) {
+  return guarded([&] {
+    if (!n || !out) fail(QTC_ERR_INVALID, "null argument");
+    auto p = std::make_unique<qtc_plan>();
+    p->plan = make_plan(n->net, opts ? *opts : default_opts());
+    *out = p.release();
+  });
+}
+
+extern "C" qtc_status qtc_plan_stats(const qtc_plan* p, qtc_plan_info* info) {
+  return guarded([&] {
+    if (!p || !info) fail(QTC_ERR_INVALID, "null argument");
+    const Plan& pl = p->plan;
+    info->n_tensors = (int)pl.net.leaves.size();
+    info->n_labels = pl.net.n_labels;
+    info->n_steps = (int)pl.steps.size();
+    info->max_rank = pl.max_rank;
+    info->cmacs = pl.cmacs;
+    info->bytes_c64 = pl.bytes_c64;
+    info->lg_width = pl.lg_width;
+  });
+}
+
+extern "C" qtc_status qtc_plan_steps(const qtc_plan* p, int32_t* lhs, int32_t* rhs) {
+  return guarded([&] {
+    if (!p || !lhs || !rhs) fail(QTC_ERR_INVALID, "null argument");
+    for (size_t s = 0; s < p->plan.steps.size(); ++s) {
+      lhs[s] = p->plan.steps[s].a;
+      rhs[s] = p->plan.steps[s].b;
+    }
+  });
+}
+
+extern "C" void qtc_plan_destroy(qtc_plan* p) { delete p; }
+
+// ---- batches --------------------------------------------------------------------
+
+extern "C" qtc_status qtc_batch_create(const qtc_circuit* c, const int32_t* obs_edges, int m,
+                                       int lightcone, int diag_mode, const qtc_plan_opts* opts,
+                                       qtc_batch** out) {
+  return guarded([&] {
+    if (!c || !out) fail(QTC_ERR_INVALID, "null argument");
+    auto b = std::make_unique<qtc_batch>();
+    b->circuit = c->c;
+    if (obs_edges) {
+      if (m <= 0) fail(QTC_ERR_INVALID, "observable edge count %d", m);
+      for (int i = 0; i < m; ++i) b->obs_edges.push_back({obs_edges[2 * i], obs_edges[2 * i + 1]});
+    } else {
+      if (c->c.edges.empty()) fail(QTC_ERR_INVALID, "circuit has no QAOA edges; pass obs_edges");
+      b->obs_edges = c->c.edges;
+    }
+    const qtc_plan_opts o = opts ? *opts : default_opts();
+    const int N = (int)b->obs_edges.size();
+    b->plans.resize(N);
+    b->weights.assign(N, 1.0);
+    std::vector<Error> errors(N, Error{QTC_OK, ""});
+    auto work = [&](int i) {
+      try {
+        qtc_observable obs{};
+        obs.kind = QTC_OBS_ZZ;
+        obs.u = b->obs_edges[i].first;
+        obs.v = b->obs_edges[i].second;
+        Network net = build_network(b->circuit, obs, lightcone != 0, diag_mode != 0);
+        qtc_plan_opts oi = o;
+        oi.seed = o.seed + 0x9E3779B97F4A7C15ull * (uint64_t)i;
+        b->plans[i] = make_plan(net, oi);
+      } catch (const Error& e) {
+        errors[i] = e;
+      }
+    };
+    unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < hw; ++t)
+      pool.emplace_back([&, t] {
+        for (int i = (int)t; i < N; i += (int)hw) work(i);
+      });
+    for (auto& th : pool) th.join();
+    for (auto& e : errors)
+      if (e.status != QTC_OK) throw e;
+    *out = b.release();
+  });
+}
+
+extern "C" qtc_status qtc_batch_stats(const qtc_batch* b, qtc_batch_info* info) {
+  return guarded([&] {
+    if (!b || !info) fail(QTC_ERR_INVALID, "null argument");
+    std::memset(info, 0, sizeof *info);
+    info->n_networks = (int)b->plans.size();
+    info->n_params = b->circuit.n_params;
+    for (const Plan& p : b->plans) {
+      const int L = (int)p.net.leaves.size(), S = (int)p.steps.size();
+      std::vector<char> need(L + S, 0);
+      for (int i = 0; i < L; ++i) need[i] = p.net.leaves[i].spec.slot >= 0;
+      for (int s = 0; s < S; ++s) need[L + s] = need[p.steps[s].a] || need[p.steps[s].b];
+      for (int s = 0; s < S; ++s) {
+        const auto& la = p.labels[p.steps[s].a];
+        const auto& lb = p.labels[p.steps[s].b];
+        std::vector<int> u(la);
+        for (int x : lb)
+          if (std::find(la.begin(), la.end(), x) == la.end()) u.push_back(x);
+        const double ec = std::ldexp(1.0, (int)p.labels[L + s].size());
+        for (int side = 0; side < 2; ++side) {
+          const int x = side ? p.steps[s].b : p.steps[s].a;
+          const int y = side ? p.steps[s].a : p.steps[s].b;
+          if (!need[x]) continue;
+          info->grad_cmacs += std::ldexp(1.0, (int)u.size());
+          info->grad_bytes_c64 += 8.0 * (ec + std::ldexp(1.0, (int)p.labels[x].size()) +
+                                         std::ldexp(1.0, (int)p.labels[y].size()));
+        }
+      }
+      info->max_rank = std::max(info->max_rank, p.max_rank);
+      info->n_steps_total += (int)p.steps.size();
+      info->cmacs += p.cmacs;
+      info->bytes_c64 += p.bytes_c64;
+      if (p.max_rank <= kMaxSmemRank) info->n_smem_networks += 1;
+      else info->n_global_networks += 1;
+    }
+  });
+}
+
+extern "C" void qtc_batch_destroy(qtc_batch* b) { delete b; }
+
+// ---- device programs ---------------------------------------------------------------
+
+static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
+                         cudaStream_t stream) {
+  if (dtype != QTC_C128 && dtype != QTC_C64 && dtype != QTC_SPLIT_BF16)
+    fail(QTC_ERR_INVALID, "unknown dtype %d", dtype);
+  want_grad = want_grad ? 1 : 0;
+  for (Prepared& p : b->prepared)
+    if (p.engine == e && p.generation == e->generation && p.dtype == dtype &&
+        p.want_grad == want_grad)
+      return p;
+  const size_t elem = dtype == QTC_C128 ? 16 : 8;
+  const int P = b->circuit.n_params;
+  const int N = (int)b->plans.size();
+
+  // gate table shared by all networks
+  GateTable table;
+  std::vector<std::vector<int>> leaf_gate(N);
+  for (int i = 0; i < N; ++i)
+    for (const Leaf& leaf : b->plans[i].net.leaves) leaf_gate[i].push_back(table.add(leaf.spec));
+  const int G = (int)table.specs.size();
+  std::vector<uint32_t> val_off(G), der_off(G);
+  uint32_t at = 0;
+  for (int g = 0; g < G; ++g) {
+    val_off[g] = at;
+    at += 1u << leaf_rank_of(table.specs[g].kind);
+  }
+  for (int g = 0; g < G; ++g) {
+    der_off[g] = at;
+    if (table.specs[g].slot >= 0) at += 1u << leaf_rank_of(table.specs[g].kind);
+  }
+  const uint32_t table_elems = (at + 1u) & ~1u;
+
+  // static shared memory of the kernel is a few KB; leave 8 KB for it
+  const size_t max_dyn = e->smem_optin > 8192 ? e->smem_optin - 8192 : 0;
+  const uint32_t max_elems = (uint32_t)(max_dyn / elem);
+
+  std::vector<int> order(N);
+  for (int i = 0; i < N; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return b->plans[x].cmacs > b->plans[y].cmacs; });
+  std::vector<SOp> ops;
+  std::vector<TaskDev> tasks;
+  uint32_t max_arena = 0;
+  for (int i : order) {
+    LoweredNet ln = lower_smem(b->plans[i], leaf_gate[i], val_off, der_off, table_elems,
+                               want_grad != 0, max_elems);
+    if (!ln.fits)
+      fail(QTC_ERR_UNSUPPORTED,
+           "network %d (max rank %d, %u arena elements) does not fit in shared memory (%u "
+           "elements); the global-memory executor handles such networks",
+           i, b->plans[i].max_rank, ln.arena_elems, max_elems);
+    TaskDev t{};
+    t.op_begin = (uint32_t)ops.size();
+    t.op_count = (uint32_t)ln.ops.size();
+    t.net = (uint32_t)i;
+    t.arena_elems = ln.arena_elems;
+    tasks.push_back(t);
+    ops.insert(ops.end(), ln.ops.begin(), ln.ops.end());
+    max_arena = std::max(max_arena, ln.arena_elems);
+  }
+  std::vector<GateEntryDev> gates(G);
+  for (int g = 0; g < G; ++g) {
+    gates[g].spec = table.specs[g];
+    gates[g].val_off = val_off[g];
+    gates[g].der_off = der_off[g];
+    gates[g].rank = (uint32_t)leaf_rank_of(table.specs[g].kind);
+  }
+
+  DeviceScope scope(e->device);
+  Prepared pr;
+  pr.engine = e;
+  pr.generation = e->generation;
+  pr.dtype = dtype;
+  pr.want_grad = want_grad;
+  ProgramDev& d = pr.prog;
+  auto* dg = (GateEntryDev*)e->alloc(sizeof(GateEntryDev) * G);
+  auto* dt = (TaskDev*)e->alloc(sizeof(TaskDev) * tasks.size());
+  auto* dops = (SOp*)e->alloc(sizeof(SOp) * ops.size());
+  auto* dw = (double*)e->alloc(sizeof(double) * N);
+  auto* dparams = (double*)e->alloc(sizeof(double) * std::max(P, 1));
+  auto* dres = (double*)e->alloc(sizeof(double) * (size_t)N * (2 + 2 * P));
+  auto* dout = (double*)e->alloc(sizeof(double) * (1 + P + N));
+  auto* dcnt = (unsigned int*)e->alloc(sizeof(unsigned int) * 4);
+  cuda_check(cudaMemcpyAsync(dg, gates.data(), sizeof(GateEntryDev) * G, cudaMemcpyHostToDevice, stream), "upload gates");
+  cuda_check(cudaMemcpyAsync(dt, tasks.data(), sizeof(TaskDev) * tasks.size(), cudaMemcpyHostToDevice, stream), "upload tasks");
+  cuda_check(cudaMemcpyAsync(dops, ops.data(), sizeof(SOp) * ops.size(), cudaMemcpyHostToDevice, stream), "upload ops");
+  cuda_check(cudaMemcpyAsync(dw, b->weights.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream), "upload weights");
+  cuda_check(cudaMemsetAsync(dcnt, 0, sizeof(unsigned int) * 4, stream), "clear counters");
+  cuda_check(cudaStreamSynchronize(stream), "prepare sync");
+  d.gates = dg;
+  d.n_gates = G;
+  d.table_elems = table_elems;
+  d.tasks = dt;
+  d.n_tasks = (int)tasks.size();
+  d.ops = dops;
+  d.n_params = P;
+  d.n_nets = N;
+  d.weights = dw;
+  d.params = dparams;
+  d.results = dres;
+  d.out = dout;
+  d.counters = dcnt;
+  d.want_grad = want_grad;
+  d.qaoa_reduce = b->qaoa_reduce;
+  pr.block = 128;
+  pr.smem = (size_t)(table_elems + max_arena) * elem;
+  int per_sm = 0;
+  cuda_check(smem_exec_configure(dtype == QTC_C128 ? 0 : 1, pr.smem, pr.block, &per_sm),
+             "configure executor");
+  if (per_sm < 1) fail(QTC_ERR_UNSUPPORTED, "executor does not fit on an SM (%zu bytes)", pr.smem);
+  pr.grid = std::max(1, std::min((int)tasks.size(), e->sm_count * per_sm));
+  b->prepared.push_back(pr);
+  return b->prepared.back();
+}
+
+static void launch(qtc_engine* e, const Prepared& pr, const double* params_dev, double* out_dev,
+                   cudaStream_t stream) {
+  ProgramDev d = pr.prog;
+  d.params = params_dev;
+  d.out = out_dev;
+  cuda_check(smem_exec_launch(d, pr.dtype == QTC_C128 ? 0 : 1, pr.grid, pr.block, pr.smem, stream),
+             "launch executor");
+  e->last_launches = 1;
+}
+
+extern "C" qtc_status qtc_batch_prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
+                                        void* stream) {
+  return guarded([&] {
+    if (!e || !b) fail(QTC_ERR_INVALID, "null argument");
+    prepare(e, b, dtype, want_grad, (cudaStream_t)stream);
+  });
+}
+
+extern "C" qtc_status qtc_qaoa_expectation_device(qtc_engine* e, qtc_batch* b,
+                                                  const double* params_dev, int dtype,
+                                                  int want_grad, void* stream, double* out_dev) {
+  return guarded([&] {
+    if (!e || !b || !params_dev || !out_dev) fail(QTC_ERR_INVALID, "null argument");
+    DeviceScope scope(e->device);
+    const Prepared& pr = prepare(e, b, dtype, want_grad, (cudaStream_t)stream);
+    launch(e, pr, params_dev, out_dev, (cudaStream_t)stream);
+  });
+}
+
+extern "C" qtc_status qtc_qaoa_expectation(qtc_engine* e, qtc_batch* b, const double* gammas,
+                                           const double* betas, int dtype, int want_grad,
+                                           void* stream, double* C_out, double* per_edge_out,
+                                           double* grad_out) {
+  return guarded([&] {
+    if (!e || !b || !gammas || !betas || !C_out) fail(QTC_ERR_INVALID, "null argument");
+    if (grad_out && !want_grad) fail(QTC_ERR_INVALID, "grad_out needs want_grad");
+    const int p = b->circuit.n_params / 2;
+    if (b->circuit.p <= 0) fail(QTC_ERR_INVALID, "the batch's circuit is not a QAOA circuit");
+    DeviceScope scope(e->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const Prepared& pr = prepare(e, b, dtype, want_grad, s);
+    const int P = 2 * p;
+    const int N = (int)b->plans.size();
+    std::vector<double> params(P), host_out(1 + P + N);
+    for (int k = 0; k < p; ++k) {
+      params[k] = gammas[k];
+      params[p + k] = betas[k];
+    }
+    cuda_check(cudaMemcpyAsync((void*)pr.prog.params, params.data(), sizeof(double) * P,
+                               cudaMemcpyHostToDevice, s), "upload parameters");
+    launch(e, pr, pr.prog.params, pr.prog.out, s);
+    cuda_check(cudaMemcpyAsync(host_out.data(), pr.prog.out, sizeof(double) * host_out.size(),
+                               cudaMemcpyDeviceToHost, s), "download results");
+    cuda_check(cudaStreamSynchronize(s), "synchronise stream");
+    *C_out = host_out[0];
+    if (grad_out)
+      for (int k = 0; k < P; ++k) grad_out[k] = host_out[1 + k];
+    if (per_edge_out)
+      for (int i = 0; i < N; ++i) per_edge_out[i] = host_out[1 + P + i];
+  });
+}
+
+// ---- single network -----------------------------------------------------------------
+
+extern "C" qtc_status qtc_contract(qtc_engine* e, const qtc_plan* p, const double* params,
+                                   int dtype, void* stream, double* out_re_im,
+                                   double* grad_re_im) {
+  return guarded([&] {
+    if (!e || !p || !out_re_im) fail(QTC_ERR_INVALID, "null argument");
+    const int P = p->plan.net.n_params;
+    if (P > 0 && !params) fail(QTC_ERR_INVALID, "null parameters");
+    auto* mp = const_cast<qtc_plan*>(p);
+    if (!mp->single) {
+      mp->single = std::make_unique<qtc_batch>();
+      mp->single->circuit.n_params = P;
+      mp->single->plans.push_back(p->plan);
+      mp->single->weights.assign(1, 1.0);
+      mp->single->obs_edges.push_back({0, 0});
+      mp->single->qaoa_reduce = 0;
+    }
+    DeviceScope scope(e->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int want_grad = grad_re_im ? 1 : 0;
+    const Prepared& pr = prepare(e, mp->single.get(), dtype, want_grad, s);
+    if (P > 0)
+      cuda_check(cudaMemcpyAsync((void*)pr.prog.params, params, sizeof(double) * P,
+                                 cudaMemcpyHostToDevice, s), "upload parameters");
+    launch(e, pr, pr.prog.params, pr.prog.out, s);
+    std::vector<double> res(2 + 2 * P);
+    cuda_check(cudaMemcpyAsync(res.data(), pr.prog.results, sizeof(double) * res.size(),
+                               cudaMemcpyDeviceToHost, s), "download result");
+    cuda_check(cudaStreamSynchronize(s), "synchronise stream");
+    out_re_im[0] = res[0];
+    out_re_im[1] = res[1];
+    if (grad_re_im)
+      for (int k = 0; k < 2 * P; ++k) grad_re_im[k] = res[2 + k];
+  });
+}

@@ -1,0 +1,253 @@
+// Circuit -> closed tensor network (Section 2), with the reverse light cone.
+#include <algorithm>
+#include <numeric>
+
+#include "qtc_internal.h"
+
+namespace qtc {
+
+bool gate_is_diagonal(int kind) {
+  return kind == QTC_GATE_Z || kind == QTC_GATE_RZ || kind == QTC_GATE_ZZ;
+}
+
+namespace {
+
+struct UnionFind {
+  std::vector<int> parent;
+  explicit UnionFind(int n) : parent(n) { std::iota(parent.begin(), parent.end(), 0); }
+  int find(int x) {
+    while (parent[x] != x) {
+      parent[x] = parent[parent[x]];
+      x = parent[x];
+    }
+    return x;
+  }
+  void unite(int a, int b) {
+    a = find(a);
+    b = find(b);
+    if (a != b) parent[std::max(a, b)] = std::min(a, b);
+  }
+};
+
+GateSpec spec_of(uint8_t kind, bool conj, const Gate* g) {
+  GateSpec s{};
+  s.kind = kind;
+  s.conj = conj ? 1 : 0;
+  s.slot = -1;
+  s.coeff = 0.0;
+  s.constant = 0.0;
+  if (g && (g->kind == QTC_GATE_RX || g->kind == QTC_GATE_RZ || g->kind == QTC_GATE_ZZ)) {
+    s.slot = (int16_t)g->slot;
+    s.coeff = g->slot >= 0 ? g->coeff : 0.0;
+    s.constant = g->constant;
+  }
+  return s;
+}
+
+GateSpec plain(uint8_t kind, bool conj) { return spec_of(kind, conj, nullptr); }
+
+}  // namespace
+
+// Builds <psi|M|psi> (or <x|psi>) as ket leaves, conjugated bra leaves and the
+// observable.  Light cone: walking the gates backwards from the observable's
+// support S, a gate that misses S commutes with the Heisenberg-picture
+// operator and is dropped; so is a diagonal gate that touches S only on
+// qubits where that operator is still diagonal (set D).  A kept diagonal gate
+// adds its other qubits to S and D; a kept non-diagonal gate adds its qubits
+// to S and removes them from D.  Only qubits of S get wires.
+Network build_network(const Circuit& c, const qtc_observable& obs, bool lightcone,
+                      bool diag) {
+  const int n = c.n;
+  std::vector<char> op(n, 'I');
+  bool amplitude = false;
+  std::vector<int> bits(n, 0);
+  switch (obs.kind) {
+    case QTC_OBS_ZZ:
+      if (obs.u < 0 || obs.u >= n || obs.v < 0 || obs.v >= n || obs.u == obs.v)
+        fail(QTC_ERR_INVALID, "ZZ observable qubits (%d, %d) invalid for n = %d", obs.u,
+             obs.v, n);
+      op[obs.u] = op[obs.v] = 'Z';
+      break;
+    case QTC_OBS_IDENTITY:
+      if (lightcone) fail(QTC_ERR_INVALID, "the identity observable has an empty light cone");
+      break;
+    case QTC_OBS_PAULI:
+      if (!obs.pauli) fail(QTC_ERR_INVALID, "Pauli observable without a string");
+      for (int q = 0; q < n; ++q) {
+        char ch = obs.pauli[q];
+        if (ch != 'I' && ch != 'X' && ch != 'Y' && ch != 'Z')
+          fail(QTC_ERR_INVALID, "Pauli character '%c' at qubit %d", ch, q);
+        op[q] = ch;
+      }
+      if (lightcone && std::all_of(op.begin(), op.end(), [](char ch) { return ch == 'I'; }))
+        fail(QTC_ERR_INVALID, "all-identity Pauli string has an empty light cone");
+      break;
+    case QTC_OBS_AMPLITUDE:
+      if (lightcone) fail(QTC_ERR_INVALID, "the amplitude network has no light cone");
+      if (!obs.bits) fail(QTC_ERR_INVALID, "amplitude observable without bits");
+      amplitude = true;
+      for (int q = 0; q < n; ++q) {
+        if (obs.bits[q] > 1) fail(QTC_ERR_INVALID, "bit %d of the basis state is not 0/1", q);
+        bits[q] = obs.bits[q];
+      }
+      break;
+    default:
+      fail(QTC_ERR_INVALID, "unknown observable kind %d", obs.kind);
+  }
+
+  const int G = (int)c.gates.size();
+  std::vector<char> keep(G, 1);
+  std::vector<char> in_s(n, 1);
+  if (lightcone) {
+    std::vector<char> in_d(n, 0);
+    for (int q = 0; q < n; ++q) {
+      in_s[q] = op[q] != 'I';
+      in_d[q] = op[q] == 'Z';
+    }
+    for (int gi = G - 1; gi >= 0; --gi) {
+      const Gate& g = c.gates[gi];
+      bool touches = false, touches_nondiag = false;
+      for (int k = 0; k < g.nq; ++k) {
+        touches |= in_s[g.q[k]] != 0;
+        touches_nondiag |= in_s[g.q[k]] && !in_d[g.q[k]];
+      }
+      if (!touches || (gate_is_diagonal(g.kind) && !touches_nondiag)) {
+        keep[gi] = 0;
+        continue;
+      }
+      for (int k = 0; k < g.nq; ++k) {
+        int q = g.q[k];
+        if (gate_is_diagonal(g.kind)) {
+          if (!in_s[q]) in_s[q] = in_d[q] = 1;
+        } else {
+          in_s[q] = 1;
+          in_d[q] = 0;
+        }
+      }
+    }
+  }
+
+  // fold a first H on |0> into |+>
+  std::vector<int> folded(n, -1);
+  {
+    std::vector<char> seen(n, 0);
+    for (int gi = 0; gi < G; ++gi) {
+      if (!keep[gi]) continue;
+      const Gate& g = c.gates[gi];
+      for (int k = 0; k < g.nq; ++k) {
+        int q = g.q[k];
+        if (seen[q]) continue;
+        seen[q] = 1;
+        if (g.kind == QTC_GATE_H) folded[q] = gi;
+      }
+    }
+  }
+
+  Network net;
+  net.n_params = c.n_params;
+  int next_label = 0;
+  auto new_label = [&]() { return next_label++; };
+
+  auto side = [&](bool conj, std::vector<int>& cur) {
+    cur.assign(n, -1);
+    for (int q = 0; q < n; ++q) {
+      if (!in_s[q]) continue;
+      cur[q] = new_label();
+      net.leaves.push_back({plain(folded[q] >= 0 ? LK_PLUS : LK_ZERO, conj), {cur[q]}});
+    }
+    for (int gi = 0; gi < G; ++gi) {
+      if (!keep[gi]) continue;
+      const Gate& g = c.gates[gi];
+      if (g.nq == 1 && folded[g.q[0]] == gi) continue;
+      if (diag && gate_is_diagonal(g.kind)) {
+        if (g.kind == QTC_GATE_ZZ)
+          net.leaves.push_back({spec_of(LK_ZZDIAG, conj, &g), {cur[g.q[0]], cur[g.q[1]]}});
+        else if (g.kind == QTC_GATE_RZ)
+          net.leaves.push_back({spec_of(LK_RZDIAG, conj, &g), {cur[g.q[0]]}});
+        else
+          net.leaves.push_back({plain(LK_ZDIAG, conj), {cur[g.q[0]]}});
+        continue;
+      }
+      if (g.nq == 1) {
+        int q = g.q[0];
+        int out = new_label();
+        uint8_t kind = 0;
+        switch (g.kind) {
+          case QTC_GATE_H: kind = LK_H; break;
+          case QTC_GATE_X: kind = LK_X; break;
+          case QTC_GATE_Y: kind = LK_Y; break;
+          case QTC_GATE_Z: kind = LK_Z; break;
+          case QTC_GATE_RX: kind = LK_RX; break;
+          case QTC_GATE_RZ: kind = LK_RZ; break;
+          default: fail(QTC_ERR_INVALID, "gate kind %d is not a one-qubit gate", g.kind);
+        }
+        net.leaves.push_back({spec_of(kind, conj, &g), {out, cur[q]}});
+        cur[q] = out;
+      } else {
+        int a = g.q[0], b = g.q[1];
+        int oa = new_label(), ob = new_label();
+        uint8_t kind = g.kind == QTC_GATE_ZZ ? LK_ZZ : LK_CNOT;
+        net.leaves.push_back({spec_of(kind, conj, &g), {oa, ob, cur[a], cur[b]}});
+        cur[a] = oa;
+        cur[b] = ob;
+      }
+    }
+  };
+
+  std::vector<int> ket, bra;
+  side(false, ket);
+  if (amplitude) {
+    for (int q = 0; q < n; ++q)
+      if (in_s[q]) net.leaves.push_back({plain(bits[q] ? LK_PROJ1 : LK_PROJ0, false), {ket[q]}});
+  } else {
+    side(true, bra);
+    std::vector<std::pair<int, int>> unite;
+    for (int q = 0; q < n; ++q) {
+      if (!in_s[q]) continue;
+      switch (op[q]) {
+        case 'I':
+          unite.push_back({bra[q], ket[q]});
+          break;
+        case 'Z':
+          if (diag) {
+            unite.push_back({bra[q], ket[q]});
+            net.leaves.push_back({plain(LK_ZDIAG, false), {ket[q]}});
+          } else {
+            net.leaves.push_back({plain(LK_OBS_Z, false), {bra[q], ket[q]}});
+          }
+          break;
+        case 'X':
+          net.leaves.push_back({plain(LK_OBS_X, false), {bra[q], ket[q]}});
+          break;
+        case 'Y':
+          net.leaves.push_back({plain(LK_OBS_Y, false), {bra[q], ket[q]}});
+          break;
+      }
+    }
+    UnionFind uf(next_label);
+    for (auto& pr : unite) uf.unite(pr.first, pr.second);
+    for (auto& leaf : net.leaves)
+      for (int& l : leaf.labels) l = uf.find(l);
+  }
+  // compact labels in order of first appearance
+  std::vector<int> remap(next_label, -1);
+  int L = 0;
+  for (auto& leaf : net.leaves)
+    for (int& l : leaf.labels) {
+      if (remap[l] < 0) remap[l] = L++;
+      l = remap[l];
+    }
+  net.n_labels = L;
+  for (auto& leaf : net.leaves) {
+    if ((int)leaf.labels.size() != leaf_rank_of(leaf.spec.kind))
+      fail(QTC_ERR_INVALID, "internal: leaf rank mismatch");
+    for (size_t i = 0; i < leaf.labels.size(); ++i)
+      for (size_t j = i + 1; j < leaf.labels.size(); ++j)
+        if (leaf.labels[i] == leaf.labels[j])
+          fail(QTC_ERR_UNSUPPORTED, "a leaf with a repeated index (trace) is not supported");
+  }
+  if (net.leaves.empty()) fail(QTC_ERR_INVALID, "the network is empty");
+  return net;
+}
+
+}  // namespace qtc

@@ -1,0 +1,243 @@
+"""Host-side logic of libqtc.so on the CPU (no GPU calls).
+
+The library's own networks (read back through qtc_network_leaves) are
+contracted in numpy along the library's own plans (qtc_plan_steps); the
+result must equal the oracle's state-vector value.  This checks the circuit
+-> network builder, the light cone, the diagonal/dense forms and both
+orderings without a GPU.  Leaf values are written here from the gate
+definitions in include/qtc.h.
+"""
+
+import math
+import re
+
+import numpy as np
+import pytest
+
+from oracle import statevector as sv
+from synth import random_regular_graph
+
+q = pytest.importorskip("paper_1709_03636_gb300")
+
+R = 1 / math.sqrt(2)
+
+
+def leaf_tensor(kind, conj, slot, coeff, constant, params):
+    t = constant + (coeff * params[slot] if slot >= 0 else 0.0)
+    c, s = math.cos(t / 2), math.sin(t / 2)
+    e = lambda z: complex(math.cos(z * t / 2), -math.sin(z * t / 2))  # exp(-i z t/2)
+    T = {
+        0: lambda: np.array([1, 0]),
+        1: lambda: np.array([R, R]),
+        2: lambda: np.array([1, 0]),
+        3: lambda: np.array([0, 1]),
+        4: lambda: np.array([[R, R], [R, -R]]),
+        5: lambda: np.array([[0, 1], [1, 0]]),
+        6: lambda: np.array([[0, -1j], [1j, 0]]),
+        7: lambda: np.array([[1, 0], [0, -1]]),
+        8: lambda: np.array([[c, -1j * s], [-1j * s, c]]),
+        9: lambda: np.diag([e(1), e(-1)]),
+        10: lambda: np.array([1, -1]),
+        11: lambda: np.array([e(1), e(-1)]),
+        12: lambda: np.array([[e(1), e(-1)], [e(-1), e(1)]]),
+        15: lambda: np.array([[0, 1], [1, 0]]),
+        16: lambda: np.array([[0, -1j], [1j, 0]]),
+        17: lambda: np.array([[1, 0], [0, -1]]),
+    }
+    if kind == 13:
+        v = np.zeros((2, 2, 2, 2), dtype=complex)
+        for a in range(2):
+            for b in range(2):
+                v[a, b, a, b] = e(1 if a == b else -1)
+    elif kind == 14:
+        v = np.zeros((2, 2, 2, 2), dtype=complex)
+        for cc in range(2):
+            for tt in range(2):
+                v[cc, tt ^ cc, cc, tt] = 1
+    else:
+        v = np.asarray(T[kind](), dtype=complex)
+    return np.conj(v) if conj else v
+
+
+def run_plan(network, plan, params):
+    leaves, n_labels = network.leaves()
+    tensors = [(leaf_tensor(l["kind"], l["conj"], l["slot"], l["coeff"], l["constant"], params),
+                tuple(l["labels"])) for l in leaves]
+    count = np.zeros(n_labels, dtype=int)
+    for _, ls in tensors:
+        for l in ls:
+            count[l] += 1
+    for a, b in plan.steps():
+        (va, la), (vb, lb) = tensors[a], tensors[b]
+        both = set(la) | set(lb)
+        shared = {l: (l in la) + (l in lb) for l in both}
+        out = tuple(sorted(l for l in both if count[l] > shared[l]))
+        for l in both:
+            count[l] -= shared[l]
+        for l in out:
+            count[l] += 1
+        letters = {l: i for i, l in enumerate(sorted(both))}
+        v = np.einsum(va, [letters[l] for l in la], vb, [letters[l] for l in lb],
+                      [letters[l] for l in out])
+        tensors.append((v, out))
+    value, labels = tensors[-1]
+    assert labels == ()
+    return complex(value)
+
+
+@pytest.mark.parametrize("ordering", ["lg", "stoch"])
+@pytest.mark.parametrize("diag", [True, False])
+@pytest.mark.parametrize("lightcone", [True, False])
+@pytest.mark.parametrize("p", [1, 2])
+def test_qaoa_networks_and_plans_match_statevector(ordering, diag, lightcone, p):
+    n = 8
+    edges = random_regular_graph(n, 3, 4 + p)
+    gammas = [0.3 + 0.4 * k for k in range(p)]
+    betas = [0.9 - 0.3 * k for k in range(p)]
+    ref = sv.edge_zz(n, edges, gammas, betas)
+    circ = q.Circuit.qaoa(n, edges, p)
+    params = gammas + betas
+    for i, e in enumerate(edges[:6]):
+        net = q.Network(circ, "zz", edge=e, lightcone=lightcone, diag=diag)
+        plan = q.Plan(net, ordering, seed=3)
+        st = plan.stats()
+        assert st["n_steps"] == st["n_tensors"] - 1
+        val = run_plan(net, plan, params)
+        assert abs(val.real - ref[i]) < 1e-12 and abs(val.imag) < 1e-12
+
+
+def test_plans_are_binary_trees():
+    edges = random_regular_graph(20, 4, 1)
+    circ = q.Circuit.qaoa(20, edges, 2)
+    for ordering in ["lg", "stoch"]:
+        net = q.Network(circ, "zz", edge=edges[3])
+        plan = q.Plan(net, ordering, seed=11)
+        st = plan.stats()
+        L = st["n_tensors"]
+        used = set()
+        for s, (a, b) in enumerate(plan.steps()):
+            assert a != b and a < L + s and b < L + s
+            assert a not in used and b not in used
+            used.update((a, b))
+        assert used == set(range(L + st["n_steps"] - 1))
+
+
+def test_light_cone_sizes():
+    # p=1 on a triangle-free 3-regular graph: 6 qubits, 5 phase gates, 2 RX
+    edges = random_regular_graph(50, 3, 0)
+    circ = q.Circuit.qaoa(50, edges, 1)
+    net = q.Network(circ, "zz", edge=edges[0], diag=True)
+    leaves, _ = net.leaves()
+    kinds = [l["kind"] for l in leaves]
+    n_plus = kinds.count(1)
+    assert n_plus in (10, 12) and kinds.count(8) == 4 and kinds.count(10) == 2
+    assert kinds.count(12) == 2 * (n_plus // 2 - 1)
+
+
+def _full_unitary_reference(n, gates, pauli):
+    """Plain state-vector reference of a generic circuit (kron-built gates)."""
+    eye = np.eye(2)
+    mats = {"h": np.array([[1, 1], [1, -1]]) * R, "x": np.array([[0, 1], [1, 0]]),
+            "y": np.array([[0, -1j], [1j, 0]]), "z": np.diag([1, -1])}
+
+    def one(u, k):
+        out = np.array([[1.0]])
+        for j in reversed(range(n)):
+            out = np.kron(out, u if j == k else eye)
+        return out
+
+    psi = np.zeros(2 ** n, dtype=complex)
+    psi[0] = 1
+    for g, qs, theta in gates:
+        if g in mats:
+            u = one(mats[g], qs[0])
+        elif g == "rx":
+            u = one(np.array([[math.cos(theta / 2), -1j * math.sin(theta / 2)],
+                              [-1j * math.sin(theta / 2), math.cos(theta / 2)]]), qs[0])
+        elif g == "rz":
+            u = one(np.diag([np.exp(-0.5j * theta), np.exp(0.5j * theta)]), qs[0])
+        elif g == "zz":
+            zz = one(mats["z"], qs[0]) @ one(mats["z"], qs[1])
+            u = np.diag(np.exp(-0.5j * theta * np.diag(zz)))
+        elif g == "cnot":
+            u = np.zeros((2 ** n, 2 ** n))
+            for s in range(2 ** n):
+                u[s ^ (((s >> qs[0]) & 1) << qs[1]), s] = 1
+        psi = u @ psi
+    obs = np.eye(1)
+    for j in reversed(range(n)):
+        obs = np.kron(obs, mats[pauli[j].lower()] if pauli[j] != "I" else eye)
+    return psi, np.vdot(psi, obs @ psi)
+
+
+GENERIC = [("h", (0,)), ("cnot", (0, 1)), ("rx", (2,)), ("zz", (1, 2)), ("rz", (0,)),
+           ("y", (3,)), ("cnot", (3, 0)), ("h", (1,)), ("zz", (0, 3)), ("x", (2,)),
+           ("rz", (3,)), ("rx", (1,)), ("z", (0,)), ("cnot", (2, 1))]
+
+
+@pytest.mark.parametrize("pauli", ["ZIIZ", "XYZI", "IYIX", "ZZZZ"])
+@pytest.mark.parametrize("diag", [True, False])
+@pytest.mark.parametrize("lightcone", [True, False])
+def test_generic_circuit_pauli_observables(pauli, diag, lightcone):
+    n = 4
+    params = [0.37, -1.1, 2.3]
+    circ = q.Circuit(n, len(params))
+    gates = []
+    slot = 0
+    for g, qs in GENERIC:
+        if g in ("rx", "rz", "zz"):
+            circ.add_gate(g, qs, slot % 3, 1.5, 0.2)
+            gates.append((g, qs, 1.5 * params[slot % 3] + 0.2))
+            slot += 1
+        else:
+            circ.add_gate(g, qs)
+            gates.append((g, qs, 0.0))
+    _, ref = _full_unitary_reference(n, gates, pauli)
+    net = q.Network(circ, "pauli", pauli=pauli, lightcone=lightcone, diag=diag)
+    val = run_plan(net, q.Plan(net, "lg"), params)
+    assert abs(val - ref) < 1e-12
+
+
+def test_generic_amplitudes():
+    n = 4
+    params = [0.37, -1.1, 2.3]
+    circ = q.Circuit(n, len(params))
+    gates = []
+    for i, (g, qs) in enumerate(GENERIC):
+        if g in ("rx", "rz", "zz"):
+            circ.add_gate(g, qs, i % 3, 1.0, 0.0)
+            gates.append((g, qs, params[i % 3]))
+        else:
+            circ.add_gate(g, qs)
+            gates.append((g, qs, 0.0))
+    psi, _ = _full_unitary_reference(n, gates, "IIII")
+    for x in range(2 ** n):
+        bits = [(x >> k) & 1 for k in range(n)]
+        net = q.Network(circ, "amplitude", bits=bits, lightcone=False)
+        assert abs(run_plan(net, q.Plan(net, "stoch", seed=x), params) - psi[x]) < 1e-12
+
+
+def test_invalid_inputs_raise():
+    with pytest.raises(q.QtcError, match="INVALID"):
+        q.Circuit.qaoa(4, [(0, 0)], 1)
+    with pytest.raises(q.QtcError, match="INVALID"):
+        q.Circuit.qaoa(4, [(0, 1), (1, 0)], 1)
+    circ = q.Circuit.qaoa(4, [(0, 1), (1, 2), (2, 3)], 1)
+    with pytest.raises(q.QtcError, match="INVALID"):
+        q.Network(circ, "zz", edge=(0, 9))
+    with pytest.raises(q.QtcError, match="INVALID"):
+        q.Network(circ, "identity", lightcone=True)
+    with pytest.raises(q.QtcError, match="INVALID"):
+        circ.add_gate("rx", (0,), 7, 1.0)
+
+
+def test_library_exports_every_declared_symbol():
+    import ctypes
+    import os
+    from paper_1709_03636_gb300 import _lib
+    header = open(os.path.join(os.path.dirname(__file__), "..", "include", "qtc.h")).read()
+    names = set(re.findall(r"\b(qtc_[a-z0-9_]+)\s*\(", header))
+    assert len(names) > 20
+    so = ctypes.CDLL(_lib.LIB_PATH)
+    missing = [n for n in sorted(names) if not hasattr(so, n)]
+    assert not missing, missing
