@@ -524,7 +524,7 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   pr.block = 128;
   pr.smem = (size_t)(table_elems + max_arena) * elem;
   int per_sm = 0;
-  cuda_check(smem_exec_configure(dtype == QTC_C128 ? 0 : 1, pr.smem, pr.block, &per_sm),
+  cuda_check(smem_exec_configure(dtype == QTC_C128 ? 0 : 1, pr.smem, max_dyn, pr.block, &per_sm),
              "configure executor");
   if (per_sm < 1) fail(QTC_ERR_UNSUPPORTED, "executor does not fit on an SM (%zu bytes)", pr.smem);
   pr.grid = std::max(1, std::min((int)tasks.size(), e->sm_count * per_sm));

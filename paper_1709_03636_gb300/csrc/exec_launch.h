@@ -8,7 +8,8 @@
 namespace qtc {
 
 // dtype: 0 = complex double, otherwise complex float.
-cudaError_t smem_exec_configure(int dtype, size_t smem_bytes, int block, int* blocks_per_sm);
+cudaError_t smem_exec_configure(int dtype, size_t smem_bytes, size_t max_dynamic, int block,
+                                int* blocks_per_sm);
 cudaError_t smem_exec_launch(const ProgramDev& prog, int dtype, int grid, int block,
                              size_t smem_bytes, cudaStream_t stream);
 

@@ -257,11 +257,16 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
   }
 }
 
-cudaError_t smem_exec_configure(int dtype, size_t smem_bytes, int block, int* blocks_per_sm) {
+cudaError_t smem_exec_configure(int dtype, size_t smem_bytes, size_t max_dynamic, int block,
+                                int* blocks_per_sm) {
   const void* fn = dtype == 0 ? (const void*)smem_exec_kernel<double2>
                               : (const void*)smem_exec_kernel<float2>;
+  // the attribute is per kernel, shared by every prepared program: always
+  // raise it to the device limit so a smaller program never lowers it below
+  // what a larger one needs
+  if (smem_bytes > max_dynamic) return cudaErrorInvalidValue;
   cudaError_t err =
-      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dynamic);
   if (err != cudaSuccess) return err;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem_bytes);
 }

@@ -117,9 +117,9 @@ def test_single_network_contract_and_gradient(engine):
     g, b = [0.9, 0.2], [0.3, 1.2]
     circ = q.Circuit.qaoa(n, edges, 2)
     e = edges[5]
-    net = q.Network(circ, "zz", edge=e, lightcone=False, diag=True)
+    net = q.Network(circ, "zz", edge=e, lightcone=True, diag=True)
     plan = q.Plan(net, "lg")
-    s_ref, ds_ref = tn.edge_value_grad(n, edges, g, b, e, lightcone=False)
+    s_ref, ds_ref = tn.edge_value_grad(n, edges, g, b, e, lightcone=True)
     for dtype, tol in (("c128", 1e-11), ("c64", 5e-6)):
         s, ds = q.contract(engine, plan, g + b, dtype, want_grad=True)
         assert abs(s - s_ref) < tol
