@@ -230,6 +230,31 @@ qtc_status qtc_qaoa_expectation_device(qtc_engine* e, qtc_batch* b,
  * engine issued (for launch accounting). */
 int qtc_engine_last_launches(const qtc_engine* e);
 
+/* ---- evaluation without device allocation --------------------------------
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory at all (code running inside another
+ * framework's memory pool, or a plugin whose host forbids cudaMalloc), so
+ * they cannot hand the library an arena either.  It computes exactly what
+ * qtc_qaoa_expectation_device computes, on the caller's current device,
+ * with the same inputs and outputs: params_dev (device, 2p doubles) and
+ * out_dev (device, 1 + 2p + m doubles, same layout).
+ *
+ * Its scratch (program tables, per-network result rows, counters) is a
+ * fixed file-scope device array of QTC_STATIC_SCRATCH_BYTES, which every GPU
+ * that loads the library keeps until the process exits.  The call allocates
+ * no device memory and calls no allocating CUDA or library routine; a batch
+ * whose program does not fit returns QTC_ERR_ARENA with the size it needs.
+ * The first call on a device resolves the array's device address on that
+ * device (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  The host-side program is built once per batch and cached.
+ * Every call shares the one array and leaves its contents behind (the call
+ * clears the counters it needs zeroed), so calls whose executions overlap on
+ * the GPU — from two streams or two host threads — race and must not be
+ * issued.  Asynchronous on `stream`. */
+#define QTC_STATIC_SCRATCH_BYTES (16u << 20)
+qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* params_dev, int dtype,
+                                       int want_grad, void* stream, double* out_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -71,6 +71,8 @@ SIGNATURES = {
                                      c_void_p, P(c_double), P(c_double), P(c_double)]),
     "qtc_qaoa_expectation_device": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int,
                                             c_void_p, c_void_p]),
+    "qtc_qaoa_expectation_static": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p,
+                                            c_void_p]),
 }
 
 

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <memory>
 #include <thread>
 
@@ -27,40 +28,6 @@ void set_last_error(const std::string& msg) { g_last_error = msg; }
   throw Error{s, buf};
 }
 
-static void cuda_check(cudaError_t err, const char* what) {
-  if (err != cudaSuccess)
-    fail(QTC_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(err), cudaGetErrorString(err));
-}
-
-template <typename F>
-static qtc_status guarded(F&& f) {
-  try {
-    f();
-    return QTC_OK;
-  } catch (const Error& e) {
-    set_last_error(e.msg);
-    return e.status;
-  } catch (const std::bad_alloc&) {
-    set_last_error("host out of memory");
-    return QTC_ERR_INVALID;
-  } catch (const std::exception& e) {
-    set_last_error(e.what());
-    return QTC_ERR_INVALID;
-  }
-}
-
-// Restores the caller's current device on scope exit.
-struct DeviceScope {
-  int prev = -1;
-  explicit DeviceScope(int dev) {
-    cuda_check(cudaGetDevice(&prev), "cudaGetDevice");
-    if (prev != dev) cuda_check(cudaSetDevice(dev), "cudaSetDevice");
-  }
-  ~DeviceScope() {
-    int cur = -1;
-    if (cudaGetDevice(&cur) == cudaSuccess && cur != prev && prev >= 0) cudaSetDevice(prev);
-  }
-};
 
 // A batch's program resident in one engine's arena.
 struct Prepared {
@@ -110,6 +77,7 @@ struct qtc_batch {
   std::vector<double> weights;
   int qaoa_reduce = 1;
   std::vector<Prepared> prepared;
+  std::vector<std::unique_ptr<HostProgram>> host_programs;
 };
 struct qtc_plan {
   Plan plan;
@@ -418,16 +386,15 @@ extern "C" void qtc_batch_destroy(qtc_batch* b) { delete b; }
 
 // ---- device programs ---------------------------------------------------------------
 
-static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
-                         cudaStream_t stream) {
+const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
+                                     size_t max_dynamic) {
   if (dtype != QTC_C128 && dtype != QTC_C64 && dtype != QTC_SPLIT_BF16)
     fail(QTC_ERR_INVALID, "unknown dtype %d", dtype);
   want_grad = want_grad ? 1 : 0;
-  for (Prepared& p : b->prepared)
-    if (p.engine == e && p.generation == e->generation && p.dtype == dtype &&
-        p.want_grad == want_grad)
-      return p;
-  const size_t elem = dtype == QTC_C128 ? 16 : 8;
+  for (const auto& hp : b->host_programs)
+    if (hp->dtype == dtype && hp->want_grad == want_grad && hp->max_dynamic == max_dynamic)
+      return *hp;
+  const size_t elem = elem_bytes(dtype);
   const int P = b->circuit.n_params;
   const int N = (int)b->plans.size();
 
@@ -448,18 +415,23 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
     if (table.specs[g].slot >= 0) at += 1u << leaf_rank_of(table.specs[g].kind);
   }
   const uint32_t table_elems = (at + 1u) & ~1u;
+  const uint32_t max_elems = (uint32_t)(max_dynamic / elem);
 
-  // static shared memory of the kernel is a few KB; leave 8 KB for it
-  const size_t max_dyn = e->smem_optin > 8192 ? e->smem_optin - 8192 : 0;
-  const uint32_t max_elems = (uint32_t)(max_dyn / elem);
-
+  static std::atomic<uint64_t> next_serial{1};
+  auto hp = std::make_unique<HostProgram>();
+  hp->serial = next_serial++;
+  hp->dtype = dtype;
+  hp->want_grad = want_grad;
+  hp->max_dynamic = max_dynamic;
+  hp->n_nets = N;
+  hp->n_params = P;
+  hp->qaoa_reduce = b->qaoa_reduce;
+  hp->weights = b->weights;
+  hp->table_elems = table_elems;
   std::vector<int> order(N);
   for (int i = 0; i < N; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(),
                    [&](int x, int y) { return b->plans[x].cmacs > b->plans[y].cmacs; });
-  std::vector<SOp> ops;
-  std::vector<TaskDev> tasks;
-  uint32_t max_arena = 0;
   for (int i : order) {
     LoweredNet ln = lower_smem(b->plans[i], leaf_gate[i], val_off, der_off, table_elems,
                                want_grad != 0, max_elems);
@@ -469,21 +441,38 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
            "elements); the global-memory executor handles such networks",
            i, b->plans[i].max_rank, ln.arena_elems, max_elems);
     TaskDev t{};
-    t.op_begin = (uint32_t)ops.size();
+    t.op_begin = (uint32_t)hp->ops.size();
     t.op_count = (uint32_t)ln.ops.size();
     t.net = (uint32_t)i;
     t.arena_elems = ln.arena_elems;
-    tasks.push_back(t);
-    ops.insert(ops.end(), ln.ops.begin(), ln.ops.end());
-    max_arena = std::max(max_arena, ln.arena_elems);
+    hp->tasks.push_back(t);
+    hp->ops.insert(hp->ops.end(), ln.ops.begin(), ln.ops.end());
+    hp->max_arena = std::max(hp->max_arena, ln.arena_elems);
   }
-  std::vector<GateEntryDev> gates(G);
+  hp->gates.resize(G);
   for (int g = 0; g < G; ++g) {
-    gates[g].spec = table.specs[g];
-    gates[g].val_off = val_off[g];
-    gates[g].der_off = der_off[g];
-    gates[g].rank = (uint32_t)leaf_rank_of(table.specs[g].kind);
+    hp->gates[g].spec = table.specs[g];
+    hp->gates[g].val_off = val_off[g];
+    hp->gates[g].der_off = der_off[g];
+    hp->gates[g].rank = (uint32_t)leaf_rank_of(table.specs[g].kind);
   }
+  hp->smem = (size_t)(table_elems + hp->max_arena) * elem;
+  b->host_programs.push_back(std::move(hp));
+  return *b->host_programs.back();
+}
+
+static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
+                         cudaStream_t stream) {
+  want_grad = want_grad ? 1 : 0;
+  for (Prepared& p : b->prepared)
+    if (p.engine == e && p.generation == e->generation && p.dtype == dtype &&
+        p.want_grad == want_grad)
+      return p;
+  const size_t max_dyn = max_dynamic_smem(e->smem_optin);
+  const HostProgram& hp = host_program(b, dtype, want_grad, max_dyn);
+  const int P = hp.n_params;
+  const int N = hp.n_nets;
+  const int G = (int)hp.gates.size();
 
   DeviceScope scope(e->device);
   Prepared pr;
@@ -493,24 +482,24 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   pr.want_grad = want_grad;
   ProgramDev& d = pr.prog;
   auto* dg = (GateEntryDev*)e->alloc(sizeof(GateEntryDev) * G);
-  auto* dt = (TaskDev*)e->alloc(sizeof(TaskDev) * tasks.size());
-  auto* dops = (SOp*)e->alloc(sizeof(SOp) * ops.size());
+  auto* dt = (TaskDev*)e->alloc(sizeof(TaskDev) * hp.tasks.size());
+  auto* dops = (SOp*)e->alloc(sizeof(SOp) * hp.ops.size());
   auto* dw = (double*)e->alloc(sizeof(double) * N);
   auto* dparams = (double*)e->alloc(sizeof(double) * std::max(P, 1));
   auto* dres = (double*)e->alloc(sizeof(double) * (size_t)N * (2 + 2 * P));
   auto* dout = (double*)e->alloc(sizeof(double) * (1 + P + N));
   auto* dcnt = (unsigned int*)e->alloc(sizeof(unsigned int) * 4);
-  cuda_check(cudaMemcpyAsync(dg, gates.data(), sizeof(GateEntryDev) * G, cudaMemcpyHostToDevice, stream), "upload gates");
-  cuda_check(cudaMemcpyAsync(dt, tasks.data(), sizeof(TaskDev) * tasks.size(), cudaMemcpyHostToDevice, stream), "upload tasks");
-  cuda_check(cudaMemcpyAsync(dops, ops.data(), sizeof(SOp) * ops.size(), cudaMemcpyHostToDevice, stream), "upload ops");
-  cuda_check(cudaMemcpyAsync(dw, b->weights.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream), "upload weights");
+  cuda_check(cudaMemcpyAsync(dg, hp.gates.data(), sizeof(GateEntryDev) * G, cudaMemcpyHostToDevice, stream), "upload gates");
+  cuda_check(cudaMemcpyAsync(dt, hp.tasks.data(), sizeof(TaskDev) * hp.tasks.size(), cudaMemcpyHostToDevice, stream), "upload tasks");
+  cuda_check(cudaMemcpyAsync(dops, hp.ops.data(), sizeof(SOp) * hp.ops.size(), cudaMemcpyHostToDevice, stream), "upload ops");
+  cuda_check(cudaMemcpyAsync(dw, hp.weights.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream), "upload weights");
   cuda_check(cudaMemsetAsync(dcnt, 0, sizeof(unsigned int) * 4, stream), "clear counters");
   cuda_check(cudaStreamSynchronize(stream), "prepare sync");
   d.gates = dg;
   d.n_gates = G;
-  d.table_elems = table_elems;
+  d.table_elems = hp.table_elems;
   d.tasks = dt;
-  d.n_tasks = (int)tasks.size();
+  d.n_tasks = (int)hp.tasks.size();
   d.ops = dops;
   d.n_params = P;
   d.n_nets = N;
@@ -520,14 +509,14 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   d.out = dout;
   d.counters = dcnt;
   d.want_grad = want_grad;
-  d.qaoa_reduce = b->qaoa_reduce;
-  pr.block = 128;
-  pr.smem = (size_t)(table_elems + max_arena) * elem;
+  d.qaoa_reduce = hp.qaoa_reduce;
+  pr.block = kExecBlock;
+  pr.smem = hp.smem;
   int per_sm = 0;
   cuda_check(smem_exec_configure(dtype == QTC_C128 ? 0 : 1, pr.smem, max_dyn, pr.block, &per_sm),
              "configure executor");
   if (per_sm < 1) fail(QTC_ERR_UNSUPPORTED, "executor does not fit on an SM (%zu bytes)", pr.smem);
-  pr.grid = std::max(1, std::min((int)tasks.size(), e->sm_count * per_sm));
+  pr.grid = std::max(1, std::min((int)hp.tasks.size(), e->sm_count * per_sm));
   b->prepared.push_back(pr);
   return b->prepared.back();
 }

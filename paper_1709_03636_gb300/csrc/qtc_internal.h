@@ -6,6 +6,8 @@
 #include <utility>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "qtc.h"
 #include "device_program.h"
 
@@ -20,6 +22,43 @@ struct Error {
 };
 [[noreturn]] void fail(qtc_status s, const char* fmt, ...);
 void set_last_error(const std::string& msg);
+
+inline void cuda_check(cudaError_t err, const char* what) {
+  if (err != cudaSuccess)
+    fail(QTC_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(err), cudaGetErrorString(err));
+}
+
+// Runs f, turning an Error (or a host exception) into a status code and the
+// thread-local message.
+template <typename F>
+qtc_status guarded(F&& f) {
+  try {
+    f();
+    return QTC_OK;
+  } catch (const Error& e) {
+    set_last_error(e.msg);
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host out of memory");
+    return QTC_ERR_INVALID;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return QTC_ERR_INVALID;
+  }
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    cuda_check(cudaGetDevice(&prev), "cudaGetDevice");
+    if (prev != dev) cuda_check(cudaSetDevice(dev), "cudaSetDevice");
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != prev && prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 // ---- SplitMix64 (Steele, Lea and Flood 2014) -------------------------------
 struct SplitMix64 {
@@ -110,5 +149,33 @@ LoweredNet lower_smem(const Plan& plan, const std::vector<int>& leaf_gate,
                       const std::vector<uint32_t>& gate_val_off,
                       const std::vector<uint32_t>& gate_der_off,
                       uint32_t table_elems, bool want_grad, uint32_t max_elems);
+
+// Host copy of a batch's device program for one element type and gradient
+// flag: the gate table, one shared-memory task per network (largest first)
+// and the op lists.
+struct HostProgram {
+  int dtype = 0, want_grad = 0;
+  size_t max_dynamic = 0;          // shared-memory budget it was lowered for
+  std::vector<GateEntryDev> gates;
+  std::vector<TaskDev> tasks;
+  std::vector<SOp> ops;
+  std::vector<double> weights;
+  uint32_t table_elems = 0, max_arena = 0;
+  size_t smem = 0;                 // dynamic shared memory per CTA, bytes
+  int n_nets = 0, n_params = 0;
+  int qaoa_reduce = 1;
+  uint64_t serial = 0;             // process-unique id of this program
+};
+
+// Built once per (batch, dtype, want_grad, budget) and cached in the batch.
+const HostProgram& host_program(qtc_batch* b, int dtype, int want_grad, size_t max_dynamic);
+
+inline size_t elem_bytes(int dtype) { return dtype == QTC_C128 ? 16 : 8; }
+
+// Dynamic shared memory a CTA of the executor may use: the opt-in limit
+// minus 8 KB for the kernel's static shared memory.
+inline size_t max_dynamic_smem(size_t optin) { return optin > 8192 ? optin - 8192 : 0; }
+
+constexpr int kExecBlock = 128;
 
 }  // namespace qtc
