@@ -41,7 +41,7 @@ METRIC = "edge-<ZZ> networks/s (value + gradient)"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
@@ -82,28 +82,36 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []          # (host time, csv line)
+        self.window = (0.0, 0.0)
 
-    def __enter__(self):
+    def start(self):
+        """Start sampling and wait for the first sample, so that nvidia-smi's
+        own start-up never overlaps the timed region."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except OSError:
             self.proc = None
-        time.sleep(0.25)
+            return self
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < 10.0:
+            time.sleep(0.02)
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def __exit__(self, *exc):
+    def mark(self, t_begin, t_end):
+        self.window = (t_begin, t_end)
+
+    def stop(self):
         if self.proc:
-            time.sleep(0.15)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -113,7 +121,9 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        t0, t1 = self.window
+        inside = [ln for t, ln in self.lines if t0 <= t <= t1]
+        for line in inside:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -252,11 +262,12 @@ def run_ours(args):
     for _ in range(args.warmup):
         device_step(True)
         device_step(False)
+    clocks = ClockSampler(local).start()
     barrier()
-    with ClockSampler(local) as clocks:
-        wall0 = time.perf_counter()
-        step_ms = timed(lambda: device_step(True), args.steps)
-        wall = time.perf_counter() - wall0
+    wall0 = time.perf_counter()
+    step_ms = timed(lambda: device_step(True), args.steps)
+    wall = time.perf_counter() - wall0
+    clocks.mark(wall0, wall0 + wall)
     launches = args.steps * engine.last_launches
     barrier()
     fwd_ms = timed(lambda: device_step(False), args.steps)
@@ -316,11 +327,13 @@ def run_ours(args):
                 "h2d_bytes_per_step": 8 * P, "d2h_bytes_per_step": 8 * (1 + P + n_nets)},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
+        "step_ms_min_median_max": [min(step_ms), statistics.median(step_ms), max(step_ms)],
         "forward_only": {"value": world * n_nets / (fwd * 1e-3), "unit": "networks/s",
                          "ms_per_step": fwd},
         "grad_fwd_ratio": ms / fwd,
         "timed_wall_s": wall,
     }
+    clocks.stop()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, done, el = oracle_networks_per_s(w, edges, g, b, want_grad, 10.0)
         line["cpu_baseline"] = {

@@ -38,6 +38,7 @@ struct Prepared {
   ProgramDev prog{};
   int grid = 0, block = 0;
   size_t smem = 0;
+  bool warp_teams = false;
 };
 
 }  // namespace qtc
@@ -456,7 +457,28 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
     hp->gates[g].der_off = der_off[g];
     hp->gates[g].rank = (uint32_t)leaf_rank_of(table.specs[g].kind);
   }
-  hp->smem = (size_t)(table_elems + hp->max_arena) * elem;
+  // Networks of rank <= 7 (<= 4 elements per lane) run one per warp;
+  // larger ones use the whole CTA.  Each team stages its op list in chunks.
+  uint32_t max_ops = 1;
+  int max_rank = 0;
+  for (const TaskDev& t : hp->tasks) max_ops = std::max(max_ops, t.op_count);
+  for (const Plan& pl : b->plans) max_rank = std::max(max_rank, pl.max_rank);
+  auto round16 = [](size_t x) { return (uint32_t)((x + 15) & ~size_t(15)); };
+  hp->table_bytes = round16((size_t)table_elems * elem);
+  auto layout = [&](bool warp, uint32_t stage) {
+    hp->warp_teams = warp;
+    hp->n_teams = warp ? kExecBlock / 32 : 1;
+    hp->stage_ops = stage;
+    hp->team_bytes = round16((size_t)stage * sizeof(SOp) + (size_t)hp->max_arena * elem);
+    hp->smem = hp->table_bytes + (size_t)hp->n_teams * hp->team_bytes;
+    return hp->smem <= max_dynamic;
+  };
+  bool ok = max_rank <= 7 && layout(true, std::min<uint32_t>(max_ops, 128));
+  for (uint32_t stage = std::min<uint32_t>(max_ops, 64); !ok && stage >= 4; stage /= 2)
+    ok = layout(false, stage);
+  if (!ok)
+    fail(QTC_ERR_UNSUPPORTED, "program needs %zu bytes of shared memory (limit %zu)", hp->smem,
+         max_dynamic);
   b->host_programs.push_back(std::move(hp));
   return *b->host_programs.back();
 }
@@ -498,6 +520,9 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   d.gates = dg;
   d.n_gates = G;
   d.table_elems = hp.table_elems;
+  d.table_bytes = hp.table_bytes;
+  d.team_bytes = hp.team_bytes;
+  d.stage_ops = hp.stage_ops;
   d.tasks = dt;
   d.n_tasks = (int)hp.tasks.size();
   d.ops = dops;
@@ -513,10 +538,13 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   pr.block = kExecBlock;
   pr.smem = hp.smem;
   int per_sm = 0;
-  cuda_check(smem_exec_configure(dtype == QTC_C128 ? 0 : 1, pr.smem, max_dyn, pr.block, &per_sm),
+  pr.warp_teams = hp.warp_teams;
+  cuda_check(smem_exec_configure(dtype == QTC_C128 ? 0 : 1, pr.warp_teams, pr.smem, max_dyn,
+                                 pr.block, &per_sm),
              "configure executor");
   if (per_sm < 1) fail(QTC_ERR_UNSUPPORTED, "executor does not fit on an SM (%zu bytes)", pr.smem);
-  pr.grid = std::max(1, std::min((int)hp.tasks.size(), e->sm_count * per_sm));
+  const int ctas = ((int)hp.tasks.size() + hp.n_teams - 1) / hp.n_teams;
+  pr.grid = std::max(1, std::min(ctas, e->sm_count * per_sm));
   b->prepared.push_back(pr);
   return b->prepared.back();
 }
@@ -526,7 +554,8 @@ static void launch(qtc_engine* e, const Prepared& pr, const double* params_dev, 
   ProgramDev d = pr.prog;
   d.params = params_dev;
   d.out = out_dev;
-  cuda_check(smem_exec_launch(d, pr.dtype == QTC_C128 ? 0 : 1, pr.grid, pr.block, pr.smem, stream),
+  cuda_check(smem_exec_launch(d, pr.dtype == QTC_C128 ? 0 : 1, pr.warp_teams, pr.grid, pr.block,
+                              pr.smem, stream),
              "launch executor");
   e->last_launches = 1;
 }

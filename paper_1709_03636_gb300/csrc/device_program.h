@@ -91,6 +91,9 @@ struct ProgramDev {
   const GateEntryDev* gates;
   int n_gates;
   uint32_t table_elems;        // gate values + derivatives, in elements
+  uint32_t table_bytes;        // table region, rounded to 16 bytes
+  uint32_t team_bytes;         // per team: staged ops, then its arena
+  uint32_t stage_ops;          // ops staged per team at a time
   const TaskDev* tasks;
   int n_tasks;
   const SOp* ops;

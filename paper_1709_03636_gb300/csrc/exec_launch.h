@@ -8,9 +8,11 @@
 namespace qtc {
 
 // dtype: 0 = complex double, otherwise complex float.
-cudaError_t smem_exec_configure(int dtype, size_t smem_bytes, size_t max_dynamic, int block,
-                                int* blocks_per_sm);
-cudaError_t smem_exec_launch(const ProgramDev& prog, int dtype, int grid, int block,
-                             size_t smem_bytes, cudaStream_t stream);
+// warp_teams: each warp of a CTA runs its own network (small networks);
+// otherwise the whole CTA runs one network at a time.
+cudaError_t smem_exec_configure(int dtype, bool warp_teams, size_t smem_bytes, size_t max_dynamic,
+                                int block, int* blocks_per_sm);
+cudaError_t smem_exec_launch(const ProgramDev& prog, int dtype, bool warp_teams, int grid,
+                             int block, size_t smem_bytes, cudaStream_t stream);
 
 }  // namespace qtc

@@ -108,14 +108,42 @@ __device__ void gate_tensor(const GateSpec& s, const double* params, double2* va
     }
 }
 
+// A team is one warp (small networks, kWarp) or the whole CTA.
+template <bool kWarp>
+struct Team {
+  int tid, size, id;
+  __device__ Team() {
+    if (kWarp) {
+      tid = threadIdx.x & 31;
+      size = 32;
+      id = threadIdx.x >> 5;
+    } else {
+      tid = threadIdx.x;
+      size = blockDim.x;
+      id = 0;
+    }
+  }
+  __device__ __forceinline__ void sync() const {
+    if (kWarp)
+      __syncwarp();
+    else
+      __syncthreads();
+  }
+};
+
+// Element pointer of an op offset: gate table below table_elems, else the
+// team's own arena.
 template <typename T>
-__device__ __forceinline__ void contract_op(T* sm, const SOp& op) {
+__device__ __forceinline__ T* resolve(uint32_t off, T* table, T* arena, uint32_t table_elems) {
+  return off < table_elems ? table + off : arena + (off - table_elems);
+}
+
+template <typename T, bool kWarp>
+__device__ __forceinline__ void contract_op(const SOp& op, T* out, const T* a, const T* b,
+                                            const Team<kWarp>& team) {
   const uint32_t nout = 1u << op.rc;
   const uint32_t ny = 1u << op.ry;
-  T* out = sm + op.out;
-  const T* a = sm + op.in1;
-  const T* b = sm + op.in2;
-  for (uint32_t c = threadIdx.x; c < nout; c += blockDim.x) {
+  for (uint32_t c = team.tid; c < nout; c += team.size) {
     uint32_t oa = 0, ob = 0;
     for (int i = 0; i < op.rc; ++i) {
       const uint32_t bit = (c >> i) & 1u;
@@ -136,15 +164,16 @@ __device__ __forceinline__ void contract_op(T* sm, const SOp& op) {
   }
 }
 
-template <typename T>
+constexpr int kMaxTeams = 8;
+
+template <typename T, bool kWarp>
 __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  __shared__ SOp s_op[2];
-  __shared__ double s_grad[2 * kMaxParams];
-  __shared__ unsigned int s_task;
+  __shared__ double s_grad[kMaxTeams][2 * kMaxParams];
+  __shared__ unsigned int s_task[kMaxTeams];
   __shared__ int s_last;
   __shared__ double s_red[256];
+  T* table = reinterpret_cast<T*>(smem_raw);
 
   // gate table (leaf values) in FP64, stored in the contraction type
   for (int e = threadIdx.x; e < prog.n_gates; e += blockDim.x) {
@@ -153,74 +182,89 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
     gate_tensor(g.spec, prog.params, val, der);
     const int n = 1 << g.rank;
     for (int i = 0; i < n; ++i) {
-      sm[g.val_off + i] = from_d2<T>(val[i]);
-      if (g.spec.slot >= 0) sm[g.der_off + i] = from_d2<T>(der[i]);
+      table[g.val_off + i] = from_d2<T>(val[i]);
+      if (g.spec.slot >= 0) table[g.der_off + i] = from_d2<T>(der[i]);
     }
   }
+  __syncthreads();
+
+  const Team<kWarp> team;
+  unsigned char* team_base = smem_raw + prog.table_bytes + (size_t)team.id * prog.team_bytes;
+  SOp* stage = reinterpret_cast<SOp*>(team_base);
+  T* arena = reinterpret_cast<T*>(team_base + (size_t)prog.stage_ops * sizeof(SOp));
+  double* grad = s_grad[team.id];
   const int P = prog.n_params;
   const int stride = 2 + 2 * P;
+  constexpr int kWords = sizeof(SOp) / sizeof(uint4);
   for (;;) {
-    if (threadIdx.x == 0) s_task = atomicAdd(&prog.counters[0], 1u);
-    for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) s_grad[i] = 0.0;
-    __syncthreads();
-    const unsigned int t = s_task;
+    if (team.tid == 0) s_task[team.id] = atomicAdd(&prog.counters[0], 1u);
+    for (int i = team.tid; i < 2 * P; i += team.size) grad[i] = 0.0;
+    team.sync();
+    const unsigned int t = s_task[team.id];
     if (t >= (unsigned)prog.n_tasks) break;
     const TaskDev task = prog.tasks[t];
-    const uint4* src = reinterpret_cast<const uint4*>(prog.ops + task.op_begin);
-    constexpr int kWords = sizeof(SOp) / sizeof(uint4);
-    if (threadIdx.x < kWords) reinterpret_cast<uint4*>(&s_op[0])[threadIdx.x] = src[threadIdx.x];
-    __syncthreads();
-    for (uint32_t k = 0; k < task.op_count; ++k) {
-      // stage the next op while this one runs
-      if (k + 1 < task.op_count && threadIdx.x >= 32 && threadIdx.x < 32 + kWords)
-        reinterpret_cast<uint4*>(&s_op[(k + 1) & 1])[threadIdx.x - 32] =
-            src[(k + 1) * kWords + threadIdx.x - 32];
-      const SOp& op = s_op[k & 1];
-      switch (op.code) {
-        case SOP_CONTRACT:
-          contract_op<T>(sm, op);
-          break;
-        case SOP_LEAFGRAD:
-          if (threadIdx.x < 32) {
-            const uint32_t n = 1u << op.rc;
-            double2 acc = make_double2(0.0, 0.0);
-            for (uint32_t j = threadIdx.x; j < n; j += 32) {
-              const double2 g = to_d2(sm[op.in1 + j]);
-              const double2 d = to_d2(sm[op.in2 + j]);
-              acc.x += g.x * d.x - g.y * d.y;
-              acc.y += g.x * d.y + g.y * d.x;
+    for (uint32_t base = 0; base < task.op_count; base += prog.stage_ops) {
+      // stage a chunk of the op list with one cooperative copy
+      const uint32_t n = min(prog.stage_ops, task.op_count - base);
+      const uint4* src = reinterpret_cast<const uint4*>(prog.ops + task.op_begin + base);
+      uint4* dst = reinterpret_cast<uint4*>(stage);
+      for (uint32_t w = team.tid; w < n * kWords; w += team.size) dst[w] = src[w];
+      team.sync();
+      for (uint32_t k = 0; k < n; ++k) {
+        const SOp& op = stage[k];
+        switch (op.code) {
+          case SOP_CONTRACT:
+            contract_op<T, kWarp>(op, resolve(op.out, table, arena, prog.table_elems),
+                                  resolve(op.in1, table, arena, prog.table_elems),
+                                  resolve(op.in2, table, arena, prog.table_elems), team);
+            break;
+          case SOP_LEAFGRAD:
+            if (threadIdx.x % team.size < 32) {
+              const T* g = resolve(op.in1, table, arena, prog.table_elems);
+              const T* d = resolve(op.in2, table, arena, prog.table_elems);
+              const uint32_t cnt = 1u << op.rc;
+              double2 acc = make_double2(0.0, 0.0);
+              for (uint32_t j = threadIdx.x & 31; j < cnt; j += 32) {
+                const double2 gj = to_d2(g[j]);
+                const double2 dj = to_d2(d[j]);
+                acc.x += gj.x * dj.x - gj.y * dj.y;
+                acc.y += gj.x * dj.y + gj.y * dj.x;
+              }
+              for (int off = 16; off > 0; off >>= 1) {
+                acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
+                acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+              }
+              if ((threadIdx.x & 31) == 0) {
+                grad[2 * op.out] += acc.x;
+                grad[2 * op.out + 1] += acc.y;
+              }
             }
-            for (int off = 16; off > 0; off >>= 1) {
-              acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
-              acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+            break;
+          case SOP_RESULT:
+            if (team.tid == 0) {
+              const double2 v = to_d2(*resolve(op.in1, table, arena, prog.table_elems));
+              prog.results[(size_t)task.net * stride] = v.x;
+              prog.results[(size_t)task.net * stride + 1] = v.y;
             }
-            if (threadIdx.x == 0) {
-              s_grad[2 * op.out] += acc.x;
-              s_grad[2 * op.out + 1] += acc.y;
-            }
-          }
-          break;
-        case SOP_RESULT:
-          if (threadIdx.x == 0) {
-            const double2 v = to_d2(sm[op.in1]);
-            prog.results[(size_t)task.net * stride] = v.x;
-            prog.results[(size_t)task.net * stride + 1] = v.y;
-          }
-          break;
-        case SOP_SEED:
-          if (threadIdx.x == 0) sm[op.out] = from_d2<T>(make_double2(1.0, 0.0));
-          break;
-        default:
-          break;
+            break;
+          case SOP_SEED:
+            if (team.tid == 0)
+              *resolve(op.out, table, arena, prog.table_elems) =
+                  from_d2<T>(make_double2(1.0, 0.0));
+            break;
+          default:
+            break;
+        }
+        team.sync();
       }
-      __syncthreads();
     }
-    for (int i = threadIdx.x; i < 2 * P; i += blockDim.x)
-      prog.results[(size_t)task.net * stride + 2 + i] = prog.want_grad ? s_grad[i] : 0.0;
-    __syncthreads();
+    for (int i = team.tid; i < 2 * P; i += team.size)
+      prog.results[(size_t)task.net * stride + 2 + i] = prog.want_grad ? grad[i] : 0.0;
+    team.sync();
   }
 
   // the last CTA reduces in FP64 and re-arms the counters
+  __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned int done = atomicAdd(&prog.counters[1], 1u);
@@ -257,10 +301,19 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
   }
 }
 
-cudaError_t smem_exec_configure(int dtype, size_t smem_bytes, size_t max_dynamic, int block,
-                                int* blocks_per_sm) {
-  const void* fn = dtype == 0 ? (const void*)smem_exec_kernel<double2>
-                              : (const void*)smem_exec_kernel<float2>;
+template <typename T, bool kWarp>
+static const void* kernel_ptr() {
+  return (const void*)smem_exec_kernel<T, kWarp>;
+}
+
+static const void* select_kernel(int dtype, bool warp) {
+  if (dtype == 0) return warp ? kernel_ptr<double2, true>() : kernel_ptr<double2, false>();
+  return warp ? kernel_ptr<float2, true>() : kernel_ptr<float2, false>();
+}
+
+cudaError_t smem_exec_configure(int dtype, bool warp_teams, size_t smem_bytes, size_t max_dynamic,
+                                int block, int* blocks_per_sm) {
+  const void* fn = select_kernel(dtype, warp_teams);
   // the attribute is per kernel, shared by every prepared program: always
   // raise it to the device limit so a smaller program never lowers it below
   // what a larger one needs
@@ -271,12 +324,19 @@ cudaError_t smem_exec_configure(int dtype, size_t smem_bytes, size_t max_dynamic
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem_bytes);
 }
 
-cudaError_t smem_exec_launch(const ProgramDev& prog, int dtype, int grid, int block,
-                             size_t smem_bytes, cudaStream_t stream) {
-  if (dtype == 0)
-    smem_exec_kernel<double2><<<grid, block, smem_bytes, stream>>>(prog);
-  else
-    smem_exec_kernel<float2><<<grid, block, smem_bytes, stream>>>(prog);
+cudaError_t smem_exec_launch(const ProgramDev& prog, int dtype, bool warp_teams, int grid,
+                             int block, size_t smem_bytes, cudaStream_t stream) {
+  if (dtype == 0) {
+    if (warp_teams)
+      smem_exec_kernel<double2, true><<<grid, block, smem_bytes, stream>>>(prog);
+    else
+      smem_exec_kernel<double2, false><<<grid, block, smem_bytes, stream>>>(prog);
+  } else {
+    if (warp_teams)
+      smem_exec_kernel<float2, true><<<grid, block, smem_bytes, stream>>>(prog);
+    else
+      smem_exec_kernel<float2, false><<<grid, block, smem_bytes, stream>>>(prog);
+  }
   return cudaGetLastError();
 }
 

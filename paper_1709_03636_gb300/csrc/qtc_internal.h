@@ -161,6 +161,11 @@ struct HostProgram {
   std::vector<SOp> ops;
   std::vector<double> weights;
   uint32_t table_elems = 0, max_arena = 0;
+  uint32_t table_bytes = 0;        // gate table region, 16-byte rounded
+  uint32_t team_bytes = 0;         // per team: staged ops + arena
+  uint32_t stage_ops = 0;          // ops staged per team at a time
+  bool warp_teams = false;         // one network per warp (small networks)
+  int n_teams = 1;                 // teams per CTA
   size_t smem = 0;                 // dynamic shared memory per CTA, bytes
   int n_nets = 0, n_params = 0;
   int qaoa_reduce = 1;
@@ -173,8 +178,8 @@ const HostProgram& host_program(qtc_batch* b, int dtype, int want_grad, size_t m
 inline size_t elem_bytes(int dtype) { return dtype == QTC_C128 ? 16 : 8; }
 
 // Dynamic shared memory a CTA of the executor may use: the opt-in limit
-// minus 8 KB for the kernel's static shared memory.
-inline size_t max_dynamic_smem(size_t optin) { return optin > 8192 ? optin - 8192 : 0; }
+// minus 16 KB for the kernel's static shared memory (about 10 KB).
+inline size_t max_dynamic_smem(size_t optin) { return optin > 16384 ? optin - 16384 : 0; }
 
 constexpr int kExecBlock = 128;
 

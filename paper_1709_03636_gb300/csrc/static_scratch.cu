@@ -100,13 +100,16 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
                "clear counters");
 
     int per_sm = 0;
-    cuda_check(smem_exec_configure(dtype == QTC_C128 ? 0 : 1, hp.smem, max_dyn, kExecBlock,
-                                   &per_sm), "configure executor");
+    cuda_check(smem_exec_configure(dtype == QTC_C128 ? 0 : 1, hp.warp_teams, hp.smem, max_dyn,
+                                   kExecBlock, &per_sm), "configure executor");
     if (per_sm < 1) fail(QTC_ERR_UNSUPPORTED, "executor does not fit on an SM");
     ProgramDev d{};
     d.gates = (const GateEntryDev*)(base + o_gates);
     d.n_gates = G;
     d.table_elems = hp.table_elems;
+    d.table_bytes = hp.table_bytes;
+    d.team_bytes = hp.team_bytes;
+    d.stage_ops = hp.stage_ops;
     d.tasks = (const TaskDev*)(base + o_tasks);
     d.n_tasks = (int)hp.tasks.size();
     d.ops = (const SOp*)(base + o_ops);
@@ -119,8 +122,10 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
     d.counters = (unsigned int*)(base + o_counters);
     d.want_grad = hp.want_grad;
     d.qaoa_reduce = hp.qaoa_reduce;
-    const int grid = std::max(1, std::min((int)hp.tasks.size(), setup.sm_count * per_sm));
-    cuda_check(smem_exec_launch(d, dtype == QTC_C128 ? 0 : 1, grid, kExecBlock, hp.smem, s),
+    const int ctas = ((int)hp.tasks.size() + hp.n_teams - 1) / hp.n_teams;
+    const int grid = std::max(1, std::min(ctas, setup.sm_count * per_sm));
+    cuda_check(smem_exec_launch(d, dtype == QTC_C128 ? 0 : 1, hp.warp_teams, grid, kExecBlock,
+                                hp.smem, s),
                "launch executor");
   });
 }
