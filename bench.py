@@ -233,7 +233,7 @@ def run_ours(args):
     batch.prepare(engine, dtype, want_grad=False)
     P = 2 * w.p
     params = torch.tensor(g + b, dtype=torch.float64, device=dev)
-    out = torch.zeros(1 + P + n_nets, dtype=torch.float64, device=dev)
+    out = torch.zeros(2 + P + n_nets, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -324,7 +324,7 @@ def run_ours(args):
                      "kernel": "smem_exec_kernel", "peak_kind": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": alg_bytes},
         "e2e": {"value": world * n_nets / e2e_s, "unit": "networks/s",
-                "h2d_bytes_per_step": 8 * P, "d2h_bytes_per_step": 8 * (1 + P + n_nets)},
+                "h2d_bytes_per_step": 8 * P, "d2h_bytes_per_step": 8 * (2 + P + n_nets)},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "step_ms_min_median_max": [min(step_ms), statistics.median(step_ms), max(step_ms)],

@@ -112,6 +112,17 @@ typedef struct qtc_batch_info {
   double grad_bytes_c64;  /* adjoint sweep only, algorithmic bytes          */
 } qtc_batch_info;
 
+typedef struct qtc_program_info {
+  int graph;              /* 1: graph executor (waves), 0: one shared-memory launch */
+  int n_waves;            /* launches per evaluation                         */
+  int n_tasks;            /* tasks over all waves                            */
+  int n_global_steps;     /* global-memory contractions over all waves       */
+  int n_smem_tasks;       /* shared-memory programs over all waves           */
+  int smem_bytes;         /* dynamic shared memory per CTA                   */
+  double work_bytes;      /* global work buffer (largest wave)               */
+  double table_bytes;     /* device program tables, all waves                */
+} qtc_program_info;
+
 typedef struct qtc_engine qtc_engine;
 typedef struct qtc_circuit qtc_circuit;
 typedef struct qtc_network qtc_network;
@@ -126,7 +137,11 @@ const char* qtc_last_error(void);
  * An engine binds one CUDA device and one caller-owned device arena
  * [arena, arena + arena_bytes), 256-byte aligned.  Plans, intermediates,
  * counters and results are carved from it; the library never calls
- * cudaMalloc.  The arena must stay valid until qtc_engine_destroy. */
+ * cudaMalloc.  Program tables grow from the front; the global-memory
+ * intermediates of the graph executor use one work buffer at the back,
+ * shared by all programs of the engine, so calls on one engine must not
+ * overlap on the GPU (issue them on one stream).  The arena must stay valid
+ * until qtc_engine_destroy. */
 qtc_status qtc_engine_create(int device, void* arena, size_t arena_bytes,
                              qtc_engine** out);
 void qtc_engine_destroy(qtc_engine* e);
@@ -199,6 +214,15 @@ qtc_status qtc_batch_create(const qtc_circuit* c, const int32_t* obs_edges,
 qtc_status qtc_batch_stats(const qtc_batch* b, qtc_batch_info* info);
 void qtc_batch_destroy(qtc_batch* b);
 
+/* Builds, validates and describes the batch's device program on the host
+ * only (no GPU call): every access range, counter and dependency order of a
+ * graph program is checked against its buffers.  force_graph, small_rank and
+ * max_wave_bytes as in qtc_engine_set_graph_options / qtc_engine_set_limits;
+ * smem_limit: shared memory per CTA to plan for (0: 227 KiB). */
+qtc_status qtc_batch_program_info(qtc_batch* b, int dtype, int want_grad, int force_graph,
+                                  int small_rank, size_t max_wave_bytes, size_t smem_limit,
+                                  qtc_program_info* info);
+
 /* Upload the batch's device program for (dtype, want_grad) into the arena.
  * Optional: the expectation calls below prepare on first use. */
 qtc_status qtc_batch_prepare(qtc_engine* e, qtc_batch* b, int dtype,
@@ -219,8 +243,12 @@ qtc_status qtc_qaoa_expectation(qtc_engine* e, qtc_batch* b,
 /* Same computation with device-resident inputs and outputs, asynchronous
  * on `stream` (no host synchronisation; capturable in a CUDA graph once the
  * batch is prepared).  params_dev: device, 2p doubles (gammas then betas).
- * out_dev: device, 1 + 2p + m doubles: [<C>, d<C>/dtheta (2p, zeros when
- * want_grad = 0), <Z_u Z_v> per edge (m)]. */
+ * out_dev: device, 2 + 2p + m doubles: [<C>, d<C>/dtheta (2p, zeros when
+ * want_grad = 0), <Z_u Z_v> per edge (m), status] where status is 0, or
+ * QTC_ERR_TIMEOUT (3) when a bounded device-side dependency wait expired
+ * (the values are then invalid).  One kernel launch per wave: batches whose
+ * networks all fit one CTA's shared memory run in one launch; larger ones
+ * run in waves whose global intermediates stay under the engine's limit. */
 qtc_status qtc_qaoa_expectation_device(qtc_engine* e, qtc_batch* b,
                                        const double* params_dev, int dtype,
                                        int want_grad, void* stream,
@@ -230,6 +258,26 @@ qtc_status qtc_qaoa_expectation_device(qtc_engine* e, qtc_batch* b,
  * engine issued (for launch accounting). */
 int qtc_engine_last_launches(const qtc_engine* e);
 
+/* Limits of the graph executor (networks too large for one CTA's shared
+ * memory): max_wave_bytes bounds the global-memory intermediates of the
+ * networks contracted in one launch (default 8 GiB; a network needing more
+ * returns QTC_ERR_ARENA), wait_limit_ms bounds every device-side wait for a
+ * producer task (default 10000 ms; on expiry the launch stops early and the
+ * status reads QTC_ERR_TIMEOUT).  Invalidates prepared programs. */
+qtc_status qtc_engine_set_limits(qtc_engine* e, size_t max_wave_bytes, double wait_limit_ms);
+
+/* Program formation (tests and tuning): force_graph != 0 runs every
+ * network through the graph executor even when it fits one CTA's shared
+ * memory; small_rank > 0 moves every tensor of higher rank to global memory
+ * (default 10).  Invalidates prepared programs. */
+qtc_status qtc_engine_set_graph_options(qtc_engine* e, int force_graph, int small_rank);
+
+/* Launches a one-task program whose task waits for a counter nothing ever
+ * signals, so that the bounded wait expires after the engine's wait limit and
+ * the kernel returns normally.  Returns QTC_ERR_TIMEOUT when the bound works
+ * (anything else is a failure).  Used by the failure-detection tests. */
+qtc_status qtc_selftest_wait_timeout(qtc_engine* e, void* stream);
+
 /* ---- evaluation without device allocation --------------------------------
  * The paper has no counterpart to this call; it exists for callers that
  * cannot allocate device memory at all (code running inside another
@@ -237,7 +285,8 @@ int qtc_engine_last_launches(const qtc_engine* e);
  * they cannot hand the library an arena either.  It computes exactly what
  * qtc_qaoa_expectation_device computes, on the caller's current device,
  * with the same inputs and outputs: params_dev (device, 2p doubles) and
- * out_dev (device, 1 + 2p + m doubles, same layout).
+ * out_dev (device, 2 + 2p + m doubles, same layout), for batches whose
+ * networks all fit one CTA's shared memory (others: QTC_ERR_UNSUPPORTED).
  *
  * Its scratch (program tables, per-network result rows, counters) is a
  * fixed file-scope device array of QTC_STATIC_SCRATCH_BYTES, which every GPU

@@ -88,6 +88,15 @@ class Engine(_Handle):
     def reset(self):
         check(lib.qtc_engine_reset(self.ptr))
 
+    def set_limits(self, max_wave_bytes=8 << 30, wait_limit_ms=10000.0):
+        """Graph-executor limits: global intermediates per launch, wait bound."""
+        check(lib.qtc_engine_set_limits(self.ptr, int(max_wave_bytes), float(wait_limit_ms)))
+
+    def set_graph_options(self, force_graph=False, small_rank=0):
+        """Run small networks through the graph executor / move tensors of
+        rank > small_rank to global memory (0: default)."""
+        check(lib.qtc_engine_set_graph_options(self.ptr, int(force_graph), int(small_rank)))
+
     @property
     def last_launches(self) -> int:
         return lib.qtc_engine_last_launches(self.ptr)
@@ -222,6 +231,16 @@ class Batch(_Handle):
         check(lib.qtc_batch_stats(self.ptr, ctypes.byref(info)))
         return {f: getattr(info, f) for f, _ in info._fields_}
 
+    def program_info(self, dtype="c64", want_grad=False, force_graph=False, small_rank=0,
+                     max_wave_bytes=0, smem_limit=0) -> dict:
+        """Build and validate the device program on the host (no GPU)."""
+        from ._lib import qtc_program_info
+        info = qtc_program_info()
+        check(lib.qtc_batch_program_info(self.ptr, _dtype(dtype), int(want_grad),
+                                         int(force_graph), int(small_rank), int(max_wave_bytes),
+                                         int(smem_limit), ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in info._fields_}
+
     def prepare(self, engine: Engine, dtype="c64", want_grad=False, stream=None):
         check(lib.qtc_batch_prepare(engine.ptr, self.ptr, _dtype(dtype), int(want_grad),
                                     _stream(stream)))
@@ -255,7 +274,8 @@ def qaoa_expectation(engine: Engine, batch: Batch, gammas, betas, dtype="c64",
 def qaoa_expectation_device(engine: Engine, batch: Batch, params_dev, out_dev, dtype="c64",
                             want_grad=False, stream=None):
     """Asynchronous form: params_dev (2p float64 CUDA tensor) -> out_dev
-    (1 + 2p + m float64 CUDA tensor: <C>, gradient, per-edge <Z_u Z_v>)."""
+    (2 + 2p + m float64 CUDA tensor: <C>, gradient, per-edge <Z_u Z_v>,
+    status (0, or 3 when a bounded device wait expired))."""
     check(lib.qtc_qaoa_expectation_device(
         engine.ptr, batch.ptr, ctypes.c_void_p(params_dev.data_ptr()), _dtype(dtype),
         int(want_grad), _stream(stream), ctypes.c_void_p(out_dev.data_ptr())))
@@ -273,7 +293,7 @@ def _autograd():
             p = batch.p
             prm = params.detach().to(device=f"cuda:{engine.device}", dtype=torch.float64)
             prm = prm.contiguous()
-            out = torch.empty(1 + 2 * p + len(batch.edges), dtype=torch.float64,
+            out = torch.empty(2 + 2 * p + len(batch.edges), dtype=torch.float64,
                               device=prm.device)
             qaoa_expectation_device(engine, batch, prm, out, dtype, want_grad=True)
             ctx.save_for_backward(out[1:1 + 2 * p].clone())

@@ -41,6 +41,12 @@ class qtc_batch_info(ctypes.Structure):
                 ("grad_cmacs", c_double), ("grad_bytes_c64", c_double)]
 
 
+class qtc_program_info(ctypes.Structure):
+    _fields_ = [("graph", c_int), ("n_waves", c_int), ("n_tasks", c_int),
+                ("n_global_steps", c_int), ("n_smem_tasks", c_int), ("smem_bytes", c_int),
+                ("work_bytes", c_double), ("table_bytes", c_double)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "qtc_last_error": (ctypes.c_char_p, []),
@@ -73,6 +79,11 @@ SIGNATURES = {
                                             c_void_p, c_void_p]),
     "qtc_qaoa_expectation_static": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p,
                                             c_void_p]),
+    "qtc_engine_set_limits": (c_int, [c_void_p, c_size_t, c_double]),
+    "qtc_selftest_wait_timeout": (c_int, [c_void_p, c_void_p]),
+    "qtc_engine_set_graph_options": (c_int, [c_void_p, c_int, c_int]),
+    "qtc_batch_program_info": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_size_t, c_size_t,
+                                       P(qtc_program_info)]),
 }
 
 

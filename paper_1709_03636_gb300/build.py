@@ -51,7 +51,8 @@ def build(verbose: bool = False, ptxas_verbose: bool = False) -> str:
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
     os.makedirs(BUILD, exist_ok=True)
-    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    headers = (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+               glob.glob(os.path.join(INCLUDE, "*.h")))
     incs = ["-I" + INCLUDE, "-I" + CSRC, "-I" + os.path.join(cuda, "include")]
     jobs = []
     objs = []

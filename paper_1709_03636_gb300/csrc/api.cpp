@@ -39,6 +39,9 @@ struct Prepared {
   int grid = 0, block = 0;
   size_t smem = 0;
   bool warp_teams = false;
+  bool graph = false;
+  std::vector<GraphProgDev> waves;   // graph form: one launch each
+  double* raw = nullptr;             // graph form: copy of the result rows
 };
 
 }  // namespace qtc
@@ -54,15 +57,33 @@ struct qtc_engine {
   int sm_count = 0;
   size_t smem_optin = 0;
   int last_launches = 0;
+  ProgramOptions options;                    // wave limit, graph forcing
+  double wait_limit_ms = 10000.0;            // bound of every device-side wait
+
+  // Program tables grow from the front of the arena; the graph executor's
+  // work buffer sits at the back and is shared by every graph program of the
+  // engine (their launches are ordered on the caller's stream).
+  size_t work = 0;
 
   char* alloc(size_t n) {
     size_t at = (used + 255) & ~size_t(255);
-    if (at + n > bytes)
-      fail(QTC_ERR_ARENA, "arena of %zu bytes is too small: need %zu more at offset %zu", bytes,
-           n, at);
+    if (at + n > bytes - work)
+      fail(QTC_ERR_ARENA, "arena of %zu bytes is too small: need %zu more at offset %zu (%zu "
+           "reserved for the work buffer)", bytes, n, at, work);
     used = at + n;
     return arena + at;
   }
+
+  void reserve_work(size_t n) {
+    n = (n + 255) & ~size_t(255);
+    if (n <= work) return;
+    if (used + n > bytes)
+      fail(QTC_ERR_ARENA, "arena of %zu bytes is too small: the work buffer needs %zu bytes and "
+           "program tables use %zu", bytes, n, used);
+    work = n;
+  }
+
+  char* work_base() const { return arena + bytes - work; }
 };
 
 struct qtc_circuit {
@@ -84,6 +105,15 @@ struct qtc_plan {
   Plan plan;
   std::unique_ptr<qtc_batch> single;  // one-network batch for qtc_contract
 };
+
+template <typename V>
+static V* upload(qtc_engine* e, const std::vector<V>& v, cudaStream_t stream, const char* what) {
+  V* d = (V*)e->alloc(sizeof(V) * std::max<size_t>(v.size(), 1));
+  if (!v.empty())
+    cuda_check(cudaMemcpyAsync(d, v.data(), sizeof(V) * v.size(), cudaMemcpyHostToDevice, stream),
+               what);
+  return d;
+}
 
 extern "C" const char* qtc_last_error(void) { return g_last_error.c_str(); }
 
@@ -117,11 +147,90 @@ extern "C" qtc_status qtc_engine_reset(qtc_engine* e) {
   return guarded([&] {
     if (!e) fail(QTC_ERR_INVALID, "null engine");
     e->used = 0;
+    e->work = 0;
     e->generation += 1;
   });
 }
 
 extern "C" int qtc_engine_last_launches(const qtc_engine* e) { return e ? e->last_launches : 0; }
+
+extern "C" qtc_status qtc_engine_set_limits(qtc_engine* e, size_t max_wave_bytes,
+                                            double wait_limit_ms) {
+  return guarded([&] {
+    if (!e) fail(QTC_ERR_INVALID, "null engine");
+    if (max_wave_bytes < (1u << 20)) fail(QTC_ERR_INVALID, "wave limit below 1 MiB");
+    if (!(wait_limit_ms > 0.0)) fail(QTC_ERR_INVALID, "wait limit must be positive");
+    e->options.wave_cap_bytes = max_wave_bytes;
+    e->wait_limit_ms = wait_limit_ms;
+    e->generation += 1;  // programs are re-prepared with the new limits
+    e->used = 0;
+    e->work = 0;
+  });
+}
+
+extern "C" qtc_status qtc_engine_set_graph_options(qtc_engine* e, int force_graph,
+                                                   int small_rank) {
+  return guarded([&] {
+    if (!e) fail(QTC_ERR_INVALID, "null engine");
+    if (small_rank < 0 || small_rank > 16) fail(QTC_ERR_INVALID, "small rank %d", small_rank);
+    e->options.force_graph = force_graph != 0;
+    e->options.small_rank = small_rank;
+    e->generation += 1;
+    e->used = 0;
+    e->work = 0;
+  });
+}
+
+extern "C" qtc_status qtc_selftest_wait_timeout(qtc_engine* e, void* stream) {
+  qtc_status result = QTC_OK;
+  qtc_status st = guarded([&] {
+    if (!e) fail(QTC_ERR_INVALID, "null engine");
+    DeviceScope scope(e->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // one task waiting for a counter that nothing signals
+    std::vector<GTask> tasks(1);
+    tasks[0] = GTask{};
+    tasks[0].kind = GT_SMEM;
+    tasks[0].wait_begin = 0;
+    tasks[0].wait_count = 1;
+    tasks[0].signal = 0xFFFFFFFFu;
+    std::vector<WaitDev> waits{{0u, 1u}};
+    const size_t mark = e->used;
+    GraphProgDev d{};
+    d.tasks = upload(e, tasks, s, "upload tasks");
+    d.n_tasks = 1;
+    d.waits = upload(e, waits, s, "upload waits");
+    d.n_counters = 1;
+    d.final_wave = 1;
+    auto* cnt = (unsigned int*)e->alloc(sizeof(unsigned int) * (CTR_FIRST_DEP + 1));
+    auto* out = (double*)e->alloc(sizeof(double) * 2);
+    auto* params = (double*)e->alloc(sizeof(double));
+    auto* res = (double*)e->alloc(sizeof(double) * 2);
+    d.counters = cnt;
+    d.out = out;
+    d.params = params;
+    d.results = res;
+    d.wait_limit_ns = (long long)(e->wait_limit_ms * 1e6);
+    d.table_bytes = 0;
+    d.arena_bytes = 0;
+    d.stage_ops = 1;
+    cuda_check(cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * (CTR_FIRST_DEP + 1), s), "clear");
+    int per_sm = 0;
+    const size_t max_dyn = max_dynamic_smem(e->smem_optin);
+    const size_t smem = 2 * (size_t)kYTab * sizeof(uint32_t) + 256 * 16;
+    cuda_check(graph_exec_configure(1, smem, max_dyn, &per_sm), "configure");
+    cuda_check(graph_exec_launch(d, 1, 1, smem, s), "launch");
+    double host_out[2] = {0, 0};
+    cuda_check(cudaMemcpyAsync(host_out, out, sizeof host_out, cudaMemcpyDeviceToHost, s), "read");
+    cuda_check(cudaStreamSynchronize(s), "synchronise");
+    e->used = mark;
+    if (host_out[1] != 0.0) {
+      result = (qtc_status)(int)host_out[1];
+      set_last_error("the forged dependency wait expired as intended");
+    }
+  });
+  return st != QTC_OK ? st : result;
+}
 
 // ---- circuits ------------------------------------------------------------------
 
@@ -388,12 +497,13 @@ extern "C" void qtc_batch_destroy(qtc_batch* b) { delete b; }
 // ---- device programs ---------------------------------------------------------------
 
 const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
-                                     size_t max_dynamic) {
+                                     size_t max_dynamic, const ProgramOptions& opts) {
   if (dtype != QTC_C128 && dtype != QTC_C64 && dtype != QTC_SPLIT_BF16)
     fail(QTC_ERR_INVALID, "unknown dtype %d", dtype);
   want_grad = want_grad ? 1 : 0;
   for (const auto& hp : b->host_programs)
-    if (hp->dtype == dtype && hp->want_grad == want_grad && hp->max_dynamic == max_dynamic)
+    if (hp->dtype == dtype && hp->want_grad == want_grad && hp->max_dynamic == max_dynamic &&
+        hp->options == opts)
       return *hp;
   const size_t elem = elem_bytes(dtype);
   const int P = b->circuit.n_params;
@@ -429,18 +539,27 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
   hp->qaoa_reduce = b->qaoa_reduce;
   hp->weights = b->weights;
   hp->table_elems = table_elems;
+  hp->options = opts;
+  hp->gates.resize(G);
+  for (int g = 0; g < G; ++g) {
+    hp->gates[g].spec = table.specs[g];
+    hp->gates[g].val_off = val_off[g];
+    hp->gates[g].der_off = der_off[g];
+    hp->gates[g].rank = (uint32_t)leaf_rank_of(table.specs[g].kind);
+  }
   std::vector<int> order(N);
   for (int i = 0; i < N; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(),
                    [&](int x, int y) { return b->plans[x].cmacs > b->plans[y].cmacs; });
+  bool all_fit = !opts.force_graph;
   for (int i : order) {
+    if (!all_fit) break;
     LoweredNet ln = lower_smem(b->plans[i], leaf_gate[i], val_off, der_off, table_elems,
                                want_grad != 0, max_elems);
-    if (!ln.fits)
-      fail(QTC_ERR_UNSUPPORTED,
-           "network %d (max rank %d, %u arena elements) does not fit in shared memory (%u "
-           "elements); the global-memory executor handles such networks",
-           i, b->plans[i].max_rank, ln.arena_elems, max_elems);
+    if (!ln.fits) {
+      all_fit = false;
+      break;
+    }
     TaskDev t{};
     t.op_begin = (uint32_t)hp->ops.size();
     t.op_count = (uint32_t)ln.ops.size();
@@ -450,12 +569,14 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
     hp->ops.insert(hp->ops.end(), ln.ops.begin(), ln.ops.end());
     hp->max_arena = std::max(hp->max_arena, ln.arena_elems);
   }
-  hp->gates.resize(G);
-  for (int g = 0; g < G; ++g) {
-    hp->gates[g].spec = table.specs[g];
-    hp->gates[g].val_off = val_off[g];
-    hp->gates[g].der_off = der_off[g];
-    hp->gates[g].rank = (uint32_t)leaf_rank_of(table.specs[g].kind);
+  if (!all_fit) {
+    // some network is too large for one CTA: the graph executor runs them all
+    hp->tasks.clear();
+    hp->ops.clear();
+    hp->max_arena = 0;
+    build_graph_program(*hp, b->plans, leaf_gate, val_off, der_off, max_dynamic, opts);
+    b->host_programs.push_back(std::move(hp));
+    return *b->host_programs.back();
   }
   // Networks of rank <= 7 (<= 4 elements per lane) run one per warp;
   // larger ones use the whole CTA.  Each team stages its op list in chunks.
@@ -483,6 +604,82 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
   return *b->host_programs.back();
 }
 
+// Uploads a graph-form program: tables per wave, one work buffer shared by
+// the waves (they run one after another on the stream), zeroed counters and
+// result rows.
+static Prepared& prepare_graph(qtc_engine* e, qtc_batch* b, const HostProgram& hp,
+                               cudaStream_t stream, size_t max_dyn) {
+  DeviceScope scope(e->device);
+  const int P = hp.n_params, N = hp.n_nets;
+  const size_t stride = 2 + 2 * (size_t)P;
+  Prepared pr;
+  pr.engine = e;
+  pr.generation = e->generation;
+  pr.dtype = hp.dtype;
+  pr.want_grad = hp.want_grad;
+  pr.graph = true;
+  auto* dg = upload(e, hp.gates, stream, "upload gates");
+  auto* dw = upload(e, hp.weights, stream, "upload weights");
+  auto* dparams = (double*)e->alloc(sizeof(double) * std::max(P, 1));
+  auto* dres = (double*)e->alloc(sizeof(double) * N * stride);
+  auto* draw = (double*)e->alloc(sizeof(double) * N * stride);
+  auto* dout = (double*)e->alloc(sizeof(double) * (2 + P + N));
+  const size_t n_ctr = CTR_FIRST_DEP + hp.max_counters;
+  auto* dcnt = (unsigned int*)e->alloc(sizeof(unsigned int) * n_ctr);
+  std::vector<GraphProgDev> waves;
+  for (const WaveHost& w : hp.waves) {
+    GraphProgDev d{};
+    d.tasks = upload(e, w.tasks, stream, "upload tasks");
+    d.n_tasks = (int)w.tasks.size();
+    d.ops = upload(e, w.ops, stream, "upload ops");
+    d.steps = upload(e, w.steps, stream, "upload steps");
+    d.waits = upload(e, w.waits, stream, "upload waits");
+    d.n_counters = (int)w.n_counters;
+    waves.push_back(d);
+  }
+  e->reserve_work(std::max<size_t>(256, hp.max_global_elems * elem_bytes(hp.dtype)));
+  cuda_check(cudaMemsetAsync(dcnt, 0, sizeof(unsigned int) * n_ctr, stream), "clear counters");
+  cuda_check(cudaMemsetAsync(dres, 0, sizeof(double) * N * stride, stream), "clear results");
+  cuda_check(cudaStreamSynchronize(stream), "prepare sync");
+  int per_sm = 0;
+  cuda_check(graph_exec_configure(hp.dtype == QTC_C128 ? 0 : 1, hp.smem, max_dyn, &per_sm),
+             "configure graph executor");
+  if (per_sm < 1) fail(QTC_ERR_UNSUPPORTED, "graph executor does not fit on an SM");
+  size_t max_tasks = 1;
+  for (const WaveHost& w : hp.waves) max_tasks = std::max(max_tasks, w.tasks.size());
+  pr.grid = (int)std::max<size_t>(1, std::min<size_t>(max_tasks, (size_t)e->sm_count * per_sm));
+  pr.smem = hp.smem;
+  for (size_t i = 0; i < waves.size(); ++i) {
+    GraphProgDev& d = waves[i];
+    d.gates = dg;
+    d.n_gates = (int)hp.gates.size();
+    d.table_elems = hp.table_elems;
+    d.table_bytes = hp.table_bytes;
+    d.arena_bytes = hp.work_bytes;
+    d.stage_ops = hp.stage_ops;
+    d.gbase = nullptr;  // the engine's work buffer, set at launch
+    d.n_params = P;
+    d.n_nets = N;
+    d.final_wave = i + 1 == waves.size();
+    d.weights = dw;
+    d.params = dparams;
+    d.results = dres;
+    d.raw_out = draw;
+    d.out = dout;
+    d.counters = dcnt;
+    d.want_grad = hp.want_grad;
+    d.qaoa_reduce = hp.qaoa_reduce;
+    d.wait_limit_ns = (long long)(e->wait_limit_ms * 1e6);
+  }
+  pr.waves = waves;
+  pr.raw = draw;
+  pr.prog.params = dparams;
+  pr.prog.out = dout;
+  pr.prog.results = dres;
+  b->prepared.push_back(pr);
+  return b->prepared.back();
+}
+
 static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
                          cudaStream_t stream) {
   want_grad = want_grad ? 1 : 0;
@@ -491,10 +688,11 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
         p.want_grad == want_grad)
       return p;
   const size_t max_dyn = max_dynamic_smem(e->smem_optin);
-  const HostProgram& hp = host_program(b, dtype, want_grad, max_dyn);
+  const HostProgram& hp = host_program(b, dtype, want_grad, max_dyn, e->options);
   const int P = hp.n_params;
   const int N = hp.n_nets;
   const int G = (int)hp.gates.size();
+  if (hp.graph) return prepare_graph(e, b, hp, stream, max_dyn);
 
   DeviceScope scope(e->device);
   Prepared pr;
@@ -509,7 +707,7 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   auto* dw = (double*)e->alloc(sizeof(double) * N);
   auto* dparams = (double*)e->alloc(sizeof(double) * std::max(P, 1));
   auto* dres = (double*)e->alloc(sizeof(double) * (size_t)N * (2 + 2 * P));
-  auto* dout = (double*)e->alloc(sizeof(double) * (1 + P + N));
+  auto* dout = (double*)e->alloc(sizeof(double) * (2 + P + N));
   auto* dcnt = (unsigned int*)e->alloc(sizeof(unsigned int) * 4);
   cuda_check(cudaMemcpyAsync(dg, hp.gates.data(), sizeof(GateEntryDev) * G, cudaMemcpyHostToDevice, stream), "upload gates");
   cuda_check(cudaMemcpyAsync(dt, hp.tasks.data(), sizeof(TaskDev) * hp.tasks.size(), cudaMemcpyHostToDevice, stream), "upload tasks");
@@ -551,6 +749,18 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
 
 static void launch(qtc_engine* e, const Prepared& pr, const double* params_dev, double* out_dev,
                    cudaStream_t stream) {
+  if (pr.graph) {
+    for (const GraphProgDev& w : pr.waves) {
+      GraphProgDev d = w;
+      d.params = params_dev;
+      d.out = out_dev;
+      d.gbase = e->work_base();
+      cuda_check(graph_exec_launch(d, pr.dtype == QTC_C128 ? 0 : 1, pr.grid, pr.smem, stream),
+                 "launch graph executor");
+    }
+    e->last_launches = (int)pr.waves.size();
+    return;
+  }
   ProgramDev d = pr.prog;
   d.params = params_dev;
   d.out = out_dev;
@@ -558,6 +768,41 @@ static void launch(qtc_engine* e, const Prepared& pr, const double* params_dev, 
                               pr.smem, stream),
              "launch executor");
   e->last_launches = 1;
+}
+
+extern "C" qtc_status qtc_batch_program_info(qtc_batch* b, int dtype, int want_grad,
+                                              int force_graph, int small_rank,
+                                              size_t max_wave_bytes, size_t smem_limit,
+                                              qtc_program_info* info) {
+  return guarded([&] {
+    if (!b || !info) fail(QTC_ERR_INVALID, "null argument");
+    ProgramOptions opts;
+    opts.force_graph = force_graph != 0;
+    opts.small_rank = small_rank;
+    if (max_wave_bytes) opts.wave_cap_bytes = max_wave_bytes;
+    const size_t max_dyn = max_dynamic_smem(smem_limit ? smem_limit : (size_t)232448);
+    const HostProgram& hp = host_program(b, dtype, want_grad, max_dyn, opts);
+    std::memset(info, 0, sizeof *info);
+    info->graph = hp.graph ? 1 : 0;
+    info->smem_bytes = (int)hp.smem;
+    double tables = sizeof(GateEntryDev) * hp.gates.size();
+    if (hp.graph) {
+      info->n_waves = (int)hp.waves.size();
+      for (const WaveHost& w : hp.waves) {
+        info->n_tasks += (int)w.tasks.size();
+        info->n_global_steps += (int)w.steps.size();
+        for (const GTask& t : w.tasks) info->n_smem_tasks += t.kind == GT_SMEM;
+        tables += sizeof(GTask) * w.tasks.size() + sizeof(SOp) * w.ops.size() +
+                  sizeof(GStep) * w.steps.size() + sizeof(WaitDev) * w.waits.size();
+      }
+      info->work_bytes = (double)hp.max_global_elems * elem_bytes(dtype);
+    } else {
+      info->n_waves = 1;
+      info->n_tasks = info->n_smem_tasks = (int)hp.tasks.size();
+      tables += sizeof(TaskDev) * hp.tasks.size() + sizeof(SOp) * hp.ops.size();
+    }
+    info->table_bytes = tables;
+  });
 }
 
 extern "C" qtc_status qtc_batch_prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
@@ -593,7 +838,7 @@ extern "C" qtc_status qtc_qaoa_expectation(qtc_engine* e, qtc_batch* b, const do
     const Prepared& pr = prepare(e, b, dtype, want_grad, s);
     const int P = 2 * p;
     const int N = (int)b->plans.size();
-    std::vector<double> params(P), host_out(1 + P + N);
+    std::vector<double> params(P), host_out(2 + P + N);
     for (int k = 0; k < p; ++k) {
       params[k] = gammas[k];
       params[p + k] = betas[k];
@@ -604,6 +849,9 @@ extern "C" qtc_status qtc_qaoa_expectation(qtc_engine* e, qtc_batch* b, const do
     cuda_check(cudaMemcpyAsync(host_out.data(), pr.prog.out, sizeof(double) * host_out.size(),
                                cudaMemcpyDeviceToHost, s), "download results");
     cuda_check(cudaStreamSynchronize(s), "synchronise stream");
+    if (host_out[1 + P + N] != 0.0)
+      fail(QTC_ERR_TIMEOUT, "a device-side dependency wait expired (status %g)",
+           host_out[1 + P + N]);
     *C_out = host_out[0];
     if (grad_out)
       for (int k = 0; k < P; ++k) grad_out[k] = host_out[1 + k];
@@ -638,10 +886,14 @@ extern "C" qtc_status qtc_contract(qtc_engine* e, const qtc_plan* p, const doubl
       cuda_check(cudaMemcpyAsync((void*)pr.prog.params, params, sizeof(double) * P,
                                  cudaMemcpyHostToDevice, s), "upload parameters");
     launch(e, pr, pr.prog.params, pr.prog.out, s);
-    std::vector<double> res(2 + 2 * P);
-    cuda_check(cudaMemcpyAsync(res.data(), pr.prog.results, sizeof(double) * res.size(),
-                               cudaMemcpyDeviceToHost, s), "download result");
+    std::vector<double> res(2 + 2 * P), status(1, 0.0);
+    cuda_check(cudaMemcpyAsync(res.data(), pr.graph ? pr.raw : pr.prog.results,
+                               sizeof(double) * res.size(), cudaMemcpyDeviceToHost, s),
+               "download result");
+    cuda_check(cudaMemcpyAsync(status.data(), pr.prog.out + 1 + P + 1, sizeof(double),
+                               cudaMemcpyDeviceToHost, s), "download status");
     cuda_check(cudaStreamSynchronize(s), "synchronise stream");
+    if (status[0] != 0.0) fail(QTC_ERR_TIMEOUT, "a device-side dependency wait expired");
     out_re_im[0] = res[0];
     out_re_im[1] = res[1];
     if (grad_re_im)

@@ -65,6 +65,15 @@ enum SOpCode : uint8_t {
   SOP_SEED = 3         // out[0] = 1 (adjoint of the root)
 };
 
+// Operand locations: by default an op offset is an element offset into the
+// task's shared memory (gate table first, then the arena); a flagged operand
+// is an element offset into the global work buffer (graph executor only).
+enum SOpFlag : uint8_t {
+  SOPF_OUT_GLOBAL = 1,
+  SOPF_IN1_GLOBAL = 2,
+  SOPF_IN2_GLOBAL = 4
+};
+
 constexpr int kMaxSmemRank = 16;
 constexpr uint8_t kAbsent = 0xFF;
 
@@ -74,7 +83,7 @@ constexpr uint8_t kAbsent = 0xFF;
 // operand does not carry that label); summed bit j reads in1 bit y1[j] and
 // in2 bit y2[j].
 struct alignas(16) SOp {
-  uint8_t code, rc, ry, pad0;
+  uint8_t code, rc, ry, flags;
   uint32_t out, in1, in2;
   uint8_t p1[kMaxSmemRank], p2[kMaxSmemRank];
   uint8_t y1[kMaxSmemRank], y2[kMaxSmemRank];
@@ -106,6 +115,103 @@ struct ProgramDev {
   unsigned int* counters;      // [0] task queue, [1] finished blocks, [2] error
   int want_grad;
   int qaoa_reduce;             // 1: reduce to the Max-Cut objective
+};
+
+// ---- graph executor: shared-memory subtrees and global-memory steps ---------
+
+constexpr int kMaxRuns = 12;
+constexpr uint32_t kGRow = 256;      // output elements per row of a global step
+constexpr uint32_t kYTab = 4096;     // summed-index offsets tabulated per pass
+
+// Maps bits of one index (output c or summed y) to bits of an operand index:
+// offset = OR_r ((idx >> src[r]) & (2^len[r] - 1)) << dst[r].  Labels kept
+// in the same relative order in both tensors form few runs.
+struct GRuns {
+  uint8_t n;
+  uint8_t src[kMaxRuns];
+  uint8_t len[kMaxRuns];
+  uint8_t dst[kMaxRuns];
+};
+
+enum GStepFlag : uint16_t {
+  GSF_A_TABLE = 1,     // operand A is a gate table entry (shared memory)
+  GSF_B_TABLE = 2,
+  GSF_SPLIT = 4,       // chunks split the summed index; the last chunk reduces
+  GSF_LEAFGRAD = 8     // output is dS/dleaf: reduce it against d(leaf)/dparam
+};
+
+// One contraction C = sum_y A * B in global memory (Eq. 1), cut into chunks.
+// Normal: chunk k computes output rows [k*chunk, (k+1)*chunk) of 256
+// elements (one element per thread and row).  Split (outputs <= 256): chunk k
+// sums y in [k*chunk, (k+1)*chunk) into partial slot k; the last chunk to
+// arrive adds the partials in slot order and writes C (or, for LEAFGRAD,
+// accumulates sum_c C[c] * dleaf[c] into the parameter gradient).
+struct alignas(16) GStep {
+  uint32_t c_off, a_off, b_off;
+  uint32_t partial_off;     // split: element offset of n_chunks * 2^rc partials
+  uint32_t n_chunks, chunk; // normal: rows per chunk; split: y values per chunk
+  uint32_t arrive_ctr;      // split: arrivals (dependency-counter index)
+  uint32_t done_ctr;        // completion counter (target n_chunks; split: 1)
+  uint32_t der_off;         // leafgrad: table offset of d(leaf)/dparam
+  uint32_t net;
+  uint16_t flags;
+  int16_t slot;             // leafgrad: parameter slot
+  uint8_t rc, ry, pad0, pad1;
+  GRuns ca, cb;             // output bits -> A bits, B bits
+  GRuns ya, yb;             // summed bits -> A bits, B bits
+};
+
+enum GTaskKind : uint8_t { GT_SMEM = 0, GT_CHUNK = 1 };
+
+struct GTask {
+  uint8_t kind;
+  uint8_t pad[3];
+  uint32_t a;              // SMEM: first op; CHUNK: step index
+  uint32_t b;              // SMEM: op count; CHUNK: chunk index
+  uint32_t net;
+  uint32_t wait_begin;     // into the wait list
+  uint32_t wait_count;
+  uint32_t signal;         // SMEM: counter incremented when done (~0u: none)
+  uint32_t pad2;
+};
+
+struct WaitDev {
+  uint32_t counter;
+  uint32_t target;
+};
+
+// Counter layout: fixed slots, then the dependency counters of the wave.
+enum CounterSlot : uint32_t {
+  CTR_QUEUE = 0, CTR_BLOCKS = 1, CTR_ERROR = 2, CTR_RESERVED = 3, CTR_FIRST_DEP = 4
+};
+
+// Kernel argument of the graph executor (one launch per wave).
+struct GraphProgDev {
+  const GateEntryDev* gates;
+  int n_gates;
+  uint32_t table_elems;
+  uint32_t table_bytes;        // gate table region, 16-byte rounded
+  uint32_t arena_bytes;        // shared-memory arena of SMEM tasks
+  uint32_t stage_ops;          // ops staged at a time
+  const GTask* tasks;
+  int n_tasks;
+  const SOp* ops;
+  const GStep* steps;
+  const WaitDev* waits;
+  void* gbase;                 // global work buffer of the wave
+  int n_params;
+  int n_nets;
+  int n_counters;              // dependency counters of this wave
+  int final_wave;              // 1: reduce, then clear the result rows
+  const double* weights;
+  const double* params;
+  double* results;             // per network: Re s, Im s, (Re, Im) ds/dparam_k
+  double* raw_out;             // optional copy of the result rows (final wave)
+  double* out;                 // [<C>, d<C>/dparam, Re s per network, status]
+  unsigned int* counters;
+  int want_grad;
+  int qaoa_reduce;
+  long long wait_limit_ns;     // bound of every dependency wait
 };
 
 }  // namespace qtc

@@ -1,0 +1,402 @@
+// Graph executor: networks whose tensors do not fit one CTA's shared memory.
+//
+// One persistent launch per wave of networks.  The task list holds two kinds
+// of tasks, ordered so that every task's producers come earlier:
+//  * shared-memory subtree programs (the ops of the shared-memory executor,
+//    whose operands may also live in the global work buffer), and
+//  * chunks of a global contraction C = sum_y A * B (Eq. 1, batch indices
+//    kept) with bit-map addressing: rows of 256 outputs, one per thread, and
+//    the summed index tabulated in shared memory; for small outputs with long
+//    sums the chunks split the summed index and the last chunk to arrive adds
+//    the partial sums in chunk order (deterministic).
+// CTAs take tasks in list order and wait for the counters of the task's
+// producers.  Every wait is bounded in time: on expiry the CTA sets the error
+// flag, and every CTA stops taking tasks once the flag is set.  The last CTA
+// of the final wave reduces the per-network rows to the Max-Cut objective
+// <C> = sum_e (1 - <Z_u Z_v>_e)/2 (Section 4.1) and its gradient in FP64,
+// records the status, and re-arms the counters.
+#include "exec_common.cuh"
+#include "exec_launch.h"
+#include "qtc.h"
+
+namespace qtc {
+
+constexpr int kGraphBlock = 256;
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t runs_offset(const GRuns& r, uint32_t idx) {
+  uint32_t off = 0;
+  for (int k = 0; k < r.n; ++k) off |= ((idx >> r.src[k]) & ((1u << r.len[k]) - 1u)) << r.dst[k];
+  return off;
+}
+
+template <typename T> __device__ __forceinline__ T load_l2(const T* p);
+template <> __device__ __forceinline__ float2 load_l2<float2>(const float2* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ double2 load_l2<double2>(const double2* p) {
+  return __ldcg(p);
+}
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+
+// Thread 0 only.  Waits until every producer counter of `task` reaches its
+// target; false when the error flag is (or becomes) set or the bound expires.
+__device__ bool wait_for_producers(const GraphProgDev& prog, const GTask& task) {
+  volatile unsigned* err = prog.counters + CTR_ERROR;
+  if (*err) return false;
+  const unsigned long long t0 = now_ns();
+  for (uint32_t i = 0; i < task.wait_count; ++i) {
+    const WaitDev w = prog.waits[task.wait_begin + i];
+    const unsigned* c = prog.counters + CTR_FIRST_DEP + w.counter;
+    while (ld_acquire(c) < w.target) {
+      if (*err) return false;
+      if ((long long)(now_ns() - t0) > prog.wait_limit_ns) {
+        atomicCAS(prog.counters + CTR_ERROR, 0u, (unsigned)QTC_ERR_TIMEOUT);
+        return false;
+      }
+      __nanosleep(200);
+    }
+  }
+  return true;
+}
+
+// Publishes this CTA's writes, then adds to a completion counter.
+__device__ __forceinline__ void signal_done(const GraphProgDev& prog, uint32_t ctr) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0 && ctr != 0xFFFFFFFFu) atomicAdd(prog.counters + CTR_FIRST_DEP + ctr, 1u);
+}
+
+template <typename T>
+__device__ __forceinline__ T* locate(uint32_t off, bool global, T* gbase, T* table, T* arena,
+                                     uint32_t table_elems) {
+  return global ? gbase + off : resolve(off, table, arena, table_elems);
+}
+
+template <typename T>
+__device__ void run_smem_task(const GraphProgDev& prog, const GTask& task, T* table,
+                              unsigned char* work, double* s_grad) {
+  const int P = prog.n_params;
+  const int stride = 2 + 2 * P;
+  for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) s_grad[i] = 0.0;
+  SOp* stage = reinterpret_cast<SOp*>(work);
+  T* arena = reinterpret_cast<T*>(work + (size_t)prog.stage_ops * sizeof(SOp));
+  T* gbase = reinterpret_cast<T*>(prog.gbase);
+  const Team<false> team;
+  constexpr int kWords = sizeof(SOp) / sizeof(uint4);
+  for (uint32_t base = 0; base < task.b; base += prog.stage_ops) {
+    const uint32_t n = min(prog.stage_ops, task.b - base);
+    __syncthreads();
+    const uint4* src = reinterpret_cast<const uint4*>(prog.ops + task.a + base);
+    uint4* dst = reinterpret_cast<uint4*>(stage);
+    for (uint32_t w = threadIdx.x; w < n * kWords; w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    for (uint32_t k = 0; k < n; ++k) {
+      const SOp& op = stage[k];
+      T* out = locate(op.out, (op.flags & SOPF_OUT_GLOBAL) != 0, gbase, table, arena,
+                      prog.table_elems);
+      T* in1 = locate(op.in1, (op.flags & SOPF_IN1_GLOBAL) != 0, gbase, table, arena,
+                      prog.table_elems);
+      T* in2 = locate(op.in2, (op.flags & SOPF_IN2_GLOBAL) != 0, gbase, table, arena,
+                      prog.table_elems);
+      switch (op.code) {
+        case SOP_CONTRACT:
+          contract_op<T, false>(op, out, in1, in2, team);
+          break;
+        case SOP_LEAFGRAD:
+          if (threadIdx.x < 32) {
+            const uint32_t cnt = 1u << op.rc;
+            double2 acc = make_double2(0.0, 0.0);
+            for (uint32_t j = threadIdx.x; j < cnt; j += 32) {
+              const double2 g = to_d2(in1[j]);
+              const double2 d = to_d2(in2[j]);
+              acc.x += g.x * d.x - g.y * d.y;
+              acc.y += g.x * d.y + g.y * d.x;
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+              acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
+              acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+            }
+            if (threadIdx.x == 0) {
+              s_grad[2 * op.out] += acc.x;
+              s_grad[2 * op.out + 1] += acc.y;
+            }
+          }
+          break;
+        case SOP_RESULT:
+          if (threadIdx.x == 0) {
+            const double2 v = to_d2(*in1);
+            prog.results[(size_t)task.net * stride] = v.x;
+            prog.results[(size_t)task.net * stride + 1] = v.y;
+          }
+          break;
+        case SOP_SEED:
+          if (threadIdx.x == 0) *out = from_d2<T>(make_double2(1.0, 0.0));
+          break;
+        default:
+          break;
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < 2 * P; i += blockDim.x)
+    if (s_grad[i] != 0.0) atomicAdd(&prog.results[(size_t)task.net * stride + 2 + i], s_grad[i]);
+  signal_done(prog, task.signal);
+}
+
+template <typename T>
+__device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
+                          unsigned char* work, GStep& s_step, int& s_last) {
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(prog.steps + task.a);
+    for (uint32_t w = threadIdx.x; w < sizeof(GStep) / sizeof(uint4); w += blockDim.x)
+      reinterpret_cast<uint4*>(&s_step)[w] = src[w];
+  }
+  __syncthreads();
+  const GStep& st = s_step;
+  T* gb = reinterpret_cast<T*>(prog.gbase);
+  const T* A = (st.flags & GSF_A_TABLE) ? table + st.a_off : gb + st.a_off;
+  const T* B = (st.flags & GSF_B_TABLE) ? table + st.b_off : gb + st.b_off;
+  uint32_t* ya = reinterpret_cast<uint32_t*>(work);
+  uint32_t* yb = ya + kYTab;
+  T* red = reinterpret_cast<T*>(yb + kYTab);
+  const uint32_t tid = threadIdx.x;
+  const uint32_t nout = 1u << st.rc;
+  const uint64_t ny = 1ull << st.ry;
+
+  if (!(st.flags & GSF_SPLIT)) {
+    T* C = gb + st.c_off;
+    const uint32_t rowlen = nout < kGRow ? nout : kGRow;
+    const uint32_t nrows = nout / rowlen;
+    const uint32_t r0 = task.b * st.chunk;
+    const uint32_t r1 = min(r0 + st.chunk, nrows);
+    const bool active = tid < rowlen;
+    const uint32_t a_lo = runs_offset(st.ca, tid), b_lo = runs_offset(st.cb, tid);
+    if (ny <= kYTab) {
+      for (uint32_t y = tid; y < ny; y += blockDim.x) {
+        ya[y] = runs_offset(st.ya, y);
+        yb[y] = runs_offset(st.yb, y);
+      }
+      __syncthreads();
+      if (active) {
+        const uint32_t n_y = (uint32_t)ny;
+        for (uint32_t row = r0; row < r1; ++row) {
+          const uint32_t hi = row * rowlen;
+          const uint32_t oa = runs_offset(st.ca, hi) | a_lo;
+          const uint32_t ob = runs_offset(st.cb, hi) | b_lo;
+          T acc = czero<T>();
+          for (uint32_t y = 0; y < n_y; ++y) acc = cfma(A[oa | ya[y]], B[ob | yb[y]], acc);
+          C[hi + tid] = acc;
+        }
+      }
+    } else {
+      // one row per chunk; the summed index in passes of kYTab values
+      const uint32_t hi = r0 * rowlen;
+      const uint32_t oa = runs_offset(st.ca, hi) | a_lo;
+      const uint32_t ob = runs_offset(st.cb, hi) | b_lo;
+      T acc = czero<T>();
+      for (uint64_t y0 = 0; y0 < ny; y0 += kYTab) {
+        __syncthreads();
+        for (uint32_t y = tid; y < kYTab; y += blockDim.x) {
+          ya[y] = runs_offset(st.ya, (uint32_t)(y0 + y));
+          yb[y] = runs_offset(st.yb, (uint32_t)(y0 + y));
+        }
+        __syncthreads();
+        if (active)
+          for (uint32_t y = 0; y < kYTab; ++y) acc = cfma(A[oa | ya[y]], B[ob | yb[y]], acc);
+      }
+      if (active) C[hi + tid] = acc;
+    }
+    signal_done(prog, st.done_ctr);
+    return;
+  }
+
+  // split: outputs <= 256, chunk task.b sums y in [y0, y0 + cnt)
+  const uint32_t groups = blockDim.x / nout;
+  const uint32_t c = tid % nout, g = tid / nout;
+  const uint64_t y0 = (uint64_t)task.b * st.chunk;
+  const uint32_t cnt = (uint32_t)min((uint64_t)st.chunk, ny - y0);
+  for (uint32_t y = tid; y < cnt; y += blockDim.x) {
+    ya[y] = runs_offset(st.ya, (uint32_t)(y0 + y));
+    yb[y] = runs_offset(st.yb, (uint32_t)(y0 + y));
+  }
+  __syncthreads();
+  const uint32_t oa = runs_offset(st.ca, c), ob = runs_offset(st.cb, c);
+  T acc = czero<T>();
+  if (g < groups)
+    for (uint32_t y = g; y < cnt; y += groups) acc = cfma(A[oa | ya[y]], B[ob | yb[y]], acc);
+  red[tid] = acc;
+  __syncthreads();
+  T* partial = gb + st.partial_off;
+  if (tid < nout) {
+    T sum = czero<T>();
+    for (uint32_t k = 0; k < groups; ++k) sum = cadd(sum, red[k * nout + tid]);
+    partial[(size_t)task.b * nout + tid] = sum;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0)
+    s_last = atomicAdd(prog.counters + CTR_FIRST_DEP + st.arrive_ctr, 1u) == st.n_chunks - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  T total = czero<T>();
+  if (tid < nout)
+    for (uint32_t k = 0; k < st.n_chunks; ++k)
+      total = cadd(total, load_l2(partial + (size_t)k * nout + tid));
+  if (st.flags & GSF_LEAFGRAD) {
+    // dS/dparam += sum_c dS/dleaf[c] * dleaf[c]/dparam  (leaf has <= 16 entries)
+    if (tid < 32) {
+      double2 prod = make_double2(0.0, 0.0);
+      if (tid < nout) {
+        const double2 t = to_d2(total);
+        const double2 d = to_d2(table[st.der_off + tid]);
+        prod.x = t.x * d.x - t.y * d.y;
+        prod.y = t.x * d.y + t.y * d.x;
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        prod.x += __shfl_down_sync(0xffffffffu, prod.x, off);
+        prod.y += __shfl_down_sync(0xffffffffu, prod.y, off);
+      }
+      if (tid == 0) {
+        const size_t row = (size_t)st.net * (2 + 2 * prog.n_params);
+        atomicAdd(&prog.results[row + 2 + 2 * st.slot], prod.x);
+        atomicAdd(&prog.results[row + 3 + 2 * st.slot], prod.y);
+      }
+    }
+  } else if (tid < nout) {
+    gb[st.c_off + tid] = total;
+  }
+  signal_done(prog, st.done_ctr);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGraphBlock) graph_exec_kernel(const GraphProgDev prog) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ GStep s_step;
+  __shared__ double s_grad[2 * kMaxParams];
+  __shared__ double s_red[kGraphBlock];
+  __shared__ unsigned int s_task;
+  __shared__ int s_flag;
+  __shared__ int s_last;
+  T* table = reinterpret_cast<T*>(smem_raw);
+  unsigned char* work = smem_raw + prog.table_bytes;
+
+  for (int e = threadIdx.x; e < prog.n_gates; e += blockDim.x) {
+    const GateEntryDev g = prog.gates[e];
+    double2 val[16], der[16];
+    gate_tensor(g.spec, prog.params, val, der);
+    const int n = 1 << g.rank;
+    for (int i = 0; i < n; ++i) {
+      table[g.val_off + i] = from_d2<T>(val[i]);
+      if (g.spec.slot >= 0) table[g.der_off + i] = from_d2<T>(der[i]);
+    }
+  }
+  __syncthreads();
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned int t = atomicAdd(&prog.counters[CTR_QUEUE], 1u);
+      int ok = t < (unsigned)prog.n_tasks;
+      if (ok) ok = wait_for_producers(prog, prog.tasks[t]);
+      s_task = t;
+      s_flag = ok;
+    }
+    __syncthreads();
+    if (!s_flag) break;
+    const GTask task = prog.tasks[s_task];
+    if (task.kind == GT_SMEM)
+      run_smem_task<T>(prog, task, table, work, s_grad);
+    else
+      run_chunk<T>(prog, task, table, work, s_step, s_last);
+    __syncthreads();
+  }
+
+  // the last CTA reduces (final wave), records the status and re-arms
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_flag = atomicAdd(&prog.counters[CTR_BLOCKS], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_flag) return;
+  __threadfence();
+  volatile unsigned* vc = prog.counters;
+  const unsigned err = vc[CTR_ERROR] | vc[CTR_RESERVED];
+  __syncthreads();
+  if (threadIdx.x == 0) prog.counters[CTR_RESERVED] = err;  // sticky across waves
+  if (prog.final_wave) {
+    const int P = prog.n_params;
+    const int N = prog.n_nets;
+    const int stride = 2 + 2 * P;
+    const volatile double* res = prog.results;
+    for (int q = 0; q < 1 + P; ++q) {
+      double part = 0.0;
+      for (int e = threadIdx.x; e < N; e += blockDim.x) {
+        const double w = prog.weights[e];
+        if (q == 0)
+          part += w * 0.5 * (1.0 - res[(size_t)e * stride]);
+        else
+          part += -0.5 * w * res[(size_t)e * stride + 2 + 2 * (q - 1)];
+      }
+      s_red[threadIdx.x] = part;
+      __syncthreads();
+      for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) s_red[threadIdx.x] += s_red[threadIdx.x + off];
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) prog.out[q] = prog.qaoa_reduce ? s_red[0] : 0.0;
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < N; e += blockDim.x)
+      prog.out[1 + P + e] = res[(size_t)e * stride];
+    if (threadIdx.x == 0) prog.out[1 + P + N] = (double)err;
+    if (prog.raw_out)
+      for (int i = threadIdx.x; i < N * stride; i += blockDim.x) prog.raw_out[i] = res[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < N * stride; i += blockDim.x) prog.results[i] = 0.0;
+    if (threadIdx.x == 0) prog.counters[CTR_RESERVED] = 0;
+  }
+  for (int i = threadIdx.x; i < prog.n_counters; i += blockDim.x)
+    prog.counters[CTR_FIRST_DEP + i] = 0;
+  if (threadIdx.x == 0) {
+    prog.counters[CTR_QUEUE] = 0;
+    prog.counters[CTR_BLOCKS] = 0;
+    prog.counters[CTR_ERROR] = 0;
+  }
+}
+
+cudaError_t graph_exec_configure(int dtype, size_t smem_bytes, size_t max_dynamic,
+                                 int* blocks_per_sm) {
+  const void* fn = dtype == 0 ? (const void*)graph_exec_kernel<double2>
+                              : (const void*)graph_exec_kernel<float2>;
+  if (smem_bytes > max_dynamic) return cudaErrorInvalidValue;
+  cudaError_t err =
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dynamic);
+  if (err != cudaSuccess) return err;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kGraphBlock, smem_bytes);
+}
+
+cudaError_t graph_exec_launch(const GraphProgDev& prog, int dtype, int grid, size_t smem_bytes,
+                              cudaStream_t stream) {
+  if (dtype == 0)
+    graph_exec_kernel<double2><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
+  else
+    graph_exec_kernel<float2><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
+  return cudaGetLastError();
+}
+
+}  // namespace qtc

@@ -15,4 +15,11 @@ cudaError_t smem_exec_configure(int dtype, bool warp_teams, size_t smem_bytes, s
 cudaError_t smem_exec_launch(const ProgramDev& prog, int dtype, bool warp_teams, int grid,
                              int block, size_t smem_bytes, cudaStream_t stream);
 
+// Graph executor (networks larger than one CTA's shared memory); one launch
+// per wave.
+cudaError_t graph_exec_configure(int dtype, size_t smem_bytes, size_t max_dynamic,
+                                 int* blocks_per_sm);
+cudaError_t graph_exec_launch(const GraphProgDev& prog, int dtype, int grid, size_t smem_bytes,
+                              cudaStream_t stream);
+
 }  // namespace qtc

@@ -1,0 +1,278 @@
+// Host side of the graph executor: per-network units -> waves of tasks.
+#include <algorithm>
+#include <tuple>
+
+#include "qtc_internal.h"
+
+namespace qtc {
+
+namespace {
+
+uint32_t rebase32(uint64_t base, uint32_t local) {
+  const uint64_t v = base + local;
+  if (v >> 32) fail(QTC_ERR_ARENA, "a wave's work buffer exceeds 2^32 elements");
+  return (uint32_t)v;
+}
+
+WaveHost assemble_wave(const std::vector<int>& nets, const std::vector<NetGraph>& graphs) {
+  WaveHost w;
+  std::vector<std::vector<uint32_t>> ctr(nets.size()), arrive(nets.size());
+  std::vector<uint64_t> base(nets.size());
+  uint32_t next_ctr = 0;
+  uint64_t gsize = 0;
+  for (size_t k = 0; k < nets.size(); ++k) {
+    const NetGraph& g = graphs[nets[k]];
+    base[k] = gsize;
+    gsize += (g.global_elems + 63) & ~uint64_t(63);
+    ctr[k].resize(g.units.size());
+    arrive[k].assign(g.units.size(), 0xFFFFFFFFu);
+    for (size_t u = 0; u < g.units.size(); ++u) {
+      ctr[k][u] = next_ctr++;
+      if (g.units[u].kind == GT_CHUNK && (g.units[u].step.flags & GSF_SPLIT))
+        arrive[k][u] = next_ctr++;
+    }
+  }
+  w.global_elems = gsize;
+  w.n_counters = next_ctr;
+  // every unit after its producers: sort by depth (producers are shallower),
+  // interleaving the networks of the wave
+  std::vector<std::tuple<int, int, int>> order;
+  for (size_t k = 0; k < nets.size(); ++k)
+    for (size_t u = 0; u < graphs[nets[k]].units.size(); ++u)
+      order.emplace_back(graphs[nets[k]].units[u].depth, (int)k, (int)u);
+  std::sort(order.begin(), order.end());
+  for (const auto& item : order) {
+    const int k = std::get<1>(item), ui = std::get<2>(item);
+    const NetGraph& g = graphs[nets[k]];
+    const GUnit& u = g.units[ui];
+    const uint32_t wait_begin = (uint32_t)w.waits.size();
+    for (int d : u.deps) w.waits.push_back({ctr[k][d], g.units[d].target});
+    const uint32_t wait_count = (uint32_t)u.deps.size();
+    if (u.kind == GT_SMEM) {
+      GTask t{};
+      t.kind = GT_SMEM;
+      t.a = (uint32_t)w.ops.size();
+      t.b = (uint32_t)u.ops.size();
+      t.net = (uint32_t)nets[k];
+      t.wait_begin = wait_begin;
+      t.wait_count = wait_count;
+      t.signal = ctr[k][ui];
+      for (SOp op : u.ops) {
+        if (op.flags & SOPF_OUT_GLOBAL) op.out = rebase32(base[k], op.out);
+        if (op.flags & SOPF_IN1_GLOBAL) op.in1 = rebase32(base[k], op.in1);
+        if (op.flags & SOPF_IN2_GLOBAL) op.in2 = rebase32(base[k], op.in2);
+        w.ops.push_back(op);
+      }
+      w.tasks.push_back(t);
+    } else {
+      GStep st = u.step;
+      st.net = (uint32_t)nets[k];
+      st.done_ctr = ctr[k][ui];
+      st.arrive_ctr = arrive[k][ui];
+      if (!(st.flags & GSF_LEAFGRAD)) st.c_off = rebase32(base[k], st.c_off);
+      if (!(st.flags & GSF_A_TABLE)) st.a_off = rebase32(base[k], st.a_off);
+      if (!(st.flags & GSF_B_TABLE)) st.b_off = rebase32(base[k], st.b_off);
+      if (st.flags & GSF_SPLIT) st.partial_off = rebase32(base[k], st.partial_off);
+      const uint32_t idx = (uint32_t)w.steps.size();
+      w.steps.push_back(st);
+      for (uint32_t c = 0; c < st.n_chunks; ++c) {
+        GTask t{};
+        t.kind = GT_CHUNK;
+        t.a = idx;
+        t.b = c;
+        t.net = (uint32_t)nets[k];
+        t.wait_begin = wait_begin;
+        t.wait_count = wait_count;
+        t.signal = 0xFFFFFFFFu;
+        w.tasks.push_back(t);
+      }
+    }
+  }
+  return w;
+}
+
+uint64_t runs_max(const GRuns& r, uint32_t bits) {
+  // largest operand offset the run map produces over indices < 2^bits
+  uint64_t off = 0;
+  for (int k = 0; k < r.n; ++k)
+    if (r.src[k] < bits) {
+      const uint32_t len = std::min<uint32_t>(r.len[k], bits - r.src[k]);
+      off |= (((uint64_t)1 << len) - 1) << r.dst[k];
+    }
+  return off;
+}
+
+uint64_t positions_max(const uint8_t* pos, int n) {
+  uint64_t off = 0;
+  for (int i = 0; i < n; ++i)
+    if (pos[i] != kAbsent) off |= (uint64_t)1 << pos[i];
+  return off;
+}
+
+// Checks every access of a wave against its buffers and the task order
+// against the dependencies, so that a lowering mistake is an error on the
+// host instead of a bad address or a wait that never ends on the device.
+void validate_wave(const WaveHost& w, uint32_t table_elems, uint32_t arena_elems) {
+  auto check_ref = [&](uint32_t off, bool global, uint64_t max_index, const char* what) {
+    const uint64_t end = (uint64_t)off + max_index + 1;
+    if (global) {
+      if (end > w.global_elems) fail(QTC_ERR_INVALID, "internal: %s beyond the work buffer", what);
+    } else if (off < table_elems) {
+      if (end > table_elems) fail(QTC_ERR_INVALID, "internal: %s beyond the gate table", what);
+    } else if (end > (uint64_t)table_elems + arena_elems) {
+      fail(QTC_ERR_INVALID, "internal: %s beyond the task arena", what);
+    }
+  };
+  for (const GTask& t : w.tasks) {
+    if (t.wait_begin + t.wait_count > w.waits.size())
+      fail(QTC_ERR_INVALID, "internal: wait list out of range");
+    if (t.kind == GT_SMEM) {
+      if ((uint64_t)t.a + t.b > w.ops.size()) fail(QTC_ERR_INVALID, "internal: op range");
+      if (t.signal != 0xFFFFFFFFu && t.signal >= w.n_counters)
+        fail(QTC_ERR_INVALID, "internal: signal counter out of range");
+      for (uint32_t i = t.a; i < t.a + t.b; ++i) {
+        const SOp& op = w.ops[i];
+        if (op.code == SOP_CONTRACT) {
+          uint64_t m1 = positions_max(op.p1, op.rc) | positions_max(op.y1, op.ry);
+          uint64_t m2 = positions_max(op.p2, op.rc) | positions_max(op.y2, op.ry);
+          check_ref(op.out, op.flags & SOPF_OUT_GLOBAL, ((uint64_t)1 << op.rc) - 1, "op output");
+          check_ref(op.in1, op.flags & SOPF_IN1_GLOBAL, m1, "op operand 1");
+          check_ref(op.in2, op.flags & SOPF_IN2_GLOBAL, m2, "op operand 2");
+        } else if (op.code == SOP_LEAFGRAD) {
+          check_ref(op.in1, false, ((uint64_t)1 << op.rc) - 1, "leaf adjoint");
+          check_ref(op.in2, false, ((uint64_t)1 << op.rc) - 1, "leaf derivative");
+        } else if (op.code == SOP_RESULT) {
+          check_ref(op.in1, op.flags & SOPF_IN1_GLOBAL, 0, "result");
+        } else if (op.code == SOP_SEED) {
+          check_ref(op.out, op.flags & SOPF_OUT_GLOBAL, 0, "seed");
+        }
+      }
+    } else {
+      if (t.a >= w.steps.size()) fail(QTC_ERR_INVALID, "internal: step index");
+      const GStep& st = w.steps[t.a];
+      if (t.b >= st.n_chunks) fail(QTC_ERR_INVALID, "internal: chunk index");
+    }
+  }
+  for (const GStep& st : w.steps) {
+    const uint64_t ma = runs_max(st.ca, st.rc) | runs_max(st.ya, st.ry);
+    const uint64_t mb = runs_max(st.cb, st.rc) | runs_max(st.yb, st.ry);
+    check_ref(st.a_off, !(st.flags & GSF_A_TABLE), ma, "step operand A");
+    check_ref(st.b_off, !(st.flags & GSF_B_TABLE), mb, "step operand B");
+    if (!(st.flags & GSF_LEAFGRAD))
+      check_ref(st.c_off, true, ((uint64_t)1 << st.rc) - 1, "step output");
+    else
+      check_ref(st.der_off, false, ((uint64_t)1 << st.rc) - 1, "leaf derivative");
+    if (st.flags & GSF_SPLIT) {
+      if (st.rc > 8) fail(QTC_ERR_INVALID, "internal: split step with more than 256 outputs");
+      check_ref(st.partial_off, true, ((uint64_t)st.n_chunks << st.rc) - 1, "partials");
+      if (st.arrive_ctr >= w.n_counters) fail(QTC_ERR_INVALID, "internal: arrive counter");
+      if (st.chunk > kYTab) fail(QTC_ERR_INVALID, "internal: split chunk above the table");
+    } else if (((uint64_t)st.chunk * std::min<uint64_t>((uint64_t)1 << st.rc, kGRow)) == 0) {
+      fail(QTC_ERR_INVALID, "internal: empty chunk");
+    }
+    if (st.done_ctr >= w.n_counters) fail(QTC_ERR_INVALID, "internal: done counter");
+  }
+  // every wait refers to a counter whose producer tasks all come earlier
+  std::vector<int64_t> last_producer(w.n_counters, -1);
+  for (size_t i = 0; i < w.tasks.size(); ++i) {
+    const GTask& t = w.tasks[i];
+    for (uint32_t k = 0; k < t.wait_count; ++k) {
+      const WaitDev& wd = w.waits[t.wait_begin + k];
+      if (wd.counter >= w.n_counters) fail(QTC_ERR_INVALID, "internal: wait counter");
+      if (last_producer[wd.counter] < 0)
+        fail(QTC_ERR_INVALID, "internal: task %zu waits for a producer that comes later", i);
+    }
+    if (t.kind == GT_SMEM) {
+      if (t.signal != 0xFFFFFFFFu) last_producer[t.signal] = (int64_t)i;
+    } else {
+      const GStep& st = w.steps[t.a];
+      // a step is complete only after its last chunk; mark it at the last chunk
+      if (t.b + 1 == st.n_chunks) last_producer[st.done_ctr] = (int64_t)i;
+    }
+  }
+}
+
+}  // namespace
+
+void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
+                         const std::vector<std::vector<int>>& leaf_gate,
+                         const std::vector<uint32_t>& val_off,
+                         const std::vector<uint32_t>& der_off, size_t max_dynamic,
+                         const ProgramOptions& opts) {
+  const size_t elem = elem_bytes(hp.dtype);
+  const size_t wave_cap_bytes = opts.wave_cap_bytes;
+  const int N = (int)plans.size();
+  GraphLimits lim;
+  lim.arena_elems = (uint32_t)(49152 / elem);
+  lim.subtree_elems = 32768 / elem;
+  if (opts.small_rank > 0) lim.small_rank = opts.small_rank;
+  std::vector<NetGraph> graphs(N);
+  for (int i = 0; i < N; ++i) {
+    // a network that fits whole in shared memory stays one fused task
+    LoweredNet ln = lower_smem(plans[i], leaf_gate[i], val_off, der_off, hp.table_elems,
+                               hp.want_grad != 0, hp.table_elems + lim.arena_elems);
+    if (ln.fits && !opts.force_graph) {
+      GUnit u;
+      u.kind = GT_SMEM;
+      u.ops = std::move(ln.ops);
+      u.arena_elems = ln.arena_elems;
+      graphs[i].units.push_back(std::move(u));
+      continue;
+    }
+    graphs[i] = lower_graph(plans[i], leaf_gate[i], val_off, der_off, hp.table_elems,
+                            hp.want_grad != 0, lim);
+    if (!graphs[i].fits)
+      fail(QTC_ERR_UNSUPPORTED, "network %d (max rank %d): %s", i, plans[i].max_rank,
+           graphs[i].why.c_str());
+  }
+  // waves: largest networks first, first fit under the cap
+  const uint64_t cap = wave_cap_bytes / elem;
+  std::vector<int> order(N);
+  for (int i = 0; i < N; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return graphs[a].global_elems > graphs[b].global_elems;
+  });
+  std::vector<std::vector<int>> waves;
+  std::vector<uint64_t> used;
+  for (int i : order) {
+    const uint64_t need = (graphs[i].global_elems + 63) & ~uint64_t(63);
+    if (need > cap)
+      fail(QTC_ERR_ARENA,
+           "network %d needs %llu bytes of intermediates in global memory, more than the wave "
+           "limit of %zu bytes",
+           i, (unsigned long long)(need * elem), wave_cap_bytes);
+    size_t w = 0;
+    while (w < waves.size() && used[w] + need > cap) ++w;
+    if (w == waves.size()) {
+      waves.emplace_back();
+      used.push_back(0);
+    }
+    waves[w].push_back(i);
+    used[w] += need;
+  }
+  hp.graph = true;
+  hp.waves.clear();
+  uint32_t max_arena = 0;
+  for (const NetGraph& g : graphs)
+    for (const GUnit& u : g.units) max_arena = std::max(max_arena, u.arena_elems);
+  for (auto& wnets : waves) {
+    std::sort(wnets.begin(), wnets.end());
+    hp.waves.push_back(assemble_wave(wnets, graphs));
+    validate_wave(hp.waves.back(), hp.table_elems, max_arena);
+    hp.max_global_elems = std::max(hp.max_global_elems, hp.waves.back().global_elems);
+    hp.max_counters = std::max(hp.max_counters, hp.waves.back().n_counters);
+  }
+  hp.max_arena = max_arena;
+  hp.stage_ops = 32;
+  auto round16 = [](size_t x) { return (uint32_t)((x + 15) & ~size_t(15)); };
+  const size_t smem_task = (size_t)hp.stage_ops * sizeof(SOp) + (size_t)max_arena * elem;
+  const size_t chunk_task = 2 * (size_t)kYTab * sizeof(uint32_t) + 256 * elem;
+  hp.work_bytes = round16(std::max(smem_task, chunk_task));
+  hp.table_bytes = round16((size_t)hp.table_elems * elem);
+  hp.smem = hp.table_bytes + hp.work_bytes;
+  if (hp.smem > max_dynamic)
+    fail(QTC_ERR_UNSUPPORTED, "graph program needs %zu bytes of shared memory (limit %zu)",
+         hp.smem, max_dynamic);
+}
+
+}  // namespace qtc

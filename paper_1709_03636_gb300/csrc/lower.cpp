@@ -2,6 +2,7 @@
 // (Eq. 1 with bit maps), the network scalar, and the adjoint sweep.
 #include <algorithm>
 #include <cstring>
+#include <string>
 
 #include "qtc_internal.h"
 
@@ -58,14 +59,78 @@ bool encode_contract(SOp& op, const std::vector<int>& lo, const std::vector<int>
 }
 
 struct Ref {
-  int buf = -1;        // arena buffer id, or -1 for an absolute table offset
+  int buf = -1;        // arena buffer id; else an absolute offset (table or global)
   uint32_t abs = 0;
+  bool global = false; // abs is an element offset into the global work buffer
 };
 
 struct Pending {
   SOp op;
   Ref out, in1, in2;
 };
+
+// Places the arena buffers referenced by `ops` (first-fit decreasing over op
+// index live ranges; a buffer written by op i and one read last by op i never
+// share memory) and writes the resolved ops.  Returns the arena size.
+uint32_t place_arena(const std::vector<Pending>& ops, const std::vector<uint32_t>& buf_size,
+                     uint32_t table_elems, std::vector<SOp>& out) {
+  const int B = (int)buf_size.size();
+  std::vector<int> first(B, -1), last(B, -1);
+  for (int i = 0; i < (int)ops.size(); ++i) {
+    for (const Ref* r : {&ops[i].out, &ops[i].in1, &ops[i].in2}) {
+      if (r->buf < 0) continue;
+      if (first[r->buf] < 0) first[r->buf] = i;
+      last[r->buf] = i;
+    }
+  }
+  std::vector<int> order;
+  for (int b = 0; b < B; ++b)
+    if (first[b] >= 0) order.push_back(b);
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    if (buf_size[a] != buf_size[b]) return buf_size[a] > buf_size[b];
+    return a < b;
+  });
+  std::vector<uint32_t> offset(B, 0);
+  std::vector<int> placed;
+  uint32_t arena = 0;
+  auto rounded = [&](int b) { return (buf_size[b] + 1u) & ~1u; };
+  for (int b : order) {
+    const uint32_t size = rounded(b);
+    std::vector<std::pair<uint32_t, uint32_t>> busy;
+    for (int q : placed)
+      if (!(last[q] < first[b] || last[b] < first[q]))
+        busy.push_back({offset[q], offset[q] + rounded(q)});
+    std::sort(busy.begin(), busy.end());
+    uint32_t at = 0;
+    for (auto& iv : busy) {
+      if (at + size <= iv.first) break;
+      at = std::max(at, iv.second);
+    }
+    offset[b] = at;
+    placed.push_back(b);
+    arena = std::max(arena, at + size);
+  }
+  auto resolve = [&](const Ref& r) { return r.buf < 0 ? r.abs : table_elems + offset[r.buf]; };
+  for (const auto& p : ops) {
+    SOp op = p.op;
+    op.out = resolve(p.out);
+    op.in1 = resolve(p.in1);
+    op.in2 = resolve(p.in2);
+    op.flags = (p.out.global ? SOPF_OUT_GLOBAL : 0) | (p.in1.global ? SOPF_IN1_GLOBAL : 0) |
+               (p.in2.global ? SOPF_IN2_GLOBAL : 0);
+    out.push_back(op);
+  }
+  return arena;
+}
+
+std::vector<char> needs_grad(const Plan& plan) {
+  const int L = (int)plan.net.leaves.size();
+  const int S = (int)plan.steps.size();
+  std::vector<char> need(L + S, 0);
+  for (int i = 0; i < L; ++i) need[i] = plan.net.leaves[i].spec.slot >= 0;
+  for (int s = 0; s < S; ++s) need[L + s] = need[plan.steps[s].a] || need[plan.steps[s].b];
+  return need;
+}
 
 }  // namespace
 
@@ -78,10 +143,9 @@ LoweredNet lower_smem(const Plan& plan, const std::vector<int>& leaf_gate,
   const int S = (int)plan.steps.size();
   const int T = L + S;
   const int root = T - 1;
-  std::vector<char> need_grad(T, 0);
-  for (int i = 0; i < L; ++i) need_grad[i] = plan.net.leaves[i].spec.slot >= 0;
-  for (int s = 0; s < S; ++s)
-    need_grad[L + s] = need_grad[plan.steps[s].a] || need_grad[plan.steps[s].b];
+  for (int t = 0; t < T; ++t)
+    if ((int)plan.labels[t].size() > kMaxSmemRank) return out;
+  const std::vector<char> need_grad = needs_grad(plan);
 
   // buffers: value of every intermediate, adjoint of every tensor that needs one
   std::vector<int> val_buf(T, -1), grad_buf(T, -1);
@@ -161,55 +225,413 @@ LoweredNet lower_smem(const Plan& plan, const std::vector<int>& leaf_gate,
       }
     }
   }
-
-  // live intervals of the arena buffers over the op sequence
-  const int B = (int)buf_size.size();
-  std::vector<int> first(B, -1), last(B, -1);
-  for (int i = 0; i < (int)ops.size(); ++i) {
-    for (const Ref* r : {&ops[i].out, &ops[i].in1, &ops[i].in2}) {
-      if (r->buf < 0) continue;
-      if (first[r->buf] < 0) first[r->buf] = i;
-      last[r->buf] = i;
-    }
-  }
-  // first-fit decreasing placement (sizes rounded to 2 elements)
-  std::vector<int> order;
-  for (int b = 0; b < B; ++b)
-    if (first[b] >= 0) order.push_back(b);
-  std::sort(order.begin(), order.end(), [&](int a, int b) {
-    if (buf_size[a] != buf_size[b]) return buf_size[a] > buf_size[b];
-    return a < b;
-  });
-  std::vector<uint32_t> offset(B, 0);
-  std::vector<int> placed;
-  uint32_t arena = 0;
-  for (int b : order) {
-    uint32_t size = (buf_size[b] + 1u) & ~1u;
-    std::vector<std::pair<uint32_t, uint32_t>> busy;
-    for (int q : placed)
-      if (!(last[q] < first[b] || last[b] < first[q]))
-        busy.push_back({offset[q], offset[q] + ((buf_size[q] + 1u) & ~1u)});
-    std::sort(busy.begin(), busy.end());
-    uint32_t at = 0;
-    for (auto& iv : busy) {
-      if (at + size <= iv.first) break;
-      at = std::max(at, iv.second);
-    }
-    offset[b] = at;
-    placed.push_back(b);
-    arena = std::max(arena, at + size);
-  }
-  out.arena_elems = arena;
-  out.fits = table_elems + arena <= max_elems;
-  auto resolve = [&](const Ref& r) { return r.buf < 0 ? r.abs : table_elems + offset[r.buf]; };
-  for (auto& p : ops) {
-    SOp op = p.op;
-    op.out = resolve(p.out);
-    op.in1 = resolve(p.in1);
-    op.in2 = resolve(p.in2);
-    out.ops.push_back(op);
-  }
+  out.arena_elems = place_arena(ops, buf_size, table_elems, out.ops);
+  out.fits = table_elems + out.arena_elems <= max_elems;
   return out;
+}
+
+// ---- graph lowering -----------------------------------------------------------
+
+namespace {
+
+// Bit maps of a global step as runs: bit i of `idx` goes to position pos[i]
+// of the operand (-1: the operand does not carry it).
+bool make_runs(const std::vector<int>& pos, GRuns& r) {
+  std::memset(&r, 0, sizeof r);
+  int i = 0;
+  const int n = (int)pos.size();
+  while (i < n) {
+    if (pos[i] < 0) {
+      ++i;
+      continue;
+    }
+    int j = i + 1;
+    while (j < n && pos[j] == pos[j - 1] + 1) ++j;
+    if (r.n == kMaxRuns) return false;
+    r.src[r.n] = (uint8_t)i;
+    r.len[r.n] = (uint8_t)(j - i);
+    r.dst[r.n] = (uint8_t)pos[i];
+    r.n++;
+    i = j;
+  }
+  return true;
+}
+
+uint32_t log2_floor(uint64_t x) {
+  uint32_t r = 0;
+  while (x > 1) {
+    x >>= 1;
+    ++r;
+  }
+  return r;
+}
+
+}  // namespace
+
+// Fills the bit maps and chunking of C = sum over (A u B) - C of A * B.
+// force_split: always reduce over chunks of the summed index (leaf adjoints).
+bool encode_gstep(GStep& g, const std::vector<int>& lc, const std::vector<int>& la,
+                  const std::vector<int>& lb, bool force_split, std::string* why) {
+  std::vector<int> pa, pb, ya, yb;
+  for (int x : lc) {
+    pa.push_back(pos_in(la, x));
+    pb.push_back(pos_in(lb, x));
+  }
+  std::vector<int> summed;
+  for (int x : la)
+    if (pos_in(lc, x) < 0) summed.push_back(x);
+  for (int x : lb)
+    if (pos_in(lc, x) < 0 && pos_in(la, x) < 0) summed.push_back(x);
+  for (int x : summed) {
+    ya.push_back(pos_in(la, x));
+    yb.push_back(pos_in(lb, x));
+  }
+  if (lc.size() > 31 || summed.size() > 31) {
+    *why = "a step's output or summed index exceeds 31 bits";
+    return false;
+  }
+  g.rc = (uint8_t)lc.size();
+  g.ry = (uint8_t)summed.size();
+  if (!make_runs(pa, g.ca) || !make_runs(pb, g.cb) || !make_runs(ya, g.ya) ||
+      !make_runs(yb, g.yb)) {
+    *why = "a step's bit maps need more than 12 runs";
+    return false;
+  }
+  const uint64_t nout = 1ull << g.rc, ny = 1ull << g.ry;
+  if (nout <= kGRow && (force_split || nout * ny >= (1ull << 14))) {
+    // small output, long sums: split the summed index over chunks
+    uint64_t per = std::max<uint64_t>(256, (1ull << 16) / nout);
+    per = std::min<uint64_t>(per, kYTab);
+    per = std::min<uint64_t>(per, ny);
+    g.flags |= GSF_SPLIT;
+    g.chunk = (uint32_t)per;
+    g.n_chunks = (uint32_t)((ny + per - 1) / per);
+  } else {
+    const uint64_t rowlen = std::min<uint64_t>(nout, kGRow);
+    const uint64_t rows = nout / rowlen;
+    uint64_t per = 1;
+    if (ny <= kYTab) {
+      per = std::max<uint64_t>(1, (1ull << 16) / (rowlen * ny));
+      per = std::min<uint64_t>(per, 64);
+      per = std::min<uint64_t>(per, rows);
+    }
+    g.chunk = (uint32_t)per;
+    g.n_chunks = (uint32_t)((rows + per - 1) / per);
+  }
+  (void)log2_floor;
+  return true;
+}
+
+NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
+                     const std::vector<uint32_t>& gate_val_off,
+                     const std::vector<uint32_t>& gate_der_off, uint32_t table_elems,
+                     bool want_grad, const GraphLimits& lim) {
+  NetGraph ng;
+  const int L = (int)plan.net.leaves.size();
+  const int S = (int)plan.steps.size();
+  const int T = L + S;
+  const int root = T - 1;
+  const std::vector<char> need_grad = needs_grad(plan);
+  auto rank = [&](int t) { return (int)plan.labels[t].size(); };
+  auto size = [&](int t) { return (uint64_t)1 << rank(t); };
+  std::vector<int> consumer(T, -1);
+  for (int s = 0; s < S; ++s) consumer[plan.steps[s].a] = consumer[plan.steps[s].b] = s;
+  std::vector<char> bigstep(S, 0);
+  for (int s = 0; s < S; ++s) {
+    const Step& st = plan.steps[s];
+    bigstep[s] = rank(st.a) > lim.small_rank || rank(st.b) > lim.small_rank ||
+                 rank(L + s) > lim.small_rank;
+  }
+
+  // subtrees of small steps (walked from the root down), capped in size
+  std::vector<int> sub(S, -1), sub_root;
+  std::vector<uint64_t> sub_size;
+  for (int s = S - 1; s >= 0; --s) {
+    if (bigstep[s]) continue;
+    const int c = consumer[L + s];
+    if (c >= 0 && !bigstep[c] && sub_size[sub[c]] + size(L + s) <= lim.subtree_elems) {
+      sub[s] = sub[c];
+      sub_size[sub[c]] += size(L + s);
+    } else {
+      sub[s] = (int)sub_root.size();
+      sub_root.push_back(s);
+      sub_size.push_back(size(L + s));
+    }
+  }
+  const int K = (int)sub_root.size();
+  std::vector<std::vector<int>> sub_steps(K);
+  for (int s = 0; s < S; ++s)
+    if (sub[s] >= 0) sub_steps[sub[s]].push_back(s);
+
+  // tensors in global memory: outputs of large steps and of subtree roots
+  // (except the network root when a subtree produces it)
+  std::vector<char> in_global(T, 0);
+  for (int s = 0; s < S; ++s)
+    if (bigstep[s] || (sub_root[sub[s]] == s && L + s != root)) in_global[L + s] = 1;
+  std::vector<int64_t> val_g(T, -1), grad_g(T, -1);
+  uint64_t gsize = 0;
+  auto galloc = [&](uint64_t elems) {
+    const uint64_t at = gsize;
+    gsize += (elems + 63) & ~uint64_t(63);
+    return (int64_t)at;
+  };
+  for (int t = L; t < T; ++t)
+    if (in_global[t]) val_g[t] = galloc(size(t));
+  if (want_grad)
+    for (int t = L; t < T; ++t)
+      if (in_global[t] && need_grad[t]) grad_g[t] = galloc(size(t));
+
+  std::vector<int> producer_val(T, -1), producer_grad(T, -1);
+  auto add_unit = [&](GUnit&& u) {
+    int depth = 0;
+    std::sort(u.deps.begin(), u.deps.end());
+    u.deps.erase(std::unique(u.deps.begin(), u.deps.end()), u.deps.end());
+    for (int d : u.deps) depth = std::max(depth, ng.units[d].depth + 1);
+    u.depth = depth;
+    ng.units.push_back(std::move(u));
+    return (int)ng.units.size() - 1;
+  };
+  auto fail_net = [&](const std::string& why) {
+    ng.fits = false;
+    ng.why = why;
+    return ng;
+  };
+
+  // ---- forward ----
+  // Shared-memory program of a subtree; `reverse` adds the adjoint sweep
+  // (recomputing the subtree's values first).
+  auto subtree_unit = [&](int k, bool reverse) -> bool {
+    const std::vector<int>& steps = sub_steps[k];
+    const int rs = sub_root[k];
+    std::vector<int> val_buf(T, -1), grad_buf(T, -1);
+    std::vector<uint32_t> buf_size;
+    GUnit u;
+    u.kind = GT_SMEM;
+    auto value_ref = [&](int t) {
+      Ref r;
+      if (t < L) {
+        r.abs = gate_val_off[leaf_gate[t]];
+      } else if (in_global[t] && !(t == L + rs && !reverse)) {
+        r.global = true;
+        r.abs = (uint32_t)val_g[t];
+        if (t != L + rs) u.deps.push_back(producer_val[t]);
+      } else {
+        if (val_buf[t] < 0) {
+          val_buf[t] = (int)buf_size.size();
+          buf_size.push_back((uint32_t)size(t));
+        }
+        r.buf = val_buf[t];
+      }
+      return r;
+    };
+    auto grad_ref = [&](int t) {
+      Ref r;
+      if (t >= L && in_global[t] && t != L + rs) {
+        r.global = true;
+        r.abs = (uint32_t)grad_g[t];
+      } else if (t == L + rs && in_global[t]) {
+        r.global = true;
+        r.abs = (uint32_t)grad_g[t];
+        u.deps.push_back(producer_grad[t]);
+      } else {
+        if (grad_buf[t] < 0) {
+          grad_buf[t] = (int)buf_size.size();
+          buf_size.push_back((uint32_t)size(t));
+        }
+        r.buf = grad_buf[t];
+      }
+      return r;
+    };
+    std::vector<Pending> ops;
+    for (int s : steps) {
+      if (reverse && s == rs) continue;  // the root's own value is not needed
+      const Step& st = plan.steps[s];
+      Pending p{};
+      p.op.code = SOP_CONTRACT;
+      if (!encode_contract(p.op, plan.labels[L + s], plan.labels[st.a], plan.labels[st.b]))
+        return false;
+      p.in1 = value_ref(st.a);
+      p.in2 = value_ref(st.b);
+      if (s == rs && in_global[L + s]) {
+        p.out.global = true;
+        p.out.abs = (uint32_t)val_g[L + s];
+      } else {
+        p.out = value_ref(L + s);
+      }
+      ops.push_back(p);
+    }
+    if (!reverse && L + rs == root) {
+      Pending p{};
+      p.op.code = SOP_RESULT;
+      p.in1 = value_ref(root);
+      ops.push_back(p);
+    }
+    if (reverse) {
+      if (L + rs == root) {
+        Pending seed{};
+        seed.op.code = SOP_SEED;
+        seed.out = grad_ref(root);
+        ops.push_back(seed);
+      }
+      for (auto it = steps.rbegin(); it != steps.rend(); ++it) {
+        const int s = *it;
+        const int c = L + s;
+        const Step& st = plan.steps[s];
+        const int pairs[2][2] = {{st.a, st.b}, {st.b, st.a}};
+        for (const auto& pr : pairs) {
+          const int x = pr[0], y = pr[1];
+          if (!need_grad[x]) continue;
+          Pending p{};
+          p.op.code = SOP_CONTRACT;
+          if (!encode_contract(p.op, plan.labels[x], plan.labels[c], plan.labels[y]))
+            return false;
+          p.in1 = grad_ref(c);
+          p.in2 = value_ref(y);
+          p.out = grad_ref(x);
+          ops.push_back(p);
+          if (x < L) {
+            Pending g{};
+            g.op.code = SOP_LEAFGRAD;
+            g.op.rc = (uint8_t)plan.labels[x].size();
+            g.in1 = grad_ref(x);
+            g.in2.abs = gate_der_off[leaf_gate[x]];
+            g.out.abs = (uint32_t)plan.net.leaves[x].spec.slot;
+            ops.push_back(g);
+          } else if (in_global[x]) {
+            producer_grad[x] = (int)ng.units.size();
+          }
+        }
+      }
+    }
+    u.arena_elems = place_arena(ops, buf_size, table_elems, u.ops);
+    if (u.arena_elems > lim.arena_elems) return false;
+    const int id = add_unit(std::move(u));
+    if (!reverse && in_global[L + rs]) producer_val[L + rs] = id;
+    return true;
+  };
+
+  auto gstep_unit = [&](int lc_t, const std::vector<int>& lc, int a, const std::vector<int>& la,
+                        Ref ra, int b, const std::vector<int>& lb, Ref rb, int64_t c_off,
+                        std::vector<int> deps, int leaf_for_grad) -> int {
+    GUnit u;
+    u.kind = GT_CHUNK;
+    std::memset(&u.step, 0, sizeof u.step);
+    std::string why;
+    if (!encode_gstep(u.step, lc, la, lb, leaf_for_grad >= 0, &why)) {
+      ng.fits = false;
+      ng.why = why;
+      return -1;
+    }
+    (void)lc_t;
+    (void)a;
+    (void)b;
+    u.step.c_off = (uint32_t)std::max<int64_t>(c_off, 0);
+    if (ra.global) u.step.a_off = ra.abs;
+    else { u.step.a_off = ra.abs; u.step.flags |= GSF_A_TABLE; }
+    if (rb.global) u.step.b_off = rb.abs;
+    else { u.step.b_off = rb.abs; u.step.flags |= GSF_B_TABLE; }
+    if (leaf_for_grad >= 0) {
+      if (!(u.step.flags & GSF_SPLIT)) {
+        // the leaf gradient is always a reduction to <= 16 outputs
+        ng.fits = false;
+        ng.why = "internal: a leaf adjoint that is not a split reduction";
+        return -1;
+      }
+      u.step.flags |= GSF_LEAFGRAD;
+      u.step.der_off = gate_der_off[leaf_gate[leaf_for_grad]];
+      u.step.slot = plan.net.leaves[leaf_for_grad].spec.slot;
+    }
+    if (u.step.flags & GSF_SPLIT) {
+      u.step.partial_off = (uint32_t)galloc((uint64_t)u.step.n_chunks << u.step.rc);
+      u.target = 1;
+    } else {
+      u.target = u.step.n_chunks;
+    }
+    u.deps = std::move(deps);
+    return add_unit(std::move(u));
+  };
+
+  auto value_ref_global = [&](int t, std::vector<int>& deps) {
+    Ref r;
+    if (t < L) {
+      r.abs = gate_val_off[leaf_gate[t]];
+    } else {
+      r.global = true;
+      r.abs = (uint32_t)val_g[t];
+      deps.push_back(producer_val[t]);
+    }
+    return r;
+  };
+
+  // forward units in step order: a subtree when its last step is reached
+  std::vector<char> sub_done(K, 0);
+  for (int s = 0; s < S; ++s) {
+    if (bigstep[s]) {
+      const Step& st = plan.steps[s];
+      std::vector<int> deps;
+      Ref ra = value_ref_global(st.a, deps);
+      Ref rb = value_ref_global(st.b, deps);
+      const int id = gstep_unit(L + s, plan.labels[L + s], st.a, plan.labels[st.a], ra, st.b,
+                                plan.labels[st.b], rb, val_g[L + s], deps, -1);
+      if (id < 0) return ng;
+      producer_val[L + s] = id;
+    } else if (sub_root[sub[s]] == s) {
+      if (!subtree_unit(sub[s], false)) return fail_net("a subtree does not fit in shared memory");
+    }
+  }
+  if (in_global[root]) {
+    // the root comes from a large step: read it (and seed the adjoint)
+    GUnit u;
+    u.kind = GT_SMEM;
+    Pending p{};
+    p.op.code = SOP_RESULT;
+    p.in1.global = true;
+    p.in1.abs = (uint32_t)val_g[root];
+    std::vector<Pending> ops{p};
+    if (want_grad && need_grad[root]) {
+      Pending seed{};
+      seed.op.code = SOP_SEED;
+      seed.out.global = true;
+      seed.out.abs = (uint32_t)grad_g[root];
+      ops.push_back(seed);
+    }
+    u.deps.push_back(producer_val[root]);
+    place_arena(ops, {}, table_elems, u.ops);
+    const int id = add_unit(std::move(u));
+    producer_grad[root] = id;
+  }
+
+  // ---- adjoint sweep, in reverse step order ----
+  if (want_grad && need_grad[root]) {
+    for (int s = S - 1; s >= 0; --s) {
+      if (bigstep[s]) {
+        const int c = L + s;
+        const Step& st = plan.steps[s];
+        const int pairs[2][2] = {{st.a, st.b}, {st.b, st.a}};
+        for (const auto& pr : pairs) {
+          const int x = pr[0], y = pr[1];
+          if (!need_grad[x]) continue;
+          std::vector<int> deps{producer_grad[c]};
+          Ref rg;
+          rg.global = true;
+          rg.abs = (uint32_t)grad_g[c];
+          Ref ry = value_ref_global(y, deps);
+          const int id = gstep_unit(x, plan.labels[x], c, plan.labels[c], rg, y, plan.labels[y],
+                                    ry, x < L ? -1 : grad_g[x], deps, x < L ? x : -1);
+          if (id < 0) return ng;
+          if (x >= L) producer_grad[x] = id;
+        }
+      } else if (sub_root[sub[s]] == s && need_grad[L + s]) {
+        if (!subtree_unit(sub[s], true)) return fail_net("a subtree does not fit in shared memory");
+      }
+    }
+  }
+  for (const GUnit& u : ng.units)
+    for (int d : u.deps)
+      if (d < 0) return fail_net("internal: a dependency without a producer");
+  ng.global_elems = gsize;
+  (void)sub_done;
+  return ng;
 }
 
 }  // namespace qtc

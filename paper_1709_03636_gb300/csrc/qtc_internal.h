@@ -150,9 +150,69 @@ LoweredNet lower_smem(const Plan& plan, const std::vector<int>& leaf_gate,
                       const std::vector<uint32_t>& gate_der_off,
                       uint32_t table_elems, bool want_grad, uint32_t max_elems);
 
+// ---- graph lowering (networks larger than one CTA's shared memory) ---------
+
+
+struct GraphLimits {
+  int small_rank = 10;               // tensors of higher rank live in global memory
+  uint64_t subtree_elems = 4096;     // elements of all values of one subtree
+  uint32_t arena_elems = 8192;       // shared-memory arena of one subtree task
+};
+
+// A unit is one shared-memory subtree task or one global step (its chunks);
+// its counter reaches `target` when it is complete.
+struct GUnit {
+  int kind = GT_SMEM;
+  std::vector<SOp> ops;              // GT_SMEM
+  GStep step{};                      // GT_CHUNK
+  uint32_t arena_elems = 0;
+  std::vector<int> deps;             // units that must be complete first
+  int depth = 0;
+  uint32_t target = 1;
+};
+
+struct NetGraph {
+  std::vector<GUnit> units;
+  uint64_t global_elems = 0;         // global buffers of this network (elements)
+  bool fits = true;
+  std::string why;
+};
+
+// Lowers one plan to units: maximal subtrees of small steps run in shared
+// memory (and are recomputed for the adjoint sweep), the other steps are
+// chunked global contractions.  Global offsets are network-local.
+NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
+                     const std::vector<uint32_t>& gate_val_off,
+                     const std::vector<uint32_t>& gate_der_off, uint32_t table_elems,
+                     bool want_grad, const GraphLimits& lim);
+
+// How programs are formed: force_graph runs even small networks through the
+// graph executor; small_rank <= 0 keeps the default threshold (10).
+struct ProgramOptions {
+  size_t wave_cap_bytes = (size_t)8 << 30;
+  bool force_graph = false;
+  int small_rank = 0;
+  bool operator==(const ProgramOptions& o) const {
+    return wave_cap_bytes == o.wave_cap_bytes && force_graph == o.force_graph &&
+           small_rank == o.small_rank;
+  }
+};
+
+// One wave of the graph executor: its tasks, op lists, global steps, waits,
+// work-buffer size and dependency counters.
+struct WaveHost {
+  std::vector<GTask> tasks;
+  std::vector<SOp> ops;
+  std::vector<GStep> steps;
+  std::vector<WaitDev> waits;
+  uint64_t global_elems = 0;
+  uint32_t n_counters = 0;
+};
+
 // Host copy of a batch's device program for one element type and gradient
-// flag: the gate table, one shared-memory task per network (largest first)
-// and the op lists.
+// flag.  Shared-memory form: the gate table, one task per network (largest
+// first) and the op lists.  Graph form (some network does not fit one CTA's
+// shared memory): waves of graph-executor tasks.
 struct HostProgram {
   int dtype = 0, want_grad = 0;
   size_t max_dynamic = 0;          // shared-memory budget it was lowered for
@@ -170,10 +230,25 @@ struct HostProgram {
   int n_nets = 0, n_params = 0;
   int qaoa_reduce = 1;
   uint64_t serial = 0;             // process-unique id of this program
+  ProgramOptions options;          // options it was built with
+  bool graph = false;
+  std::vector<WaveHost> waves;
+  uint32_t work_bytes = 0;         // graph form: shared memory after the table
+  uint64_t max_global_elems = 0;
+  uint32_t max_counters = 0;
 };
 
-// Built once per (batch, dtype, want_grad, budget) and cached in the batch.
-const HostProgram& host_program(qtc_batch* b, int dtype, int want_grad, size_t max_dynamic);
+// Built once per (batch, dtype, want_grad, budget, options) and cached in the
+// batch.
+const HostProgram& host_program(qtc_batch* b, int dtype, int want_grad, size_t max_dynamic,
+                                const ProgramOptions& opts = ProgramOptions());
+
+// Fills hp's graph form (hp.dtype, want_grad and table_elems already set).
+void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
+                         const std::vector<std::vector<int>>& leaf_gate,
+                         const std::vector<uint32_t>& val_off,
+                         const std::vector<uint32_t>& der_off, size_t max_dynamic,
+                         const ProgramOptions& opts);
 
 inline size_t elem_bytes(int dtype) { return dtype == QTC_C128 ? 16 : 8; }
 

@@ -64,6 +64,10 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
     DeviceSetup& setup = setup_device(dev);
     const size_t max_dyn = max_dynamic_smem(setup.smem_optin);
     const HostProgram& hp = host_program(b, dtype, want_grad, max_dyn);
+    if (hp.graph)
+      fail(QTC_ERR_UNSUPPORTED,
+           "this batch has networks larger than one CTA's shared memory; use "
+           "qtc_qaoa_expectation_device with an arena");
     const int P = hp.n_params, N = hp.n_nets, G = (int)hp.gates.size();
 
     // layout of one call inside the array

@@ -1,0 +1,158 @@
+"""Parity of the graph executor (networks larger than one CTA's shared memory).
+
+Small networks are forced through the graph path (every tensor above rank 2
+in global memory) so they can be checked against the oracle exactly; the
+p=3 and full 7-regular workloads run there by necessity and are checked on
+sampled edges or against the state vector.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+import paper_1709_03636_gb300 as q  # noqa: E402
+from paper_1709_03636_gb300 import _lib  # noqa: E402
+from oracle import statevector as sv  # noqa: E402
+from oracle import tensornet as tn  # noqa: E402
+from synth import WORKLOADS, random_regular_graph  # noqa: E402
+
+C_REL, G_REL, EDGE_TOL = 1e-5, 1e-4, 2e-6
+
+
+@pytest.fixture(scope="module")
+def engine():
+    return q.Engine(0, arena_bytes=12 << 30)
+
+
+@pytest.fixture
+def forced(engine):
+    engine.set_graph_options(force_graph=True, small_rank=2)
+    yield engine
+    engine.set_graph_options(False, 0)
+
+
+def _grad_close(got, want, rel=G_REL):
+    got, want = np.asarray(got), np.asarray(want)
+    assert np.max(np.abs(got - want)) <= rel * max(np.max(np.abs(want)), 1e-12), (got, want)
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-11), ("c64", 2e-6)])
+def test_forced_graph_matches_statevector(forced, dtype, tol):
+    n = 12
+    edges = random_regular_graph(n, 3, 6)
+    g, b = [0.35, 1.2], [0.8, 0.25]
+    circ = q.Circuit.qaoa(n, edges, 2)
+    batch = q.Batch(circ, ordering="lg")
+    info = batch.program_info(dtype, True, force_graph=True, small_rank=2)
+    assert info["graph"] == 1 and info["n_global_steps"] > 0
+    C, per_edge, grad = q.qaoa_expectation(forced, batch, g, b, dtype, want_grad=True)
+    ref_C, ref_grad = sv.gradient(n, edges, g, b)
+    assert np.max(np.abs(np.array(per_edge) - sv.edge_zz(n, edges, g, b))) < tol
+    assert abs(C - ref_C) < tol * len(edges)
+    _grad_close(grad, ref_grad, 1e-9 if dtype == "c128" else G_REL)
+
+
+def test_forced_graph_dense_stoch_and_full_networks(forced):
+    n = 10
+    edges = random_regular_graph(n, 3, 2)
+    g, b = [0.6], [0.45]
+    circ = q.Circuit.qaoa(n, edges, 1)
+    ref = sv.edge_zz(n, edges, g, b)
+    for kw in (dict(diag=False, ordering="stoch"), dict(lightcone=False, ordering="lg")):
+        batch = q.Batch(circ, **kw)
+        C, per_edge, grad = q.qaoa_expectation(forced, batch, g, b, "c128", want_grad=True)
+        assert np.max(np.abs(np.array(per_edge) - ref)) < 1e-11
+        _grad_close(grad, sv.gradient(n, edges, g, b)[1], 1e-9)
+
+
+def test_forced_graph_single_network_and_amplitude(forced):
+    n = 8
+    edges = random_regular_graph(n, 3, 4)
+    g, b = [0.9, 0.2], [0.3, 1.2]
+    circ = q.Circuit.qaoa(n, edges, 2)
+    e = edges[3]
+    net = q.Network(circ, "zz", edge=e, lightcone=False)
+    s, ds = q.contract(forced, q.Plan(net, "lg"), g + b, "c128", want_grad=True)
+    s_ref, ds_ref = tn.edge_value_grad(n, edges, g, b, e, lightcone=False)
+    assert abs(s - s_ref) < 1e-11
+    assert np.max(np.abs(np.array(ds) - ds_ref)) < 1e-10
+    bits = [1, 0, 0, 1, 1, 0, 1, 0]
+    amp_net = q.Network(circ, "amplitude", bits=bits, lightcone=False)
+    amp = q.contract(forced, q.Plan(amp_net, "stoch", seed=2), g + b, "c128")
+    assert abs(amp - sv.amplitude(n, edges, g, b, bits)) < 1e-12
+
+
+def test_p3_n60_d4_sampled_edges_value_and_gradient(engine):
+    w = WORKLOADS["qaoa_p3_n60_d4"]
+    edges = w.graph()
+    g, b = w.angles()
+    circ = q.Circuit.qaoa(w.n, edges, w.p)
+    sample = [edges[i] for i in (0, 17, 42, 77, 101, 119)]
+    batch = q.Batch(circ, obs_edges=sample, ordering="lg")
+    assert batch.program_info("c64", True)["graph"] == 1
+    C, per_edge, grad = q.qaoa_expectation(engine, batch, g, b, "c64", want_grad=True)
+    ref_C, ref_grad = 0.0, np.zeros(2 * w.p)
+    for i, e in enumerate(sample):
+        s, ds = tn.edge_value_grad(w.n, edges, g, b, e)
+        assert abs(per_edge[i] - s.real) < EDGE_TOL
+        ref_C += (1 - s.real) / 2
+        ref_grad -= 0.5 * ds.real
+    assert abs(C - ref_C) <= C_REL * abs(ref_C)
+    _grad_close(grad, ref_grad)
+
+
+def test_p3_n60_d4_all_edges_waves_agree(engine):
+    """The whole graph with gradient (two waves under the 8 GiB limit) against
+    a run split into many more waves, and the forward values per edge."""
+    w = WORKLOADS["qaoa_p3_n60_d4"]
+    edges = w.graph()
+    g, b = w.angles()
+    circ = q.Circuit.qaoa(w.n, edges, w.p)
+    batch = q.Batch(circ, ordering="lg")
+    C, per_edge, grad = q.qaoa_expectation(engine, batch, g, b, "c64", want_grad=True)
+    assert engine.last_launches >= 2
+    C1, per_edge1, _ = q.qaoa_expectation(engine, batch, g, b, "c64", want_grad=False)
+    assert abs(C - C1) <= 1e-12 * abs(C) + 1e-9
+    assert np.max(np.abs(np.array(per_edge) - np.array(per_edge1))) < 1e-6
+    engine.set_limits(max_wave_bytes=1 << 30)
+    try:
+        C2, per_edge2, grad2 = q.qaoa_expectation(engine, batch, g, b, "c64", want_grad=True)
+        assert engine.last_launches > 2
+    finally:
+        engine.set_limits()
+    assert abs(C - C2) <= 1e-9 * abs(C)
+    assert np.max(np.abs(np.array(per_edge) - np.array(per_edge2))) < 1e-6
+    _grad_close(grad2, grad, 1e-6)
+    for i in (3, 58, 99):
+        assert abs(per_edge[i] - tn.edge_value(w.n, edges, g, b, edges[i]).real) < EDGE_TOL
+
+
+def test_d7_full_networks_match_statevector(engine):
+    w = WORKLOADS["qaoa_p1_n20_d7"]
+    edges = w.graph()
+    g, b = w.angles()
+    circ = q.Circuit.qaoa(w.n, edges, 1)
+    batch = q.Batch(circ, lightcone=False, ordering="lg")
+    C, per_edge, grad = q.qaoa_expectation(engine, batch, g, b, "c64", want_grad=True)
+    ref_C, ref_grad = sv.gradient(w.n, edges, g, b)
+    assert np.max(np.abs(np.array(per_edge) - sv.edge_zz(w.n, edges, g, b))) < EDGE_TOL
+    assert abs(C - ref_C) <= C_REL * abs(ref_C)
+    _grad_close(grad, ref_grad)
+
+
+def test_bounded_wait_expires_and_reports_timeout():
+    eng = q.Engine(0, arena_bytes=16 << 20)
+    eng.set_limits(wait_limit_ms=20.0)
+    status = _lib.lib.qtc_selftest_wait_timeout(eng.ptr, ctypes.c_void_p(
+        torch.cuda.current_stream().cuda_stream))
+    assert status == 3, _lib.lib.qtc_last_error()
+    # the context is still usable afterwards
+    edges = random_regular_graph(8, 3, 1)
+    batch = q.Batch(q.Circuit.qaoa(8, edges, 1))
+    C, _, _ = q.qaoa_expectation(eng, batch, [0.4], [0.3], "c128")
+    assert abs(C - sv.maxcut_expectation(8, edges, [0.4], [0.3])) < 1e-11

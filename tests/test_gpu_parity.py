@@ -173,7 +173,7 @@ def test_device_api_graph_capture_and_repeat(engine):
     batch = q.Batch(circ, ordering="lg")
     C_host, per_edge, grad = q.qaoa_expectation(engine, batch, g, b, "c64", want_grad=True)
     params = torch.tensor(g + b, dtype=torch.float64, device="cuda")
-    out = torch.zeros(1 + 2 + len(edges), dtype=torch.float64, device="cuda")
+    out = torch.zeros(2 + 2 + len(edges), dtype=torch.float64, device="cuda")
     batch.prepare(engine, "c64", want_grad=True)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):

@@ -50,7 +50,7 @@ def test_static_entry_point_matches_arena_entry_point(name, dtype):
     engine = q.Engine(0, arena_bytes=64 << 20)
     stream = torch.cuda.current_stream()
     params = torch.tensor(g + b, dtype=torch.float64, device="cuda")
-    ref = torch.zeros(1 + 2 * w.p + len(edges), dtype=torch.float64, device="cuda")
+    ref = torch.zeros(2 + 2 * w.p + len(edges), dtype=torch.float64, device="cuda")
     q.qaoa_expectation_device(engine, batch, params, ref, dtype, want_grad=True)
     for _ in range(2):  # two calls in a row share the array
         out = torch.full_like(ref, float("nan"))
@@ -70,7 +70,7 @@ def test_static_entry_point_switches_batches():
         batch = q.Batch(circ, ordering="lg")
         params = torch.tensor([0.3 * (k + 1) for k in range(2 * p)], dtype=torch.float64,
                               device="cuda")
-        ref = torch.zeros(1 + 2 * p + len(edges), dtype=torch.float64, device="cuda")
+        ref = torch.zeros(2 + 2 * p + len(edges), dtype=torch.float64, device="cuda")
         q.qaoa_expectation_device(engine, batch, params, ref, "c64", want_grad=True)
         runs.append((batch, params, ref, p))
     for batch, params, ref, p in runs + runs:
@@ -86,6 +86,6 @@ def test_static_entry_point_rejects_programs_that_do_not_fit():
     circ = q.Circuit.qaoa(w.n, edges, w.p)
     batch = q.Batch(circ, obs_edges=edges * 3, ordering="lg")  # 750 networks
     params = torch.zeros(2 * w.p, dtype=torch.float64, device="cuda")
-    out = torch.zeros(1 + 2 * w.p + 3 * len(edges), dtype=torch.float64, device="cuda")
+    out = torch.zeros(2 + 2 * w.p + 3 * len(edges), dtype=torch.float64, device="cuda")
     with pytest.raises(q.QtcError, match="ARENA.*static scratch"):
         _static_call(batch, params, out, "c64", True, torch.cuda.current_stream())
