@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--dtype", default=None, help="override the workload's element type")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--edges", type=int, default=0,
+                    help="contract only the first K edge networks (small profiling cases)")
     return ap.parse_args()
 
 
@@ -225,10 +227,15 @@ def run_ours(args):
     edges = w.graph()
     g, b = w.angles()
     circ = q.Circuit.qaoa(w.n, edges, w.p)
-    batch = q.Batch(circ, lightcone=w.lightcone, diag=w.diag, ordering=w.ordering)
+    obs = edges[:args.edges] if args.edges else None
+    batch = q.Batch(circ, obs, lightcone=w.lightcone, diag=w.diag, ordering=w.ordering)
     stats = batch.stats()
     n_nets = stats["n_networks"]
-    engine = q.Engine(local, arena_bytes=1 << 30)
+    need = 0
+    for grad in (True, False):
+        info = batch.program_info(dtype, grad)
+        need += info["work_bytes"] + 2 * info["table_bytes"]
+    engine = q.Engine(local, arena_bytes=int(need) + (256 << 20))
     batch.prepare(engine, dtype, want_grad=want_grad)
     batch.prepare(engine, dtype, want_grad=False)
     P = 2 * w.p
@@ -269,6 +276,7 @@ def run_ours(args):
     wall = time.perf_counter() - wall0
     clocks.mark(wall0, wall0 + wall)
     launches = args.steps * engine.last_launches
+    prog = batch.program_info(dtype, True)
     barrier()
     fwd_ms = timed(lambda: device_step(False), args.steps)
     barrier()
@@ -321,8 +329,10 @@ def run_ours(args):
         "data": "synthetic", "config": workload_config(w, n_nets, want_grad, dtype),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "smem_exec_kernel", "peak_kind": f"{peak_kind} hbm_gbs",
-                     "algorithmic_bytes_per_launch": alg_bytes},
+                     "kernel": "graph_exec_kernel" if prog["graph"] else "smem_exec_kernel",
+                     "launches_per_step": engine.last_launches,
+                     "peak_kind": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_step": alg_bytes},
         "e2e": {"value": world * n_nets / e2e_s, "unit": "networks/s",
                 "h2d_bytes_per_step": 8 * P, "d2h_bytes_per_step": 8 * (2 + P + n_nets)},
         "gpu_launches": launches,

@@ -278,6 +278,23 @@ qtc_status qtc_engine_set_graph_options(qtc_engine* e, int force_graph, int smal
  * (anything else is a failure).  Used by the failure-detection tests. */
 qtc_status qtc_selftest_wait_timeout(qtc_engine* e, void* stream);
 
+/* ---- full-Hilbert-space reference (Section 5's comparison method) ---------
+ * <C> of a QAOA circuit (qtc_circuit_qaoa) from the 2^n state vector on the
+ * GPU: |+>^n, per layer the diagonal phase and the RX mixer, moved through
+ * shared memory in tiles of up to 12 qubits per pass.  n <= 32, m <= 512; the
+ * state lives in the engine's work buffer (2^n * 8 or 16 bytes).  per_edge
+ * != 0 also computes <Z_a Z_b> per edge (extra passes).  dtype C128 or C64.
+ * Host form: gammas, betas (p each) in, C_out (1) and per_edge_out
+ * (nullable, m) out, synchronous.  Device form: params_dev (2p doubles),
+ * out_dev (1 + m doubles: <C>, then <Z_a Z_b> per edge when per_edge),
+ * asynchronous on `stream`. */
+qtc_status qtc_statevector_qaoa(qtc_engine* e, const qtc_circuit* c, const double* gammas,
+                                const double* betas, int dtype, int per_edge, void* stream,
+                                double* C_out, double* per_edge_out);
+qtc_status qtc_statevector_qaoa_device(qtc_engine* e, const qtc_circuit* c,
+                                       const double* params_dev, int dtype, int per_edge,
+                                       void* stream, double* out_dev);
+
 /* ---- evaluation without device allocation --------------------------------
  * The paper has no counterpart to this call; it exists for callers that
  * cannot allocate device memory at all (code running inside another

@@ -16,6 +16,7 @@ from ._lib import (QtcError, check, lib, qtc_batch_info, qtc_observable, qtc_pla
 __all__ = [
     "QtcError", "Engine", "Circuit", "Network", "Plan", "Batch", "DTYPES", "ORDERINGS",
     "contract", "qaoa_expectation", "qaoa_expectation_device", "QAOAExpectation",
+    "statevector_expectation", "statevector_expectation_device",
     "GATES",
 ]
 
@@ -279,6 +280,27 @@ def qaoa_expectation_device(engine: Engine, batch: Batch, params_dev, out_dev, d
     check(lib.qtc_qaoa_expectation_device(
         engine.ptr, batch.ptr, ctypes.c_void_p(params_dev.data_ptr()), _dtype(dtype),
         int(want_grad), _stream(stream), ctypes.c_void_p(out_dev.data_ptr())))
+    return out_dev
+
+
+def statevector_expectation(engine: Engine, circuit: Circuit, gammas, betas, dtype="c64",
+                            per_edge=False, stream=None):
+    """<C> (and per-edge <Z_a Z_b>) from the full 2^n state vector on the GPU."""
+    C = ctypes.c_double()
+    pe = (ctypes.c_double * len(circuit.edges))() if per_edge else None
+    check(lib.qtc_statevector_qaoa(engine.ptr, circuit.ptr, _f64(gammas), _f64(betas),
+                                   _dtype(dtype), int(per_edge), _stream(stream),
+                                   ctypes.byref(C), pe))
+    return C.value, (list(pe) if per_edge else None)
+
+
+def statevector_expectation_device(engine: Engine, circuit: Circuit, params_dev, out_dev,
+                                   dtype="c64", per_edge=False, stream=None):
+    """Asynchronous form: out_dev (1 + m float64) = [<C>, <Z_a Z_b> per edge]."""
+    check(lib.qtc_statevector_qaoa_device(engine.ptr, circuit.ptr,
+                                          ctypes.c_void_p(params_dev.data_ptr()), _dtype(dtype),
+                                          int(per_edge), _stream(stream),
+                                          ctypes.c_void_p(out_dev.data_ptr())))
     return out_dev
 
 

@@ -12,6 +12,7 @@
 
 #include "exec_launch.h"
 #include "qtc_internal.h"
+#include "sv_launch.h"
 
 namespace qtc {
 
@@ -86,8 +87,19 @@ struct qtc_engine {
   char* work_base() const { return arena + bytes - work; }
 };
 
+// Device tables of the state-vector reference for one circuit and engine.
+struct SvPrepared {
+  const void* engine = nullptr;
+  uint64_t generation = 0;
+  uint32_t* adj = nullptr;
+  int2* edges = nullptr;
+  double* params = nullptr;
+  double* acc = nullptr;
+};
+
 struct qtc_circuit {
   Circuit c;
+  std::vector<SvPrepared> sv;
 };
 struct qtc_network {
   Network net;
@@ -898,5 +910,90 @@ extern "C" qtc_status qtc_contract(qtc_engine* e, const qtc_plan* p, const doubl
     out_re_im[1] = res[1];
     if (grad_re_im)
       for (int k = 0; k < 2 * P; ++k) grad_re_im[k] = res[2 + k];
+  });
+}
+
+// ---- state-vector reference (full Hilbert space) ----------------------------------
+
+static SvPrepared& sv_prepare(qtc_engine* e, qtc_circuit* c, cudaStream_t s) {
+  for (SvPrepared& p : c->sv)
+    if (p.engine == e && p.generation == e->generation) return p;
+  const Circuit& cc = c->c;
+  if (cc.p <= 0) fail(QTC_ERR_INVALID, "the state-vector reference needs a QAOA circuit");
+  if (cc.n > 32) fail(QTC_ERR_UNSUPPORTED, "state vector of %d qubits (at most 32)", cc.n);
+  if (cc.edges.size() > 512) fail(QTC_ERR_UNSUPPORTED, "more than 512 edges");
+  std::vector<uint32_t> adj(cc.n, 0);
+  std::vector<int2> edges;
+  for (auto& ed : cc.edges) {
+    adj[ed.first] |= 1u << ed.second;
+    adj[ed.second] |= 1u << ed.first;
+    edges.push_back(make_int2(ed.first, ed.second));
+  }
+  SvPrepared p;
+  p.engine = e;
+  p.generation = e->generation;
+  p.adj = upload(e, adj, s, "upload adjacency");
+  p.edges = upload(e, edges, s, "upload edges");
+  p.params = (double*)e->alloc(sizeof(double) * 2 * cc.p);
+  p.acc = (double*)e->alloc(sizeof(double) * (1 + cc.edges.size()));
+  cuda_check(cudaStreamSynchronize(s), "prepare sync");
+  c->sv.push_back(p);
+  return c->sv.back();
+}
+
+static void sv_run(qtc_engine* e, qtc_circuit* c, const SvPrepared& p, const double* params_dev,
+                   int dtype, int per_edge, cudaStream_t s, double* acc) {
+  if (dtype != QTC_C128 && dtype != QTC_C64)
+    fail(QTC_ERR_INVALID, "the state vector runs in complex128 or complex64");
+  const Circuit& cc = c->c;
+  const size_t elem = elem_bytes(dtype);
+  e->reserve_work(elem << cc.n);
+  int launches = 0;
+  cuda_check(sv_qaoa_launch(dtype == QTC_C128 ? 0 : 1, e->work_base(), cc.n,
+                            (int)cc.edges.size(), p.adj, p.edges, params_dev, cc.p, acc, per_edge,
+                            s, &launches),
+             "launch state vector");
+  e->last_launches = launches;
+}
+
+extern "C" qtc_status qtc_statevector_qaoa(qtc_engine* e, const qtc_circuit* c,
+                                           const double* gammas, const double* betas, int dtype,
+                                           int per_edge, void* stream, double* C_out,
+                                           double* per_edge_out) {
+  return guarded([&] {
+    if (!e || !c || !gammas || !betas || !C_out) fail(QTC_ERR_INVALID, "null argument");
+    if (per_edge_out && !per_edge) fail(QTC_ERR_INVALID, "per_edge_out needs per_edge");
+    DeviceScope scope(e->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    auto* mc = const_cast<qtc_circuit*>(c);
+    const SvPrepared& p = sv_prepare(e, mc, s);
+    const int P = mc->c.p, m = (int)mc->c.edges.size();
+    std::vector<double> params(2 * P), out(1 + m);
+    for (int k = 0; k < P; ++k) {
+      params[k] = gammas[k];
+      params[P + k] = betas[k];
+    }
+    cuda_check(cudaMemcpyAsync(p.params, params.data(), sizeof(double) * 2 * P,
+                               cudaMemcpyHostToDevice, s), "upload parameters");
+    sv_run(e, mc, p, p.params, dtype, per_edge, s, p.acc);
+    cuda_check(cudaMemcpyAsync(out.data(), p.acc, sizeof(double) * out.size(),
+                               cudaMemcpyDeviceToHost, s), "download results");
+    cuda_check(cudaStreamSynchronize(s), "synchronise stream");
+    *C_out = out[0];
+    if (per_edge_out)
+      for (int i = 0; i < m; ++i) per_edge_out[i] = out[1 + i];
+  });
+}
+
+extern "C" qtc_status qtc_statevector_qaoa_device(qtc_engine* e, const qtc_circuit* c,
+                                                  const double* params_dev, int dtype,
+                                                  int per_edge, void* stream, double* out_dev) {
+  return guarded([&] {
+    if (!e || !c || !params_dev || !out_dev) fail(QTC_ERR_INVALID, "null argument");
+    DeviceScope scope(e->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    auto* mc = const_cast<qtc_circuit*>(c);
+    const SvPrepared& p = sv_prepare(e, mc, s);
+    sv_run(e, mc, p, params_dev, dtype, per_edge, s, out_dev);
   });
 }
