@@ -121,6 +121,7 @@ typedef struct qtc_program_info {
   int smem_bytes;         /* dynamic shared memory per CTA                   */
   double work_bytes;      /* global work buffer (largest wave)               */
   double table_bytes;     /* device program tables, all waves                */
+  int n_gemm_steps;       /* of which split-BF16 tensor-core GEMMs            */
 } qtc_program_info;
 
 typedef struct qtc_engine qtc_engine;

@@ -645,6 +645,7 @@ static Prepared& prepare_graph(qtc_engine* e, qtc_batch* b, const HostProgram& h
     d.n_tasks = (int)w.tasks.size();
     d.ops = upload(e, w.ops, stream, "upload ops");
     d.steps = upload(e, w.steps, stream, "upload steps");
+    d.tsteps = upload(e, w.tsteps, stream, "upload GEMM steps");
     d.waits = upload(e, w.waits, stream, "upload waits");
     d.n_counters = (int)w.n_counters;
     waves.push_back(d);
@@ -657,6 +658,15 @@ static Prepared& prepare_graph(qtc_engine* e, qtc_batch* b, const HostProgram& h
   cuda_check(graph_exec_configure(hp.dtype == QTC_C128 ? 0 : 1, hp.smem, max_dyn, &per_sm),
              "configure graph executor");
   if (per_sm < 1) fail(QTC_ERR_UNSUPPORTED, "graph executor does not fit on an SM");
+  // tensor memory: 512 columns per SM shared by the resident CTAs; a GEMM
+  // tile needs 128 fp32 columns (N = 128 reals)
+  int tmem_cols = 0;
+  if (hp.tensor_cores) {
+    if (per_sm > 4)
+      fail(QTC_ERR_UNSUPPORTED, "%d resident CTAs per SM leave too little tensor memory",
+           per_sm);
+    tmem_cols = 128;
+  }
   size_t max_tasks = 1;
   for (const WaveHost& w : hp.waves) max_tasks = std::max(max_tasks, w.tasks.size());
   pr.grid = (int)std::max<size_t>(1, std::min<size_t>(max_tasks, (size_t)e->sm_count * per_sm));
@@ -682,6 +692,7 @@ static Prepared& prepare_graph(qtc_engine* e, qtc_batch* b, const HostProgram& h
     d.want_grad = hp.want_grad;
     d.qaoa_reduce = hp.qaoa_reduce;
     d.wait_limit_ns = (long long)(e->wait_limit_ms * 1e6);
+    d.tmem_cols = tmem_cols;
   }
   pr.waves = waves;
   pr.raw = draw;
@@ -802,10 +813,12 @@ extern "C" qtc_status qtc_batch_program_info(qtc_batch* b, int dtype, int want_g
       info->n_waves = (int)hp.waves.size();
       for (const WaveHost& w : hp.waves) {
         info->n_tasks += (int)w.tasks.size();
-        info->n_global_steps += (int)w.steps.size();
+        info->n_global_steps += (int)(w.steps.size() + w.tsteps.size());
+        info->n_gemm_steps += (int)w.tsteps.size();
         for (const GTask& t : w.tasks) info->n_smem_tasks += t.kind == GT_SMEM;
         tables += sizeof(GTask) * w.tasks.size() + sizeof(SOp) * w.ops.size() +
-                  sizeof(GStep) * w.steps.size() + sizeof(WaitDev) * w.waits.size();
+                  sizeof(GStep) * w.steps.size() + sizeof(TStep) * w.tsteps.size() +
+                  sizeof(WaitDev) * w.waits.size();
       }
       info->work_bytes = (double)hp.max_global_elems * elem_bytes(dtype);
     } else {

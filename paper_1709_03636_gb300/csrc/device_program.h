@@ -161,13 +161,34 @@ struct alignas(16) GStep {
   GRuns ya, yb;             // summed bits -> A bits, B bits
 };
 
-enum GTaskKind : uint8_t { GT_SMEM = 0, GT_CHUNK = 1 };
+// One complex GEMM C[b][m][n] = sum_k A[b][m][k] B[b][k][n] (Eq. 1 with the
+// batch labels b, free labels m of A and n of B, summed labels k) on the
+// tensor cores.  Each FP32 operand component is split into BF16 hi + lo and
+// the products hi*hi + hi*lo + lo*hi accumulate in FP32 in tensor memory.
+// Every tensor offset is a bit gather from the logical (b, m, k, n) indices.
+// A task computes one tile of 128 rows m by 64 complex columns n.
+constexpr uint32_t kTcRows = 128;      // m per tile (the MMA's M)
+constexpr uint32_t kTcCols = 64;       // complex n per tile (MMA N = 128 reals)
+constexpr uint32_t kTcK = 16;          // complex k per shared-memory stage
+
+struct alignas(16) TStep {
+  uint32_t c_off, a_off, b_off;
+  uint32_t done_ctr;
+  uint32_t net;
+  uint32_t m_tiles, n_tiles;
+  uint8_t mb, kb, nb, bb;   // log2 of M, K, N and of the batch
+  GRuns am, ak, ab;         // A offset from m, k, b
+  GRuns bk, bn, bbt;        // B offset from k, n, b
+  GRuns cm, cn, cb;         // C offset from m, n, b
+};
+
+enum GTaskKind : uint8_t { GT_SMEM = 0, GT_CHUNK = 1, GT_TC = 2 };
 
 struct GTask {
   uint8_t kind;
   uint8_t pad[3];
-  uint32_t a;              // SMEM: first op; CHUNK: step index
-  uint32_t b;              // SMEM: op count; CHUNK: chunk index
+  uint32_t a;              // SMEM: first op; CHUNK, TC: step index
+  uint32_t b;              // SMEM: op count; CHUNK: chunk index; TC: tile index
   uint32_t net;
   uint32_t wait_begin;     // into the wait list
   uint32_t wait_count;
@@ -197,8 +218,10 @@ struct GraphProgDev {
   int n_tasks;
   const SOp* ops;
   const GStep* steps;
+  const TStep* tsteps;         // tensor-core GEMMs
   const WaitDev* waits;
   void* gbase;                 // global work buffer of the wave
+  int tmem_cols;               // tensor memory columns per CTA (0: no GEMM tasks)
   int n_params;
   int n_nets;
   int n_counters;              // dependency counters of this wave

@@ -15,6 +15,8 @@
 // of the final wave reduces the per-network rows to the Max-Cut objective
 // <C> = sum_e (1 - <Z_u Z_v>_e)/2 (Section 4.1) and its gradient in FP64,
 // records the status, and re-arms the counters.
+#include <cuda_bf16.h>
+
 #include "exec_common.cuh"
 #include "exec_launch.h"
 #include "qtc.h"
@@ -283,17 +285,240 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
   signal_done(prog, st.done_ctr);
 }
 
+// ---- tensor-core GEMM tasks (split BF16, tcgen05, accumulator in TMEM) ----
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: K-major, no swizzle.  lbo = byte stride
+// between core matrices (8 rows x 16 bytes) along K, sbo = along M/N.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of this architecture
+  return d;
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
+// K-major, M = 128, N = 128.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) |
+                              ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait for the tensor cores' arrival on `mbar` with `parity`.
+__device__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, long long limit_ns) {
+  const unsigned long long t0 = now_ns();
+  while (!mbar_try_wait(mbar, parity))
+    if ((long long)(now_ns() - t0) > limit_ns) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Byte offset of element (row r, real k index kk) in a K-major tile of 32 BF16
+// per row made of 8x8 core matrices (rows 16 bytes apart, core matrices 128
+// bytes apart along K, 512 bytes apart along the rows).
+__device__ __forceinline__ uint32_t core_offset(uint32_t r, uint32_t kk) {
+  return ((((r >> 3) << 2) + (kk >> 3)) << 7) + ((r & 7u) << 4) + ((kk & 7u) << 1);
+}
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// One tile (128 rows m x 64 complex columns n, one batch index) of a complex
+// GEMM.  The complex product becomes a real GEMM with K' = 2K and N' = 2N:
+// A' row m = (Re A[m][k], Im A[m][k]) interleaved over k, and B'^T row 2n =
+// (Re B[k][n], -Im B[k][n]), row 2n + 1 = (Im B[k][n], Re B[k][n]), so that the
+// accumulator columns 2n and 2n + 1 are Re C[m][n] and Im C[m][n].
+template <typename T>
+__device__ bool run_tc(const GraphProgDev& prog, const GTask& task, unsigned char* work,
+                       TStep& s_ts, uint32_t tmem, uint32_t mbar, uint32_t& phase) {
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(prog.tsteps + task.a);
+    for (uint32_t w = threadIdx.x; w < sizeof(TStep) / sizeof(uint4); w += blockDim.x)
+      reinterpret_cast<uint4*>(&s_ts)[w] = src[w];
+  }
+  __syncthreads();
+  const TStep& ts = s_ts;
+  T* gb = reinterpret_cast<T*>(prog.gbase);
+  const T* A = gb + ts.a_off;
+  const T* B = gb + ts.b_off;
+  T* C = gb + ts.c_off;
+  const uint32_t per_b = ts.m_tiles * ts.n_tiles;
+  const uint32_t bi = task.b / per_b, rem = task.b % per_b;
+  const uint32_t mt = rem / ts.n_tiles, nt = rem % ts.n_tiles;
+  const uint32_t M = 1u << ts.mb, K = 1u << ts.kb;
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(work) + 127) & ~uintptr_t(127));
+  unsigned char* a_hi = base;
+  unsigned char* a_lo = base + 8192;
+  unsigned char* b_hi = base + 16384;
+  unsigned char* b_lo = base + 24576;
+  const uint32_t tid = threadIdx.x;
+  // loaders: A by (row, 8 consecutive k), B by (column, 4 consecutive k)
+  const uint32_t a_r = tid & 127u, a_k0 = (tid >> 7) * 8;
+  const uint32_t m_g = mt * kTcRows + a_r;
+  const bool m_ok = m_g < M;
+  const uint32_t a_row = m_ok ? (runs_offset(ts.am, m_g) | runs_offset(ts.ab, bi)) : 0;
+  const uint32_t b_c = tid & 63u, b_k0 = (tid >> 6) * 4;
+  const uint32_t n_g = nt * kTcCols + b_c;
+  const uint32_t b_col = runs_offset(ts.bn, n_g) | runs_offset(ts.bbt, bi);
+  const uint32_t nk = (K + kTcK - 1) / kTcK;
+  for (uint32_t kc = 0; kc < nk; ++kc) {
+    for (uint32_t j = 0; j < 8; ++j) {
+      const uint32_t kl = a_k0 + j, k = kc * kTcK + kl;
+      double2 v = make_double2(0.0, 0.0);
+      if (m_ok && k < K) v = to_d2(A[a_row | runs_offset(ts.ak, k)]);
+      __nv_bfloat16 rh, rl, ih, il;
+      split_bf16((float)v.x, rh, rl);
+      split_bf16((float)v.y, ih, il);
+      const uint32_t off = core_offset(a_r, 2 * kl);
+      *reinterpret_cast<uint32_t*>(a_hi + off) = pack_bf16(rh, ih);
+      *reinterpret_cast<uint32_t*>(a_lo + off) = pack_bf16(rl, il);
+    }
+    for (uint32_t j = 0; j < 4; ++j) {
+      const uint32_t kl = b_k0 + j, k = kc * kTcK + kl;
+      double2 v = make_double2(0.0, 0.0);
+      if (k < K) v = to_d2(B[b_col | runs_offset(ts.bk, k)]);
+      __nv_bfloat16 rh, rl, ih, il;
+      split_bf16((float)v.x, rh, rl);
+      split_bf16((float)v.y, ih, il);
+      const uint32_t o0 = core_offset(2 * b_c, 2 * kl), o1 = core_offset(2 * b_c + 1, 2 * kl);
+      *reinterpret_cast<uint32_t*>(b_hi + o0) = pack_bf16(rh, __hneg(ih));
+      *reinterpret_cast<uint32_t*>(b_lo + o0) = pack_bf16(rl, __hneg(il));
+      *reinterpret_cast<uint32_t*>(b_hi + o1) = pack_bf16(ih, rh);
+      *reinterpret_cast<uint32_t*>(b_lo + o1) = pack_bf16(il, rl);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ah = smem_addr(a_hi), al = smem_addr(a_lo);
+      const uint32_t bh = smem_addr(b_hi), bl = smem_addr(b_lo);
+      for (uint32_t ks = 0; ks < 2; ++ks) {
+        const uint32_t off = ks * 256;  // 16 reals = two core matrices along K
+        const uint32_t acc = (kc | ks) != 0;
+        tc_mma(tmem, smem_desc(ah + off, 128, 512), smem_desc(bh + off, 128, 512), acc);
+        tc_mma(tmem, smem_desc(ah + off, 128, 512), smem_desc(bl + off, 128, 512), 1);
+        tc_mma(tmem, smem_desc(al + off, 128, 512), smem_desc(bh + off, 128, 512), 1);
+      }
+      tc_commit(mbar);
+    }
+    const bool ok = mbar_wait_bounded(mbar, phase, prog.wait_limit_ns);
+    phase ^= 1u;
+    if (!ok) {
+      atomicCAS(prog.counters + CTR_ERROR, 0u, (unsigned)QTC_ERR_TIMEOUT);
+      return false;
+    }
+  }
+  tc_fence_after();
+  const uint32_t warp = tid >> 5, lane = tid & 31u;
+  const uint32_t sub = warp & 3u, half = warp >> 2;
+  const uint32_t row = sub * 32 + lane;
+  const uint32_t m = mt * kTcRows + row;
+  const uint32_t c_row = (m < M) ? (runs_offset(ts.cm, m) | runs_offset(ts.cb, bi)) : 0;
+  for (uint32_t c16 = 0; c16 < 4; ++c16) {
+    const uint32_t col = half * 64 + c16 * 16;
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(tmem + ((sub * 32u) << 16) + col));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (m < M)
+      for (uint32_t q = 0; q < 8; ++q) {
+        const uint32_t n = nt * kTcCols + (col >> 1) + q;
+        C[c_row | runs_offset(ts.cn, n)] =
+            from_d2<T>(make_double2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1])));
+      }
+  }
+  tc_fence_before();
+  signal_done(prog, ts.done_ctr);
+  return true;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kGraphBlock) graph_exec_kernel(const GraphProgDev prog) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ GStep s_step;
+  __shared__ TStep s_tstep;
   __shared__ double s_grad[2 * kMaxParams];
   __shared__ double s_red[kGraphBlock];
   __shared__ unsigned int s_task;
   __shared__ int s_flag;
   __shared__ int s_last;
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) unsigned long long s_mbar;
   T* table = reinterpret_cast<T*>(smem_raw);
   unsigned char* work = smem_raw + prog.table_bytes;
+  // tensor memory for GEMM tasks: prog.tmem_cols columns per CTA, sized on
+  // the host so that every CTA resident on an SM gets its columns at once
+  uint32_t tmem = 0, phase = 0;
+  bool tc_pending = false;
+  if (prog.tmem_cols > 0) {
+    if (threadIdx.x < 32) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_addr(&s_tmem)),
+                   "r"(prog.tmem_cols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_mbar)), "r"(1)
+                   : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    tmem = s_tmem;
+  }
 
   for (int e = threadIdx.x; e < prog.n_gates; e += blockDim.x) {
     const GateEntryDev g = prog.gates[e];
@@ -318,11 +543,31 @@ __global__ void __launch_bounds__(kGraphBlock) graph_exec_kernel(const GraphProg
     __syncthreads();
     if (!s_flag) break;
     const GTask task = prog.tasks[s_task];
-    if (task.kind == GT_SMEM)
+    if (task.kind == GT_SMEM) {
       run_smem_task<T>(prog, task, table, work, s_grad);
-    else
+    } else if (task.kind == GT_CHUNK) {
       run_chunk<T>(prog, task, table, work, s_step, s_last);
+    } else if (prog.tmem_cols > 0) {
+      if (!run_tc<T>(prog, task, work, s_tstep, tmem, smem_addr(&s_mbar), phase)) {
+        tc_pending = true;
+        __syncthreads();
+        break;
+      }
+    }
     __syncthreads();
+  }
+  if (prog.tmem_cols > 0) {
+    // a GEMM whose completion wait expired may still be running: wait for it
+    // once more (bounded) before giving the tensor memory back
+    if (tc_pending) mbar_wait_bounded(smem_addr(&s_mbar), phase ^ 1u, prog.wait_limit_ns);
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      tc_fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(prog.tmem_cols)
+                   : "memory");
+    }
   }
 
   // the last CTA reduces (final wave), records the status and re-arms

@@ -64,6 +64,26 @@ WaveHost assemble_wave(const std::vector<int>& nets, const std::vector<NetGraph>
         w.ops.push_back(op);
       }
       w.tasks.push_back(t);
+    } else if (u.kind == GT_TC) {
+      TStep ts = u.tstep;
+      ts.net = (uint32_t)nets[k];
+      ts.done_ctr = ctr[k][ui];
+      ts.c_off = rebase32(base[k], ts.c_off);
+      ts.a_off = rebase32(base[k], ts.a_off);
+      ts.b_off = rebase32(base[k], ts.b_off);
+      const uint32_t idx = (uint32_t)w.tsteps.size();
+      w.tsteps.push_back(ts);
+      for (uint32_t tile = 0; tile < u.target; ++tile) {
+        GTask t{};
+        t.kind = GT_TC;
+        t.a = idx;
+        t.b = tile;
+        t.net = (uint32_t)nets[k];
+        t.wait_begin = wait_begin;
+        t.wait_count = wait_count;
+        t.signal = 0xFFFFFFFFu;
+        w.tasks.push_back(t);
+      }
     } else {
       GStep st = u.step;
       st.net = (uint32_t)nets[k];
@@ -147,11 +167,26 @@ void validate_wave(const WaveHost& w, uint32_t table_elems, uint32_t arena_elems
           check_ref(op.out, op.flags & SOPF_OUT_GLOBAL, 0, "seed");
         }
       }
+    } else if (t.kind == GT_TC) {
+      if (t.a >= w.tsteps.size()) fail(QTC_ERR_INVALID, "internal: GEMM index");
+      const TStep& ts = w.tsteps[t.a];
+      if (t.b >= (((uint64_t)ts.m_tiles * ts.n_tiles) << ts.bb))
+        fail(QTC_ERR_INVALID, "internal: GEMM tile index");
     } else {
       if (t.a >= w.steps.size()) fail(QTC_ERR_INVALID, "internal: step index");
       const GStep& st = w.steps[t.a];
       if (t.b >= st.n_chunks) fail(QTC_ERR_INVALID, "internal: chunk index");
     }
+  }
+  for (const TStep& ts : w.tsteps) {
+    check_ref(ts.a_off, true, runs_max(ts.am, ts.mb) | runs_max(ts.ak, ts.kb) |
+                                  runs_max(ts.ab, ts.bb), "GEMM operand A");
+    check_ref(ts.b_off, true, runs_max(ts.bk, ts.kb) | runs_max(ts.bn, ts.nb) |
+                                  runs_max(ts.bbt, ts.bb), "GEMM operand B");
+    check_ref(ts.c_off, true, runs_max(ts.cm, ts.mb) | runs_max(ts.cn, ts.nb) |
+                                  runs_max(ts.cb, ts.bb), "GEMM output");
+    if (ts.done_ctr >= w.n_counters) fail(QTC_ERR_INVALID, "internal: GEMM counter");
+    if (ts.nb < 6 || ((1ull << ts.nb) % kTcCols)) fail(QTC_ERR_INVALID, "internal: GEMM N");
   }
   for (const GStep& st : w.steps) {
     const uint64_t ma = runs_max(st.ca, st.rc) | runs_max(st.ya, st.ry);
@@ -184,6 +219,10 @@ void validate_wave(const WaveHost& w, uint32_t table_elems, uint32_t arena_elems
     }
     if (t.kind == GT_SMEM) {
       if (t.signal != 0xFFFFFFFFu) last_producer[t.signal] = (int64_t)i;
+    } else if (t.kind == GT_TC) {
+      const TStep& ts = w.tsteps[t.a];
+      if (t.b + 1 == (((uint64_t)ts.m_tiles * ts.n_tiles) << ts.bb))
+        last_producer[ts.done_ctr] = (int64_t)i;
     } else {
       const GStep& st = w.steps[t.a];
       // a step is complete only after its last chunk; mark it at the last chunk
@@ -206,6 +245,7 @@ void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
   lim.arena_elems = (uint32_t)(49152 / elem);
   lim.subtree_elems = 32768 / elem;
   if (opts.small_rank > 0) lim.small_rank = opts.small_rank;
+  lim.tensor_cores = hp.dtype == QTC_SPLIT_BF16;
   std::vector<NetGraph> graphs(N);
   for (int i = 0; i < N; ++i) {
     // a network that fits whole in shared memory stays one fused task
@@ -255,10 +295,12 @@ void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
   uint32_t max_arena = 0;
   for (const NetGraph& g : graphs)
     for (const GUnit& u : g.units) max_arena = std::max(max_arena, u.arena_elems);
+  hp.tensor_cores = false;
   for (auto& wnets : waves) {
     std::sort(wnets.begin(), wnets.end());
     hp.waves.push_back(assemble_wave(wnets, graphs));
     validate_wave(hp.waves.back(), hp.table_elems, max_arena);
+    if (!hp.waves.back().tsteps.empty()) hp.tensor_cores = true;
     hp.max_global_elems = std::max(hp.max_global_elems, hp.waves.back().global_elems);
     hp.max_counters = std::max(hp.max_counters, hp.waves.back().n_counters);
   }

@@ -322,6 +322,49 @@ bool encode_gstep(GStep& g, const std::vector<int>& lc, const std::vector<int>& 
   return true;
 }
 
+// A step as a batched complex GEMM for the tensor cores: C labels are batch
+// (in both operands) or free in exactly one operand, summed labels are in
+// both operands.  Eligible when M and N have >= 64 entries and K >= 8.
+bool encode_tstep(TStep& t, const std::vector<int>& lc, const std::vector<int>& la,
+                  const std::vector<int>& lb) {
+  std::vector<int> bl, ml, nl, kl;
+  for (int x : lc) {
+    const bool in_a = pos_in(la, x) >= 0, in_b = pos_in(lb, x) >= 0;
+    if (in_a && in_b) bl.push_back(x);
+    else if (in_a) ml.push_back(x);
+    else if (in_b) nl.push_back(x);
+    else return false;  // an output label in neither operand
+  }
+  for (int x : la)
+    if (pos_in(lc, x) < 0) {
+      if (pos_in(lb, x) < 0) return false;  // summed in one operand only
+      kl.push_back(x);
+    }
+  for (int x : lb)
+    if (pos_in(lc, x) < 0 && pos_in(la, x) < 0) return false;
+  if (ml.size() < 6 || nl.size() < 6 || kl.size() < 3) return false;
+  if (ml.size() > 24 || nl.size() > 24 || kl.size() > 24 || bl.size() > 24) return false;
+  std::memset(&t, 0, sizeof t);
+  auto pos = [](const std::vector<int>& labels, const std::vector<int>& in) {
+    std::vector<int> p;
+    for (int x : labels) p.push_back(pos_in(in, x));
+    return p;
+  };
+  bool ok = make_runs(pos(ml, la), t.am) && make_runs(pos(kl, la), t.ak) &&
+            make_runs(pos(bl, la), t.ab) && make_runs(pos(kl, lb), t.bk) &&
+            make_runs(pos(nl, lb), t.bn) && make_runs(pos(bl, lb), t.bbt) &&
+            make_runs(pos(ml, lc), t.cm) && make_runs(pos(nl, lc), t.cn) &&
+            make_runs(pos(bl, lc), t.cb);
+  if (!ok) return false;
+  t.mb = (uint8_t)ml.size();
+  t.kb = (uint8_t)kl.size();
+  t.nb = (uint8_t)nl.size();
+  t.bb = (uint8_t)bl.size();
+  t.m_tiles = (uint32_t)(((1ull << t.mb) + kTcRows - 1) / kTcRows);
+  t.n_tiles = (uint32_t)((1ull << t.nb) / kTcCols);
+  return true;
+}
+
 NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
                      const std::vector<uint32_t>& gate_val_off,
                      const std::vector<uint32_t>& gate_der_off, uint32_t table_elems,
@@ -514,6 +557,16 @@ NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
                         Ref ra, int b, const std::vector<int>& lb, Ref rb, int64_t c_off,
                         std::vector<int> deps, int leaf_for_grad) -> int {
     GUnit u;
+    if (lim.tensor_cores && leaf_for_grad < 0 && ra.global && rb.global &&
+        encode_tstep(u.tstep, lc, la, lb)) {
+      u.kind = GT_TC;
+      u.tstep.c_off = (uint32_t)c_off;
+      u.tstep.a_off = ra.abs;
+      u.tstep.b_off = rb.abs;
+      u.target = (uint32_t)(((uint64_t)u.tstep.m_tiles * u.tstep.n_tiles) << u.tstep.bb);
+      u.deps = std::move(deps);
+      return add_unit(std::move(u));
+    }
     u.kind = GT_CHUNK;
     std::memset(&u.step, 0, sizeof u.step);
     std::string why;

@@ -157,6 +157,7 @@ struct GraphLimits {
   int small_rank = 10;               // tensors of higher rank live in global memory
   uint64_t subtree_elems = 4096;     // elements of all values of one subtree
   uint32_t arena_elems = 8192;       // shared-memory arena of one subtree task
+  bool tensor_cores = false;         // split-BF16 GEMM tasks for GEMM-shaped steps
 };
 
 // A unit is one shared-memory subtree task or one global step (its chunks);
@@ -165,6 +166,7 @@ struct GUnit {
   int kind = GT_SMEM;
   std::vector<SOp> ops;              // GT_SMEM
   GStep step{};                      // GT_CHUNK
+  TStep tstep{};                     // GT_TC
   uint32_t arena_elems = 0;
   std::vector<int> deps;             // units that must be complete first
   int depth = 0;
@@ -204,6 +206,7 @@ struct WaveHost {
   std::vector<GTask> tasks;
   std::vector<SOp> ops;
   std::vector<GStep> steps;
+  std::vector<TStep> tsteps;
   std::vector<WaitDev> waits;
   uint64_t global_elems = 0;
   uint32_t n_counters = 0;
@@ -236,6 +239,7 @@ struct HostProgram {
   uint32_t work_bytes = 0;         // graph form: shared memory after the table
   uint64_t max_global_elems = 0;
   uint32_t max_counters = 0;
+  bool tensor_cores = false;       // some wave has tensor-core GEMM tasks
 };
 
 // Built once per (batch, dtype, want_grad, budget, options) and cached in the
