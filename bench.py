@@ -49,6 +49,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--edges", type=int, default=0,
                     help="contract only the first K edge networks (small profiling cases)")
+    ap.add_argument("--dense", action="store_true",
+                    help="rank-4 ZZ tensors instead of diagonal (hyperedge) ZZ")
+    ap.add_argument("--per-network", action="store_true",
+                    help="also time the plain form: one launch per edge network")
+    ap.add_argument("--statevector", action="store_true",
+                    help="also time the full 2^n state vector on the GPU for the same graph")
+    ap.add_argument("--crossover", action="store_true",
+                    help="tensor network vs state vector over regularities 3..7 (table)")
     return ap.parse_args()
 
 
@@ -224,6 +232,8 @@ def run_ours(args):
     # rank r contracts graph seed (seed + r): independent problems
     from dataclasses import replace
     w = replace(base, graph_seed=base.graph_seed + rank)
+    if args.dense:
+        w = replace(w, diag=False)
     edges = w.graph()
     g, b = w.angles()
     circ = q.Circuit.qaoa(w.n, edges, w.p)
@@ -344,6 +354,43 @@ def run_ours(args):
         "timed_wall_s": wall,
     }
     clocks.stop()
+    if args.per_network:
+        # the plain form: every edge network is its own batch and launch, c64
+        singles = [q.Batch(circ, [e], lightcone=w.lightcone, diag=w.diag, ordering=w.ordering)
+                   for e in (obs or edges)]
+        outs = [torch.zeros(2 + P + 1, dtype=torch.float64, device=dev) for _ in singles]
+        for sb in singles:
+            sb.prepare(engine, "c64", want_grad=False)
+
+        def per_network_step():
+            for sb, o in zip(singles, outs):
+                q.qaoa_expectation_device(engine, sb, params, o, "c64", want_grad=False,
+                                          stream=stream)
+
+        for _ in range(args.warmup):
+            per_network_step()
+        pn_ms = timed(per_network_step, args.steps)
+        pn = sum(pn_ms) / len(pn_ms)
+        line["per_network_c64_forward"] = {
+            "value": n_nets / (pn * 1e-3), "unit": "networks/s", "ms_per_step": pn,
+            "launches_per_step": len(singles),
+            "batched_forward_speedup": pn / fwd}
+    if args.statevector:
+        out_sv = torch.zeros(1 + len(edges), dtype=torch.float64, device=dev)
+        sv_dtype = "c128" if dtype == "c128" else "c64"
+
+        def sv_step():
+            q.statevector_expectation_device(engine, circ, params, out_sv, sv_dtype,
+                                             stream=stream)
+
+        for _ in range(args.warmup):
+            sv_step()
+        sv_ms = timed(sv_step, args.steps)
+        svt = sum(sv_ms) / len(sv_ms)
+        line["statevector_forward"] = {
+            "ms_per_eval": svt, "launches": engine.last_launches,
+            "tensor_network_forward_ms": fwd, "tn_over_sv_time": fwd / svt,
+            "C_statevector": out_sv[0].item(), "C_tensor_network": out[0].item()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, done, el = oracle_networks_per_s(w, edges, g, b, want_grad, 10.0)
         line["cpu_baseline"] = {
@@ -356,8 +403,69 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_crossover(args):
+    """Time per <C> evaluation (forward) of the light-cone tensor networks, the
+    full un-reduced networks and the 2^n state vector, for d = 3..7 at each n."""
+    import torch
+    import paper_1709_03636_gb300 as q
+    from synth import qaoa_angles, random_regular_graph
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for n in (20, 24, 26):
+        for d in (3, 4, 5, 6, 7):
+            if (n * d) % 2:
+                continue
+            edges = random_regular_graph(n, d, 0)
+            g, b = qaoa_angles(1, 0)
+            circ = q.Circuit.qaoa(n, edges, 1)
+            params = torch.tensor(g + b, dtype=torch.float64, device=dev)
+            row = {"n": n, "d": d, "edges": len(edges)}
+            batches = {"lightcone": q.Batch(circ, lightcone=True),
+                       "full": q.Batch(circ, lightcone=False)}
+            need = max(bt.program_info("c64", False)["work_bytes"] for bt in batches.values())
+            engine = q.Engine(0, arena_bytes=int(need + (8 << 8) * (1 << n) / 256) + (1 << 30))
+            for name, bt in batches.items():
+                out = torch.zeros(3 + len(edges), dtype=torch.float64, device=dev)
+                bt.prepare(engine, "c64", False)
+                f = lambda: q.qaoa_expectation_device(engine, bt, params, out, "c64",  # noqa
+                                                      stream=stream)
+                for _ in range(2):
+                    f()
+                torch.cuda.synchronize()
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                for _ in range(args.steps):
+                    f()
+                s1.record(stream)
+                torch.cuda.synchronize()
+                row[f"tn_{name}_ms"] = s0.elapsed_time(s1) / args.steps
+                row[f"tn_{name}_max_rank"] = bt.stats()["max_rank"]
+            out_sv = torch.zeros(1 + len(edges), dtype=torch.float64, device=dev)
+            f = lambda: q.statevector_expectation_device(engine, circ, params, out_sv, "c64",  # noqa
+                                                         stream=stream)
+            for _ in range(2):
+                f()
+            torch.cuda.synchronize()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            for _ in range(args.steps):
+                f()
+            s1.record(stream)
+            torch.cuda.synchronize()
+            row["sv_ms"] = s0.elapsed_time(s1) / args.steps
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+            del engine
+            torch.cuda.empty_cache()
+    print(json.dumps({"crossover": rows}), flush=True)
+
+
 def main():
     args = parse()
+    if args.crossover:
+        run_crossover(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -230,7 +230,7 @@ extern "C" qtc_status qtc_selftest_wait_timeout(qtc_engine* e, void* stream) {
     int per_sm = 0;
     const size_t max_dyn = max_dynamic_smem(e->smem_optin);
     const size_t smem = 2 * (size_t)kYTab * sizeof(uint32_t) + 256 * 16;
-    cuda_check(graph_exec_configure(1, smem, max_dyn, &per_sm), "configure");
+    cuda_check(graph_exec_configure(1, false, smem, max_dyn, &per_sm), "configure");
     cuda_check(graph_exec_launch(d, 1, 1, smem, s), "launch");
     double host_out[2] = {0, 0};
     cuda_check(cudaMemcpyAsync(host_out, out, sizeof host_out, cudaMemcpyDeviceToHost, s), "read");
@@ -655,7 +655,8 @@ static Prepared& prepare_graph(qtc_engine* e, qtc_batch* b, const HostProgram& h
   cuda_check(cudaMemsetAsync(dres, 0, sizeof(double) * N * stride, stream), "clear results");
   cuda_check(cudaStreamSynchronize(stream), "prepare sync");
   int per_sm = 0;
-  cuda_check(graph_exec_configure(hp.dtype == QTC_C128 ? 0 : 1, hp.smem, max_dyn, &per_sm),
+  cuda_check(graph_exec_configure(hp.dtype == QTC_C128 ? 0 : 1, hp.tensor_cores, hp.smem,
+                                  max_dyn, &per_sm),
              "configure graph executor");
   if (per_sm < 1) fail(QTC_ERR_UNSUPPORTED, "graph executor does not fit on an SM");
   // tensor memory: 512 columns per SM shared by the resident CTAs; a GEMM

@@ -194,14 +194,33 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
       }
       __syncthreads();
       if (active) {
+        // four rows at a time: eight independent loads in flight per thread
+        constexpr uint32_t R = 4;
         const uint32_t n_y = (uint32_t)ny;
-        for (uint32_t row = r0; row < r1; ++row) {
-          const uint32_t hi = row * rowlen;
-          const uint32_t oa = runs_offset(st.ca, hi) | a_lo;
-          const uint32_t ob = runs_offset(st.cb, hi) | b_lo;
-          T acc = czero<T>();
-          for (uint32_t y = 0; y < n_y; ++y) acc = cfma(A[oa | ya[y]], B[ob | yb[y]], acc);
-          C[hi + tid] = acc;
+        for (uint32_t row = r0; row < r1; row += R) {
+          uint32_t oa[R], ob[R];
+          T acc[R];
+#pragma unroll
+          for (uint32_t r = 0; r < R; ++r) {
+            const uint32_t hi = min(row + r, r1 - 1) * rowlen;
+            oa[r] = runs_offset(st.ca, hi) | a_lo;
+            ob[r] = runs_offset(st.cb, hi) | b_lo;
+            acc[r] = czero<T>();
+          }
+          for (uint32_t y = 0; y < n_y; ++y) {
+            const uint32_t ay = ya[y], by = yb[y];
+            T av[R], bv[R];
+#pragma unroll
+            for (uint32_t r = 0; r < R; ++r) {
+              av[r] = A[oa[r] | ay];
+              bv[r] = B[ob[r] | by];
+            }
+#pragma unroll
+            for (uint32_t r = 0; r < R; ++r) acc[r] = cfma(av[r], bv[r], acc[r]);
+          }
+#pragma unroll
+          for (uint32_t r = 0; r < R; ++r)
+            if (row + r < r1) C[(row + r) * rowlen + tid] = acc[r];
         }
       }
     } else {
@@ -483,7 +502,10 @@ __device__ bool run_tc(const GraphProgDev& prog, const GTask& task, unsigned cha
   return true;
 }
 
-template <typename T>
+// kTc: the program has tensor-core GEMM tasks.  Programs without them use the
+// instantiation that contains no tensor-core code, so its registers and
+// schedule are those of the memory-bound task kinds alone.
+template <typename T, bool kTc>
 __global__ void __launch_bounds__(kGraphBlock) graph_exec_kernel(const GraphProgDev prog) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ GStep s_step;
@@ -501,7 +523,7 @@ __global__ void __launch_bounds__(kGraphBlock) graph_exec_kernel(const GraphProg
   // the host so that every CTA resident on an SM gets its columns at once
   uint32_t tmem = 0, phase = 0;
   bool tc_pending = false;
-  if (prog.tmem_cols > 0) {
+  if (kTc && prog.tmem_cols > 0) {
     if (threadIdx.x < 32) {
       asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                        smem_addr(&s_tmem)),
@@ -547,7 +569,7 @@ __global__ void __launch_bounds__(kGraphBlock) graph_exec_kernel(const GraphProg
       run_smem_task<T>(prog, task, table, work, s_grad);
     } else if (task.kind == GT_CHUNK) {
       run_chunk<T>(prog, task, table, work, s_step, s_last);
-    } else if (prog.tmem_cols > 0) {
+    } else if (kTc && prog.tmem_cols > 0) {
       if (!run_tc<T>(prog, task, work, s_tstep, tmem, smem_addr(&s_mbar), phase)) {
         tc_pending = true;
         __syncthreads();
@@ -556,7 +578,7 @@ __global__ void __launch_bounds__(kGraphBlock) graph_exec_kernel(const GraphProg
     }
     __syncthreads();
   }
-  if (prog.tmem_cols > 0) {
+  if (kTc && prog.tmem_cols > 0) {
     // a GEMM whose completion wait expired may still be running: wait for it
     // once more (bounded) before giving the tensor memory back
     if (tc_pending) mbar_wait_bounded(smem_addr(&s_mbar), phase ^ 1u, prog.wait_limit_ns);
@@ -624,10 +646,17 @@ __global__ void __launch_bounds__(kGraphBlock) graph_exec_kernel(const GraphProg
   }
 }
 
-cudaError_t graph_exec_configure(int dtype, size_t smem_bytes, size_t max_dynamic,
+static const void* graph_kernel(int dtype, bool tc) {
+  if (dtype == 0)
+    return tc ? (const void*)graph_exec_kernel<double2, true>
+              : (const void*)graph_exec_kernel<double2, false>;
+  return tc ? (const void*)graph_exec_kernel<float2, true>
+            : (const void*)graph_exec_kernel<float2, false>;
+}
+
+cudaError_t graph_exec_configure(int dtype, bool tc, size_t smem_bytes, size_t max_dynamic,
                                  int* blocks_per_sm) {
-  const void* fn = dtype == 0 ? (const void*)graph_exec_kernel<double2>
-                              : (const void*)graph_exec_kernel<float2>;
+  const void* fn = graph_kernel(dtype, tc);
   if (smem_bytes > max_dynamic) return cudaErrorInvalidValue;
   cudaError_t err =
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dynamic);
@@ -637,10 +666,18 @@ cudaError_t graph_exec_configure(int dtype, size_t smem_bytes, size_t max_dynami
 
 cudaError_t graph_exec_launch(const GraphProgDev& prog, int dtype, int grid, size_t smem_bytes,
                               cudaStream_t stream) {
-  if (dtype == 0)
-    graph_exec_kernel<double2><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
-  else
-    graph_exec_kernel<float2><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
+  const bool tc = prog.tmem_cols > 0;
+  if (dtype == 0) {
+    if (tc)
+      graph_exec_kernel<double2, true><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
+    else
+      graph_exec_kernel<double2, false><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
+  } else {
+    if (tc)
+      graph_exec_kernel<float2, true><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
+    else
+      graph_exec_kernel<float2, false><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
+  }
   return cudaGetLastError();
 }
 

@@ -17,7 +17,8 @@ cudaError_t smem_exec_launch(const ProgramDev& prog, int dtype, bool warp_teams,
 
 // Graph executor (networks larger than one CTA's shared memory); one launch
 // per wave.
-cudaError_t graph_exec_configure(int dtype, size_t smem_bytes, size_t max_dynamic,
+// tc: the program has tensor-core GEMM tasks (GraphProgDev.tmem_cols > 0).
+cudaError_t graph_exec_configure(int dtype, bool tc, size_t smem_bytes, size_t max_dynamic,
                                  int* blocks_per_sm);
 cudaError_t graph_exec_launch(const GraphProgDev& prog, int dtype, int grid, size_t smem_bytes,
                               cudaStream_t stream);

@@ -43,13 +43,18 @@ __device__ __forceinline__ int cut_of(uint32_t x, const uint32_t* adj, int n) {
   return c;
 }
 
+template <typename T> struct RealOf;
+template <> struct RealOf<float2> { using type = float; };
+template <> struct RealOf<double2> { using type = double; };
+
 template <typename T>
 __global__ void __launch_bounds__(kSvThreads) sv_pass_kernel(const SvArgs args) {
+  using R = typename RealOf<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);
   __shared__ uint32_t s_adj[32];
   __shared__ double s_red[kSvThreads];
-  __shared__ double2 s_phase[kSvMaxEdges + 1];
+  __shared__ T s_phase[kSvMaxEdges + 1];
   const int n = args.n;
   if (threadIdx.x < n) s_adj[threadIdx.x] = args.adj[threadIdx.x];
   // tile bits: pass 0: 0..len-1; else 0..3 and lo..lo+len-1
@@ -71,49 +76,60 @@ __global__ void __launch_bounds__(kSvThreads) sv_pass_kernel(const SvArgs args) 
     for (int c = threadIdx.x; c <= args.m; c += blockDim.x) {
       double sn, cs;
       sincos(-0.5 * gamma * (double)(args.m - 2 * c), &sn, &cs);
-      s_phase[c] = make_double2(cs, sn);
+      s_phase[c] = from_d2<T>(make_double2(cs, sn));
     }
   __syncthreads();
   T* psi = reinterpret_cast<T*>(args.psi);
-  const double amp0 = exp2(-0.5 * n);
+  const R amp0 = (R)exp2(-0.5 * n);
   for (uint32_t t = threadIdx.x; t < tsize; t += blockDim.x) {
     const uint64_t x = global_index(t);
-    double2 v = args.first ? make_double2(amp0, 0.0) : to_d2(psi[x]);
+    T v;
+    if (args.first) {
+      v.x = amp0;
+      v.y = 0;
+    } else {
+      v = psi[x];
+    }
     if (pass0) {
       // the layer's phase exp(-i gamma/2 (m - 2 cut(x)))
-      const double2 ph = s_phase[cut_of((uint32_t)x, s_adj, n)];
-      v = make_double2(v.x * ph.x - v.y * ph.y, v.x * ph.y + v.y * ph.x);
+      const T ph = s_phase[cut_of((uint32_t)x, s_adj, n)];
+      const R re = v.x * ph.x - v.y * ph.y;
+      v.y = v.x * ph.y + v.y * ph.x;
+      v.x = re;
     }
-    tile[t] = from_d2<T>(v);
+    tile[t] = v;
   }
   __syncthreads();
   // exp(-i beta X) = [[c, -i s], [-i s, c]] on the pass's own qubits (qubits
   // 0..3 ride along in later passes only for coalescing)
-  double sb, cb;
-  sincos(beta, &sb, &cb);
+  double sbd, cbd;
+  sincos(beta, &sbd, &cbd);
+  const R sb = (R)sbd, cb = (R)cbd;
   for (int k = pass0 ? 0 : 4; k < tbits; ++k) {
     const uint32_t bit = 1u << k;
     for (uint32_t j = threadIdx.x; j < tsize / 2; j += blockDim.x) {
       const uint32_t i0 = ((j & ~(bit - 1)) << 1) | (j & (bit - 1));
       const uint32_t i1 = i0 | bit;
-      const double2 a = to_d2(tile[i0]), b = to_d2(tile[i1]);
-      tile[i0] = from_d2<T>(make_double2(cb * a.x + sb * b.y, cb * a.y - sb * b.x));
-      tile[i1] = from_d2<T>(make_double2(cb * b.x + sb * a.y, cb * b.y - sb * a.x));
+      const T a = tile[i0], b = tile[i1];
+      T a2, b2;
+      a2.x = cb * a.x + sb * b.y;
+      a2.y = cb * a.y - sb * b.x;
+      b2.x = cb * b.x + sb * a.y;
+      b2.y = cb * b.y - sb * a.x;
+      tile[i0] = a2;
+      tile[i1] = b2;
     }
     __syncthreads();
   }
-  double part = 0.0;
+  R part = 0;
   for (uint32_t t = threadIdx.x; t < tsize; t += blockDim.x) {
     const uint64_t x = global_index(t);
     const T v = tile[t];
     psi[x] = v;
-    if (args.last) {
-      const double2 d = to_d2(v);
-      part += (d.x * d.x + d.y * d.y) * cut_of((uint32_t)x, s_adj, n);
-    }
+    if (args.last) part += (v.x * v.x + v.y * v.y) * (R)cut_of((uint32_t)x, s_adj, n);
   }
   if (!args.last) return;
-  s_red[threadIdx.x] = part;
+  s_red[threadIdx.x] = (double)part;
   __syncthreads();
   for (int off = blockDim.x / 2; off > 0; off >>= 1) {
     if (threadIdx.x < off) s_red[threadIdx.x] += s_red[threadIdx.x + off];
