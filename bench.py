@@ -259,6 +259,10 @@ def run_ours(args):
                                   stream=stream)
 
     def timed(fn, steps):
+        # a short device-side sleep first, so that the following steps are all
+        # queued before the GPU reaches them: the events then time the GPU
+        # alone, not the host's enqueue latency
+        torch.cuda._sleep(int(4e6))
         evs = []
         for _ in range(steps):
             flush.zero_()

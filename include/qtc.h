@@ -224,6 +224,13 @@ qtc_status qtc_batch_program_info(qtc_batch* b, int dtype, int want_grad, int fo
                                   int small_rank, size_t max_wave_bytes, size_t smem_limit,
                                   qtc_program_info* info);
 
+/* Launch configuration of the batch's prepared program on this engine
+ * (prepares it when needed): grid and block size, dynamic shared memory per
+ * CTA, CTAs resident per SM, launches per evaluation, tensor-memory columns
+ * per CTA (0: no tensor-core tasks).  out: host, 6 ints. */
+qtc_status qtc_batch_launch_info(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
+                                 int32_t* out);
+
 /* Upload the batch's device program for (dtype, want_grad) into the arena.
  * Optional: the expectation calls below prepare on first use. */
 qtc_status qtc_batch_prepare(qtc_engine* e, qtc_batch* b, int dtype,

@@ -242,6 +242,12 @@ class Batch(_Handle):
                                          int(smem_limit), ctypes.byref(info)))
         return {f: getattr(info, f) for f, _ in info._fields_}
 
+    def launch_info(self, engine: Engine, dtype="c64", want_grad=False) -> dict:
+        """Grid, block, shared memory, CTAs per SM, launches, TMEM columns."""
+        out = (ctypes.c_int32 * 6)()
+        check(lib.qtc_batch_launch_info(engine.ptr, self.ptr, _dtype(dtype), int(want_grad), out))
+        return dict(zip(["grid", "block", "smem", "per_sm", "launches", "tmem_cols"], out))
+
     def prepare(self, engine: Engine, dtype="c64", want_grad=False, stream=None):
         check(lib.qtc_batch_prepare(engine.ptr, self.ptr, _dtype(dtype), int(want_grad),
                                     _stream(stream)))

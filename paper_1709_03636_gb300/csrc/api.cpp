@@ -41,6 +41,7 @@ struct Prepared {
   size_t smem = 0;
   bool warp_teams = false;
   bool graph = false;
+  int per_sm = 0;                    // resident CTAs per SM reported by the runtime
   std::vector<GraphProgDev> waves;   // graph form: one launch each
   double* raw = nullptr;             // graph form: copy of the result rows
 };
@@ -663,7 +664,8 @@ static Prepared& prepare_graph(qtc_engine* e, qtc_batch* b, const HostProgram& h
   // tile needs 128 fp32 columns (N = 128 reals)
   int tmem_cols = 0;
   if (hp.tensor_cores) {
-    if (per_sm > 4)
+    // one 1024-thread CTA per SM, four teams of 128 columns each
+    if (per_sm > 1)
       fail(QTC_ERR_UNSUPPORTED, "%d resident CTAs per SM leave too little tensor memory",
            per_sm);
     tmem_cols = 128;
@@ -672,6 +674,7 @@ static Prepared& prepare_graph(qtc_engine* e, qtc_batch* b, const HostProgram& h
   for (const WaveHost& w : hp.waves) max_tasks = std::max(max_tasks, w.tasks.size());
   pr.grid = (int)std::max<size_t>(1, std::min<size_t>(max_tasks, (size_t)e->sm_count * per_sm));
   pr.smem = hp.smem;
+  pr.per_sm = per_sm;
   for (size_t i = 0; i < waves.size(); ++i) {
     GraphProgDev& d = waves[i];
     d.gates = dg;
@@ -767,6 +770,7 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   if (per_sm < 1) fail(QTC_ERR_UNSUPPORTED, "executor does not fit on an SM (%zu bytes)", pr.smem);
   const int ctas = ((int)hp.tasks.size() + hp.n_teams - 1) / hp.n_teams;
   pr.grid = std::max(1, std::min(ctas, e->sm_count * per_sm));
+  pr.per_sm = per_sm;
   b->prepared.push_back(pr);
   return b->prepared.back();
 }
@@ -828,6 +832,21 @@ extern "C" qtc_status qtc_batch_program_info(qtc_batch* b, int dtype, int want_g
       tables += sizeof(TaskDev) * hp.tasks.size() + sizeof(SOp) * hp.ops.size();
     }
     info->table_bytes = tables;
+  });
+}
+
+extern "C" qtc_status qtc_batch_launch_info(qtc_engine* e, qtc_batch* b, int dtype,
+                                             int want_grad, int32_t* out) {
+  return guarded([&] {
+    if (!e || !b || !out) fail(QTC_ERR_INVALID, "null argument");
+    DeviceScope scope(e->device);
+    const Prepared& pr = prepare(e, b, dtype, want_grad, nullptr);
+    out[0] = pr.grid;
+    out[1] = pr.graph ? (pr.waves.empty() || pr.waves[0].tmem_cols == 0 ? 256 : 1024) : pr.block;
+    out[2] = (int32_t)pr.smem;
+    out[3] = pr.per_sm;
+    out[4] = pr.graph ? (int32_t)pr.waves.size() : 1;
+    out[5] = pr.graph && !pr.waves.empty() ? pr.waves[0].tmem_cols : 0;
   });
 }
 

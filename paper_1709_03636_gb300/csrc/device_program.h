@@ -122,6 +122,7 @@ struct ProgramDev {
 constexpr int kMaxRuns = 12;
 constexpr uint32_t kGRow = 256;      // output elements per row of a global step
 constexpr uint32_t kYTab = 4096;     // summed-index offsets tabulated per pass
+constexpr uint32_t kMaxChunkRows = 64;  // rows of one normal chunk
 
 // Maps bits of one index (output c or summed y) to bits of an operand index:
 // offset = OR_r ((idx >> src[r]) & (2^len[r] - 1)) << dst[r].  Labels kept

@@ -132,9 +132,11 @@ __device__ __forceinline__ T* resolve(uint32_t off, T* table, T* arena, uint32_t
   return off < table_elems ? table + off : arena + (off - table_elems);
 }
 
-template <typename T, bool kWarp>
+// out = sum over the summed bits of a * b for every output element; the
+// team's threads (team.tid of team.size) share the outputs.
+template <typename T, typename TeamT>
 __device__ __forceinline__ void contract_op(const SOp& op, T* out, const T* a, const T* b,
-                                            const Team<kWarp>& team) {
+                                            const TeamT& team) {
   const uint32_t nout = 1u << op.rc;
   const uint32_t ny = 1u << op.ry;
   for (uint32_t c = team.tid; c < nout; c += team.size) {

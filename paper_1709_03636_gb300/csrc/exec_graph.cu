@@ -23,7 +23,24 @@
 
 namespace qtc {
 
-constexpr int kGraphBlock = 256;
+constexpr int kGraphBlock = 256;   // threads per team
+
+// A team of 256 threads runs one task at a time.  The instantiation without
+// tensor-core tasks has one team per CTA (4 CTAs per SM); the one with them
+// has four teams in a 1024-thread CTA (the runtime keeps one such CTA per
+// SM), synchronised with named barriers 1..4.
+template <int kTeams>
+struct GTeam {
+  int tid, size, id;
+  __device__ GTeam() : tid(threadIdx.x % kGraphBlock), size(kGraphBlock),
+                       id(threadIdx.x / kGraphBlock) {}
+  __device__ __forceinline__ void sync() const {
+    if (kTeams == 1)
+      __syncthreads();
+    else
+      asm volatile("bar.sync %0, %1;" ::"r"(id + 1), "r"(kGraphBlock) : "memory");
+  }
+};
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
@@ -75,11 +92,13 @@ __device__ bool wait_for_producers(const GraphProgDev& prog, const GTask& task) 
   return true;
 }
 
-// Publishes this CTA's writes, then adds to a completion counter.
-__device__ __forceinline__ void signal_done(const GraphProgDev& prog, uint32_t ctr) {
+// Publishes the team's writes, then adds to a completion counter.
+template <int kTeams>
+__device__ __forceinline__ void signal_done(const GraphProgDev& prog, uint32_t ctr,
+                                            const GTeam<kTeams>& team) {
   __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0 && ctr != 0xFFFFFFFFu) atomicAdd(prog.counters + CTR_FIRST_DEP + ctr, 1u);
+  team.sync();
+  if (team.tid == 0 && ctr != 0xFFFFFFFFu) atomicAdd(prog.counters + CTR_FIRST_DEP + ctr, 1u);
 }
 
 template <typename T>
@@ -88,24 +107,23 @@ __device__ __forceinline__ T* locate(uint32_t off, bool global, T* gbase, T* tab
   return global ? gbase + off : resolve(off, table, arena, table_elems);
 }
 
-template <typename T>
+template <typename T, int kTeams>
 __device__ void run_smem_task(const GraphProgDev& prog, const GTask& task, T* table,
-                              unsigned char* work, double* s_grad) {
+                              unsigned char* work, double* s_grad, const GTeam<kTeams>& team) {
   const int P = prog.n_params;
   const int stride = 2 + 2 * P;
-  for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) s_grad[i] = 0.0;
+  for (int i = team.tid; i < 2 * P; i += team.size) s_grad[i] = 0.0;
   SOp* stage = reinterpret_cast<SOp*>(work);
   T* arena = reinterpret_cast<T*>(work + (size_t)prog.stage_ops * sizeof(SOp));
   T* gbase = reinterpret_cast<T*>(prog.gbase);
-  const Team<false> team;
   constexpr int kWords = sizeof(SOp) / sizeof(uint4);
   for (uint32_t base = 0; base < task.b; base += prog.stage_ops) {
     const uint32_t n = min(prog.stage_ops, task.b - base);
-    __syncthreads();
+    team.sync();
     const uint4* src = reinterpret_cast<const uint4*>(prog.ops + task.a + base);
     uint4* dst = reinterpret_cast<uint4*>(stage);
-    for (uint32_t w = threadIdx.x; w < n * kWords; w += blockDim.x) dst[w] = src[w];
-    __syncthreads();
+    for (uint32_t w = team.tid; w < n * kWords; w += team.size) dst[w] = src[w];
+    team.sync();
     for (uint32_t k = 0; k < n; ++k) {
       const SOp& op = stage[k];
       T* out = locate(op.out, (op.flags & SOPF_OUT_GLOBAL) != 0, gbase, table, arena,
@@ -116,13 +134,13 @@ __device__ void run_smem_task(const GraphProgDev& prog, const GTask& task, T* ta
                       prog.table_elems);
       switch (op.code) {
         case SOP_CONTRACT:
-          contract_op<T, false>(op, out, in1, in2, team);
+          contract_op<T>(op, out, in1, in2, team);
           break;
         case SOP_LEAFGRAD:
-          if (threadIdx.x < 32) {
+          if (team.tid < 32) {
             const uint32_t cnt = 1u << op.rc;
             double2 acc = make_double2(0.0, 0.0);
-            for (uint32_t j = threadIdx.x; j < cnt; j += 32) {
+            for (uint32_t j = team.tid; j < cnt; j += 32) {
               const double2 g = to_d2(in1[j]);
               const double2 d = to_d2(in2[j]);
               acc.x += g.x * d.x - g.y * d.y;
@@ -132,42 +150,43 @@ __device__ void run_smem_task(const GraphProgDev& prog, const GTask& task, T* ta
               acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
               acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
             }
-            if (threadIdx.x == 0) {
+            if (team.tid == 0) {
               s_grad[2 * op.out] += acc.x;
               s_grad[2 * op.out + 1] += acc.y;
             }
           }
           break;
         case SOP_RESULT:
-          if (threadIdx.x == 0) {
+          if (team.tid == 0) {
             const double2 v = to_d2(*in1);
             prog.results[(size_t)task.net * stride] = v.x;
             prog.results[(size_t)task.net * stride + 1] = v.y;
           }
           break;
         case SOP_SEED:
-          if (threadIdx.x == 0) *out = from_d2<T>(make_double2(1.0, 0.0));
+          if (team.tid == 0) *out = from_d2<T>(make_double2(1.0, 0.0));
           break;
         default:
           break;
       }
-      __syncthreads();
+      team.sync();
     }
   }
-  for (int i = threadIdx.x; i < 2 * P; i += blockDim.x)
+  for (int i = team.tid; i < 2 * P; i += team.size)
     if (s_grad[i] != 0.0) atomicAdd(&prog.results[(size_t)task.net * stride + 2 + i], s_grad[i]);
-  signal_done(prog, task.signal);
+  signal_done(prog, task.signal, team);
 }
 
-template <typename T>
+template <typename T, int kTeams>
 __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
-                          unsigned char* work, GStep& s_step, int& s_last) {
+                          unsigned char* work, GStep& s_step, int& s_last,
+                          const GTeam<kTeams>& team) {
   {
     const uint4* src = reinterpret_cast<const uint4*>(prog.steps + task.a);
-    for (uint32_t w = threadIdx.x; w < sizeof(GStep) / sizeof(uint4); w += blockDim.x)
+    for (uint32_t w = team.tid; w < sizeof(GStep) / sizeof(uint4); w += team.size)
       reinterpret_cast<uint4*>(&s_step)[w] = src[w];
   }
-  __syncthreads();
+  team.sync();
   const GStep& st = s_step;
   T* gb = reinterpret_cast<T*>(prog.gbase);
   const T* A = (st.flags & GSF_A_TABLE) ? table + st.a_off : gb + st.a_off;
@@ -175,7 +194,7 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
   uint32_t* ya = reinterpret_cast<uint32_t*>(work);
   uint32_t* yb = ya + kYTab;
   T* red = reinterpret_cast<T*>(yb + kYTab);
-  const uint32_t tid = threadIdx.x;
+  const uint32_t tid = team.tid;
   const uint32_t nout = 1u << st.rc;
   const uint64_t ny = 1ull << st.ry;
 
@@ -188,11 +207,18 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
     const bool active = tid < rowlen;
     const uint32_t a_lo = runs_offset(st.ca, tid), b_lo = runs_offset(st.cb, tid);
     if (ny <= kYTab) {
-      for (uint32_t y = tid; y < ny; y += blockDim.x) {
+      // offsets of the summed index and of this chunk's rows, tabulated once
+      uint32_t* rowa = reinterpret_cast<uint32_t*>(red + kGraphBlock);
+      uint32_t* rowb = rowa + kMaxChunkRows;
+      for (uint32_t y = tid; y < ny; y += team.size) {
         ya[y] = runs_offset(st.ya, y);
         yb[y] = runs_offset(st.yb, y);
       }
-      __syncthreads();
+      for (uint32_t r = tid; r < r1 - r0; r += team.size) {
+        rowa[r] = runs_offset(st.ca, (r0 + r) * rowlen);
+        rowb[r] = runs_offset(st.cb, (r0 + r) * rowlen);
+      }
+      team.sync();
       if (active) {
         // four rows at a time: eight independent loads in flight per thread
         constexpr uint32_t R = 4;
@@ -202,9 +228,9 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
           T acc[R];
 #pragma unroll
           for (uint32_t r = 0; r < R; ++r) {
-            const uint32_t hi = min(row + r, r1 - 1) * rowlen;
-            oa[r] = runs_offset(st.ca, hi) | a_lo;
-            ob[r] = runs_offset(st.cb, hi) | b_lo;
+            const uint32_t rr = min(row + r, r1 - 1) - r0;
+            oa[r] = rowa[rr] | a_lo;
+            ob[r] = rowb[rr] | b_lo;
             acc[r] = czero<T>();
           }
           for (uint32_t y = 0; y < n_y; ++y) {
@@ -230,37 +256,37 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
       const uint32_t ob = runs_offset(st.cb, hi) | b_lo;
       T acc = czero<T>();
       for (uint64_t y0 = 0; y0 < ny; y0 += kYTab) {
-        __syncthreads();
-        for (uint32_t y = tid; y < kYTab; y += blockDim.x) {
+        team.sync();
+        for (uint32_t y = tid; y < kYTab; y += team.size) {
           ya[y] = runs_offset(st.ya, (uint32_t)(y0 + y));
           yb[y] = runs_offset(st.yb, (uint32_t)(y0 + y));
         }
-        __syncthreads();
+        team.sync();
         if (active)
           for (uint32_t y = 0; y < kYTab; ++y) acc = cfma(A[oa | ya[y]], B[ob | yb[y]], acc);
       }
       if (active) C[hi + tid] = acc;
     }
-    signal_done(prog, st.done_ctr);
+    signal_done(prog, st.done_ctr, team);
     return;
   }
 
   // split: outputs <= 256, chunk task.b sums y in [y0, y0 + cnt)
-  const uint32_t groups = blockDim.x / nout;
+  const uint32_t groups = team.size / nout;
   const uint32_t c = tid % nout, g = tid / nout;
   const uint64_t y0 = (uint64_t)task.b * st.chunk;
   const uint32_t cnt = (uint32_t)min((uint64_t)st.chunk, ny - y0);
-  for (uint32_t y = tid; y < cnt; y += blockDim.x) {
+  for (uint32_t y = tid; y < cnt; y += team.size) {
     ya[y] = runs_offset(st.ya, (uint32_t)(y0 + y));
     yb[y] = runs_offset(st.yb, (uint32_t)(y0 + y));
   }
-  __syncthreads();
+  team.sync();
   const uint32_t oa = runs_offset(st.ca, c), ob = runs_offset(st.cb, c);
   T acc = czero<T>();
   if (g < groups)
     for (uint32_t y = g; y < cnt; y += groups) acc = cfma(A[oa | ya[y]], B[ob | yb[y]], acc);
   red[tid] = acc;
-  __syncthreads();
+  team.sync();
   T* partial = gb + st.partial_off;
   if (tid < nout) {
     T sum = czero<T>();
@@ -268,10 +294,10 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
     partial[(size_t)task.b * nout + tid] = sum;
   }
   __threadfence();
-  __syncthreads();
+  team.sync();
   if (tid == 0)
     s_last = atomicAdd(prog.counters + CTR_FIRST_DEP + st.arrive_ctr, 1u) == st.n_chunks - 1;
-  __syncthreads();
+  team.sync();
   if (!s_last) return;
   __threadfence();
   T total = czero<T>();
@@ -301,7 +327,7 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
   } else if (tid < nout) {
     gb[st.c_off + tid] = total;
   }
-  signal_done(prog, st.done_ctr);
+  signal_done(prog, st.done_ctr, team);
 }
 
 // ---- tensor-core GEMM tasks (split BF16, tcgen05, accumulator in TMEM) ----
@@ -392,15 +418,16 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) 
 // A' row m = (Re A[m][k], Im A[m][k]) interleaved over k, and B'^T row 2n =
 // (Re B[k][n], -Im B[k][n]), row 2n + 1 = (Im B[k][n], Re B[k][n]), so that the
 // accumulator columns 2n and 2n + 1 are Re C[m][n] and Im C[m][n].
-template <typename T>
+template <typename T, int kTeams>
 __device__ bool run_tc(const GraphProgDev& prog, const GTask& task, unsigned char* work,
-                       TStep& s_ts, uint32_t tmem, uint32_t mbar, uint32_t& phase) {
+                       TStep& s_ts, uint32_t tmem, uint32_t mbar, uint32_t& phase,
+                       const GTeam<kTeams>& team) {
   {
     const uint4* src = reinterpret_cast<const uint4*>(prog.tsteps + task.a);
-    for (uint32_t w = threadIdx.x; w < sizeof(TStep) / sizeof(uint4); w += blockDim.x)
+    for (uint32_t w = team.tid; w < sizeof(TStep) / sizeof(uint4); w += team.size)
       reinterpret_cast<uint4*>(&s_ts)[w] = src[w];
   }
-  __syncthreads();
+  team.sync();
   const TStep& ts = s_ts;
   T* gb = reinterpret_cast<T*>(prog.gbase);
   const T* A = gb + ts.a_off;
@@ -416,7 +443,7 @@ __device__ bool run_tc(const GraphProgDev& prog, const GTask& task, unsigned cha
   unsigned char* a_lo = base + 8192;
   unsigned char* b_hi = base + 16384;
   unsigned char* b_lo = base + 24576;
-  const uint32_t tid = threadIdx.x;
+  const uint32_t tid = team.tid;
   // loaders: A by (row, 8 consecutive k), B by (column, 4 consecutive k)
   const uint32_t a_r = tid & 127u, a_k0 = (tid >> 7) * 8;
   const uint32_t m_g = mt * kTcRows + a_r;
@@ -452,7 +479,7 @@ __device__ bool run_tc(const GraphProgDev& prog, const GTask& task, unsigned cha
       *reinterpret_cast<uint32_t*>(b_lo + o1) = pack_bf16(il, rl);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    team.sync();
     if (tid == 0) {
       tc_fence_after();
       const uint32_t ah = smem_addr(a_hi), al = smem_addr(a_lo);
@@ -498,50 +525,55 @@ __device__ bool run_tc(const GraphProgDev& prog, const GTask& task, unsigned cha
       }
   }
   tc_fence_before();
-  signal_done(prog, ts.done_ctr);
+  signal_done(prog, ts.done_ctr, team);
   return true;
 }
 
 // kTc: the program has tensor-core GEMM tasks.  Programs without them use the
-// instantiation that contains no tensor-core code, so its registers and
-// schedule are those of the memory-bound task kinds alone.
+// instantiation that contains no tensor-core code (one 256-thread team per
+// CTA, four CTAs per SM), so its registers and schedule are those of the
+// memory-bound task kinds alone.  The tensor-core instantiation runs four
+// teams in one 1024-thread CTA per SM and gives each team 128 columns of
+// tensor memory.
 template <typename T, bool kTc>
-__global__ void __launch_bounds__(kGraphBlock) graph_exec_kernel(const GraphProgDev prog) {
+__global__ void __launch_bounds__(kGraphBlock*(kTc ? 4 : 1))
+    graph_exec_kernel(const GraphProgDev prog) {
+  constexpr int kTeams = kTc ? 4 : 1;
+  constexpr int kBlock = kGraphBlock * kTeams;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ GStep s_step;
-  __shared__ TStep s_tstep;
-  __shared__ double s_grad[2 * kMaxParams];
-  __shared__ double s_red[kGraphBlock];
-  __shared__ unsigned int s_task;
-  __shared__ int s_flag;
-  __shared__ int s_last;
+  __shared__ GStep s_step[kTeams];
+  __shared__ TStep s_tstep[kTc ? kTeams : 1];
+  __shared__ double s_grad[kTeams][2 * kMaxParams];
+  __shared__ double s_red[kBlock];
+  __shared__ unsigned int s_task[kTeams];
+  __shared__ int s_flag[kTeams];
+  __shared__ int s_last[kTeams];
+  __shared__ int s_final;
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) unsigned long long s_mbar;
+  __shared__ __align__(8) unsigned long long s_mbar[kTeams];
+  const GTeam<kTeams> team;
   T* table = reinterpret_cast<T*>(smem_raw);
-  unsigned char* work = smem_raw + prog.table_bytes;
-  // tensor memory for GEMM tasks: prog.tmem_cols columns per CTA, sized on
-  // the host so that every CTA resident on an SM gets its columns at once
+  unsigned char* work = smem_raw + prog.table_bytes + (size_t)team.id * prog.arena_bytes;
+  // tensor memory: the CTA allocates kTeams x 128 columns once (at most one
+  // such CTA is resident per SM, 512 columns per SM)
   uint32_t tmem = 0, phase = 0;
   bool tc_pending = false;
   if (kTc && prog.tmem_cols > 0) {
     if (threadIdx.x < 32) {
       asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                        smem_addr(&s_tmem)),
-                   "r"(prog.tmem_cols)
+                   "r"(prog.tmem_cols * kTeams)
                    : "memory");
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (threadIdx.x == 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_mbar)), "r"(1)
+    if (threadIdx.x < kTeams) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_mbar[threadIdx.x])),
+                   "r"(1)
                    : "memory");
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    tmem = s_tmem;
   }
-
   for (int e = threadIdx.x; e < prog.n_gates; e += blockDim.x) {
     const GateEntryDev g = prog.gates[e];
     double2 val[16], der[16];
@@ -553,53 +585,58 @@ __global__ void __launch_bounds__(kGraphBlock) graph_exec_kernel(const GraphProg
     }
   }
   __syncthreads();
+  if (kTc && prog.tmem_cols > 0) {
+    tc_fence_after();
+    tmem = s_tmem + (uint32_t)(team.id * prog.tmem_cols);
+  }
 
   for (;;) {
-    if (threadIdx.x == 0) {
+    if (team.tid == 0) {
       const unsigned int t = atomicAdd(&prog.counters[CTR_QUEUE], 1u);
       int ok = t < (unsigned)prog.n_tasks;
       if (ok) ok = wait_for_producers(prog, prog.tasks[t]);
-      s_task = t;
-      s_flag = ok;
+      s_task[team.id] = t;
+      s_flag[team.id] = ok;
     }
-    __syncthreads();
-    if (!s_flag) break;
-    const GTask task = prog.tasks[s_task];
+    team.sync();
+    if (!s_flag[team.id]) break;
+    const GTask task = prog.tasks[s_task[team.id]];
     if (task.kind == GT_SMEM) {
-      run_smem_task<T>(prog, task, table, work, s_grad);
+      run_smem_task<T, kTeams>(prog, task, table, work, s_grad[team.id], team);
     } else if (task.kind == GT_CHUNK) {
-      run_chunk<T>(prog, task, table, work, s_step, s_last);
+      run_chunk<T, kTeams>(prog, task, table, work, s_step[team.id], s_last[team.id], team);
     } else if (kTc && prog.tmem_cols > 0) {
-      if (!run_tc<T>(prog, task, work, s_tstep, tmem, smem_addr(&s_mbar), phase)) {
+      if (!run_tc<T, kTeams>(prog, task, work, s_tstep[kTc ? team.id : 0], tmem,
+                             smem_addr(&s_mbar[team.id]), phase, team)) {
         tc_pending = true;
-        __syncthreads();
+        team.sync();
         break;
       }
     }
-    __syncthreads();
+    team.sync();
   }
   if (kTc && prog.tmem_cols > 0) {
     // a GEMM whose completion wait expired may still be running: wait for it
-    // once more (bounded) before giving the tensor memory back
-    if (tc_pending) mbar_wait_bounded(smem_addr(&s_mbar), phase ^ 1u, prog.wait_limit_ns);
+    // once more (bounded) before the tensor memory is given back
+    if (tc_pending)
+      mbar_wait_bounded(smem_addr(&s_mbar[team.id]), phase ^ 1u, prog.wait_limit_ns);
     tc_fence_before();
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      tc_fence_after();
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                   "r"(prog.tmem_cols)
-                   : "memory");
-    }
+  }
+  __syncthreads();
+  if (kTc && prog.tmem_cols > 0 && threadIdx.x < 32) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem),
+                 "r"(prog.tmem_cols * kTeams)
+                 : "memory");
   }
 
   // the last CTA reduces (final wave), records the status and re-arms
-  __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    s_flag = atomicAdd(&prog.counters[CTR_BLOCKS], 1u) == gridDim.x - 1;
+    s_final = atomicAdd(&prog.counters[CTR_BLOCKS], 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!s_flag) return;
+  if (!s_final) return;
   __threadfence();
   volatile unsigned* vc = prog.counters;
   const unsigned err = vc[CTR_ERROR] | vc[CTR_RESERVED];
@@ -661,7 +698,8 @@ cudaError_t graph_exec_configure(int dtype, bool tc, size_t smem_bytes, size_t m
   cudaError_t err =
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dynamic);
   if (err != cudaSuccess) return err;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kGraphBlock, smem_bytes);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn,
+                                                       kGraphBlock * (tc ? 4 : 1), smem_bytes);
 }
 
 cudaError_t graph_exec_launch(const GraphProgDev& prog, int dtype, int grid, size_t smem_bytes,
@@ -669,12 +707,12 @@ cudaError_t graph_exec_launch(const GraphProgDev& prog, int dtype, int grid, siz
   const bool tc = prog.tmem_cols > 0;
   if (dtype == 0) {
     if (tc)
-      graph_exec_kernel<double2, true><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
+      graph_exec_kernel<double2, true><<<grid, 4 * kGraphBlock, smem_bytes, stream>>>(prog);
     else
       graph_exec_kernel<double2, false><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
   } else {
     if (tc)
-      graph_exec_kernel<float2, true><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
+      graph_exec_kernel<float2, true><<<grid, 4 * kGraphBlock, smem_bytes, stream>>>(prog);
     else
       graph_exec_kernel<float2, false><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
   }

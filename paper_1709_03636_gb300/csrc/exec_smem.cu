@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
         const SOp& op = stage[k];
         switch (op.code) {
           case SOP_CONTRACT:
-            contract_op<T, kWarp>(op, resolve(op.out, table, arena, prog.table_elems),
+            contract_op<T>(op, resolve(op.out, table, arena, prog.table_elems),
                                   resolve(op.in1, table, arena, prog.table_elems),
                                   resolve(op.in2, table, arena, prog.table_elems), team);
             break;

@@ -202,6 +202,8 @@ void validate_wave(const WaveHost& w, uint32_t table_elems, uint32_t arena_elems
       check_ref(st.partial_off, true, ((uint64_t)st.n_chunks << st.rc) - 1, "partials");
       if (st.arrive_ctr >= w.n_counters) fail(QTC_ERR_INVALID, "internal: arrive counter");
       if (st.chunk > kYTab) fail(QTC_ERR_INVALID, "internal: split chunk above the table");
+    } else if (st.chunk > kMaxChunkRows) {
+      fail(QTC_ERR_INVALID, "internal: chunk of more rows than the row table");
     } else if (((uint64_t)st.chunk * std::min<uint64_t>((uint64_t)1 << st.rc, kGRow)) == 0) {
       fail(QTC_ERR_INVALID, "internal: empty chunk");
     }
@@ -246,6 +248,8 @@ void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
   lim.subtree_elems = 32768 / elem;
   if (opts.small_rank > 0) lim.small_rank = opts.small_rank;
   lim.tensor_cores = hp.dtype == QTC_SPLIT_BF16;
+  // with tensor cores four teams share one CTA's shared memory
+  if (lim.tensor_cores) lim.arena_elems = (uint32_t)(32768 / elem);
   std::vector<NetGraph> graphs(N);
   for (int i = 0; i < N; ++i) {
     // a network that fits whole in shared memory stays one fused task
@@ -259,8 +263,14 @@ void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
       graphs[i].units.push_back(std::move(u));
       continue;
     }
-    graphs[i] = lower_graph(plans[i], leaf_gate[i], val_off, der_off, hp.table_elems,
-                            hp.want_grad != 0, lim);
+    // a subtree that does not fit its arena is cut into smaller ones
+    GraphLimits li = lim;
+    for (;;) {
+      graphs[i] = lower_graph(plans[i], leaf_gate[i], val_off, der_off, hp.table_elems,
+                              hp.want_grad != 0, li);
+      if (graphs[i].fits || li.subtree_elems <= 64) break;
+      li.subtree_elems /= 2;
+    }
     if (!graphs[i].fits)
       fail(QTC_ERR_UNSUPPORTED, "network %d (max rank %d): %s", i, plans[i].max_rank,
            graphs[i].why.c_str());
@@ -308,10 +318,11 @@ void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
   hp.stage_ops = 32;
   auto round16 = [](size_t x) { return (uint32_t)((x + 15) & ~size_t(15)); };
   const size_t smem_task = (size_t)hp.stage_ops * sizeof(SOp) + (size_t)max_arena * elem;
-  const size_t chunk_task = 2 * (size_t)kYTab * sizeof(uint32_t) + 256 * elem;
+  const size_t chunk_task = 2 * (size_t)kYTab * sizeof(uint32_t) + 256 * elem +
+                            2 * (size_t)kMaxChunkRows * sizeof(uint32_t);
   hp.work_bytes = round16(std::max(smem_task, chunk_task));
   hp.table_bytes = round16((size_t)hp.table_elems * elem);
-  hp.smem = hp.table_bytes + hp.work_bytes;
+  hp.smem = hp.table_bytes + (size_t)(hp.tensor_cores ? 4 : 1) * hp.work_bytes;
   if (hp.smem > max_dynamic)
     fail(QTC_ERR_UNSUPPORTED, "graph program needs %zu bytes of shared memory (limit %zu)",
          hp.smem, max_dynamic);

@@ -312,7 +312,7 @@ bool encode_gstep(GStep& g, const std::vector<int>& lc, const std::vector<int>& 
     uint64_t per = 1;
     if (ny <= kYTab) {
       per = std::max<uint64_t>(1, (1ull << 16) / (rowlen * ny));
-      per = std::min<uint64_t>(per, 64);
+      per = std::min<uint64_t>(per, kMaxChunkRows);
       per = std::min<uint64_t>(per, rows);
     }
     g.chunk = (uint32_t)per;
