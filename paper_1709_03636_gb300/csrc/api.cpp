@@ -599,20 +599,62 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
   for (const Plan& pl : b->plans) max_rank = std::max(max_rank, pl.max_rank);
   auto round16 = [](size_t x) { return (uint32_t)((x + 15) & ~size_t(15)); };
   hp->table_bytes = round16((size_t)table_elems * elem);
+  // warp teams need every op within the pre-expanded tables
+  bool warp_ok = max_rank <= kWarpMaxRank;
+  for (const SOp& op : hp->ops)
+    if (op.code == SOP_CONTRACT && (op.rc > kWarpMaxRank || op.ry > kWarpMaxSummed))
+      warp_ok = false;
   auto layout = [&](bool warp, uint32_t stage) {
     hp->warp_teams = warp;
     hp->n_teams = warp ? kExecBlock / 32 : 1;
     hp->stage_ops = stage;
-    hp->team_bytes = round16((size_t)stage * sizeof(SOp) + (size_t)hp->max_arena * elem);
+    const size_t op_bytes = warp ? sizeof(WOp) : sizeof(SOp);
+    hp->team_bytes = round16((size_t)stage * op_bytes + (size_t)hp->max_arena * elem);
     hp->smem = hp->table_bytes + (size_t)hp->n_teams * hp->team_bytes;
     return hp->smem <= max_dynamic;
   };
-  bool ok = max_rank <= 7 && layout(true, std::min<uint32_t>(max_ops, 128));
+  bool ok = warp_ok && layout(true, std::min<uint32_t>(max_ops, 128));
   for (uint32_t stage = std::min<uint32_t>(max_ops, 64); !ok && stage >= 4; stage /= 2)
     ok = layout(false, stage);
   if (!ok)
     fail(QTC_ERR_UNSUPPORTED, "program needs %zu bytes of shared memory (limit %zu)", hp->smem,
          max_dynamic);
+  if (hp->warp_teams) {
+    // expand the bit maps into per-lane byte offset tables
+    for (const SOp& op : hp->ops) {
+      WOp w{};
+      w.code = op.code;
+      w.rc = op.rc;
+      w.ry = op.ry;
+      w.out = (uint16_t)op.out;
+      w.in1 = (uint16_t)op.in1;
+      w.in2 = (uint16_t)op.in2;
+      w.slot = (uint16_t)op.out;
+      if (op.code == SOP_CONTRACT) {
+        auto deposit = [](const uint8_t* pos, int first, int count, uint32_t idx) {
+          uint32_t off = 0;
+          for (int i = 0; i < count; ++i)
+            if (((idx >> i) & 1u) && pos[first + i] != kAbsent) off |= 1u << pos[first + i];
+          return (uint8_t)off;
+        };
+        const int lo = std::min<int>(op.rc, 5), hi = std::max<int>(op.rc - 5, 0);
+        for (uint32_t c = 0; c < 32; ++c) {
+          w.a_lo[c] = deposit(op.p1, 0, lo, c);
+          w.b_lo[c] = deposit(op.p2, 0, lo, c);
+        }
+        for (uint32_t j = 0; j < 4; ++j) {
+          w.a_hi[j] = deposit(op.p1, 5, hi, j);
+          w.b_hi[j] = deposit(op.p2, 5, hi, j);
+        }
+        for (uint32_t y = 0; y < 16; ++y) {
+          w.ya[y] = deposit(op.y1, 0, op.ry, y);
+          w.yb[y] = deposit(op.y2, 0, op.ry, y);
+        }
+      }
+      hp->wops.push_back(w);
+    }
+    hp->ops.clear();
+  }
   b->host_programs.push_back(std::move(hp));
   return *b->host_programs.back();
 }
@@ -730,7 +772,8 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   ProgramDev& d = pr.prog;
   auto* dg = (GateEntryDev*)e->alloc(sizeof(GateEntryDev) * G);
   auto* dt = (TaskDev*)e->alloc(sizeof(TaskDev) * hp.tasks.size());
-  auto* dops = (SOp*)e->alloc(sizeof(SOp) * hp.ops.size());
+  auto* dops = (SOp*)e->alloc(sizeof(SOp) * std::max<size_t>(1, hp.ops.size()));
+  auto* dwops = (WOp*)e->alloc(sizeof(WOp) * std::max<size_t>(1, hp.wops.size()));
   auto* dw = (double*)e->alloc(sizeof(double) * N);
   auto* dparams = (double*)e->alloc(sizeof(double) * std::max(P, 1));
   auto* dres = (double*)e->alloc(sizeof(double) * (size_t)N * (2 + 2 * P));
@@ -738,7 +781,10 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   auto* dcnt = (unsigned int*)e->alloc(sizeof(unsigned int) * 4);
   cuda_check(cudaMemcpyAsync(dg, hp.gates.data(), sizeof(GateEntryDev) * G, cudaMemcpyHostToDevice, stream), "upload gates");
   cuda_check(cudaMemcpyAsync(dt, hp.tasks.data(), sizeof(TaskDev) * hp.tasks.size(), cudaMemcpyHostToDevice, stream), "upload tasks");
-  cuda_check(cudaMemcpyAsync(dops, hp.ops.data(), sizeof(SOp) * hp.ops.size(), cudaMemcpyHostToDevice, stream), "upload ops");
+  if (!hp.ops.empty())
+    cuda_check(cudaMemcpyAsync(dops, hp.ops.data(), sizeof(SOp) * hp.ops.size(), cudaMemcpyHostToDevice, stream), "upload ops");
+  if (!hp.wops.empty())
+    cuda_check(cudaMemcpyAsync(dwops, hp.wops.data(), sizeof(WOp) * hp.wops.size(), cudaMemcpyHostToDevice, stream), "upload warp ops");
   cuda_check(cudaMemcpyAsync(dw, hp.weights.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream), "upload weights");
   cuda_check(cudaMemsetAsync(dcnt, 0, sizeof(unsigned int) * 4, stream), "clear counters");
   cuda_check(cudaStreamSynchronize(stream), "prepare sync");
@@ -751,6 +797,7 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   d.tasks = dt;
   d.n_tasks = (int)hp.tasks.size();
   d.ops = dops;
+  d.wops = dwops;
   d.n_params = P;
   d.n_nets = N;
   d.weights = dw;
@@ -829,7 +876,8 @@ extern "C" qtc_status qtc_batch_program_info(qtc_batch* b, int dtype, int want_g
     } else {
       info->n_waves = 1;
       info->n_tasks = info->n_smem_tasks = (int)hp.tasks.size();
-      tables += sizeof(TaskDev) * hp.tasks.size() + sizeof(SOp) * hp.ops.size();
+      tables += sizeof(TaskDev) * hp.tasks.size() + sizeof(SOp) * hp.ops.size() +
+                sizeof(WOp) * hp.wops.size();
     }
     info->table_bytes = tables;
   });

@@ -89,6 +89,22 @@ struct alignas(16) SOp {
   uint8_t y1[kMaxSmemRank], y2[kMaxSmemRank];
 };
 
+// The same ops for networks run one per warp (every tensor of rank <= 7,
+// at most 4 summed bits per op): the bit maps are pre-expanded into byte
+// offset tables.  Output element c = 32 j + lane of a CONTRACT reads
+// in1[a_lo[lane] | a_hi[j] | ya[y]] and in2[b_lo[lane] | b_hi[j] | yb[y]].
+constexpr int kWarpMaxRank = 7;
+constexpr int kWarpMaxSummed = 4;
+
+struct alignas(16) WOp {
+  uint8_t code, rc, ry, pad0;
+  uint16_t out, in1, in2, slot;   // element offsets (team relative), LEAFGRAD slot
+  uint8_t a_lo[32], b_lo[32];
+  uint8_t a_hi[4], b_hi[4];
+  uint8_t ya[16], yb[16];
+  uint8_t pad1[4];
+};
+
 struct TaskDev {
   uint32_t op_begin, op_count;
   uint32_t net;
@@ -105,7 +121,8 @@ struct ProgramDev {
   uint32_t stage_ops;          // ops staged per team at a time
   const TaskDev* tasks;
   int n_tasks;
-  const SOp* ops;
+  const SOp* ops;              // CTA teams
+  const WOp* wops;             // warp teams
   int n_params;
   int n_nets;
   const double* weights;       // per network, for <C>

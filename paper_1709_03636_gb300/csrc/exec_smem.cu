@@ -10,6 +10,8 @@
 // Section 4.1 and its gradient, in FP64, and re-arms the counters.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "device_program.h"
 #include "exec_common.cuh"
 #include "exec_launch.h"
@@ -17,6 +19,26 @@
 namespace qtc {
 
 constexpr int kMaxTeams = 8;
+
+// One CONTRACT op of a warp team from its pre-expanded offset tables: lane
+// handles outputs c = 32 j + lane.
+template <typename T>
+__device__ __forceinline__ void warp_contract(const WOp& op, T* out, const T* a, const T* b,
+                                              uint32_t lane) {
+  const uint32_t nout = 1u << op.rc, ny = 1u << op.ry;
+  const uint32_t alo = op.a_lo[lane], blo = op.b_lo[lane];
+  for (uint32_t j = 0; 32 * j < nout; ++j) {
+    const uint32_t c = 32 * j + lane;
+    if (c >= nout) break;
+    const uint32_t oa = alo | op.a_hi[j], ob = blo | op.b_hi[j];
+    T acc = czero<T>();
+    for (uint32_t y = 0; y < ny; ++y) acc = cfma(a[oa | op.ya[y]], b[ob | op.yb[y]], acc);
+    out[c] = acc;
+  }
+}
+
+__device__ __forceinline__ uint32_t op_slot(const WOp& op) { return op.slot; }
+__device__ __forceinline__ uint32_t op_slot(const SOp& op) { return op.out; }
 
 template <typename T, bool kWarp>
 __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
@@ -40,14 +62,17 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
   }
   __syncthreads();
 
+  using OpT = typename std::conditional<kWarp, WOp, SOp>::type;
   const Team<kWarp> team;
   unsigned char* team_base = smem_raw + prog.table_bytes + (size_t)team.id * prog.team_bytes;
-  SOp* stage = reinterpret_cast<SOp*>(team_base);
-  T* arena = reinterpret_cast<T*>(team_base + (size_t)prog.stage_ops * sizeof(SOp));
+  OpT* stage = reinterpret_cast<OpT*>(team_base);
+  T* arena = reinterpret_cast<T*>(team_base + (size_t)prog.stage_ops * sizeof(OpT));
+  const OpT* ops = kWarp ? reinterpret_cast<const OpT*>(prog.wops)
+                         : reinterpret_cast<const OpT*>(prog.ops);
   double* grad = s_grad[team.id];
   const int P = prog.n_params;
   const int stride = 2 + 2 * P;
-  constexpr int kWords = sizeof(SOp) / sizeof(uint4);
+  constexpr int kWords = sizeof(OpT) / sizeof(uint4);
   for (;;) {
     if (team.tid == 0) s_task[team.id] = atomicAdd(&prog.counters[0], 1u);
     for (int i = team.tid; i < 2 * P; i += team.size) grad[i] = 0.0;
@@ -58,17 +83,23 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
     for (uint32_t base = 0; base < task.op_count; base += prog.stage_ops) {
       // stage a chunk of the op list with one cooperative copy
       const uint32_t n = min(prog.stage_ops, task.op_count - base);
-      const uint4* src = reinterpret_cast<const uint4*>(prog.ops + task.op_begin + base);
+      const uint4* src = reinterpret_cast<const uint4*>(ops + task.op_begin + base);
       uint4* dst = reinterpret_cast<uint4*>(stage);
       for (uint32_t w = team.tid; w < n * kWords; w += team.size) dst[w] = src[w];
       team.sync();
       for (uint32_t k = 0; k < n; ++k) {
-        const SOp& op = stage[k];
+        const OpT& op = stage[k];
         switch (op.code) {
           case SOP_CONTRACT:
-            contract_op<T>(op, resolve(op.out, table, arena, prog.table_elems),
-                                  resolve(op.in1, table, arena, prog.table_elems),
-                                  resolve(op.in2, table, arena, prog.table_elems), team);
+            if constexpr (kWarp) {
+              warp_contract<T>(op, resolve<T>(op.out, table, arena, prog.table_elems),
+                               resolve<T>(op.in1, table, arena, prog.table_elems),
+                               resolve<T>(op.in2, table, arena, prog.table_elems), team.tid);
+            } else {
+              contract_op<T>(op, resolve(op.out, table, arena, prog.table_elems),
+                             resolve(op.in1, table, arena, prog.table_elems),
+                             resolve(op.in2, table, arena, prog.table_elems), team);
+            }
             break;
           case SOP_LEAFGRAD:
             if (threadIdx.x % team.size < 32) {
@@ -87,8 +118,9 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
                 acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
               }
               if ((threadIdx.x & 31) == 0) {
-                grad[2 * op.out] += acc.x;
-                grad[2 * op.out + 1] += acc.y;
+                const uint32_t slot = kWarp ? op_slot(op) : op.out;
+                grad[2 * slot] += acc.x;
+                grad[2 * slot + 1] += acc.y;
               }
             }
             break;

@@ -221,7 +221,8 @@ struct HostProgram {
   size_t max_dynamic = 0;          // shared-memory budget it was lowered for
   std::vector<GateEntryDev> gates;
   std::vector<TaskDev> tasks;
-  std::vector<SOp> ops;
+  std::vector<SOp> ops;            // CTA teams (empty for warp teams)
+  std::vector<WOp> wops;           // warp teams
   std::vector<double> weights;
   uint32_t table_elems = 0, max_arena = 0;
   uint32_t table_bytes = 0;        // gate table region, 16-byte rounded
