@@ -122,6 +122,10 @@ typedef struct qtc_program_info {
   double work_bytes;      /* global work buffer (largest wave)               */
   double table_bytes;     /* device program tables, all waves                */
   int n_gemm_steps;       /* of which split-BF16 tensor-core GEMMs            */
+  int warp_teams;         /* 1: shared-memory networks run one per warp      */
+  int n_ops;              /* shared-memory ops over all networks (CTA teams) */
+  int n_warp_steps;       /* warp steps over all networks (warp teams)       */
+  int max_warp_steps;     /* warp steps of the longest network               */
 } qtc_program_info;
 
 typedef struct qtc_engine qtc_engine;

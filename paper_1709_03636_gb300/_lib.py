@@ -44,7 +44,9 @@ class qtc_batch_info(ctypes.Structure):
 class qtc_program_info(ctypes.Structure):
     _fields_ = [("graph", c_int), ("n_waves", c_int), ("n_tasks", c_int),
                 ("n_global_steps", c_int), ("n_smem_tasks", c_int), ("smem_bytes", c_int),
-                ("work_bytes", c_double), ("table_bytes", c_double), ("n_gemm_steps", c_int)]
+                ("work_bytes", c_double), ("table_bytes", c_double), ("n_gemm_steps", c_int),
+                ("warp_teams", c_int), ("n_ops", c_int), ("n_warp_steps", c_int),
+                ("max_warp_steps", c_int)]
 
 
 # name -> (restype, argtypes)

@@ -608,53 +608,43 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
     hp->warp_teams = warp;
     hp->n_teams = warp ? kExecBlock / 32 : 1;
     hp->stage_ops = stage;
-    const size_t op_bytes = warp ? sizeof(WOp) : sizeof(SOp);
+    const size_t op_bytes = warp ? sizeof(WStep) : sizeof(SOp);
     hp->team_bytes = round16((size_t)stage * op_bytes + (size_t)hp->max_arena * elem);
     hp->smem = hp->table_bytes + (size_t)hp->n_teams * hp->team_bytes;
     return hp->smem <= max_dynamic;
   };
-  bool ok = warp_ok && layout(true, std::min<uint32_t>(max_ops, 128));
-  for (uint32_t stage = std::min<uint32_t>(max_ops, 64); !ok && stage >= 4; stage /= 2)
-    ok = layout(false, stage);
+  auto try_layout = [&](bool warp, uint32_t first) {
+    for (uint32_t stage = first;; stage /= 2) {
+      if (layout(warp, stage)) return true;
+      if (stage <= 4) return false;
+    }
+  };
+  bool ok = false;
+  if (warp_ok) {
+    // schedule each network's ops into warp steps (lane-packed bundles)
+    std::vector<TaskDev> wtasks = hp->tasks;
+    std::vector<WStep> wsteps;
+    uint32_t max_steps = 1;
+    for (TaskDev& t : wtasks) {
+      const std::vector<SOp> net_ops(hp->ops.begin() + t.op_begin,
+                                     hp->ops.begin() + t.op_begin + t.op_count);
+      const uint32_t begin = (uint32_t)wsteps.size();
+      build_warp_steps(net_ops, table_elems, t.arena_elems, wsteps);
+      t.op_begin = begin;
+      t.op_count = (uint32_t)wsteps.size() - begin;
+      max_steps = std::max(max_steps, t.op_count);
+    }
+    ok = try_layout(true, std::min<uint32_t>(max_steps, 128));
+    if (ok) {
+      hp->tasks = std::move(wtasks);
+      hp->wsteps = std::move(wsteps);
+      hp->ops.clear();
+    }
+  }
+  if (!ok) ok = try_layout(false, std::min<uint32_t>(max_ops, 64));
   if (!ok)
     fail(QTC_ERR_UNSUPPORTED, "program needs %zu bytes of shared memory (limit %zu)", hp->smem,
          max_dynamic);
-  if (hp->warp_teams) {
-    // expand the bit maps into per-lane byte offset tables
-    for (const SOp& op : hp->ops) {
-      WOp w{};
-      w.code = op.code;
-      w.rc = op.rc;
-      w.ry = op.ry;
-      w.out = (uint16_t)op.out;
-      w.in1 = (uint16_t)op.in1;
-      w.in2 = (uint16_t)op.in2;
-      w.slot = (uint16_t)op.out;
-      if (op.code == SOP_CONTRACT) {
-        auto deposit = [](const uint8_t* pos, int first, int count, uint32_t idx) {
-          uint32_t off = 0;
-          for (int i = 0; i < count; ++i)
-            if (((idx >> i) & 1u) && pos[first + i] != kAbsent) off |= 1u << pos[first + i];
-          return (uint8_t)off;
-        };
-        const int lo = std::min<int>(op.rc, 5), hi = std::max<int>(op.rc - 5, 0);
-        for (uint32_t c = 0; c < 32; ++c) {
-          w.a_lo[c] = deposit(op.p1, 0, lo, c);
-          w.b_lo[c] = deposit(op.p2, 0, lo, c);
-        }
-        for (uint32_t j = 0; j < 4; ++j) {
-          w.a_hi[j] = deposit(op.p1, 5, hi, j);
-          w.b_hi[j] = deposit(op.p2, 5, hi, j);
-        }
-        for (uint32_t y = 0; y < 16; ++y) {
-          w.ya[y] = deposit(op.y1, 0, op.ry, y);
-          w.yb[y] = deposit(op.y2, 0, op.ry, y);
-        }
-      }
-      hp->wops.push_back(w);
-    }
-    hp->ops.clear();
-  }
   b->host_programs.push_back(std::move(hp));
   return *b->host_programs.back();
 }
@@ -773,7 +763,7 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   auto* dg = (GateEntryDev*)e->alloc(sizeof(GateEntryDev) * G);
   auto* dt = (TaskDev*)e->alloc(sizeof(TaskDev) * hp.tasks.size());
   auto* dops = (SOp*)e->alloc(sizeof(SOp) * std::max<size_t>(1, hp.ops.size()));
-  auto* dwops = (WOp*)e->alloc(sizeof(WOp) * std::max<size_t>(1, hp.wops.size()));
+  auto* dwsteps = (WStep*)e->alloc(sizeof(WStep) * std::max<size_t>(1, hp.wsteps.size()));
   auto* dw = (double*)e->alloc(sizeof(double) * N);
   auto* dparams = (double*)e->alloc(sizeof(double) * std::max(P, 1));
   auto* dres = (double*)e->alloc(sizeof(double) * (size_t)N * (2 + 2 * P));
@@ -783,8 +773,10 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   cuda_check(cudaMemcpyAsync(dt, hp.tasks.data(), sizeof(TaskDev) * hp.tasks.size(), cudaMemcpyHostToDevice, stream), "upload tasks");
   if (!hp.ops.empty())
     cuda_check(cudaMemcpyAsync(dops, hp.ops.data(), sizeof(SOp) * hp.ops.size(), cudaMemcpyHostToDevice, stream), "upload ops");
-  if (!hp.wops.empty())
-    cuda_check(cudaMemcpyAsync(dwops, hp.wops.data(), sizeof(WOp) * hp.wops.size(), cudaMemcpyHostToDevice, stream), "upload warp ops");
+  if (!hp.wsteps.empty())
+    cuda_check(cudaMemcpyAsync(dwsteps, hp.wsteps.data(), sizeof(WStep) * hp.wsteps.size(),
+                               cudaMemcpyHostToDevice, stream),
+               "upload warp steps");
   cuda_check(cudaMemcpyAsync(dw, hp.weights.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream), "upload weights");
   cuda_check(cudaMemsetAsync(dcnt, 0, sizeof(unsigned int) * 4, stream), "clear counters");
   cuda_check(cudaStreamSynchronize(stream), "prepare sync");
@@ -797,7 +789,7 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   d.tasks = dt;
   d.n_tasks = (int)hp.tasks.size();
   d.ops = dops;
-  d.wops = dwops;
+  d.wsteps = dwsteps;
   d.n_params = P;
   d.n_nets = N;
   d.weights = dw;
@@ -877,7 +869,12 @@ extern "C" qtc_status qtc_batch_program_info(qtc_batch* b, int dtype, int want_g
       info->n_waves = 1;
       info->n_tasks = info->n_smem_tasks = (int)hp.tasks.size();
       tables += sizeof(TaskDev) * hp.tasks.size() + sizeof(SOp) * hp.ops.size() +
-                sizeof(WOp) * hp.wops.size();
+                sizeof(WStep) * hp.wsteps.size();
+      info->warp_teams = hp.warp_teams ? 1 : 0;
+      info->n_ops = (int)hp.ops.size();
+      info->n_warp_steps = (int)hp.wsteps.size();
+      for (const TaskDev& t : hp.tasks)
+        if (hp.warp_teams) info->max_warp_steps = std::max(info->max_warp_steps, (int)t.op_count);
     }
     info->table_bytes = tables;
   });

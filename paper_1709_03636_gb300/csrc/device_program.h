@@ -93,17 +93,60 @@ struct alignas(16) SOp {
 // at most 4 summed bits per op): the bit maps are pre-expanded into byte
 // offset tables.  Output element c = 32 j + lane of a CONTRACT reads
 // in1[a_lo[lane] | a_hi[j] | ya[y]] and in2[b_lo[lane] | b_hi[j] | yb[y]].
+// A CONTRACT flagged WOPF_LEAFGRAD produces dS/dleaf and also adds
+// sum_c out[c] * table[der + c] to the parameter gradient slot `slot` (the
+// leaf-gradient dot fused into the op that produces it).
 constexpr int kWarpMaxRank = 7;
 constexpr int kWarpMaxSummed = 4;
 
+enum WOpFlag : uint8_t { WOPF_LEAFGRAD = 1 };
+
 struct alignas(16) WOp {
-  uint8_t code, rc, ry, pad0;
-  uint16_t out, in1, in2, slot;   // element offsets (team relative), LEAFGRAD slot
-  uint8_t a_lo[32], b_lo[32];
+  uint8_t code, rc, ry, flags;
+  uint16_t out, in1, in2, slot;   // element offsets (team relative), gradient slot
+  uint16_t der, pad0;             // WOPF_LEAFGRAD: table offset of d(leaf)/dparam
   uint8_t a_hi[4], b_hi[4];
   uint8_t ya[16], yb[16];
-  uint8_t pad1[4];
+  uint8_t a_lo[32], b_lo[32];
+  uint8_t pad1[8];
 };
+static_assert(sizeof(WOp) == 128, "WOp is staged as eight 16-byte words");
+
+// Warp programs are sequences of steps.  A bundle step packs mutually
+// independent small ops into aligned lane groups of one warp (the host
+// schedules the op graph of the network; hazards are tracked per element):
+// each lane computes at most one output element with at most two summed
+// terms.  A solo step runs one WOp on the whole warp (outputs above 32
+// elements or more than one summed bit).
+enum WLaneKind : uint8_t { WL_IDLE = 0, WL_CONTRACT = 1, WL_RESULT = 2, WL_SEED = 3 };
+enum WLaneFlag : uint8_t {
+  WLF_STORE = 1,    // write the lane's output element
+  WLF_Y1 = 2,       // add the second summed term
+  WLF_LG_MUL = 4,   // leaf gradient: group-sum of out * d(leaf)/dparam into slot
+  WLF_LG_ADD = 8    // leaf gradient: group-sum of the product itself into slot
+};
+// Lane operand offsets: bit 15 set = gate table element, else team arena.
+constexpr uint16_t kWTable = 0x8000;
+// WStep::rounds bit 7: some lane adds a leaf gradient (low bits: rounds).
+constexpr uint8_t kWHasLeafGrad = 0x80;
+
+struct alignas(16) WLane {
+  uint8_t kind, flags, gw, slot;   // gw: log2 of the op's lane-group width
+  uint16_t c_off, a_off, b_off;    // output (arena), first-term operands
+  uint16_t der_off;                // WLF_LG_MUL: table offset of d(leaf)/dparam
+  uint16_t ya1, yb1;               // WLF_Y1: element deltas of the second term
+};
+
+struct alignas(16) WStep {
+  uint8_t solo;     // 1: `op` runs on the whole warp
+  uint8_t rounds;   // kWHasLeafGrad | shuffle rounds of the leaf-gradient group sums
+  uint8_t pad[14];
+  union {
+    WLane lane[32];
+    WOp op;
+  };
+};
+static_assert(sizeof(WStep) == 528, "WStep is staged as 33 16-byte words");
 
 struct TaskDev {
   uint32_t op_begin, op_count;
@@ -122,7 +165,7 @@ struct ProgramDev {
   const TaskDev* tasks;
   int n_tasks;
   const SOp* ops;              // CTA teams
-  const WOp* wops;             // warp teams
+  const WStep* wsteps;         // warp teams
   int n_params;
   int n_nets;
   const double* weights;       // per network, for <C>

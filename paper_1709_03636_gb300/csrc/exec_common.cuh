@@ -36,62 +36,72 @@ template <> __device__ __forceinline__ double2 from_d2<double2>(double2 v) { ret
 __device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
 __device__ __forceinline__ double2 to_d2(double2 v) { return v; }
 
+__device__ __forceinline__ void sincos_r(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_r(double x, double* s, double* c) { sincos(x, s, c); }
+
 // Values (and derivatives with respect to params[slot]) of one gate table
-// entry, element index bit k = label k (see LeafKind).
-__device__ inline void gate_tensor(const GateSpec& s, const double* params, double2* val,
-                            double2* der) {
+// entry, element index bit k = label k (see LeafKind), written straight into
+// val and der (der may be null: no derivative wanted).  The angle is formed in
+// FP64; sine and cosine are taken in the element precision (FP32 for
+// complex64: GB300's FP64 pipe is slow, and the tensor is stored in FP32).
+template <typename T>
+__device__ inline void gate_tensor(const GateSpec& s, const double* params, T* val, T* der_out) {
+  T scratch[16];
+  T* der = der_out ? der_out : scratch;
+  using R = decltype(T::x);
   const double theta = s.constant + (s.slot >= 0 ? s.coeff * params[s.slot] : 0.0);
-  const double dth = s.slot >= 0 ? s.coeff : 0.0;  // d theta / d param
+  const R dth = s.slot >= 0 ? (R)s.coeff : R(0);  // d theta / d param
   const int rank = leaf_rank_of(s.kind);
   const int n = 1 << rank;
   for (int i = 0; i < n; ++i) {
-    val[i] = make_double2(0.0, 0.0);
-    der[i] = make_double2(0.0, 0.0);
+    val[i] = T{R(0), R(0)};
+    der[i] = T{R(0), R(0)};
   }
-  const double r = 0.70710678118654752440;
-  double sh, ch;
-  sincos(0.5 * theta, &sh, &ch);
+  const R r = R(0.70710678118654752440);
+  const R half = R(0.5);
+  R sh, ch;
+  sincos_r((R)(0.5 * theta), &sh, &ch);
   switch (s.kind) {
-    case LK_ZERO: case LK_PROJ0: val[0].x = 1.0; break;
-    case LK_PROJ1: val[1].x = 1.0; break;
+    case LK_ZERO: case LK_PROJ0: val[0].x = R(1); break;
+    case LK_PROJ1: val[1].x = R(1); break;
     case LK_PLUS: val[0].x = r; val[1].x = r; break;
-    case LK_ZDIAG: val[0].x = 1.0; val[1].x = -1.0; break;
+    case LK_ZDIAG: val[0].x = R(1); val[1].x = R(-1); break;
     case LK_H:
       for (int i = 0; i < 4; ++i) val[i].x = (i == 3) ? -r : r;
       break;
-    case LK_X: case LK_OBS_X: val[2].x = 1.0; val[1].x = 1.0; break;
+    case LK_X: case LK_OBS_X: val[2].x = R(1); val[1].x = R(1); break;
     case LK_Y: case LK_OBS_Y:
-      val[2].y = -1.0;  // [0][1] = -i  (index out=0 | in=1 << 1)
-      val[1].y = 1.0;   // [1][0] = +i
+      val[2].y = R(-1);  // [0][1] = -i  (index out=0 | in=1 << 1)
+      val[1].y = R(1);   // [1][0] = +i
       break;
-    case LK_Z: case LK_OBS_Z: val[0].x = 1.0; val[3].x = -1.0; break;
+    case LK_Z: case LK_OBS_Z: val[0].x = R(1); val[3].x = R(-1); break;
     case LK_RX:  // cos(t/2) I - i sin(t/2) X, [out, in]
       val[0].x = ch; val[3].x = ch; val[1].y = -sh; val[2].y = -sh;
-      der[0].x = -0.5 * sh * dth; der[3].x = -0.5 * sh * dth;
-      der[1].y = -0.5 * ch * dth; der[2].y = -0.5 * ch * dth;
+      der[0].x = -half * sh * dth; der[3].x = -half * sh * dth;
+      der[1].y = -half * ch * dth; der[2].y = -half * ch * dth;
       break;
     case LK_RZ: case LK_RZDIAG: {
       // diag(exp(-i t/2), exp(+i t/2)); dense form at [0][0] and [1][1]
       const int i1 = s.kind == LK_RZ ? 3 : 1;
-      val[0] = make_double2(ch, -sh);
-      val[i1] = make_double2(ch, sh);
-      der[0] = make_double2(-0.5 * sh * dth, -0.5 * ch * dth);
-      der[i1] = make_double2(-0.5 * sh * dth, 0.5 * ch * dth);
+      val[0] = T{ch, -sh};
+      val[i1] = T{ch, sh};
+      der[0] = T{-half * sh * dth, -half * ch * dth};
+      der[i1] = T{-half * sh * dth, half * ch * dth};
       break;
     }
     case LK_ZZDIAG: case LK_ZZ:
       for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) {
-          const double zz = (a == b) ? 1.0 : -1.0;  // z_a z_b
+          const R zz = (a == b) ? R(1) : R(-1);  // z_a z_b
           const int idx = s.kind == LK_ZZDIAG ? (a | b << 1) : (a | b << 1 | a << 2 | b << 3);
-          val[idx] = make_double2(ch, -zz * sh);  // exp(-i zz t/2)
+          val[idx] = T{ch, -zz * sh};  // exp(-i zz t/2)
           // d/dt = -i zz/2 * value
-          der[idx] = make_double2(-0.5 * sh * dth, -0.5 * zz * ch * dth);
+          der[idx] = T{-half * sh * dth, -half * zz * ch * dth};
         }
       break;
     case LK_CNOT:
       for (int c = 0; c < 2; ++c)
-        for (int t = 0; t < 2; ++t) val[c | (t ^ c) << 1 | c << 2 | t << 3].x = 1.0;
+        for (int t = 0; t < 2; ++t) val[c | (t ^ c) << 1 | c << 2 | t << 3].x = R(1);
       break;
     default: break;
   }
@@ -100,6 +110,155 @@ __device__ inline void gate_tensor(const GateSpec& s, const double* params, doub
       val[i].y = -val[i].y;
       der[i].y = -der[i].y;
     }
+}
+
+// Writes every gate table entry (values, and derivatives for parameterised
+// entries) into the table at the start of shared memory; all threads of the
+// CTA take part.
+template <typename T>
+__device__ __forceinline__ void build_gate_table(const GateEntryDev* gates, int n_gates,
+                                                 const double* params, T* table) {
+  for (int e = threadIdx.x; e < n_gates; e += blockDim.x) {
+    const GateEntryDev g = gates[e];
+    gate_tensor<T>(g.spec, params, table + g.val_off,
+                   g.spec.slot >= 0 ? table + g.der_off : nullptr);
+  }
+}
+
+// Sum of v over aligned groups of `width` lanes (a power of two <= 32); every
+// lane of the group receives it.
+template <typename T>
+__device__ __forceinline__ T warp_csum(T v, uint32_t width) {
+  for (uint32_t off = 1; off < width; off <<= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+  }
+  return v;
+}
+
+// One warp: grad[2 slot], grad[2 slot + 1] += sum_j g[j] * d[j] over cnt
+// terms (at most 16 for a leaf), in the element precision.  grad holds one
+// network's partial derivatives; the sums over networks are taken in FP64.
+template <typename T, typename G>
+__device__ __forceinline__ void warp_leaf_dot(const T* g, const T* d, uint32_t cnt,
+                                              uint32_t lane, G* grad, uint32_t slot) {
+  T acc = czero<T>();
+  for (uint32_t j = lane; j < cnt; j += 32) acc = cfma(g[j], d[j], acc);
+  acc = warp_csum(acc, cnt < 32 ? cnt : 32u);
+  if (lane == 0) {
+    grad[2 * slot] += (G)acc.x;
+    grad[2 * slot + 1] += (G)acc.y;
+  }
+}
+
+// Explicit shared-memory accesses on 32-bit shared addresses (the warp
+// program loop addresses its operands this way, never through generic
+// pointers).  Ordered with respect to barriers and each other.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint4 lds_u4(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(a)
+               : "memory");
+  return v;
+}
+template <typename T> __device__ __forceinline__ T lds_c(uint32_t a);
+template <> __device__ __forceinline__ float2 lds_c<float2>(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+  return v;
+}
+template <> __device__ __forceinline__ double2 lds_c<double2>(uint32_t a) {
+  double2 v;
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts_c(uint32_t a, float2 v) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void sts_c(uint32_t a, double2 v) {
+  asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v.x), "d"(v.y) : "memory");
+}
+
+// 16-byte asynchronous global -> shared copy (L2 only) and the wait for all
+// of this thread's outstanding copies.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Adds one to a counter with acquire-release semantics at GPU scope and
+// returns the old value.  Called by one thread after a CTA barrier, it
+// publishes the writes of the whole CTA (the barrier orders them before it)
+// and, for the CTA that sees the last count, makes every other CTA's
+// published writes visible.
+__device__ __forceinline__ unsigned atomic_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
+               : "memory");
+  return old;
+}
+
+constexpr int kReduceThreads = 128;   // threads of the final reduction
+
+// Final reduction of the last CTA (threads < kReduceThreads take part; all
+// threads of the CTA must call it): <C> = sum_e w_e (1 - Re s_e)/2 and
+// d<C>/dparam_q = -1/2 sum_e w_e Re ds_e/dparam_q (Section 4.1), in FP64, one
+// pass over the per-network rows (stride 2 + 2P: s_e, then ds_e/dparam as
+// complex pairs).  out = [<C>, gradient (P), Re s_e per network (N)].
+// s_part holds (1 + P) * kReduceThreads / 32 doubles.
+__device__ inline void reduce_network_rows(const volatile double* res, const double* weights,
+                                           int N, int P, bool qaoa_reduce, double* out,
+                                           double* s_part) {
+  constexpr int kW = kReduceThreads / 32;
+  const int stride = 2 + 2 * P;
+  const int nq = 1 + P;
+  const int tid = threadIdx.x;
+  if (tid < kReduceThreads) {
+    for (int q0 = 0; q0 < nq; q0 += 8) {
+      double part[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) part[i] = 0.0;
+      for (int e = tid; e < N; e += kReduceThreads) {
+        const double w = weights[e];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int q = q0 + i;
+          if (q == 0)
+            part[i] += w * 0.5 * (1.0 - res[(size_t)e * stride]);
+          else if (q < nq)
+            part[i] += -0.5 * w * res[(size_t)e * stride + 2 + 2 * (q - 1)];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (q0 + i >= nq) break;
+        double v = part[i];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if ((tid & 31) == 0) s_part[(q0 + i) * kW + tid / 32] = v;
+      }
+    }
+    for (int e = tid; e < N; e += kReduceThreads) out[1 + P + e] = res[(size_t)e * stride];
+  }
+  __syncthreads();
+  for (int q = tid; q < nq; q += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < kW; ++w) t += s_part[q * kW + w];
+    out[q] = qaoa_reduce ? t : 0.0;
+  }
 }
 
 // A team is one warp (small networks, kWarp) or the whole CTA.

@@ -137,24 +137,8 @@ __device__ void run_smem_task(const GraphProgDev& prog, const GTask& task, T* ta
           contract_op<T>(op, out, in1, in2, team);
           break;
         case SOP_LEAFGRAD:
-          if (team.tid < 32) {
-            const uint32_t cnt = 1u << op.rc;
-            double2 acc = make_double2(0.0, 0.0);
-            for (uint32_t j = team.tid; j < cnt; j += 32) {
-              const double2 g = to_d2(in1[j]);
-              const double2 d = to_d2(in2[j]);
-              acc.x += g.x * d.x - g.y * d.y;
-              acc.y += g.x * d.y + g.y * d.x;
-            }
-            for (int off = 16; off > 0; off >>= 1) {
-              acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
-              acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
-            }
-            if (team.tid == 0) {
-              s_grad[2 * op.out] += acc.x;
-              s_grad[2 * op.out + 1] += acc.y;
-            }
-          }
+          if (team.tid < 32)
+            warp_leaf_dot<T>(in1, in2, 1u << op.rc, team.tid, s_grad, op.out);
           break;
         case SOP_RESULT:
           if (team.tid == 0) {
@@ -539,12 +523,11 @@ template <typename T, bool kTc>
 __global__ void __launch_bounds__(kGraphBlock*(kTc ? 4 : 1))
     graph_exec_kernel(const GraphProgDev prog) {
   constexpr int kTeams = kTc ? 4 : 1;
-  constexpr int kBlock = kGraphBlock * kTeams;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ GStep s_step[kTeams];
   __shared__ TStep s_tstep[kTc ? kTeams : 1];
   __shared__ double s_grad[kTeams][2 * kMaxParams];
-  __shared__ double s_red[kBlock];
+  __shared__ double s_red[(1 + kMaxParams) * kReduceThreads / 32];
   __shared__ unsigned int s_task[kTeams];
   __shared__ int s_flag[kTeams];
   __shared__ int s_last[kTeams];
@@ -574,16 +557,7 @@ __global__ void __launch_bounds__(kGraphBlock*(kTc ? 4 : 1))
     }
     tc_fence_before();
   }
-  for (int e = threadIdx.x; e < prog.n_gates; e += blockDim.x) {
-    const GateEntryDev g = prog.gates[e];
-    double2 val[16], der[16];
-    gate_tensor(g.spec, prog.params, val, der);
-    const int n = 1 << g.rank;
-    for (int i = 0; i < n; ++i) {
-      table[g.val_off + i] = from_d2<T>(val[i]);
-      if (g.spec.slot >= 0) table[g.der_off + i] = from_d2<T>(der[i]);
-    }
-  }
+  build_gate_table<T>(prog.gates, prog.n_gates, prog.params, table);
   __syncthreads();
   if (kTc && prog.tmem_cols > 0) {
     tc_fence_after();
@@ -647,26 +621,7 @@ __global__ void __launch_bounds__(kGraphBlock*(kTc ? 4 : 1))
     const int N = prog.n_nets;
     const int stride = 2 + 2 * P;
     const volatile double* res = prog.results;
-    for (int q = 0; q < 1 + P; ++q) {
-      double part = 0.0;
-      for (int e = threadIdx.x; e < N; e += blockDim.x) {
-        const double w = prog.weights[e];
-        if (q == 0)
-          part += w * 0.5 * (1.0 - res[(size_t)e * stride]);
-        else
-          part += -0.5 * w * res[(size_t)e * stride + 2 + 2 * (q - 1)];
-      }
-      s_red[threadIdx.x] = part;
-      __syncthreads();
-      for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-        if (threadIdx.x < off) s_red[threadIdx.x] += s_red[threadIdx.x + off];
-        __syncthreads();
-      }
-      if (threadIdx.x == 0) prog.out[q] = prog.qaoa_reduce ? s_red[0] : 0.0;
-      __syncthreads();
-    }
-    for (int e = threadIdx.x; e < N; e += blockDim.x)
-      prog.out[1 + P + e] = res[(size_t)e * stride];
+    reduce_network_rows(res, prog.weights, N, P, prog.qaoa_reduce != 0, prog.out, s_red);
     if (threadIdx.x == 0) prog.out[1 + P + N] = (double)err;
     if (prog.raw_out)
       for (int i = threadIdx.x; i < N * stride; i += blockDim.x) prog.raw_out[i] = res[i];

@@ -21,166 +21,284 @@ namespace qtc {
 constexpr int kMaxTeams = 8;
 
 // One CONTRACT op of a warp team from its pre-expanded offset tables: lane
-// handles outputs c = 32 j + lane.
+// handles outputs c = 32 j + lane.  The op's tables are read with 16-byte
+// loads up front; ops with zero or one summed bit (most of them) take
+// straight-line paths whose operand loads issue together.  With WOPF_LEAFGRAD the op also adds sum_c out[c] * der[c] to the
+// parameter gradient (the leaf-gradient dot of the adjoint, fused).
 template <typename T>
-__device__ __forceinline__ void warp_contract(const WOp& op, T* out, const T* a, const T* b,
-                                              uint32_t lane) {
-  const uint32_t nout = 1u << op.rc, ny = 1u << op.ry;
+__device__ __forceinline__ void warp_contract(const WOp& op, const uint4 head, T* out,
+                                              const T* a, const T* b, const T* table,
+                                              decltype(T::x)* grad, uint32_t lane) {
+  const uint32_t rc = (head.x >> 8) & 0xffu, ry = (head.x >> 16) & 0xffu;
+  const bool leafgrad = ((head.x >> 24) & WOPF_LEAFGRAD) != 0;
+  const uint32_t nout = 1u << rc, ny = 1u << ry;
+  const uint4 hy = *reinterpret_cast<const uint4*>(&op.a_hi[0]);  // a_hi, b_hi, ya[0..7]
+  const uint4 hy2 = *reinterpret_cast<const uint4*>(&op.ya[8]);   // ya[8..15], yb[0..7]
+  const uint2 hy3 = *reinterpret_cast<const uint2*>(&op.yb[8]);   // yb[8..15]
   const uint32_t alo = op.a_lo[lane], blo = op.b_lo[lane];
+  T dot = czero<T>();
   for (uint32_t j = 0; 32 * j < nout; ++j) {
     const uint32_t c = 32 * j + lane;
-    if (c >= nout) break;
-    const uint32_t oa = alo | op.a_hi[j], ob = blo | op.b_hi[j];
-    T acc = czero<T>();
-    for (uint32_t y = 0; y < ny; ++y) acc = cfma(a[oa | op.ya[y]], b[ob | op.yb[y]], acc);
-    out[c] = acc;
+    const uint32_t oa = alo | ((hy.x >> (8 * j)) & 0xffu);
+    const uint32_t ob = blo | ((hy.y >> (8 * j)) & 0xffu);
+    T acc;
+    if (ry == 0) {  // a product (batch and free labels only)
+      acc = cfma(a[oa], b[ob], czero<T>());
+    } else if (ry == 1) {
+      const uint32_t ay = (hy.z >> 8) & 0xffu, by = (hy2.z >> 8) & 0xffu;
+      const T a0 = a[oa], b0 = b[ob], a1 = a[oa | ay], b1 = b[ob | by];
+      acc = cfma(a1, b1, cfma(a0, b0, czero<T>()));
+    } else {
+      const uint64_t yal = ((uint64_t)hy.w << 32) | hy.z, yah = ((uint64_t)hy2.y << 32) | hy2.x;
+      const uint64_t ybl = ((uint64_t)hy2.w << 32) | hy2.z, ybh = ((uint64_t)hy3.y << 32) | hy3.x;
+      acc = czero<T>();
+      for (uint32_t y = 0; y < ny; ++y) {
+        const uint32_t ay = (uint32_t)(((y < 8 ? yal : yah) >> (8 * (y & 7))) & 0xffu);
+        const uint32_t by = (uint32_t)(((y < 8 ? ybl : ybh) >> (8 * (y & 7))) & 0xffu);
+        acc = cfma(a[oa | ay], b[ob | by], acc);
+      }
+    }
+    if (c < nout) {
+      out[c] = acc;
+      if (leafgrad) dot = cfma(acc, table[(head.w & 0xffffu) + c], dot);
+    }
+  }
+  if (leafgrad) {
+    dot = warp_csum(dot, nout < 32 ? nout : 32u);
+    if (lane == 0) {
+      const uint32_t slot = head.z >> 16;
+      grad[2 * slot] += dot.x;
+      grad[2 * slot + 1] += dot.y;
+    }
   }
 }
 
-__device__ __forceinline__ uint32_t op_slot(const WOp& op) { return op.slot; }
-__device__ __forceinline__ uint32_t op_slot(const SOp& op) { return op.out; }
+// Parameter slots whose leaf-gradient terms a warp team accumulates in
+// registers (per lane; summed over the warp once per network).
+constexpr int kRegSlots = 8;
+
+// One bundle step of a warp program: every lane computes its own output
+// element (one or two summed terms, Eq. 1) of the op its lane group belongs
+// to.  Leaf-gradient lanes form out * d(leaf)/dparam (or the plain product);
+// with few parameters each lane adds its term to its own register
+// accumulator of the slot, otherwise the lane group sums with shuffles and
+// its first lane adds the sum to the slot in shared memory.
+template <typename T>
+__device__ __forceinline__ void warp_bundle(const uint4 L, uint32_t rounds, uint32_t table_s,
+                                            uint32_t arena_s, decltype(T::x)* grad,
+                                            decltype(T::x) (&racc)[2 * kRegSlots], bool reg_grad,
+                                            double* res_row, uint32_t lane) {
+  constexpr uint32_t kE = sizeof(T);
+  const uint32_t kind = L.x & 0xffu, flags = (L.x >> 8) & 0xffu;
+  const uint32_t gw = (L.x >> 16) & 0xffu, slot = L.x >> 24;
+  const uint32_t a_off = L.y >> 16, b_off = L.z & 0xffffu;
+  const uint32_t pa = ((a_off & kWTable) ? table_s : arena_s) + (a_off & 0x7fffu) * kE;
+  const uint32_t pb = ((b_off & kWTable) ? table_s : arena_s) + (b_off & 0x7fffu) * kE;
+  const T a0 = lds_c<T>(pa), b0 = lds_c<T>(pb);
+  T acc = cfma(a0, b0, czero<T>());
+  if (flags & WLF_Y1)
+    acc = cfma(lds_c<T>(pa + (L.w & 0xffffu) * kE), lds_c<T>(pb + (L.w >> 16) * kE), acc);
+  if (kind == WL_SEED) acc = from_d2<T>(make_double2(1.0, 0.0));
+  if (flags & WLF_STORE) sts_c(arena_s + (L.y & 0xffffu) * kE, acc);
+  if (kind == WL_RESULT) {
+    const double2 v = to_d2(a0);
+    res_row[0] = v.x;
+    res_row[1] = v.y;
+  }
+  if (rounds & kWHasLeafGrad) {
+    T v = czero<T>();
+    if (flags & WLF_LG_MUL) v = cfma(acc, lds_c<T>(table_s + (L.z >> 16) * kE), v);
+    else if (flags & WLF_LG_ADD) v = acc;
+    if (reg_grad) {
+#pragma unroll
+      for (uint32_t q = 0; q < (uint32_t)kRegSlots; ++q)
+        if (q == slot) {
+          racc[2 * q] += v.x;
+          racc[2 * q + 1] += v.y;
+        }
+      return;
+    }
+    for (uint32_t r = 0; r < (rounds & 0x7fu); ++r) {
+      const decltype(T::x) ox = __shfl_xor_sync(0xffffffffu, v.x, 1u << r);
+      const decltype(T::x) oy = __shfl_xor_sync(0xffffffffu, v.y, 1u << r);
+      if (r < gw) {
+        v.x += ox;
+        v.y += oy;
+      }
+    }
+    if ((flags & (WLF_LG_MUL | WLF_LG_ADD)) && (lane & ((1u << gw) - 1u)) == 0) {
+      atomicAdd(&grad[2 * slot], v.x);
+      atomicAdd(&grad[2 * slot + 1], v.y);
+    }
+  }
+}
 
 template <typename T, bool kWarp>
 __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
+  using R = decltype(T::x);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double s_grad[kMaxTeams][2 * kMaxParams];
+  // one network's partial derivatives per team, in the element precision
+  __shared__ R s_grad[kMaxTeams][2 * kMaxParams];
   __shared__ unsigned int s_task[kMaxTeams];
   __shared__ int s_last;
-  __shared__ double s_red[256];
+  __shared__ double s_part[(1 + kMaxParams) * kReduceThreads / 32];
   T* table = reinterpret_cast<T*>(smem_raw);
 
-  // gate table (leaf values) in FP64, stored in the contraction type
-  for (int e = threadIdx.x; e < prog.n_gates; e += blockDim.x) {
-    const GateEntryDev g = prog.gates[e];
-    double2 val[16], der[16];
-    gate_tensor(g.spec, prog.params, val, der);
-    const int n = 1 << g.rank;
-    for (int i = 0; i < n; ++i) {
-      table[g.val_off + i] = from_d2<T>(val[i]);
-      if (g.spec.slot >= 0) table[g.der_off + i] = from_d2<T>(der[i]);
-    }
-  }
-  __syncthreads();
-
-  using OpT = typename std::conditional<kWarp, WOp, SOp>::type;
+  using OpT = typename std::conditional<kWarp, WStep, SOp>::type;
   const Team<kWarp> team;
+  const int teams_per_cta = blockDim.x / team.size;
   unsigned char* team_base = smem_raw + prog.table_bytes + (size_t)team.id * prog.team_bytes;
   OpT* stage = reinterpret_cast<OpT*>(team_base);
   T* arena = reinterpret_cast<T*>(team_base + (size_t)prog.stage_ops * sizeof(OpT));
-  const OpT* ops = kWarp ? reinterpret_cast<const OpT*>(prog.wops)
+  const OpT* ops = kWarp ? reinterpret_cast<const OpT*>(prog.wsteps)
                          : reinterpret_cast<const OpT*>(prog.ops);
-  double* grad = s_grad[team.id];
+  R* grad = s_grad[team.id];
   const int P = prog.n_params;
   const int stride = 2 + 2 * P;
   constexpr int kWords = sizeof(OpT) / sizeof(uint4);
-  for (;;) {
-    if (team.tid == 0) s_task[team.id] = atomicAdd(&prog.counters[0], 1u);
-    for (int i = team.tid; i < 2 * P; i += team.size) grad[i] = 0.0;
-    team.sync();
-    const unsigned int t = s_task[team.id];
-    if (t >= (unsigned)prog.n_tasks) break;
-    const TaskDev task = prog.tasks[t];
+  const uint32_t stage_s = smem_u32(stage), table_s = smem_u32(table), arena_s = smem_u32(arena);
+
+  // Each team's first network is fixed by its position (no queue round
+  // trip); its first op chunk is copied asynchronously while the gate table
+  // (leaf values and derivatives) is built.  Later networks come from the
+  // queue, numbered after the statically assigned ones.
+  unsigned int t = blockIdx.x * teams_per_cta + team.id;
+  TaskDev task{};
+  if (t < (unsigned)prog.n_tasks) {
+    task = prog.tasks[t];
+    const uint32_t n = min(prog.stage_ops, task.op_count);
+    const uint4* src = reinterpret_cast<const uint4*>(ops + task.op_begin);
+    uint4* dst = reinterpret_cast<uint4*>(stage);
+    for (uint32_t w = team.tid; w < n * kWords; w += team.size) cp_async16(dst + w, src + w);
+  }
+  build_gate_table<T>(prog.gates, prog.n_gates, prog.params, table);
+  cp_async_wait_all();
+  __syncthreads();
+  bool staged = true;
+  const bool reg_grad = kWarp && P <= kRegSlots;
+  R racc[2 * kRegSlots];
+  while (t < (unsigned)prog.n_tasks) {
+    for (int i = team.tid; i < 2 * P; i += team.size) grad[i] = R(0);
+#pragma unroll
+    for (int i = 0; i < 2 * kRegSlots; ++i) racc[i] = R(0);
     for (uint32_t base = 0; base < task.op_count; base += prog.stage_ops) {
-      // stage a chunk of the op list with one cooperative copy
       const uint32_t n = min(prog.stage_ops, task.op_count - base);
-      const uint4* src = reinterpret_cast<const uint4*>(ops + task.op_begin + base);
-      uint4* dst = reinterpret_cast<uint4*>(stage);
-      for (uint32_t w = team.tid; w < n * kWords; w += team.size) dst[w] = src[w];
+      if (!staged) {
+        // stage a chunk of the op list with one cooperative copy
+        team.sync();
+        const uint4* src = reinterpret_cast<const uint4*>(ops + task.op_begin + base);
+        uint4* dst = reinterpret_cast<uint4*>(stage);
+        for (uint32_t w = team.tid; w < n * kWords; w += team.size) dst[w] = src[w];
+      }
+      staged = false;
       team.sync();
+      // warp programs: the next step's header and this lane's descriptor are
+      // loaded while the current step runs
+      uint32_t h_next = 0;
+      uint4 l_next = make_uint4(0, 0, 0, 0);
+      if (kWarp) {
+        h_next = lds_u32(stage_s);
+        l_next = lds_u4(stage_s + 16 + 16 * team.tid);
+      }
       for (uint32_t k = 0; k < n; ++k) {
         const OpT& op = stage[k];
-        switch (op.code) {
-          case SOP_CONTRACT:
-            if constexpr (kWarp) {
-              warp_contract<T>(op, resolve<T>(op.out, table, arena, prog.table_elems),
-                               resolve<T>(op.in1, table, arena, prog.table_elems),
-                               resolve<T>(op.in2, table, arena, prog.table_elems), team.tid);
-            } else {
+        if constexpr (kWarp) {
+          const uint32_t h = h_next;  // solo | rounds << 8
+          const uint4 L = l_next;
+          if (k + 1 < n) {
+            const uint32_t nxt = stage_s + (k + 1) * (uint32_t)sizeof(WStep);
+            h_next = lds_u32(nxt);
+            l_next = lds_u4(nxt + 16 + 16 * team.tid);
+          }
+          if (!(h & 0xffu)) {
+            warp_bundle<T>(L, (h >> 8) & 0xffu, table_s, arena_s, grad, racc, reg_grad,
+                           prog.results + (size_t)task.net * stride, team.tid);
+          } else {
+            // solo step; header word: code, rc, ry, flags | out, in1 | in2, slot | der
+            const WOp& w = op.op;
+            const uint4 head = *reinterpret_cast<const uint4*>(&w);
+            const uint32_t code = head.x & 0xffu;
+            T* out = resolve<T>(head.y & 0xffffu, table, arena, prog.table_elems);
+            T* in1 = resolve<T>(head.y >> 16, table, arena, prog.table_elems);
+            T* in2 = resolve<T>(head.z & 0xffffu, table, arena, prog.table_elems);
+            if (code == SOP_CONTRACT) {
+              warp_contract<T>(w, head, out, in1, in2, table, grad, team.tid);
+            } else if (code == SOP_LEAFGRAD) {
+              warp_leaf_dot<T>(in1, in2, 1u << ((head.x >> 8) & 0xffu), team.tid, grad,
+                               head.z >> 16);
+            } else if (code == SOP_RESULT) {
+              if (team.tid == 0) {
+                const double2 v = to_d2(*in1);
+                prog.results[(size_t)task.net * stride] = v.x;
+                prog.results[(size_t)task.net * stride + 1] = v.y;
+              }
+            } else if (code == SOP_SEED) {
+              if (team.tid == 0) *out = from_d2<T>(make_double2(1.0, 0.0));
+            }
+          }
+        } else {
+          switch (op.code) {
+            case SOP_CONTRACT:
               contract_op<T>(op, resolve(op.out, table, arena, prog.table_elems),
                              resolve(op.in1, table, arena, prog.table_elems),
                              resolve(op.in2, table, arena, prog.table_elems), team);
-            }
-            break;
-          case SOP_LEAFGRAD:
-            if (threadIdx.x % team.size < 32) {
-              const T* g = resolve(op.in1, table, arena, prog.table_elems);
-              const T* d = resolve(op.in2, table, arena, prog.table_elems);
-              const uint32_t cnt = 1u << op.rc;
-              double2 acc = make_double2(0.0, 0.0);
-              for (uint32_t j = threadIdx.x & 31; j < cnt; j += 32) {
-                const double2 gj = to_d2(g[j]);
-                const double2 dj = to_d2(d[j]);
-                acc.x += gj.x * dj.x - gj.y * dj.y;
-                acc.y += gj.x * dj.y + gj.y * dj.x;
+              break;
+            case SOP_LEAFGRAD:
+              if (team.tid < 32)
+                warp_leaf_dot<T>(resolve(op.in1, table, arena, prog.table_elems),
+                                 resolve(op.in2, table, arena, prog.table_elems), 1u << op.rc,
+                                 team.tid, grad, op.out);
+              break;
+            case SOP_RESULT:
+              if (team.tid == 0) {
+                const double2 v = to_d2(*resolve(op.in1, table, arena, prog.table_elems));
+                prog.results[(size_t)task.net * stride] = v.x;
+                prog.results[(size_t)task.net * stride + 1] = v.y;
               }
-              for (int off = 16; off > 0; off >>= 1) {
-                acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
-                acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
-              }
-              if ((threadIdx.x & 31) == 0) {
-                const uint32_t slot = kWarp ? op_slot(op) : op.out;
-                grad[2 * slot] += acc.x;
-                grad[2 * slot + 1] += acc.y;
-              }
-            }
-            break;
-          case SOP_RESULT:
-            if (team.tid == 0) {
-              const double2 v = to_d2(*resolve(op.in1, table, arena, prog.table_elems));
-              prog.results[(size_t)task.net * stride] = v.x;
-              prog.results[(size_t)task.net * stride + 1] = v.y;
-            }
-            break;
-          case SOP_SEED:
-            if (team.tid == 0)
-              *resolve(op.out, table, arena, prog.table_elems) =
-                  from_d2<T>(make_double2(1.0, 0.0));
-            break;
-          default:
-            break;
+              break;
+            case SOP_SEED:
+              if (team.tid == 0)
+                *resolve(op.out, table, arena, prog.table_elems) =
+                    from_d2<T>(make_double2(1.0, 0.0));
+              break;
+            default:
+              break;
+          }
         }
         team.sync();
       }
     }
+    if (reg_grad) {
+      // sum the lanes' register accumulators into the network's slots
+#pragma unroll
+      for (int i = 0; i < 2 * kRegSlots; ++i) {
+        if (i >= 2 * P) break;
+        R v = racc[i];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (team.tid == 0) grad[i] += v;
+      }
+      team.sync();
+    }
     for (int i = team.tid; i < 2 * P; i += team.size)
-      prog.results[(size_t)task.net * stride + 2 + i] = prog.want_grad ? grad[i] : 0.0;
+      prog.results[(size_t)task.net * stride + 2 + i] = prog.want_grad ? (double)grad[i] : 0.0;
+    // networks beyond the statically assigned ones come from the queue
+    const unsigned int n_static = gridDim.x * teams_per_cta;
+    if (n_static >= (unsigned)prog.n_tasks) break;
+    if (team.tid == 0) s_task[team.id] = n_static + atomicAdd(&prog.counters[0], 1u);
     team.sync();
+    t = s_task[team.id];
+    if (t < (unsigned)prog.n_tasks) task = prog.tasks[t];
   }
 
   // the last CTA reduces in FP64 and re-arms the counters
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned int done = atomicAdd(&prog.counters[1], 1u);
-    s_last = (done == gridDim.x - 1);
-  }
+  if (threadIdx.x == 0) s_last = atomic_add_acq_rel(&prog.counters[1], 1u) == gridDim.x - 1;
   __syncthreads();
   if (!s_last) return;
-  __threadfence();
-  const int N = prog.n_nets;
-  const volatile double* res = prog.results;
-  // quantities: q = 0 -> <C>, q = 1 + k -> d<C>/dparam_k
-  for (int q = 0; q < 1 + P; ++q) {
-    double part = 0.0;
-    for (int e = threadIdx.x; e < N; e += blockDim.x) {
-      const double w = prog.weights[e];
-      if (q == 0)
-        part += w * 0.5 * (1.0 - res[(size_t)e * stride]);
-      else
-        part += -0.5 * w * res[(size_t)e * stride + 2 + 2 * (q - 1)];
-    }
-    s_red[threadIdx.x] = part;
-    __syncthreads();
-    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-      if (threadIdx.x < off) s_red[threadIdx.x] += s_red[threadIdx.x + off];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) prog.out[q] = prog.qaoa_reduce ? s_red[0] : 0.0;
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < N; e += blockDim.x) prog.out[1 + P + e] = res[(size_t)e * stride];
-  if (threadIdx.x == 0) prog.out[1 + P + N] = 0.0;  // status: this executor never waits
+  reduce_network_rows(prog.results, prog.weights, prog.n_nets, P, prog.qaoa_reduce != 0,
+                      prog.out, s_part);
   if (threadIdx.x == 0) {
+    prog.out[1 + P + prog.n_nets] = 0.0;  // status: this executor never waits
     prog.counters[0] = 0;
     prog.counters[1] = 0;
   }

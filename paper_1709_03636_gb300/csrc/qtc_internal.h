@@ -145,6 +145,11 @@ struct LoweredNet {
 
 // Lowers one plan to a shared-memory op program.  table_elems: size of the
 // gate value + derivative region that precedes the arena.
+// One network's shared-memory ops as warp steps (lane-packed bundles of
+// independent small ops, solo steps for the rest), appended to `out`.
+void build_warp_steps(const std::vector<SOp>& ops, uint32_t table_elems, uint32_t arena_elems,
+                      std::vector<WStep>& out);
+
 LoweredNet lower_smem(const Plan& plan, const std::vector<int>& leaf_gate,
                       const std::vector<uint32_t>& gate_val_off,
                       const std::vector<uint32_t>& gate_der_off,
@@ -222,7 +227,7 @@ struct HostProgram {
   std::vector<GateEntryDev> gates;
   std::vector<TaskDev> tasks;
   std::vector<SOp> ops;            // CTA teams (empty for warp teams)
-  std::vector<WOp> wops;           // warp teams
+  std::vector<WStep> wsteps;       // warp teams
   std::vector<double> weights;
   uint32_t table_elems = 0, max_arena = 0;
   uint32_t table_bytes = 0;        // gate table region, 16-byte rounded

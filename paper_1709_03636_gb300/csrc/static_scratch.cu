@@ -74,8 +74,8 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
     const size_t o_gates = 0;
     const size_t o_tasks = align256(o_gates + sizeof(GateEntryDev) * G);
     const size_t o_ops = align256(o_tasks + sizeof(TaskDev) * hp.tasks.size());
-    const size_t o_wops = align256(o_ops + sizeof(SOp) * hp.ops.size());
-    const size_t o_weights = align256(o_wops + sizeof(WOp) * hp.wops.size());
+    const size_t o_wsteps = align256(o_ops + sizeof(SOp) * hp.ops.size());
+    const size_t o_weights = align256(o_wsteps + sizeof(WStep) * hp.wsteps.size());
     const size_t o_results = align256(o_weights + sizeof(double) * N);
     const size_t o_counters = align256(o_results + sizeof(double) * (size_t)N * (2 + 2 * P));
     const size_t total = o_counters + sizeof(unsigned int) * 4;
@@ -96,8 +96,9 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
       if (!hp.ops.empty())
         cuda_check(cudaMemcpyAsync(base + o_ops, hp.ops.data(), sizeof(SOp) * hp.ops.size(),
                                    cudaMemcpyHostToDevice, s), "upload ops");
-      if (!hp.wops.empty())
-        cuda_check(cudaMemcpyAsync(base + o_wops, hp.wops.data(), sizeof(WOp) * hp.wops.size(),
+      if (!hp.wsteps.empty())
+        cuda_check(cudaMemcpyAsync(base + o_wsteps, hp.wsteps.data(),
+                                   sizeof(WStep) * hp.wsteps.size(),
                                    cudaMemcpyHostToDevice, s), "upload warp ops");
       cuda_check(cudaMemcpyAsync(base + o_weights, hp.weights.data(), sizeof(double) * N,
                                  cudaMemcpyHostToDevice, s), "upload weights");
@@ -122,7 +123,7 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
     d.tasks = (const TaskDev*)(base + o_tasks);
     d.n_tasks = (int)hp.tasks.size();
     d.ops = (const SOp*)(base + o_ops);
-    d.wops = (const WOp*)(base + o_wops);
+    d.wsteps = (const WStep*)(base + o_wsteps);
     d.n_params = P;
     d.n_nets = N;
     d.weights = (const double*)(base + o_weights);
