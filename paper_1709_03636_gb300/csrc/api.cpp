@@ -215,7 +215,7 @@ extern "C" qtc_status qtc_selftest_wait_timeout(qtc_engine* e, void* stream) {
     d.waits = upload(e, waits, s, "upload waits");
     d.n_counters = 1;
     d.final_wave = 1;
-    auto* cnt = (unsigned int*)e->alloc(sizeof(unsigned int) * (CTR_FIRST_DEP + 1));
+    auto* cnt = (unsigned int*)e->alloc(sizeof(unsigned int) * ctr_words(1));
     auto* out = (double*)e->alloc(sizeof(double) * 2);
     auto* params = (double*)e->alloc(sizeof(double));
     auto* res = (double*)e->alloc(sizeof(double) * 2);
@@ -227,7 +227,7 @@ extern "C" qtc_status qtc_selftest_wait_timeout(qtc_engine* e, void* stream) {
     d.table_bytes = 0;
     d.arena_bytes = 0;
     d.stage_ops = 1;
-    cuda_check(cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * (CTR_FIRST_DEP + 1), s), "clear");
+    cuda_check(cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * ctr_words(1), s), "clear");
     int per_sm = 0;
     const size_t max_dyn = max_dynamic_smem(e->smem_optin);
     const size_t smem = 2 * (size_t)kYTab * sizeof(uint32_t) + 256 * 16;
@@ -669,7 +669,7 @@ static Prepared& prepare_graph(qtc_engine* e, qtc_batch* b, const HostProgram& h
   auto* dres = (double*)e->alloc(sizeof(double) * N * stride);
   auto* draw = (double*)e->alloc(sizeof(double) * N * stride);
   auto* dout = (double*)e->alloc(sizeof(double) * (2 + P + N));
-  const size_t n_ctr = CTR_FIRST_DEP + hp.max_counters;
+  const size_t n_ctr = ctr_words(hp.max_counters);
   auto* dcnt = (unsigned int*)e->alloc(sizeof(unsigned int) * n_ctr);
   std::vector<GraphProgDev> waves;
   for (const WaveHost& w : hp.waves) {
@@ -782,6 +782,7 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   cuda_check(cudaStreamSynchronize(stream), "prepare sync");
   d.gates = dg;
   d.n_gates = G;
+  for (int g = 0; g < G && g < kInlineGates; ++g) d.gates_inline[g] = hp.gates[g];
   d.table_elems = hp.table_elems;
   d.table_bytes = hp.table_bytes;
   d.team_bytes = hp.team_bytes;

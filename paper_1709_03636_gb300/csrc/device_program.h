@@ -155,9 +155,15 @@ struct TaskDev {
 };
 
 // Kernel argument of the shared-memory executor.
+// Gate table entries passed in the kernel parameters (the rest, if any, are
+// read from `gates`): building the gate table then waits only for the
+// parameter values themselves.
+constexpr int kInlineGates = 16;
+
 struct ProgramDev {
   const GateEntryDev* gates;
   int n_gates;
+  GateEntryDev gates_inline[kInlineGates];   // the first min(n_gates, 16) entries
   uint32_t table_elems;        // gate values + derivatives, in elements
   uint32_t table_bytes;        // table region, rounded to 16 bytes
   uint32_t team_bytes;         // per team: staged ops, then its arena
@@ -262,10 +268,16 @@ struct WaitDev {
   uint32_t target;
 };
 
-// Counter layout: fixed slots, then the dependency counters of the wave.
+// Counter layout: fixed slots in the first 128-byte line, then the
+// dependency counters of the wave, one per 128-byte line (teams poll them
+// while producers increment others: no two share a line).
 enum CounterSlot : uint32_t {
-  CTR_QUEUE = 0, CTR_BLOCKS = 1, CTR_ERROR = 2, CTR_RESERVED = 3, CTR_FIRST_DEP = 4
+  CTR_QUEUE = 0, CTR_BLOCKS = 1, CTR_ERROR = 2, CTR_RESERVED = 3
 };
+constexpr uint32_t kCtrHead = 32;     // words before the first dependency counter
+constexpr uint32_t kCtrStride = 32;   // words per dependency counter
+QTC_HD inline uint64_t ctr_index(uint32_t dep) { return kCtrHead + (uint64_t)dep * kCtrStride; }
+QTC_HD inline uint64_t ctr_words(uint32_t n_dep) { return kCtrHead + (uint64_t)n_dep * kCtrStride; }
 
 // Kernel argument of the graph executor (one launch per wave).
 struct GraphProgDev {

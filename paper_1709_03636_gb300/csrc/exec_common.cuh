@@ -117,9 +117,11 @@ __device__ inline void gate_tensor(const GateSpec& s, const double* params, T* v
 // CTA take part.
 template <typename T>
 __device__ __forceinline__ void build_gate_table(const GateEntryDev* gates, int n_gates,
-                                                 const double* params, T* table) {
+                                                 const double* params, T* table,
+                                                 const GateEntryDev* inline_gates = nullptr,
+                                                 int n_inline = 0) {
   for (int e = threadIdx.x; e < n_gates; e += blockDim.x) {
-    const GateEntryDev g = gates[e];
+    const GateEntryDev g = e < n_inline ? inline_gates[e] : gates[e];
     gate_tensor<T>(g.spec, params, table + g.val_off,
                    g.spec.slot >= 0 ? table + g.der_off : nullptr);
   }

@@ -79,14 +79,16 @@ __device__ bool wait_for_producers(const GraphProgDev& prog, const GTask& task) 
   const unsigned long long t0 = now_ns();
   for (uint32_t i = 0; i < task.wait_count; ++i) {
     const WaitDev w = prog.waits[task.wait_begin + i];
-    const unsigned* c = prog.counters + CTR_FIRST_DEP + w.counter;
+    const unsigned* c = prog.counters + ctr_index(w.counter);
+    unsigned sleep_ns = 64;   // exponential backoff, capped at 1 us
     while (ld_acquire(c) < w.target) {
       if (*err) return false;
       if ((long long)(now_ns() - t0) > prog.wait_limit_ns) {
         atomicCAS(prog.counters + CTR_ERROR, 0u, (unsigned)QTC_ERR_TIMEOUT);
         return false;
       }
-      __nanosleep(200);
+      __nanosleep(sleep_ns);
+      if (sleep_ns < 1024) sleep_ns <<= 1;
     }
   }
   return true;
@@ -98,7 +100,7 @@ __device__ __forceinline__ void signal_done(const GraphProgDev& prog, uint32_t c
                                             const GTeam<kTeams>& team) {
   __threadfence();
   team.sync();
-  if (team.tid == 0 && ctr != 0xFFFFFFFFu) atomicAdd(prog.counters + CTR_FIRST_DEP + ctr, 1u);
+  if (team.tid == 0 && ctr != 0xFFFFFFFFu) atomicAdd(prog.counters + ctr_index(ctr), 1u);
 }
 
 template <typename T>
@@ -161,6 +163,66 @@ __device__ void run_smem_task(const GraphProgDev& prog, const GTask& task, T* ta
   signal_done(prog, task.signal, team);
 }
 
+// sum over y = y0, y0 + step, ... < y1 of A[oa | ya[y]] * B[ob | yb[y]] with
+// eight independent accumulators, so that eight load pairs are in flight
+// (long summed indices are otherwise latency bound); fixed summation order.
+template <typename T>
+__device__ __forceinline__ T ysum(const T* A, const T* B, uint32_t oa, uint32_t ob,
+                                  const uint32_t* ya, const uint32_t* yb, uint32_t y0,
+                                  uint32_t y1, uint32_t step) {
+  T acc[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) acc[u] = czero<T>();
+  uint32_t y = y0;
+  for (; y + 7 * step < y1; y += 8 * step) {
+#pragma unroll
+    for (uint32_t u = 0; u < 8; ++u) {
+      const uint32_t yy = y + u * step;
+      acc[u] = cfma(A[oa | ya[yy]], B[ob | yb[yy]], acc[u]);
+    }
+  }
+  for (; y < y1; y += step) acc[0] = cfma(A[oa | ya[y]], B[ob | yb[y]], acc[0]);
+  return cadd(cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3])),
+              cadd(cadd(acc[4], acc[5]), cadd(acc[6], acc[7])));
+}
+
+// Rows r0..r1 of a chunk whose summed index has NY values: R rows at a
+// time with every term's operands loaded before any product, so R * NY load
+// pairs are in flight per thread.  Rows past r1 load row r1 - 1 again and
+// store nothing.
+template <typename T, uint32_t R, uint32_t NY>
+__device__ __forceinline__ void rows_unrolled(const T* A, const T* B, T* C, const uint32_t* rowa,
+                                              const uint32_t* rowb, uint32_t a_lo, uint32_t b_lo,
+                                              const uint32_t* ya, const uint32_t* yb, uint32_t r0,
+                                              uint32_t r1, uint32_t rowlen, uint32_t tid) {
+  uint32_t yav[NY], ybv[NY];
+#pragma unroll
+  for (uint32_t y = 0; y < NY; ++y) {
+    yav[y] = ya[y];
+    ybv[y] = yb[y];
+  }
+  for (uint32_t row = r0; row < r1; row += R) {
+    T av[R][NY], bv[R][NY];
+#pragma unroll
+    for (uint32_t r = 0; r < R; ++r) {
+      const uint32_t rr = min(row + r, r1 - 1) - r0;
+      const uint32_t oa = rowa[rr] | a_lo, ob = rowb[rr] | b_lo;
+#pragma unroll
+      for (uint32_t y = 0; y < NY; ++y) {
+        av[r][y] = A[oa | yav[y]];
+        bv[r][y] = B[ob | ybv[y]];
+      }
+    }
+#pragma unroll
+    for (uint32_t r = 0; r < R; ++r) {
+      T acc = czero<T>();
+#pragma unroll
+      for (uint32_t y = 0; y < NY; ++y) acc = cfma(av[r][y], bv[r][y], acc);
+      if (row + r < r1) C[(row + r) * rowlen + tid] = acc;
+    }
+  }
+}
+
 template <typename T, int kTeams>
 __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
                           unsigned char* work, GStep& s_step, int& s_last,
@@ -203,10 +265,21 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
         rowb[r] = runs_offset(st.cb, (r0 + r) * rowlen);
       }
       team.sync();
-      if (active) {
+      constexpr uint32_t R = 4;
+      const uint32_t n_y = (uint32_t)ny;
+      if (active && r1 - r0 < R) {
+        // few rows with long sums: the summed index unrolled instead
+        for (uint32_t row = r0; row < r1; ++row)
+          C[row * rowlen + tid] = ysum(A, B, rowa[row - r0] | a_lo, rowb[row - r0] | b_lo, ya,
+                                       yb, 0u, n_y, 1u);
+      } else if (active && n_y == 1) {
+        rows_unrolled<T, 8, 1>(A, B, C, rowa, rowb, a_lo, b_lo, ya, yb, r0, r1, rowlen, tid);
+      } else if (active && n_y == 2) {
+        rows_unrolled<T, 4, 2>(A, B, C, rowa, rowb, a_lo, b_lo, ya, yb, r0, r1, rowlen, tid);
+      } else if (active && n_y == 4) {
+        rows_unrolled<T, 2, 4>(A, B, C, rowa, rowb, a_lo, b_lo, ya, yb, r0, r1, rowlen, tid);
+      } else if (active) {
         // four rows at a time: eight independent loads in flight per thread
-        constexpr uint32_t R = 4;
-        const uint32_t n_y = (uint32_t)ny;
         for (uint32_t row = r0; row < r1; row += R) {
           uint32_t oa[R], ob[R];
           T acc[R];
@@ -246,8 +319,7 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
           yb[y] = runs_offset(st.yb, (uint32_t)(y0 + y));
         }
         team.sync();
-        if (active)
-          for (uint32_t y = 0; y < kYTab; ++y) acc = cfma(A[oa | ya[y]], B[ob | yb[y]], acc);
+        if (active) acc = cadd(acc, ysum(A, B, oa, ob, ya, yb, 0u, kYTab, 1u));
       }
       if (active) C[hi + tid] = acc;
     }
@@ -267,8 +339,7 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
   team.sync();
   const uint32_t oa = runs_offset(st.ca, c), ob = runs_offset(st.cb, c);
   T acc = czero<T>();
-  if (g < groups)
-    for (uint32_t y = g; y < cnt; y += groups) acc = cfma(A[oa | ya[y]], B[ob | yb[y]], acc);
+  if (g < groups) acc = ysum(A, B, oa, ob, ya, yb, g, cnt, groups);
   red[tid] = acc;
   team.sync();
   T* partial = gb + st.partial_off;
@@ -280,7 +351,7 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
   __threadfence();
   team.sync();
   if (tid == 0)
-    s_last = atomicAdd(prog.counters + CTR_FIRST_DEP + st.arrive_ctr, 1u) == st.n_chunks - 1;
+    s_last = atomicAdd(prog.counters + ctr_index(st.arrive_ctr), 1u) == st.n_chunks - 1;
   team.sync();
   if (!s_last) return;
   __threadfence();
@@ -630,7 +701,7 @@ __global__ void __launch_bounds__(kGraphBlock*(kTc ? 4 : 1))
     if (threadIdx.x == 0) prog.counters[CTR_RESERVED] = 0;
   }
   for (int i = threadIdx.x; i < prog.n_counters; i += blockDim.x)
-    prog.counters[CTR_FIRST_DEP + i] = 0;
+    prog.counters[ctr_index(i)] = 0;
   if (threadIdx.x == 0) {
     prog.counters[CTR_QUEUE] = 0;
     prog.counters[CTR_BLOCKS] = 0;

@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
     uint4* dst = reinterpret_cast<uint4*>(stage);
     for (uint32_t w = team.tid; w < n * kWords; w += team.size) cp_async16(dst + w, src + w);
   }
-  build_gate_table<T>(prog.gates, prog.n_gates, prog.params, table);
+  build_gate_table<T>(prog.gates, prog.n_gates, prog.params, table, prog.gates_inline,
+                      kInlineGates);
   cp_async_wait_all();
   __syncthreads();
   bool staged = true;

@@ -116,6 +116,7 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
     ProgramDev d{};
     d.gates = (const GateEntryDev*)(base + o_gates);
     d.n_gates = G;
+    for (int g = 0; g < G && g < kInlineGates; ++g) d.gates_inline[g] = hp.gates[g];
     d.table_elems = hp.table_elems;
     d.table_bytes = hp.table_bytes;
     d.team_bytes = hp.team_bytes;
