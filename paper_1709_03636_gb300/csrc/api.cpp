@@ -96,6 +96,7 @@ struct SvPrepared {
   int2* edges = nullptr;
   double* params = nullptr;
   double* acc = nullptr;
+  SvTables tabs[2];   // per dtype (0: complex double, 1: complex float)
 };
 
 struct qtc_circuit {
@@ -1015,6 +1016,18 @@ static SvPrepared& sv_prepare(qtc_engine* e, qtc_circuit* c, cudaStream_t s) {
   p.edges = upload(e, edges, s, "upload edges");
   p.params = (double*)e->alloc(sizeof(double) * 2 * cc.p);
   p.acc = (double*)e->alloc(sizeof(double) * (1 + cc.edges.size()));
+  void* scratch = e->alloc((size_t)16 * (cc.p * (cc.edges.size() + 1) + cc.p));
+  for (int d = 0; d < 2; ++d) {
+    int lo[16], len[16], rl[16];
+    const int passes = sv_passes(cc.n, sv_tile_bits(d), lo, len, rl);
+    const int l = passes - 1;
+    p.tabs[d].scratch = scratch;
+    p.tabs[d].wcut_first =
+        upload(e, sv_cut_table(adj, cc.n, lo[0], len[0], rl[0]), s, "upload cut table");
+    p.tabs[d].wcut_last =
+        passes > 1 ? upload(e, sv_cut_table(adj, cc.n, lo[l], len[l], rl[l]), s, "upload cut table")
+                   : p.tabs[d].wcut_first;
+  }
   cuda_check(cudaStreamSynchronize(s), "prepare sync");
   c->sv.push_back(p);
   return c->sv.back();
@@ -1028,9 +1041,9 @@ static void sv_run(qtc_engine* e, qtc_circuit* c, const SvPrepared& p, const dou
   const size_t elem = elem_bytes(dtype);
   e->reserve_work(elem << cc.n);
   int launches = 0;
-  cuda_check(sv_qaoa_launch(dtype == QTC_C128 ? 0 : 1, e->work_base(), cc.n,
-                            (int)cc.edges.size(), p.adj, p.edges, params_dev, cc.p, acc, per_edge,
-                            s, &launches),
+  const int d = dtype == QTC_C128 ? 0 : 1;
+  cuda_check(sv_qaoa_launch(d, e->work_base(), cc.n, (int)cc.edges.size(), p.adj, p.edges,
+                            params_dev, cc.p, p.tabs[d], acc, per_edge, s, &launches),
              "launch state vector");
   e->last_launches = launches;
 }

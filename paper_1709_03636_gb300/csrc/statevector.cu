@@ -4,153 +4,298 @@
 // every qubit; finally <C> = sum_x |psi_x|^2 cut(x) (Eqs. 9-10) and, on request,
 // <Z_a Z_b> per edge.
 //
-// Layout: qubit q is bit q of the element index.  A pass moves tiles of 2^t
-// elements through shared memory: pass 0 holds qubits 0..11 (contiguous
-// tiles; the layer's phase is applied on load), every further pass holds
-// qubits 0..3 (so each row of 16 elements is one 128-byte line) plus the next
-// group of up to 8 qubits.  The mixer's 2x2 rotation is applied to every tile
-// qubit in shared memory.  The last pass of the last layer accumulates
-// |psi|^2 * cut(x) in FP64.
+// Layout: qubit q is bit q of the element index.  A pass moves tiles of 2^tb
+// elements through shared memory (64 KB: 2^13 complex64 or 2^12 complex128,
+// two or three CTAs per SM).  Pass 0 of a layer holds qubits 0..tb-1
+// (contiguous tiles) and applies the layer's phase on load; every further pass
+// mixes its own group of qubits and carries as many low qubits along
+// (unmixed) as fill the tile, so tiles stay full and rows contiguous.  The
+// qubits above pass 0 are split evenly over the fewest passes.  The mixer's
+// 2x2 rotation is applied to the pass's own qubits three at a time on eight
+// elements held in registers.
+// The last pass of the last layer accumulates |psi|^2 cut(x).
+//
+// cut(x) without a loop over vertices: with the tile's vertices T and the
+// block's fixed bits f on the other vertices F,
+//   cut(x) = c0(f) + sum_{a in T} t_a coef_a(f) + W[t],
+// c0 = cut edges inside F plus edges from T to F whose F end is 1,
+// coef_a = deg_F(a) - 2 |N_F(a) and f|, W = cut edges inside T (a host-built
+// table per pass layout).  The linear term comes from two per-block tables.
+// The phase and rotation values are computed once per launch (FP64 angles).
 #include <cuda_runtime.h>
+
+#include <vector>
 
 #include "exec_common.cuh"
 #include "sv_launch.h"
 
 namespace qtc {
 
-constexpr int kSvThreads = 256;
+constexpr int kSvThreads = 512;
 constexpr int kSvMaxEdges = 512;
-
-struct SvArgs {
-  void* psi;
-  int n, m;
-  const uint32_t* adj;       // per qubit: bit mask of its neighbours (n <= 32)
-  const int2* edges;         // m edges (a, b)
-  const double* params;      // gammas (p), betas (p)
-  int p, layer;
-  int lo, len;               // pass: tile qubits are 0..3 and lo..lo+len-1 (pass 0: 0..len-1)
-  int first;                 // 1: the state is |+>, do not read it
-  int last;                  // 1: accumulate <C> (and per-edge) after this pass
-  double* acc;               // [<C>, <ZZ> per edge]
-  int per_edge;
-};
-
-// number of cut edges of basis state x
-__device__ __forceinline__ int cut_of(uint32_t x, const uint32_t* adj, int n) {
-  int c = 0;
-  for (int a = 0; a < n; ++a)
-    if ((x >> a) & 1u) c += __popc(adj[a] & ~x);
-  return c;
-}
 
 template <typename T> struct RealOf;
 template <> struct RealOf<float2> { using type = float; };
 template <> struct RealOf<double2> { using type = double; };
 
+int sv_tile_bits(int dtype) { return dtype == 0 ? 12 : 13; }
+
+int sv_passes(int n, int tmax, int* lo, int* len, int* rl) {
+  lo[0] = 0;
+  len[0] = n < tmax ? n : tmax;
+  rl[0] = 0;
+  const int rest = n - len[0];
+  if (rest <= 0) return 1;
+  const int per = tmax - 4;                    // at least 4 carried qubits per pass
+  const int k = (rest + per - 1) / per;
+  int q = len[0];
+  for (int i = 0; i < k; ++i) {
+    const int l = rest / k + (i < rest % k ? 1 : 0);
+    lo[1 + i] = q;
+    len[1 + i] = l;
+    rl[1 + i] = tmax - l;
+    q += l;
+  }
+  return 1 + k;
+}
+
+// Tile vertex of tile bit j for a pass (lo = 0: bits 0..len-1; else the
+// carried bits 0..rl-1 then lo..lo+len-1).
+static inline int tile_vertex(int lo, int rl, int j) {
+  return lo == 0 || j < rl ? j : lo + j - rl;
+}
+
+std::vector<uint16_t> sv_cut_table(const std::vector<uint32_t>& adj, int n, int lo, int len,
+                                   int rl) {
+  const int tb = lo == 0 ? len : rl + len;
+  std::vector<int> va(tb);
+  for (int j = 0; j < tb; ++j) va[j] = tile_vertex(lo, rl, j);
+  std::vector<std::pair<int, int>> inner;  // tile-internal edges as tile bit pairs
+  for (int j = 0; j < tb; ++j)
+    for (int k = j + 1; k < tb; ++k)
+      if ((adj[va[j]] >> va[k]) & 1u) inner.emplace_back(j, k);
+  std::vector<uint16_t> w((size_t)1 << tb);
+  for (uint32_t t = 0; t < (1u << tb); ++t) {
+    int c = 0;
+    for (auto& e : inner) c += ((t >> e.first) ^ (t >> e.second)) & 1u;
+    w[t] = (uint16_t)c;
+  }
+  (void)n;
+  return w;
+}
+
+struct SvArgs {
+  void* psi;
+  int n, m;
+  const uint32_t* adj;       // per qubit: bit mask of its neighbours (n <= 32)
+  const void* phase;         // per layer m + 1 values exp(-i gamma (m - 2c) / 2)
+  const void* rot;           // per layer (cos beta, sin beta)
+  const uint16_t* wcut;      // cut edges inside the tile (passes that need cut(x)), else null
+  int layer;
+  int lo, len, rl;           // pass: tile bits 0..len-1 (lo = 0) or 0..rl-1 and lo..lo+len-1
+  int first;                 // 1: the state is |+>, do not read it
+  int last;                  // 1: accumulate <C> after this pass
+  double* acc;               // [<C>, <ZZ> per edge]
+};
+
+// Sets up the per-launch tables: phase[layer][c] and rot[layer].
 template <typename T>
-__global__ void __launch_bounds__(kSvThreads) sv_pass_kernel(const SvArgs args) {
+__global__ void sv_setup_kernel(const double* params, int p, int m, T* phase, T* rot) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p * (m + 1) + p;
+       i += gridDim.x * blockDim.x) {
+    double sn, cs;
+    if (i < p * (m + 1)) {
+      const int layer = i / (m + 1), c = i % (m + 1);
+      sincos(-0.5 * params[layer] * (double)(m - 2 * c), &sn, &cs);
+      phase[i] = from_d2<T>(make_double2(cs, sn));
+    } else {
+      const int layer = i - p * (m + 1);
+      sincos(params[p + layer], &sn, &cs);
+      rot[layer] = from_d2<T>(make_double2(cs, sn));
+    }
+  }
+}
+
+// exp(-i beta X) on the pair (x0, x1) = amplitudes with the qubit at 0 and 1:
+// [[c, -i s], [-i s, c]].
+template <typename T, typename R>
+__device__ __forceinline__ void rx_pair(T& x0, T& x1, R c, R s) {
+  const T a = x0, b = x1;
+  x0.x = c * a.x + s * b.y;
+  x0.y = c * a.y - s * b.x;
+  x1.x = c * b.x + s * a.y;
+  x1.y = c * b.y - s * a.x;
+}
+
+// The rotation on k = 1..3 consecutive qubit bits of 2^k amplitudes in registers.
+template <int K, typename T, typename R>
+__device__ __forceinline__ void rx_bits(T (&v)[8], R c, R s) {
+#pragma unroll
+  for (int q = 0; q < K; ++q)
+#pragma unroll
+    for (int i = 0; i < (1 << K); ++i)
+      if (!((i >> q) & 1)) rx_pair(v[i], v[i | (1 << q)], c, s);
+}
+
+// One mixer round on tile bits b..b+K-1: groups of 2^K amplitudes.
+template <int K, typename T, typename R>
+__device__ __forceinline__ void rx_round(T* tile, uint32_t tsize, int b, R c, R s) {
+  const uint32_t ngroups = tsize >> K;
+  const uint32_t lowm = (1u << b) - 1u;
+  for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
+    const uint32_t base = (g & lowm) | ((g & ~lowm) << K);
+    T v[8];
+#pragma unroll
+    for (int i = 0; i < (1 << K); ++i) v[i] = tile[base | ((uint32_t)i << b)];
+    rx_bits<K>(v, c, s);
+#pragma unroll
+    for (int i = 0; i < (1 << K); ++i) tile[base | ((uint32_t)i << b)] = v[i];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSvThreads) sv_pass_kernel(const SvArgs a) {
   using R = typename RealOf<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);
-  __shared__ uint32_t s_adj[32];
-  __shared__ double s_red[kSvThreads];
   __shared__ T s_phase[kSvMaxEdges + 1];
-  const int n = args.n;
-  if (threadIdx.x < n) s_adj[threadIdx.x] = args.adj[threadIdx.x];
-  // tile bits: pass 0: 0..len-1; else 0..3 and lo..lo+len-1
-  const bool pass0 = args.lo == 0;
-  const int tbits = pass0 ? args.len : 4 + args.len;
-  const uint32_t tsize = 1u << tbits;
-  // fixed bits of this tile from blockIdx: every bit outside the tile bits
-  uint64_t rest = blockIdx.x;
-  auto global_index = [&](uint32_t t) -> uint64_t {
-    if (pass0) return (rest << args.len) | t;
-    const uint64_t low = t & 15u, mid = t >> 4;
-    const uint64_t below = rest & ((1ull << (args.lo - 4)) - 1);  // bits 4..lo-1
-    const uint64_t above = rest >> (args.lo - 4);                  // bits lo+len..
-    return low | (below << 4) | (mid << args.lo) | (above << (args.lo + args.len));
+  __shared__ int s_lo[128], s_hi[64], s_coef[16];
+  __shared__ int s_c0;
+  __shared__ double s_red[kSvThreads / 32];
+  const int n = a.n;
+  const bool pass0 = a.lo == 0;
+  const int rl = a.rl;
+  const int tb = pass0 ? a.len : rl + a.len;
+  const uint32_t tsize = 1u << tb;
+  const uint64_t blk = blockIdx.x;
+  auto gidx = [&](uint32_t t) -> uint64_t {
+    if (pass0) return (blk << a.len) | t;
+    const uint64_t low = t & ((1u << rl) - 1u), mid = t >> rl;
+    const uint64_t below = blk & ((1ull << (a.lo - rl)) - 1);  // bits rl..lo-1
+    const uint64_t above = blk >> (a.lo - rl);                   // bits lo+len..
+    return low | (below << rl) | (mid << a.lo) | (above << (a.lo + a.len));
   };
-  const double gamma = args.params[args.layer];
-  const double beta = args.params[args.p + args.layer];
-  if (pass0)  // the layer's phase depends on x only through cut(x) in 0..m
-    for (int c = threadIdx.x; c <= args.m; c += blockDim.x) {
-      double sn, cs;
-      sincos(-0.5 * gamma * (double)(args.m - 2 * c), &sn, &cs);
-      s_phase[c] = from_d2<T>(make_double2(cs, sn));
+  const bool need_cut = a.wcut != nullptr;
+  if (need_cut) {
+    const uint32_t full = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+    const uint32_t tmask =
+        pass0 ? (uint32_t)(tsize - 1u) : (((1u << rl) - 1u) | (((1u << a.len) - 1u) << a.lo));
+    const uint32_t fm = full & ~tmask;
+    const uint32_t f = (uint32_t)gidx(0);  // this block's fixed bits (tile bits zero)
+    if (threadIdx.x < 32) {
+      int part = 0;
+      const int v = threadIdx.x;
+      if (v < n) {
+        const uint32_t adj_f = a.adj[v] & fm;
+        if ((tmask >> v) & 1u)
+          part = __popc(adj_f & f);          // tile vertex at 0: edges to fixed ones at 1
+        else if ((f >> v) & 1u)
+          part = __popc(adj_f & ~f);         // fixed-fixed cut edges, counted from the 1 end
+      }
+      for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+      if (v == 0) s_c0 = part;
     }
-  __syncthreads();
-  T* psi = reinterpret_cast<T*>(args.psi);
-  const R amp0 = (R)exp2(-0.5 * n);
-  for (uint32_t t = threadIdx.x; t < tsize; t += blockDim.x) {
-    const uint64_t x = global_index(t);
-    T v;
-    if (args.first) {
-      v.x = amp0;
-      v.y = 0;
-    } else {
-      v = psi[x];
-    }
-    if (pass0) {
-      // the layer's phase exp(-i gamma/2 (m - 2 cut(x)))
-      const T ph = s_phase[cut_of((uint32_t)x, s_adj, n)];
-      const R re = v.x * ph.x - v.y * ph.y;
-      v.y = v.x * ph.y + v.y * ph.x;
-      v.x = re;
-    }
-    tile[t] = v;
-  }
-  __syncthreads();
-  // exp(-i beta X) = [[c, -i s], [-i s, c]] on the pass's own qubits (qubits
-  // 0..3 ride along in later passes only for coalescing)
-  double sbd, cbd;
-  sincos(beta, &sbd, &cbd);
-  const R sb = (R)sbd, cb = (R)cbd;
-  for (int k = pass0 ? 0 : 4; k < tbits; ++k) {
-    const uint32_t bit = 1u << k;
-    for (uint32_t j = threadIdx.x; j < tsize / 2; j += blockDim.x) {
-      const uint32_t i0 = ((j & ~(bit - 1)) << 1) | (j & (bit - 1));
-      const uint32_t i1 = i0 | bit;
-      const T a = tile[i0], b = tile[i1];
-      T a2, b2;
-      a2.x = cb * a.x + sb * b.y;
-      a2.y = cb * a.y - sb * b.x;
-      b2.x = cb * b.x + sb * a.y;
-      b2.y = cb * b.y - sb * a.x;
-      tile[i0] = a2;
-      tile[i1] = b2;
+    if (threadIdx.x < (unsigned)tb) {
+      const int j = threadIdx.x;
+      const int v = pass0 || j < rl ? j : a.lo + j - rl;
+      const uint32_t adj_f = a.adj[v] & fm;
+      s_coef[j] = __popc(adj_f) - 2 * __popc(adj_f & f);
     }
     __syncthreads();
+    if (threadIdx.x < 128) {
+      const int u = threadIdx.x;
+      int sl = 0, sh = 0;
+      for (int j = 0; j < 7 && j < tb; ++j) sl += ((u >> j) & 1) * s_coef[j];
+      for (int j = 7; j < tb && u < 64; ++j) sh += ((u >> (j - 7)) & 1) * s_coef[j];
+      s_lo[u] = sl;
+      if (u < 64) s_hi[u] = sh;
+    }
   }
+  if (pass0) {
+    const T* ph = reinterpret_cast<const T*>(a.phase) + (size_t)a.layer * (a.m + 1);
+    for (int c = threadIdx.x; c <= a.m; c += blockDim.x) s_phase[c] = ph[c];
+  }
+  const T rot = reinterpret_cast<const T*>(a.rot)[a.layer];
+  const R cb = rot.x, sb = rot.y;
+  __syncthreads();
+  auto cut = [&](uint32_t t) -> int {
+    return s_c0 + s_lo[t & 127u] + s_hi[t >> 7] + (int)__ldg(a.wcut + t);
+  };
+  T* psi = reinterpret_cast<T*>(a.psi);
+  const R amp0 = (R)exp2(-0.5 * n);
+
+  if (pass0) {
+    // load with the phase, and the rotation on qubits 0..2 in registers
+    const int k0 = tb < 3 ? tb : 3;
+    const uint32_t gsize = 1u << k0;
+    for (uint32_t g = threadIdx.x; g < (tsize >> k0); g += blockDim.x) {
+      T v[8];
+#pragma unroll
+      for (uint32_t i = 0; i < 8; ++i) {
+        if (i < gsize) {
+          const uint32_t t = g * gsize + i;
+          T x;
+          if (a.first) {
+            x.x = amp0;
+            x.y = 0;
+          } else {
+            x = psi[gidx(t)];
+          }
+          const T ph = s_phase[cut(t)];
+          v[i].x = x.x * ph.x - x.y * ph.y;
+          v[i].y = x.x * ph.y + x.y * ph.x;
+        }
+      }
+      if (k0 == 3) rx_bits<3>(v, cb, sb);
+      else if (k0 == 2) rx_bits<2>(v, cb, sb);
+      else if (k0 == 1) rx_bits<1>(v, cb, sb);
+#pragma unroll
+      for (uint32_t i = 0; i < 8; ++i)
+        if (i < gsize) tile[g * gsize + i] = v[i];
+    }
+  } else {
+    for (uint32_t t = threadIdx.x; t < tsize; t += blockDim.x) tile[t] = psi[gidx(t)];
+  }
+  // the remaining qubits of the pass, three at a time
+  for (int b = pass0 ? 3 : rl; b < tb; b += 3) {
+    __syncthreads();
+    const int k = tb - b < 3 ? tb - b : 3;
+    if (k == 3) rx_round<3>(tile, tsize, b, cb, sb);
+    else if (k == 2) rx_round<2>(tile, tsize, b, cb, sb);
+    else rx_round<1>(tile, tsize, b, cb, sb);
+  }
+  __syncthreads();
   R part = 0;
   for (uint32_t t = threadIdx.x; t < tsize; t += blockDim.x) {
-    const uint64_t x = global_index(t);
     const T v = tile[t];
-    psi[x] = v;
-    if (args.last) part += (v.x * v.x + v.y * v.y) * (R)cut_of((uint32_t)x, s_adj, n);
+    psi[gidx(t)] = v;
+    if (a.last) part += (v.x * v.x + v.y * v.y) * (R)cut(t);
   }
-  if (!args.last) return;
-  s_red[threadIdx.x] = (double)part;
+  if (!a.last) return;
+  for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = (double)part;
   __syncthreads();
-  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-    if (threadIdx.x < off) s_red[threadIdx.x] += s_red[threadIdx.x + off];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += s_red[w];
+    atomicAdd(&a.acc[0], sum);
   }
-  if (threadIdx.x == 0) atomicAdd(&args.acc[0], s_red[0]);
 }
 
 // <Z_a Z_b> for edges [e0, e0 + 16): one pass over the state.
 template <typename T>
-__global__ void __launch_bounds__(kSvThreads) sv_edge_kernel(const SvArgs args, int e0) {
-  __shared__ double s_red[16][kSvThreads / 32];
-  const T* psi = reinterpret_cast<const T*>(args.psi);
-  const int ne = min(16, args.m - e0);
-  double acc[16];
+__global__ void __launch_bounds__(256) sv_edge_kernel(void* psi_v, int n, int m,
+                                                      const int2* edges, double* acc, int e0) {
+  __shared__ double s_red[16][256 / 32];
+  const T* psi = reinterpret_cast<const T*>(psi_v);
+  const int ne = min(16, m - e0);
+  double sums[16];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+  for (int k = 0; k < 16; ++k) sums[k] = 0.0;
   int2 ed[16];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) ed[k] = k < ne ? args.edges[e0 + k] : make_int2(0, 0);
-  const uint64_t total = 1ull << args.n;
+  for (int k = 0; k < 16; ++k) ed[k] = k < ne ? edges[e0 + k] : make_int2(0, 0);
+  const uint64_t total = 1ull << n;
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
        x += (uint64_t)gridDim.x * blockDim.x) {
     const double2 d = to_d2(psi[x]);
@@ -158,46 +303,39 @@ __global__ void __launch_bounds__(kSvThreads) sv_edge_kernel(const SvArgs args, 
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       const uint32_t diff = ((x >> ed[k].x) ^ (x >> ed[k].y)) & 1u;
-      acc[k] += diff ? -pr : pr;
+      sums[k] += diff ? -pr : pr;
     }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
-    double v = acc[k];
+    double v = sums[k];
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     if (lane == 0) s_red[k][warp] = v;
   }
   __syncthreads();
   if (threadIdx.x < ne) {
     double v = 0.0;
-    for (int w = 0; w < kSvThreads / 32; ++w) v += s_red[threadIdx.x][w];
-    atomicAdd(&args.acc[1 + e0 + threadIdx.x], v);
+    for (int w = 0; w < 256 / 32; ++w) v += s_red[threadIdx.x][w];
+    atomicAdd(&acc[1 + e0 + threadIdx.x], v);
   }
 }
 
-int sv_passes(int n, int* lo, int* len) {
-  // pass 0: qubits 0..min(n,12)-1; then groups of up to 8 qubits with 0..3
-  int k = 0;
-  lo[k] = 0;
-  len[k] = n < 12 ? n : 12;
-  ++k;
-  for (int q = 12; q < n; q += 8) {
-    lo[k] = q;
-    len[k] = n - q < 8 ? n - q : 8;
-    ++k;
-  }
-  return k;
-}
-
-cudaError_t sv_qaoa_launch(int dtype, void* psi, int n, int m, const uint32_t* adj_dev,
-                           const int2* edges_dev, const double* params_dev, int p,
-                           double* acc_dev, int per_edge, cudaStream_t stream, int* launches) {
-  int lo[8], len[8];
-  const int passes = sv_passes(n, lo, len);
-  const size_t elem = dtype == 0 ? 16 : 8;
+template <typename T>
+static cudaError_t sv_launch_t(void* psi, int n, int m, const uint32_t* adj_dev,
+                               const int2* edges_dev, const double* params_dev, int p,
+                               const SvTables& tabs, double* acc_dev, int per_edge,
+                               cudaStream_t stream, int* launches) {
+  int lo[16], len[16], rl[16];
+  const int passes = sv_passes(n, sv_tile_bits(sizeof(T) == 16 ? 0 : 1), lo, len, rl);
   *launches = 0;
   cudaError_t err = cudaMemsetAsync(acc_dev, 0, sizeof(double) * (1 + m), stream);
+  if (err != cudaSuccess) return err;
+  T* phase = reinterpret_cast<T*>(tabs.scratch);
+  T* rot = phase + (size_t)p * (m + 1);
+  sv_setup_kernel<T><<<4, 256, 0, stream>>>(params_dev, p, m, phase, rot);
+  ++*launches;
+  err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   for (int layer = 0; layer < p; ++layer)
     for (int k = 0; k < passes; ++k) {
@@ -206,49 +344,45 @@ cudaError_t sv_qaoa_launch(int dtype, void* psi, int n, int m, const uint32_t* a
       a.n = n;
       a.m = m;
       a.adj = adj_dev;
-      a.edges = edges_dev;
-      a.params = params_dev;
-      a.p = p;
+      a.phase = phase;
+      a.rot = rot;
       a.layer = layer;
       a.lo = lo[k];
       a.len = len[k];
+      a.rl = rl[k];
       a.first = layer == 0 && k == 0;
       a.last = layer == p - 1 && k == passes - 1;
+      a.wcut = k == 0 ? tabs.wcut_first : (a.last ? tabs.wcut_last : nullptr);
       a.acc = acc_dev;
-      const int tbits = k == 0 ? len[k] : 4 + len[k];
-      const size_t smem = elem << tbits;
-      const unsigned blocks = (unsigned)(1ull << (n - tbits));
-      if (dtype == 0) {
-        cudaFuncSetAttribute(sv_pass_kernel<double2>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        sv_pass_kernel<double2><<<blocks, kSvThreads, smem, stream>>>(a);
-      } else {
-        cudaFuncSetAttribute(sv_pass_kernel<float2>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        sv_pass_kernel<float2><<<blocks, kSvThreads, smem, stream>>>(a);
-      }
+      const int tb = k == 0 ? len[k] : rl[k] + len[k];
+      const size_t smem = sizeof(T) << tb;
+      const unsigned blocks = (unsigned)(1ull << (n - tb));
+      cudaFuncSetAttribute(sv_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      sv_pass_kernel<T><<<blocks, kSvThreads, smem, stream>>>(a);
       ++*launches;
       err = cudaGetLastError();
       if (err != cudaSuccess) return err;
     }
-  if (per_edge) {
-    SvArgs a{};
-    a.psi = psi;
-    a.n = n;
-    a.m = m;
-    a.edges = edges_dev;
-    a.acc = acc_dev;
+  if (per_edge)
     for (int e0 = 0; e0 < m; e0 += 16) {
-      if (dtype == 0)
-        sv_edge_kernel<double2><<<1024, kSvThreads, 0, stream>>>(a, e0);
-      else
-        sv_edge_kernel<float2><<<1024, kSvThreads, 0, stream>>>(a, e0);
+      sv_edge_kernel<T><<<1024, 256, 0, stream>>>(psi, n, m, edges_dev, acc_dev, e0);
       ++*launches;
       err = cudaGetLastError();
       if (err != cudaSuccess) return err;
     }
-  }
   return cudaSuccess;
+}
+
+cudaError_t sv_qaoa_launch(int dtype, void* psi, int n, int m, const uint32_t* adj_dev,
+                           const int2* edges_dev, const double* params_dev, int p,
+                           const SvTables& tabs, double* acc_dev, int per_edge,
+                           cudaStream_t stream, int* launches) {
+  if (dtype == 0)
+    return sv_launch_t<double2>(psi, n, m, adj_dev, edges_dev, params_dev, p, tabs, acc_dev,
+                                per_edge, stream, launches);
+  return sv_launch_t<float2>(psi, n, m, adj_dev, edges_dev, params_dev, p, tabs, acc_dev,
+                             per_edge, stream, launches);
 }
 
 }  // namespace qtc
