@@ -90,6 +90,9 @@ def parse():
                     help="also time the full 2^n state vector on the GPU for the same graph")
     ap.add_argument("--crossover", action="store_true",
                     help="tensor network vs state vector over regularities 3..7 (table)")
+    ap.add_argument("--noise", default=None, metavar="CHANNEL:STRENGTH",
+                    help="noisy QAOA: depolarize|dephase|ampdamp channel of that strength on "
+                         "every qubit after each mixer (density-matrix networks)")
     return ap.parse_args()
 
 
@@ -100,8 +103,8 @@ def dist_env():
     return world, rank, local
 
 
-def workload_config(w, networks, want_grad, dtype):
-    return {
+def workload_config(w, networks, want_grad, dtype, noise=None):
+    cfg = {
         "workload": w.name,
         "graph": f"{w.d}-regular, n={w.n}, configuration model seed {w.graph_seed}",
         "p": w.p,
@@ -113,6 +116,9 @@ def workload_config(w, networks, want_grad, dtype):
         "dtype": dtype,
         "l2": "flushed between timed steps (256 MiB write outside the events)",
     }
+    if noise:
+        cfg["noise"] = f"{noise[0]} channel, strength {noise[1]}, every qubit after each mixer"
+    return cfg
 
 
 class ClockSampler:
@@ -269,7 +275,11 @@ def run_ours(args):
         w = replace(w, diag=False)
     edges = w.graph()
     g, b = w.angles()
-    circ = q.Circuit.qaoa(w.n, edges, w.p)
+    noise = None
+    if args.noise:
+        kind, strength = args.noise.split(":")
+        noise = (kind, float(strength))
+    circ = q.Circuit.qaoa(w.n, edges, w.p, noise=noise)
     obs = edges[:args.edges] if args.edges else None
     batch = q.Batch(circ, obs, lightcone=w.lightcone, diag=w.diag, ordering=w.ordering)
     stats = batch.stats()
@@ -370,12 +380,13 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (ms * 1e-3) / 1e9
     kernel = "graph_exec_kernel" if prog["graph"] else "smem_exec_kernel"
-    traffic, traffic_src = ncu_traffic(w.name, kernel, dtype, want_grad)
+    traffic, traffic_src = ncu_traffic(w.name, kernel, dtype, want_grad) if not noise \
+        else (None, None)
     line = {
         "metric": METRIC, "value": value, "unit": "networks/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
-        "data": "synthetic", "config": workload_config(w, n_nets, want_grad, dtype),
+        "data": "synthetic", "config": workload_config(w, n_nets, want_grad, dtype, noise),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "traffic_source": traffic_src,
@@ -431,7 +442,7 @@ def run_ours(args):
             "ms_per_eval": svt, "launches": engine.last_launches,
             "tensor_network_forward_ms": fwd, "tn_over_sv_time": fwd / svt,
             "C_statevector": out_sv[0].item(), "C_tensor_network": out[0].item()}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not noise:
         rate, done, el = oracle_networks_per_s(w, edges, g, b, want_grad, 10.0)
         line["cpu_baseline"] = {
             "value": rate, "unit": "networks/s", "cores": 1, "kind": "oracle",

@@ -55,7 +55,17 @@ typedef enum qtc_dtype { QTC_C128 = 0, QTC_C64 = 1, QTC_SPLIT_BF16 = 2 } qtc_dty
  * exp(-i beta X) is RX(2 beta). */
 typedef enum qtc_gate {
   QTC_GATE_H = 0, QTC_GATE_X = 1, QTC_GATE_Y = 2, QTC_GATE_Z = 3,
-  QTC_GATE_RX = 4, QTC_GATE_RZ = 5, QTC_GATE_ZZ = 6, QTC_GATE_CNOT = 7
+  QTC_GATE_RX = 4, QTC_GATE_RZ = 5, QTC_GATE_ZZ = 6, QTC_GATE_CNOT = 7,
+  /* One-qubit noise channels (Section 2's density-matrix form admits
+   * operations that are not unitary): rho -> sum_k K_k rho K_k^dagger with
+   * strength s = the gate's constant, 0 <= s <= 1, no parameter slot.
+   * DEPOLARIZE: (1-s) rho + s/3 (X rho X + Y rho Y + Z rho Z);
+   * DEPHASE: (1-s) rho + s Z rho Z;
+   * AMPDAMP: K0 = [[1,0],[0,sqrt(1-s)]], K1 = [[0,sqrt(s)],[0,0]].
+   * In the network a channel is one rank-4 tensor joining the ket and bra
+   * wires of its qubit; it needs an expectation-value observable (not
+   * QTC_OBS_AMPLITUDE). */
+  QTC_GATE_DEPOLARIZE = 8, QTC_GATE_DEPHASE = 9, QTC_GATE_AMPDAMP = 10
 } qtc_gate;
 
 /* Observables (Section 3.3: <psi|M|psi> for a Pauli string M, or the
@@ -167,6 +177,11 @@ qtc_status qtc_circuit_add_gate(qtc_circuit* c, int gate, const int32_t* qubits,
  * kept as the default set of ZZ observables of qtc_batch_create. */
 qtc_status qtc_circuit_qaoa(int n, const int32_t* edges, int m, int p,
                             qtc_circuit** out);
+/* The same circuit with the channel `channel` (QTC_GATE_DEPOLARIZE, _DEPHASE
+ * or _AMPDAMP) of strength `strength` on every qubit after each layer's
+ * mixer: the noisy QAOA model.  Parameters and observables as above. */
+qtc_status qtc_circuit_qaoa_noisy(int n, const int32_t* edges, int m, int p, int channel,
+                                  double strength, qtc_circuit** out);
 void qtc_circuit_destroy(qtc_circuit* c);
 
 /* ---- networks (Section 2) ----------------------------------------------

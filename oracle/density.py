@@ -138,3 +138,37 @@ def maxcut_grad(n: int, edges, gammas, betas, channel=None, strength: float = 0.
         fm = maxcut(n, edges, xm[:p], xm[p:], channel, strength)
         g[i] = (fp - fm) / (2 * h)
     return g
+
+
+def edge_zz_lightcone(n: int, edges, gammas, betas, edge, channel=None, strength: float = 0.0,
+                      max_qubits: int = 11) -> float:
+    """<Z_u Z_v> for one edge from the density matrix of the radius-p ball
+    around it (the induced subgraph, same channel placement).  Exact: a
+    trace-preserving channel maps the identity to itself in the Heisenberg
+    picture, so channels outside the reverse light cone drop out exactly as
+    gates do (see ``lightcone``)."""
+    from .lightcone import ball, induced
+    u, v = edge
+    verts = ball(n, edges, (u, v), len(gammas))
+    if len(verts) > max_qubits:
+        raise ValueError(f"light cone of {edge} has {len(verts)} qubits")
+    sub, index = induced(edges, verts)
+    k = sub.index((index[u], index[v])) if (index[u], index[v]) in sub else \
+        sub.index((index[v], index[u]))
+    return float(edge_zz(len(verts), sub, gammas, betas, channel, strength)[k])
+
+
+def edge_grad_lightcone(n: int, edges, gammas, betas, edge, channel=None,
+                        strength: float = 0.0, h: float = 1e-4) -> np.ndarray:
+    """d<Z_u Z_v>/d(gamma_1..p, beta_1..p) by central differences of
+    ``edge_zz_lightcone``."""
+    x = np.array(list(gammas) + list(betas), dtype=np.float64)
+    p = len(gammas)
+    g = np.zeros_like(x)
+    for i in range(len(x)):
+        xp, xm = x.copy(), x.copy()
+        xp[i] += h
+        xm[i] -= h
+        g[i] = (edge_zz_lightcone(n, edges, xp[:p], xp[p:], edge, channel, strength)
+                - edge_zz_lightcone(n, edges, xm[:p], xm[p:], edge, channel, strength)) / (2 * h)
+    return g

@@ -22,7 +22,8 @@ __all__ = [
 
 DTYPES = {"c128": 0, "c64": 1, "split_bf16": 2}
 ORDERINGS = {"stoch": 0, "lg": 1}
-GATES = {"h": 0, "x": 1, "y": 2, "z": 3, "rx": 4, "rz": 5, "zz": 6, "cnot": 7}
+GATES = {"h": 0, "x": 1, "y": 2, "z": 3, "rx": 4, "rz": 5, "zz": 6, "cnot": 7,
+         "depolarize": 8, "dephase": 9, "ampdamp": 10}
 OBS = {"zz": 0, "identity": 1, "pauli": 2, "amplitude": 3}
 
 
@@ -118,11 +119,18 @@ class Circuit(_Handle):
         self.p = 0
 
     @classmethod
-    def qaoa(cls, n: int, edges, p: int) -> "Circuit":
-        """Section 4.1 circuit: H, then p x (ZZ(gamma_k) per edge, RX(2 beta_k))."""
+    def qaoa(cls, n: int, edges, p: int, noise=None) -> "Circuit":
+        """Section 4.1 circuit: H, then p x (ZZ(gamma_k) per edge, RX(2 beta_k)).
+        noise = (channel, strength), channel in "depolarize", "dephase",
+        "ampdamp": that channel on every qubit after each layer's mixer."""
         flat = [v for e in edges for v in e]
         h = ctypes.c_void_p()
-        check(lib.qtc_circuit_qaoa(n, _i32(flat), len(edges), p, ctypes.byref(h)))
+        if noise is None:
+            check(lib.qtc_circuit_qaoa(n, _i32(flat), len(edges), p, ctypes.byref(h)))
+        else:
+            kind, strength = noise
+            check(lib.qtc_circuit_qaoa_noisy(n, _i32(flat), len(edges), p, GATES[kind],
+                                             float(strength), ctypes.byref(h)))
         c = cls(n, 2 * p, _ptr=h)
         c.edges = [tuple(e) for e in edges]
         c.p = p

@@ -275,6 +275,13 @@ static void add_gate(Circuit& c, int kind, const int32_t* qubits, int slot, doub
     case QTC_GATE_ZZ: case QTC_GATE_CNOT:
       g.nq = 2;
       break;
+    case QTC_GATE_DEPOLARIZE: case QTC_GATE_DEPHASE: case QTC_GATE_AMPDAMP:
+      g.nq = 1;
+      if (slot != -1) fail(QTC_ERR_INVALID, "a channel's strength is a constant (slot -1)");
+      if (!(constant >= 0.0 && constant <= 1.0))
+        fail(QTC_ERR_INVALID, "channel strength %g outside [0, 1]", constant);
+      g.coeff = 0.0;
+      break;
     default:
       fail(QTC_ERR_INVALID, "unknown gate kind %d", kind);
   }
@@ -300,38 +307,58 @@ extern "C" qtc_status qtc_circuit_add_gate(qtc_circuit* c, int gate, const int32
   });
 }
 
+// QAOA Max-Cut circuit of Section 4.1; channel >= 0 adds that channel on
+// every qubit after each layer's mixer.
+static qtc_circuit* make_qaoa(int n, const int32_t* edges, int m, int p, int channel,
+                              double strength) {
+  if (n <= 1 || n > 4096) fail(QTC_ERR_INVALID, "qubit count %d", n);
+  if (p <= 0 || 2 * p > 64) fail(QTC_ERR_INVALID, "depth p = %d (1..32)", p);
+  if (m <= 0 || !edges) fail(QTC_ERR_INVALID, "empty edge list");
+  auto c = std::make_unique<qtc_circuit>();
+  Circuit& cc = c->c;
+  cc.n = n;
+  cc.n_params = 2 * p;
+  cc.p = p;
+  std::vector<std::pair<int, int>> seen;
+  for (int i = 0; i < m; ++i) {
+    int a = edges[2 * i], b = edges[2 * i + 1];
+    if (a < 0 || a >= n || b < 0 || b >= n || a == b)
+      fail(QTC_ERR_INVALID, "edge %d = (%d, %d) invalid", i, a, b);
+    std::pair<int, int> key(std::min(a, b), std::max(a, b));
+    if (std::find(seen.begin(), seen.end(), key) != seen.end())
+      fail(QTC_ERR_INVALID, "edge (%d, %d) repeated", a, b);
+    seen.push_back(key);
+    cc.edges.push_back({a, b});
+  }
+  for (int q = 0; q < n; ++q) add_gate(cc, QTC_GATE_H, &q, -1, 0, 0);
+  for (int k = 0; k < p; ++k) {
+    for (auto& e : cc.edges) {
+      int32_t qs[2] = {e.first, e.second};
+      add_gate(cc, QTC_GATE_ZZ, qs, k, 1.0, 0.0);        // exp(-i gamma_k ZZ/2)
+    }
+    for (int q = 0; q < n; ++q) add_gate(cc, QTC_GATE_RX, &q, p + k, 2.0, 0.0);  // RX(2 beta_k)
+    if (channel >= 0)
+      for (int q = 0; q < n; ++q) add_gate(cc, channel, &q, -1, 0.0, strength);
+  }
+  return c.release();
+}
+
 extern "C" qtc_status qtc_circuit_qaoa(int n, const int32_t* edges, int m, int p,
                                        qtc_circuit** out) {
   return guarded([&] {
     if (!out) fail(QTC_ERR_INVALID, "null output handle");
-    if (n <= 1 || n > 4096) fail(QTC_ERR_INVALID, "qubit count %d", n);
-    if (p <= 0 || 2 * p > 64) fail(QTC_ERR_INVALID, "depth p = %d (1..32)", p);
-    if (m <= 0 || !edges) fail(QTC_ERR_INVALID, "empty edge list");
-    auto c = std::make_unique<qtc_circuit>();
-    Circuit& cc = c->c;
-    cc.n = n;
-    cc.n_params = 2 * p;
-    cc.p = p;
-    std::vector<std::pair<int, int>> seen;
-    for (int i = 0; i < m; ++i) {
-      int a = edges[2 * i], b = edges[2 * i + 1];
-      if (a < 0 || a >= n || b < 0 || b >= n || a == b)
-        fail(QTC_ERR_INVALID, "edge %d = (%d, %d) invalid", i, a, b);
-      std::pair<int, int> key(std::min(a, b), std::max(a, b));
-      if (std::find(seen.begin(), seen.end(), key) != seen.end())
-        fail(QTC_ERR_INVALID, "edge (%d, %d) repeated", a, b);
-      seen.push_back(key);
-      cc.edges.push_back({a, b});
-    }
-    for (int q = 0; q < n; ++q) add_gate(cc, QTC_GATE_H, &q, -1, 0, 0);
-    for (int k = 0; k < p; ++k) {
-      for (auto& e : cc.edges) {
-        int32_t qs[2] = {e.first, e.second};
-        add_gate(cc, QTC_GATE_ZZ, qs, k, 1.0, 0.0);        // exp(-i gamma_k ZZ/2)
-      }
-      for (int q = 0; q < n; ++q) add_gate(cc, QTC_GATE_RX, &q, p + k, 2.0, 0.0);  // RX(2 beta_k)
-    }
-    *out = c.release();
+    *out = make_qaoa(n, edges, m, p, -1, 0.0);
+  });
+}
+
+extern "C" qtc_status qtc_circuit_qaoa_noisy(int n, const int32_t* edges, int m, int p,
+                                             int channel, double strength, qtc_circuit** out) {
+  return guarded([&] {
+    if (!out) fail(QTC_ERR_INVALID, "null output handle");
+    if (channel != QTC_GATE_DEPOLARIZE && channel != QTC_GATE_DEPHASE &&
+        channel != QTC_GATE_AMPDAMP)
+      fail(QTC_ERR_INVALID, "gate kind %d is not a noise channel", channel);
+    *out = make_qaoa(n, edges, m, p, channel, strength);
   });
 }
 

@@ -18,13 +18,18 @@ namespace qtc {
 //   rank 2 observable [bra, ket]: index = bra | ket << 1, value O[bra][ket]
 //   ZZDIAG (a, b):           index = a | b << 1, value exp(-i t z_a z_b / 2)
 //   rank 4 [a_out, b_out, a_in, b_in]: value U[(a_out b_out), (a_in b_in)]
+//   channel [ket_out, bra_out, ket_in, bra_in] (DEPOL, DEPHASE, AMPDAMP; the
+//     strength is the spec's constant): sum_k K_k[ket_out][ket_in]
+//     conj(K_k[bra_out][bra_in])
 enum LeafKind : uint8_t {
   LK_ZERO = 0, LK_PLUS = 1, LK_PROJ0 = 2, LK_PROJ1 = 3,
   LK_H = 4, LK_X = 5, LK_Y = 6, LK_Z = 7, LK_RX = 8, LK_RZ = 9,
   LK_ZDIAG = 10, LK_RZDIAG = 11, LK_ZZDIAG = 12,
   LK_ZZ = 13, LK_CNOT = 14,
   LK_OBS_X = 15, LK_OBS_Y = 16, LK_OBS_Z = 17,
-  LK_COUNT = 18
+  LK_DEPOL = 18, LK_DEPHASE = 19, LK_AMPDAMP = 20,
+  LK_OBS_I = 21,          // [bra, ket] identity: closes a wire explicitly
+  LK_COUNT = 22
 };
 
 QTC_HD inline int leaf_rank_of(int kind) {
@@ -32,7 +37,7 @@ QTC_HD inline int leaf_rank_of(int kind) {
     case LK_ZERO: case LK_PLUS: case LK_PROJ0: case LK_PROJ1:
     case LK_ZDIAG: case LK_RZDIAG:
       return 1;
-    case LK_ZZ: case LK_CNOT:
+    case LK_ZZ: case LK_CNOT: case LK_DEPOL: case LK_DEPHASE: case LK_AMPDAMP:
       return 4;
     default:
       return 2;

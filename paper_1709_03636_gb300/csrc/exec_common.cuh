@@ -75,6 +75,7 @@ __device__ inline void gate_tensor(const GateSpec& s, const double* params, T* v
       val[1].y = R(1);   // [1][0] = +i
       break;
     case LK_Z: case LK_OBS_Z: val[0].x = R(1); val[3].x = R(-1); break;
+    case LK_OBS_I: val[0].x = R(1); val[3].x = R(1); break;
     case LK_RX:  // cos(t/2) I - i sin(t/2) X, [out, in]
       val[0].x = ch; val[3].x = ch; val[1].y = -sh; val[2].y = -sh;
       der[0].x = -half * sh * dth; der[3].x = -half * sh * dth;
@@ -103,6 +104,39 @@ __device__ inline void gate_tensor(const GateSpec& s, const double* params, T* v
       for (int c = 0; c < 2; ++c)
         for (int t = 0; t < 2; ++t) val[c | (t ^ c) << 1 | c << 2 | t << 3].x = R(1);
       break;
+    case LK_DEPOL: case LK_DEPHASE: case LK_AMPDAMP: {
+      // Kraus operators K[k][row][col] of the channel, then
+      // value[ko | bo<<1 | ki<<2 | bi<<3] = sum_k K[ko][ki] conj(K[bo][bi])
+      const R st = (R)s.constant;
+      T K[4][2][2];
+      for (int k = 0; k < 4; ++k)
+        for (int r = 0; r < 2; ++r)
+          for (int c = 0; c < 2; ++c) K[k][r][c] = T{R(0), R(0)};
+      int nk = 2;
+      if (s.kind == LK_DEPOL) {
+        const R a = sqrt(R(1) - st), b = sqrt(st / R(3));
+        K[0][0][0].x = a; K[0][1][1].x = a;
+        K[1][0][1].x = b; K[1][1][0].x = b;                  // X
+        K[2][0][1].y = -b; K[2][1][0].y = b;                 // Y = [[0, -i], [i, 0]]
+        K[3][0][0].x = b; K[3][1][1].x = -b;                 // Z
+        nk = 4;
+      } else if (s.kind == LK_DEPHASE) {
+        const R a = sqrt(R(1) - st), b = sqrt(st);
+        K[0][0][0].x = a; K[0][1][1].x = a;
+        K[1][0][0].x = b; K[1][1][1].x = -b;
+      } else {
+        K[0][0][0].x = R(1); K[0][1][1].x = sqrt(R(1) - st);
+        K[1][0][1].x = sqrt(st);
+      }
+      for (int k = 0; k < nk; ++k)
+        for (int i = 0; i < 16; ++i) {
+          const T a = K[k][i & 1][(i >> 2) & 1];         // K[ko][ki]
+          const T b = K[k][(i >> 1) & 1][(i >> 3) & 1];  // K[bo][bi]
+          val[i].x += a.x * b.x + a.y * b.y;
+          val[i].y += a.y * b.x - a.x * b.y;
+        }
+      break;
+    }
     default: break;
   }
   if (s.conj)

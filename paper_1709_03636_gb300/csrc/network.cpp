@@ -10,6 +10,10 @@ bool gate_is_diagonal(int kind) {
   return kind == QTC_GATE_Z || kind == QTC_GATE_RZ || kind == QTC_GATE_ZZ;
 }
 
+bool gate_is_channel(int kind) {
+  return kind == QTC_GATE_DEPOLARIZE || kind == QTC_GATE_DEPHASE || kind == QTC_GATE_AMPDAMP;
+}
+
 namespace {
 
 struct UnionFind {
@@ -41,6 +45,7 @@ GateSpec spec_of(uint8_t kind, bool conj, const Gate* g) {
     s.coeff = g->slot >= 0 ? g->coeff : 0.0;
     s.constant = g->constant;
   }
+  if (g && gate_is_channel(g->kind)) s.constant = g->constant;  // the channel's strength
   return s;
 }
 
@@ -54,7 +59,12 @@ GateSpec plain(uint8_t kind, bool conj) { return spec_of(kind, conj, nullptr); }
 // operator and is dropped; so is a diagonal gate that touches S only on
 // qubits where that operator is still diagonal (set D).  A kept diagonal gate
 // adds its other qubits to S and D; a kept non-diagonal gate adds its qubits
-// to S and removes them from D.  Only qubits of S get wires.
+// to S and removes them from D.  Only qubits of S get wires.  A noise channel
+// (trace preserving: its Heisenberg-picture map fixes the identity) is
+// dropped when it misses S and kept otherwise; it maps operators diagonal on
+// its qubit to diagonal ones, so S and D are unchanged.  With channels the
+// ket and bra sides are built in step: a channel is one tensor joining the
+// ket and bra wires of its qubit (Section 2's density-matrix form).
 Network build_network(const Circuit& c, const qtc_observable& obs, bool lightcone,
                       bool diag) {
   const int n = c.n;
@@ -115,6 +125,7 @@ Network build_network(const Circuit& c, const qtc_observable& obs, bool lightcon
         keep[gi] = 0;
         continue;
       }
+      if (gate_is_channel(g.kind)) continue;
       for (int k = 0; k < g.nq; ++k) {
         int q = g.q[k];
         if (gate_is_diagonal(g.kind)) {
@@ -148,68 +159,124 @@ Network build_network(const Circuit& c, const qtc_observable& obs, bool lightcon
   int next_label = 0;
   auto new_label = [&]() { return next_label++; };
 
-  auto side = [&](bool conj, std::vector<int>& cur) {
+  auto init_side = [&](bool conj, std::vector<int>& cur) {
     cur.assign(n, -1);
     for (int q = 0; q < n; ++q) {
       if (!in_s[q]) continue;
       cur[q] = new_label();
       net.leaves.push_back({plain(folded[q] >= 0 ? LK_PLUS : LK_ZERO, conj), {cur[q]}});
     }
+  };
+  // one unitary gate on one side (ket: conj = false, bra: conj = true)
+  auto apply_gate = [&](int gi, bool conj, std::vector<int>& cur) {
+    const Gate& g = c.gates[gi];
+    if (g.nq == 1 && folded[g.q[0]] == gi) return;
+    if (diag && gate_is_diagonal(g.kind)) {
+      if (g.kind == QTC_GATE_ZZ)
+        net.leaves.push_back({spec_of(LK_ZZDIAG, conj, &g), {cur[g.q[0]], cur[g.q[1]]}});
+      else if (g.kind == QTC_GATE_RZ)
+        net.leaves.push_back({spec_of(LK_RZDIAG, conj, &g), {cur[g.q[0]]}});
+      else
+        net.leaves.push_back({plain(LK_ZDIAG, conj), {cur[g.q[0]]}});
+      return;
+    }
+    if (g.nq == 1) {
+      int q = g.q[0];
+      int out = new_label();
+      uint8_t kind = 0;
+      switch (g.kind) {
+        case QTC_GATE_H: kind = LK_H; break;
+        case QTC_GATE_X: kind = LK_X; break;
+        case QTC_GATE_Y: kind = LK_Y; break;
+        case QTC_GATE_Z: kind = LK_Z; break;
+        case QTC_GATE_RX: kind = LK_RX; break;
+        case QTC_GATE_RZ: kind = LK_RZ; break;
+        default: fail(QTC_ERR_INVALID, "gate kind %d is not a one-qubit gate", g.kind);
+      }
+      net.leaves.push_back({spec_of(kind, conj, &g), {out, cur[q]}});
+      cur[q] = out;
+    } else {
+      int a = g.q[0], b = g.q[1];
+      int oa = new_label(), ob = new_label();
+      uint8_t kind = g.kind == QTC_GATE_ZZ ? LK_ZZ : LK_CNOT;
+      net.leaves.push_back({spec_of(kind, conj, &g), {oa, ob, cur[a], cur[b]}});
+      cur[a] = oa;
+      cur[b] = ob;
+    }
+  };
+  auto side = [&](bool conj, std::vector<int>& cur) {
+    init_side(conj, cur);
+    for (int gi = 0; gi < G; ++gi)
+      if (keep[gi]) apply_gate(gi, conj, cur);
+  };
+  bool channels = false;
+  for (int gi = 0; gi < G; ++gi) channels |= keep[gi] && gate_is_channel(c.gates[gi].kind);
+  if (channels && amplitude)
+    fail(QTC_ERR_INVALID, "a circuit with noise channels has no amplitude network");
+  if (channels) {
+    // A channel that is the last operation on a qubit closed by the trace
+    // (identity observable) is the identity there (trace preserving): drop
+    // it, and any channels it uncovers.
+    for (int q = 0; q < n; ++q) {
+      if (!in_s[q] || op[q] != 'I') continue;
+      for (int gi = G - 1; gi >= 0; --gi) {
+        if (!keep[gi]) continue;
+        const Gate& g = c.gates[gi];
+        bool on_q = false;
+        for (int k = 0; k < g.nq; ++k) on_q |= g.q[k] == q;
+        if (!on_q) continue;
+        if (!gate_is_channel(g.kind)) break;
+        keep[gi] = 0;
+      }
+    }
+    channels = false;
+    for (int gi = 0; gi < G; ++gi) channels |= keep[gi] && gate_is_channel(c.gates[gi].kind);
+  }
+
+  std::vector<int> ket, bra;
+  if (channels) {
+    // ket and bra in step; a channel joins the two wires of its qubit
+    init_side(false, ket);
+    init_side(true, bra);
     for (int gi = 0; gi < G; ++gi) {
       if (!keep[gi]) continue;
       const Gate& g = c.gates[gi];
-      if (g.nq == 1 && folded[g.q[0]] == gi) continue;
-      if (diag && gate_is_diagonal(g.kind)) {
-        if (g.kind == QTC_GATE_ZZ)
-          net.leaves.push_back({spec_of(LK_ZZDIAG, conj, &g), {cur[g.q[0]], cur[g.q[1]]}});
-        else if (g.kind == QTC_GATE_RZ)
-          net.leaves.push_back({spec_of(LK_RZDIAG, conj, &g), {cur[g.q[0]]}});
-        else
-          net.leaves.push_back({plain(LK_ZDIAG, conj), {cur[g.q[0]]}});
+      if (!gate_is_channel(g.kind)) {
+        apply_gate(gi, false, ket);
+        apply_gate(gi, true, bra);
         continue;
       }
-      if (g.nq == 1) {
-        int q = g.q[0];
-        int out = new_label();
-        uint8_t kind = 0;
-        switch (g.kind) {
-          case QTC_GATE_H: kind = LK_H; break;
-          case QTC_GATE_X: kind = LK_X; break;
-          case QTC_GATE_Y: kind = LK_Y; break;
-          case QTC_GATE_Z: kind = LK_Z; break;
-          case QTC_GATE_RX: kind = LK_RX; break;
-          case QTC_GATE_RZ: kind = LK_RZ; break;
-          default: fail(QTC_ERR_INVALID, "gate kind %d is not a one-qubit gate", g.kind);
-        }
-        net.leaves.push_back({spec_of(kind, conj, &g), {out, cur[q]}});
-        cur[q] = out;
-      } else {
-        int a = g.q[0], b = g.q[1];
-        int oa = new_label(), ob = new_label();
-        uint8_t kind = g.kind == QTC_GATE_ZZ ? LK_ZZ : LK_CNOT;
-        net.leaves.push_back({spec_of(kind, conj, &g), {oa, ob, cur[a], cur[b]}});
-        cur[a] = oa;
-        cur[b] = ob;
-      }
+      const int q = g.q[0];
+      const int ko = new_label(), bo = new_label();
+      const uint8_t kind = g.kind == QTC_GATE_DEPOLARIZE ? LK_DEPOL
+                           : g.kind == QTC_GATE_DEPHASE  ? LK_DEPHASE
+                                                         : LK_AMPDAMP;
+      net.leaves.push_back({spec_of(kind, false, &g), {ko, bo, ket[q], bra[q]}});
+      ket[q] = ko;
+      bra[q] = bo;
     }
-  };
-
-  std::vector<int> ket, bra;
-  side(false, ket);
+  } else {
+    side(false, ket);
+  }
   if (amplitude) {
     for (int q = 0; q < n; ++q)
       if (in_s[q]) net.leaves.push_back({plain(bits[q] ? LK_PROJ1 : LK_PROJ0, false), {ket[q]}});
   } else {
-    side(true, bra);
+    if (!channels) side(true, bra);
     std::vector<std::pair<int, int>> unite;
     for (int q = 0; q < n; ++q) {
       if (!in_s[q]) continue;
       switch (op[q]) {
         case 'I':
-          unite.push_back({bra[q], ket[q]});
+          // with channels a wire is closed by an explicit identity tensor: a
+          // merged label could repeat an index of a channel tensor
+          if (channels)
+            net.leaves.push_back({plain(LK_OBS_I, false), {bra[q], ket[q]}});
+          else
+            unite.push_back({bra[q], ket[q]});
           break;
         case 'Z':
-          if (diag) {
+          if (diag && !channels) {
             unite.push_back({bra[q], ket[q]});
             net.leaves.push_back({plain(LK_ZDIAG, false), {ket[q]}});
           } else {

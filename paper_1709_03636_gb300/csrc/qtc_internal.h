@@ -95,6 +95,7 @@ struct Circuit {
 };
 
 bool gate_is_diagonal(int kind);
+bool gate_is_channel(int kind);
 
 // ---- networks ---------------------------------------------------------------
 // One leaf tensor: the gate table entry that gives its values and its labels

@@ -224,40 +224,49 @@ __global__ void __launch_bounds__(kSvThreads) sv_pass_kernel(const SvArgs a) {
   T* psi = reinterpret_cast<T*>(a.psi);
   const R amp0 = (R)exp2(-0.5 * n);
 
-  if (pass0) {
-    // load with the phase, and the rotation on qubits 0..2 in registers
-    const int k0 = tb < 3 ? tb : 3;
-    const uint32_t gsize = 1u << k0;
-    for (uint32_t g = threadIdx.x; g < (tsize >> k0); g += blockDim.x) {
-      T v[8];
+  // Load.  With at least one element per thread, lanes hold consecutive tile
+  // elements (coalesced loads, conflict-free stores) and pass 0 mixes tile
+  // qubits 0..4 with shuffles (the partner of lane l for qubit q is l ^ 2^q:
+  // x' = c x - i s partner, the same on both sides of the pair).
+  const bool full_warps = tsize >= (uint32_t)blockDim.x;
+  const int shuffled = pass0 && full_warps ? (tb < 5 ? tb : 5) : 0;
+  constexpr int kBatch = 8;
+  for (uint32_t t0 = 0; t0 < tsize; t0 += kBatch * blockDim.x) {
+    T v[kBatch];
 #pragma unroll
-      for (uint32_t i = 0; i < 8; ++i) {
-        if (i < gsize) {
-          const uint32_t t = g * gsize + i;
-          T x;
-          if (a.first) {
-            x.x = amp0;
-            x.y = 0;
-          } else {
-            x = psi[gidx(t)];
-          }
-          const T ph = s_phase[cut(t)];
-          v[i].x = x.x * ph.x - x.y * ph.y;
-          v[i].y = x.x * ph.y + x.y * ph.x;
+    for (int k = 0; k < kBatch; ++k) {
+      const uint32_t t = t0 + k * blockDim.x + threadIdx.x;
+      if (t < tsize) {
+        if (pass0 && a.first) {
+          v[k].x = amp0;
+          v[k].y = 0;
+        } else {
+          v[k] = psi[gidx(t)];
         }
       }
-      if (k0 == 3) rx_bits<3>(v, cb, sb);
-      else if (k0 == 2) rx_bits<2>(v, cb, sb);
-      else if (k0 == 1) rx_bits<1>(v, cb, sb);
-#pragma unroll
-      for (uint32_t i = 0; i < 8; ++i)
-        if (i < gsize) tile[g * gsize + i] = v[i];
     }
-  } else {
-    for (uint32_t t = threadIdx.x; t < tsize; t += blockDim.x) tile[t] = psi[gidx(t)];
+#pragma unroll
+    for (int k = 0; k < kBatch; ++k) {
+      const uint32_t t = t0 + k * blockDim.x + threadIdx.x;
+      if (pass0 && t < tsize) {
+        const T ph = s_phase[cut(t)];
+        const T x = v[k];
+        v[k].x = x.x * ph.x - x.y * ph.y;
+        v[k].y = x.x * ph.y + x.y * ph.x;
+      }
+      if (t0 + k * blockDim.x < tsize)  // uniform: whole warps
+        for (int q = 0; q < shuffled; ++q) {
+          const R px = __shfl_xor_sync(0xffffffffu, v[k].x, 1u << q);
+          const R py = __shfl_xor_sync(0xffffffffu, v[k].y, 1u << q);
+          const R x = v[k].x, y = v[k].y;
+          v[k].x = cb * x + sb * py;
+          v[k].y = cb * y - sb * px;
+        }
+      if (t < tsize) tile[t] = v[k];
+    }
   }
   // the remaining qubits of the pass, three at a time
-  for (int b = pass0 ? 3 : rl; b < tb; b += 3) {
+  for (int b = pass0 ? shuffled : rl; b < tb; b += 3) {
     __syncthreads();
     const int k = tb - b < 3 ? tb - b : 3;
     if (k == 3) rx_round<3>(tile, tsize, b, cb, sb);

@@ -44,6 +44,23 @@ def leaf_tensor(kind, conj, slot, coeff, constant, params):
         16: lambda: np.array([[0, -1j], [1j, 0]]),
         17: lambda: np.array([[1, 0], [0, -1]]),
     }
+    if kind in (18, 19, 20):
+        # channel [ket_out, bra_out, ket_in, bra_in] = sum_k K[ko, ki] conj(K[bo, bi])
+        st = constant
+        if kind == 18:
+            ks = [math.sqrt(1 - st) * np.eye(2)] + [
+                math.sqrt(st / 3) * np.array(m) for m in
+                ([[0, 1], [1, 0]], [[0, -1j], [1j, 0]], [[1, 0], [0, -1]])]
+        elif kind == 19:
+            ks = [math.sqrt(1 - st) * np.eye(2), math.sqrt(st) * np.diag([1, -1])]
+        else:
+            ks = [np.array([[1, 0], [0, math.sqrt(1 - st)]]),
+                  np.array([[0, math.sqrt(st)], [0, 0]])]
+        v = sum(np.einsum("ac,bd->abcd", np.asarray(k, complex), np.conj(np.asarray(k, complex)))
+                for k in ks)
+        return v
+    if kind == 21:
+        return np.eye(2, dtype=complex)
     if kind == 13:
         v = np.zeros((2, 2, 2, 2), dtype=complex)
         for a in range(2):
@@ -104,6 +121,37 @@ def test_qaoa_networks_and_plans_match_statevector(ordering, diag, lightcone, p)
         assert st["n_steps"] == st["n_tensors"] - 1
         val = run_plan(net, plan, params)
         assert abs(val.real - ref[i]) < 1e-12 and abs(val.imag) < 1e-12
+
+
+@pytest.mark.parametrize("channel", ["depolarize", "dephase", "ampdamp"])
+@pytest.mark.parametrize("diag", [True, False])
+@pytest.mark.parametrize("lightcone", [True, False])
+def test_noisy_qaoa_networks_match_density_matrix(channel, diag, lightcone):
+    """Channels after every mixer (Section 2's density-matrix form): the
+    library's networks and plans against the density-matrix oracle."""
+    from oracle import density as dm
+    n, p, s = 8, 2, 0.07
+    edges = random_regular_graph(n, 3, 9)
+    gammas, betas = [0.45, 1.05], [0.8, 0.35]
+    ref = dm.edge_zz(n, edges, gammas, betas, channel, s)
+    circ = q.Circuit.qaoa(n, edges, p, noise=(channel, s))
+    for i, e in enumerate(edges[:4]):
+        net = q.Network(circ, "zz", edge=e, lightcone=lightcone, diag=diag)
+        for ordering in ("lg", "stoch"):
+            val = run_plan(net, q.Plan(net, ordering, seed=5), gammas + betas)
+            assert abs(val.real - ref[i]) < 1e-12 and abs(val.imag) < 1e-12
+
+
+def test_channel_arguments_are_checked():
+    edges = random_regular_graph(6, 3, 1)
+    with pytest.raises(q.QtcError):
+        q.Circuit.qaoa(6, edges, 1, noise=("depolarize", 1.5))
+    c = q.Circuit(2, 0)
+    with pytest.raises(q.QtcError):
+        c.add_gate("dephase", [0], slot=0, constant=0.1)
+    c.add_gate("h", [0]).add_gate("ampdamp", [0], constant=0.3)
+    with pytest.raises(q.QtcError):
+        q.Network(c, "amplitude", bits=[0, 0], lightcone=False)
 
 
 def test_plans_are_binary_trees():

@@ -13,7 +13,8 @@ Each check is against something other than the oracle itself:
 * the paper's own dimension-4 superoperator network (Section 2 tensors,
   contracted by variable elimination) with the channel's superoperator
   sum_k kron(K, conj K), on a two-qubit circuit;
-* a planted mistake (K rho K instead of K rho K^dagger) breaks a pin.
+* a planted mistake (K rho K instead of K rho K^dagger) breaks a pin;
+* the radius-p light-cone density matrix against the full one.
 """
 
 import numpy as np
@@ -125,3 +126,15 @@ def test_planted_mistake_is_caught():
     good = dm.apply_channel(rho, n, 0, ks).reshape(2 ** n, 2 ** n)
     assert abs(np.trace(good) - 1) < 1e-12
     assert abs(np.trace(bad) - 1) > 1e-3
+
+
+@pytest.mark.parametrize("kind", dm.CHANNELS)
+def test_lightcone_density_matches_full(kind):
+    """The radius-p ball (p = 1 and 2) against the full density matrix."""
+    n = 10
+    edges = random_regular_graph(n, 3, 6)
+    for p in (1, 2):
+        full = dm.edge_zz(n, edges, G[:p], B[:p], kind, 0.15)
+        for i in (0, 4, 9):
+            got = dm.edge_zz_lightcone(n, edges, G[:p], B[:p], edges[i], kind, 0.15)
+            assert abs(got - full[i]) < 1e-12
