@@ -90,6 +90,8 @@ def parse():
                     help="also time the full 2^n state vector on the GPU for the same graph")
     ap.add_argument("--crossover", action="store_true",
                     help="tensor network vs state vector over regularities 3..7 (table)")
+    ap.add_argument("--width-sweep", action="store_true",
+                    help="time per <C> against the ordering's width, 18-qubit circuits (table)")
     ap.add_argument("--noise", default=None, metavar="CHANNEL:STRENGTH",
                     help="noisy QAOA: depolarize|dephase|ampdamp channel of that strength on "
                          "every qubit after each mixer (density-matrix networks)")
@@ -454,6 +456,49 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_width_sweep(args):
+    """Time per <C> evaluation (forward, full un-reduced networks, p = 1) of
+    18-qubit QAOA circuits on 3- to 7-regular graphs against the width of
+    the contraction ordering (largest intermediate rank minus one: the upper
+    bound on the treewidth that the ordering certifies), for both orderings
+    (Section 5, simulation time against approximate treewidth)."""
+    import torch
+    import paper_1709_03636_gb300 as q
+    from synth import qaoa_angles, random_regular_graph
+    dev = torch.device("cuda", 0)
+    rows = []
+    n = 18
+    for d in (3, 4, 5, 6, 7):
+        for seed in range(4):
+            edges = random_regular_graph(n, d, seed)
+            g, b = qaoa_angles(1, seed)
+            circ = q.Circuit.qaoa(n, edges, 1)
+            params = torch.tensor(g + b, dtype=torch.float64, device=dev)
+            for ordering in ("lg", "stoch"):
+                bt = q.Batch(circ, lightcone=False, ordering=ordering, seed=seed)
+                need = bt.program_info("c64", False)["work_bytes"]
+                engine = q.Engine(0, arena_bytes=int(need) + (1 << 30))
+                out = torch.zeros(3 + len(edges), dtype=torch.float64, device=dev)
+                f = lambda: q.qaoa_expectation_device(engine, bt, params, out, "c64")  # noqa
+                for _ in range(2):
+                    f()
+                torch.cuda.synchronize()
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record()
+                for _ in range(args.steps):
+                    f()
+                s1.record()
+                torch.cuda.synchronize()
+                st = bt.stats()
+                row = {"d": d, "seed": seed, "ordering": ordering, "width": st["max_rank"] - 1,
+                       "ms": s0.elapsed_time(s1) / args.steps, "C": out[0].item()}
+                rows.append(row)
+                print(json.dumps(row), file=sys.stderr, flush=True)
+                del engine
+                torch.cuda.empty_cache()
+    print(json.dumps({"width_sweep": rows}), flush=True)
+
+
 def run_crossover(args):
     """Time per <C> evaluation (forward) of the light-cone tensor networks, the
     full un-reduced networks and the 2^n state vector, for d = 3..7 at each n."""
@@ -516,6 +561,9 @@ def main():
     args = parse()
     if args.crossover:
         run_crossover(args)
+        return
+    if args.width_sweep:
+        run_width_sweep(args)
         return
     if args.impl == "reference":
         run_reference(args)

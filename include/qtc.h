@@ -191,9 +191,11 @@ void qtc_circuit_destroy(qtc_circuit* c);
  * pair gives that form back).  lightcone != 0 keeps only the gates in the
  * reverse light cone of the observable.  diag_mode != 0 attaches diagonal
  * gates (ZZ, RZ, Z) to the wire they act on, so one index may be shared by
- * more than two tensors; diag_mode = 0 gives every gate its own input and
- * output wires (rank-4 ZZ tensors).  A leading H on |0> is folded into the
- * state |+>. */
+ * more than two tensors, and gives CNOT its sparse form: the control wire
+ * passes through and the target gets a rank-3 tensor t_out = t_in xor c
+ * (the gate sparsity Sections 5-6 name as missing); diag_mode = 0 gives
+ * every gate its own input and output wires (rank-4 ZZ and CNOT tensors).
+ * A leading H on |0> is folded into the state |+>. */
 qtc_status qtc_network_build(const qtc_circuit* c, const qtc_observable* obs,
                              int lightcone, int diag_mode, qtc_network** out);
 /* Leaves of a network, for inspection.  counts: host, 2 ints

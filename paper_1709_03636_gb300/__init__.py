@@ -16,7 +16,7 @@ from ._lib import (QtcError, check, lib, qtc_batch_info, qtc_observable, qtc_pla
 __all__ = [
     "QtcError", "Engine", "Circuit", "Network", "Plan", "Batch", "DTYPES", "ORDERINGS",
     "contract", "qaoa_expectation", "qaoa_expectation_device", "QAOAExpectation",
-    "statevector_expectation", "statevector_expectation_device",
+    "statevector_expectation", "statevector_expectation_device", "optimize_angles",
     "GATES",
 ]
 
@@ -343,6 +343,33 @@ def _autograd():
             return grad_out * g, None, None, None
 
     return QAOAExpectation
+
+
+def optimize_angles(engine: Engine, batch: Batch, gammas, betas, *, steps: int = 200,
+                    lr: float = 0.05, dtype="c64", tol: float = 1e-9):
+    """Maximise <C>(gamma, beta) with Adam on the adjoint gradient (the loop
+    the paper drives with NLopt, Section 4.1): every step is one launch of
+    the executor for <C> and d<C>/d(gamma, beta).  Returns (best <C>, gammas,
+    betas, history of <C>).  Stops early when <C> changes by less than tol
+    (relative) over 10 steps."""
+    import torch
+    p = len(gammas)
+    x = torch.tensor(list(gammas) + list(betas), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([x], lr=lr)
+    hist = []
+    best = (-float("inf"), None)
+    for _ in range(steps):
+        opt.zero_grad()
+        c = QAOAExpectation.apply(x, engine, batch, dtype)
+        (-c).backward()
+        hist.append(float(c.detach()))
+        if hist[-1] > best[0]:
+            best = (hist[-1], x.detach().clone())
+        opt.step()
+        if len(hist) > 10 and abs(hist[-1] - hist[-11]) <= tol * abs(hist[-1]):
+            break
+    xb = best[1].tolist()
+    return best[0], xb[:p], xb[p:], hist
 
 
 class _LazyAutograd:

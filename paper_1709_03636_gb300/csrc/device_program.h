@@ -18,6 +18,8 @@ namespace qtc {
 //   rank 2 observable [bra, ket]: index = bra | ket << 1, value O[bra][ket]
 //   ZZDIAG (a, b):           index = a | b << 1, value exp(-i t z_a z_b / 2)
 //   rank 4 [a_out, b_out, a_in, b_in]: value U[(a_out b_out), (a_in b_in)]
+//   CNOTX [t_out, c, t_in]: 1 where t_out = t_in xor c (sparse CNOT: the
+//     control wire is shared, as for diagonal gates)
 //   channel [ket_out, bra_out, ket_in, bra_in] (DEPOL, DEPHASE, AMPDAMP; the
 //     strength is the spec's constant): sum_k K_k[ket_out][ket_in]
 //     conj(K_k[bra_out][bra_in])
@@ -29,7 +31,8 @@ enum LeafKind : uint8_t {
   LK_OBS_X = 15, LK_OBS_Y = 16, LK_OBS_Z = 17,
   LK_DEPOL = 18, LK_DEPHASE = 19, LK_AMPDAMP = 20,
   LK_OBS_I = 21,          // [bra, ket] identity: closes a wire explicitly
-  LK_COUNT = 22
+  LK_CNOTX = 22,          // CNOT as XOR [t_out, c, t_in]; the control is a hyperedge
+  LK_COUNT = 23
 };
 
 QTC_HD inline int leaf_rank_of(int kind) {
@@ -39,6 +42,8 @@ QTC_HD inline int leaf_rank_of(int kind) {
       return 1;
     case LK_ZZ: case LK_CNOT: case LK_DEPOL: case LK_DEPHASE: case LK_AMPDAMP:
       return 4;
+    case LK_CNOTX:
+      return 3;
     default:
       return 2;
   }

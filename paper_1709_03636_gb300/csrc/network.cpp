@@ -195,6 +195,13 @@ Network build_network(const Circuit& c, const qtc_observable& obs, bool lightcon
       }
       net.leaves.push_back({spec_of(kind, conj, &g), {out, cur[q]}});
       cur[q] = out;
+    } else if (diag && g.kind == QTC_GATE_CNOT) {
+      // sparse CNOT: the control wire passes through (a hyperedge), the
+      // target gets t_out = t_in xor control
+      int a = g.q[0], b = g.q[1];
+      int ob = new_label();
+      net.leaves.push_back({plain(LK_CNOTX, conj), {ob, cur[a], cur[b]}});
+      cur[b] = ob;
     } else {
       int a = g.q[0], b = g.q[1];
       int oa = new_label(), ob = new_label();

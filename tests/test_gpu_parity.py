@@ -223,3 +223,20 @@ def test_trivial_angles_give_half_the_edges(engine):
     C, per_edge, _ = q.qaoa_expectation(engine, batch, [0.0, 0.0], [0.4, 0.9], "c64")
     assert abs(C - len(edges) / 2) < 1e-6
     assert np.max(np.abs(per_edge)) < 1e-6
+
+
+@pytest.mark.parametrize("diag", [True, False])
+def test_cnot_heavy_circuit_sparse_and_dense(engine, diag):
+    """A random 12-qubit circuit of H, RX, RZ and CNOT (sparse XOR CNOT
+    tensors in diag mode, dense rank-4 otherwise), full network, against a
+    state-vector reference."""
+    from test_host_plans import build_generic, random_cnot_circuit, statevector_reference
+    n = 12
+    gates = random_cnot_circuit(n, 80, 3)
+    circ = build_generic(n, gates)
+    pauli = "ZIIXIIIIYIIZ"
+    ref = statevector_reference(n, gates, pauli)
+    net = q.Network(circ, "pauli", pauli=pauli, lightcone=False, diag=diag)
+    plan = q.Plan(net, "lg", seed=1)
+    assert abs(q.contract(engine, plan, [], "c128") - ref) < 1e-11
+    assert abs(q.contract(engine, plan, [], "c64") - ref) < 2e-5

@@ -61,6 +61,12 @@ def leaf_tensor(kind, conj, slot, coeff, constant, params):
         return v
     if kind == 21:
         return np.eye(2, dtype=complex)
+    if kind == 22:  # sparse CNOT [t_out, c, t_in]
+        v = np.zeros((2, 2, 2), dtype=complex)
+        for cc in range(2):
+            for tt in range(2):
+                v[tt ^ cc, cc, tt] = 1
+        return v
     if kind == 13:
         v = np.zeros((2, 2, 2, 2), dtype=complex)
         for a in range(2):
@@ -244,6 +250,80 @@ def test_generic_circuit_pauli_observables(pauli, diag, lightcone):
     net = q.Network(circ, "pauli", pauli=pauli, lightcone=lightcone, diag=diag)
     val = run_plan(net, q.Plan(net, "lg"), params)
     assert abs(val - ref) < 1e-12
+
+
+def random_cnot_circuit(n, n_gates, seed):
+    """A CNOT-heavy random circuit: (gate, qubits, angle) with H, RX, RZ, CNOT."""
+    rng = np.random.default_rng(seed)
+    gates = [("h", (q,), 0.0) for q in range(n)]
+    for _ in range(n_gates):
+        k = rng.integers(4)
+        if k < 2:
+            a, b = rng.choice(n, 2, replace=False)
+            gates.append(("cnot", (int(a), int(b)), 0.0))
+        else:
+            gates.append((("rx", "rz")[k - 2], (int(rng.integers(n)),), float(rng.uniform(-3, 3))))
+    return gates
+
+
+def statevector_reference(n, gates, pauli):
+    """<psi|P|psi> by applying the gates to a 2^n state one by one."""
+    psi = np.zeros((2,) * n, dtype=complex)
+    psi[(0,) * n] = 1
+    ax = lambda q: n - 1 - q  # noqa: E731
+    mats = {"h": np.array([[1, 1], [1, -1]]) * R, "x": np.array([[0, 1], [1, 0]]),
+            "y": np.array([[0, -1j], [1j, 0]]), "z": np.diag([1, -1])}
+    for g, qs, t in gates:
+        if g == "cnot":
+            c, tq = qs
+            sel = [slice(None)] * n
+            sel[ax(c)] = 1
+            sub = psi[tuple(sel)].copy()
+            t_axis = ax(tq) - (1 if ax(tq) > ax(c) else 0)
+            psi[tuple(sel)] = np.flip(sub, axis=t_axis)
+            continue
+        if g == "rx":
+            u = np.array([[math.cos(t / 2), -1j * math.sin(t / 2)],
+                          [-1j * math.sin(t / 2), math.cos(t / 2)]])
+        elif g == "rz":
+            u = np.diag([np.exp(-0.5j * t), np.exp(0.5j * t)])
+        else:
+            u = mats[g]
+        psi = np.moveaxis(np.tensordot(u, psi, axes=([1], [ax(qs[0])])), 0, ax(qs[0]))
+    phi = psi
+    for q_ in range(n):
+        if pauli[q_] != "I":
+            phi = np.moveaxis(np.tensordot(mats[pauli[q_].lower()], phi, axes=([1], [ax(q_)])),
+                              0, ax(q_))
+    return complex(np.vdot(psi, phi))
+
+
+def build_generic(n, gates):
+    circ = q.Circuit(n, 0)
+    for g, qs, t in gates:
+        circ.add_gate(g, list(qs), -1, 0.0, t)
+    return circ
+
+
+def test_sparse_cnot_matches_and_lowers_cost():
+    """CNOT as a rank-3 XOR tensor with a shared control wire (diag mode)
+    against the dense rank-4 form: the same value, and a far cheaper
+    contraction (multiply-adds of the best of three LG plans, summed over
+    random CNOT-heavy circuits; measured ~4x fewer at 8-16 qubits)."""
+    n = 8
+    cost = {True: 0.0, False: 0.0}
+    for seed in range(4):
+        gates = random_cnot_circuit(n, 40, seed)
+        circ = build_generic(n, gates)
+        pauli = "ZIXIYIIZ"
+        ref = statevector_reference(n, gates, pauli)
+        for diag in (True, False):
+            net = q.Network(circ, "pauli", pauli=pauli, lightcone=False, diag=diag)
+            plans = [q.Plan(net, "lg", seed=s) for s in range(3)]
+            best = min(plans, key=lambda pl: pl.stats()["cmacs"])
+            cost[diag] += best.stats()["cmacs"]
+            assert abs(run_plan(net, best, []) - ref) < 1e-11
+    assert cost[True] < 0.5 * cost[False], cost
 
 
 def test_generic_amplitudes():
