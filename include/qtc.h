@@ -74,14 +74,21 @@ typedef enum qtc_obs_kind {
   QTC_OBS_ZZ = 0,         /* Z_u Z_v                                        */
   QTC_OBS_IDENTITY = 1,   /* the identity: <psi|psi> = 1 (needs lightcone=0) */
   QTC_OBS_PAULI = 2,      /* pauli[q] in {'I','X','Y','Z'} for q = 0..n-1    */
-  QTC_OBS_AMPLITUDE = 3   /* <x|psi>, x given by bits[q] in {0,1}            */
+  QTC_OBS_AMPLITUDE = 3,  /* <x|psi>, x given by bits[q] in {0,1}            */
+  QTC_OBS_PROJECTOR = 4   /* <psi| prod_q P_q |psi>: bits[q] = 0 or 1 projects
+                           * qubit q on |0> or |1>, 2 leaves it unmeasured;
+                           * the probability of the measured outcomes
+                           * (Section 3.3).  Every qubit gets one closing
+                           * tensor, so with lightcone = 0 all projector
+                           * networks of a circuit share one structure
+                           * (see qtc_plan_reuse).                           */
 } qtc_obs_kind;
 
 typedef struct qtc_observable {
   int kind;               /* qtc_obs_kind                                   */
   int u, v;               /* qubits of QTC_OBS_ZZ                           */
   const char* pauli;      /* QTC_OBS_PAULI: n characters, host              */
-  const uint8_t* bits;    /* QTC_OBS_AMPLITUDE: n bytes, host               */
+  const uint8_t* bits;    /* QTC_OBS_AMPLITUDE, _PROJECTOR: n bytes, host   */
 } qtc_observable;
 
 /* Contraction ordering (Section 3.1). */
@@ -212,6 +219,12 @@ void qtc_network_destroy(qtc_network* n);
 /* ---- plans (Section 3.1, Algorithms 1 and 2) ---------------------------- */
 qtc_status qtc_plan_create(const qtc_network* n, const qtc_plan_opts* opts,
                            qtc_plan** out);
+/* A plan for network n with the contraction tree of `like`, without a new
+ * ordering search: n must have the same structure (leaf count, and every
+ * leaf's labels) as like's network; only the tensor values may differ (e.g.
+ * the projector networks of one circuit, Section 3.3's sequence of
+ * contractions reusing one ordering).  QTC_ERR_INVALID otherwise. */
+qtc_status qtc_plan_reuse(const qtc_plan* like, const qtc_network* n, qtc_plan** out);
 qtc_status qtc_plan_stats(const qtc_plan* p, qtc_plan_info* info);
 /* Writes the contraction tree: for step s, operands (lhs[s], rhs[s]) are
  * tensor ids (0..n_tensors-1 leaves, n_tensors+t the result of step t).

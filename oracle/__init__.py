@@ -20,6 +20,8 @@ Parts (each module cites the passage it follows):
 * ``superop``    — the paper's dim-4 superoperator tensors (Section 2) and
   a density-matrix network evaluator, used to pin the bond-dimension-2
   sandwich reading against the paper's own form.
+* ``answer``     — Section 3.3's sequential answer-string estimate over an
+  exact probability vector.
 * ``density``    — O-DM: the density matrix of the QAOA circuit with a
   Kraus channel (depolarizing, dephasing, amplitude damping) on every qubit
   after each layer's mixer; <Z_a Z_b>, <C> and a finite-difference gradient.

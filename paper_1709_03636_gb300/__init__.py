@@ -17,6 +17,7 @@ __all__ = [
     "QtcError", "Engine", "Circuit", "Network", "Plan", "Batch", "DTYPES", "ORDERINGS",
     "contract", "qaoa_expectation", "qaoa_expectation_device", "QAOAExpectation",
     "statevector_expectation", "statevector_expectation_device", "optimize_angles",
+    "answer_string",
     "GATES",
 ]
 
@@ -24,7 +25,7 @@ DTYPES = {"c128": 0, "c64": 1, "split_bf16": 2}
 ORDERINGS = {"stoch": 0, "lg": 1}
 GATES = {"h": 0, "x": 1, "y": 2, "z": 3, "rx": 4, "rz": 5, "zz": 6, "cnot": 7,
          "depolarize": 8, "dephase": 9, "ampdamp": 10}
-OBS = {"zz": 0, "identity": 1, "pauli": 2, "amplitude": 3}
+OBS = {"zz": 0, "identity": 1, "pauli": 2, "amplitude": 3, "projector": 4}
 
 
 def _dtype(d):
@@ -156,7 +157,7 @@ class Network(_Handle):
             s = pauli.encode()
             keep.append(s)
             obs.pauli = s
-        elif observable == "amplitude":
+        elif observable in ("amplitude", "projector"):
             arr = (ctypes.c_uint8 * len(bits))(*[int(b) for b in bits])
             keep.append(arr)
             obs.bits = ctypes.cast(arr, ctypes.POINTER(ctypes.c_uint8))
@@ -193,10 +194,15 @@ def plan_opts(ordering="lg", seed=0, max_rejections=10, restarts=8, budget_ms=0.
 class Plan(_Handle):
     _destroy = "qtc_plan_destroy"
 
-    def __init__(self, network: Network, ordering="lg", seed=0, **kw):
+    def __init__(self, network: Network, ordering="lg", seed=0, *, like=None, **kw):
+        """Ordering search for `network`; with like=<Plan> the contraction tree
+        of that plan is reused (same network structure, other values)."""
         h = ctypes.c_void_p()
-        opts = plan_opts(ordering, seed, **kw)
-        check(lib.qtc_plan_create(network.ptr, ctypes.byref(opts), ctypes.byref(h)))
+        if like is not None:
+            check(lib.qtc_plan_reuse(like.ptr, network.ptr, ctypes.byref(h)))
+        else:
+            opts = plan_opts(ordering, seed, **kw)
+            check(lib.qtc_plan_create(network.ptr, ctypes.byref(opts), ctypes.byref(h)))
         super().__init__(h)
         self.n_params = network.n_params
 
@@ -343,6 +349,38 @@ def _autograd():
             return grad_out * g, None, None, None
 
     return QAOAExpectation
+
+
+def answer_string(engine: Engine, circuit: Circuit, params, dtype="c128", ordering="lg",
+                  seed=0, rng=None):
+    """Section 3.3's estimate of a likely output bit string: qubit by qubit,
+    contract <psi| P |psi> with the earlier qubits projected on their chosen
+    values and the current one on |0>; keep the more probable value (a tie
+    is broken at random with `rng`, default numpy's seeded generator).  All
+    n contractions share one contraction tree (the networks differ only in
+    projector values).  Returns (bits, probabilities of each chosen prefix).
+    The circuit may hold noise channels (density-matrix marginals)."""
+    import numpy as np
+    rng = rng or np.random.default_rng(seed)
+    n = circuit.n
+    bits = [2] * n
+    probs = []
+    prev = 1.0
+    first = None
+    for q in range(n):
+        bits[q] = 0
+        net = Network(circuit, "projector", bits=bits, lightcone=False)
+        plan = Plan(net, like=first) if first is not None else Plan(net, ordering, seed)
+        if first is None:
+            first = plan
+        p0 = contract(engine, plan, params, dtype).real
+        p1 = prev - p0
+        if p0 > p1 or (p0 == p1 and rng.integers(2) == 0):
+            bits[q], prev = 0, p0
+        else:
+            bits[q], prev = 1, p1
+        probs.append(prev)
+    return bits, probs
 
 
 def optimize_angles(engine: Engine, batch: Batch, gammas, betas, *, steps: int = 200,

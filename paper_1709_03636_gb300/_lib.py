@@ -59,6 +59,7 @@ SIGNATURES = {
     "qtc_circuit_create": (c_int, [c_int, c_int, P(c_void_p)]),
     "qtc_circuit_add_gate": (c_int, [c_void_p, c_int, P(c_int32), c_int, c_double, c_double]),
     "qtc_circuit_qaoa": (c_int, [c_int, P(c_int32), c_int, c_int, P(c_void_p)]),
+    "qtc_plan_reuse": (c_int, [c_void_p, c_void_p, P(c_void_p)]),
     "qtc_circuit_qaoa_noisy": (c_int, [c_int, P(c_int32), c_int, c_int, c_int, c_double,
                                        P(c_void_p)]),
     "qtc_circuit_destroy": (None, [c_void_p]),

@@ -422,6 +422,25 @@ extern "C" qtc_status qtc_plan_create(const qtc_network* n, const qtc_plan_opts*
   });
 }
 
+extern "C" qtc_status qtc_plan_reuse(const qtc_plan* like, const qtc_network* n,
+                                     qtc_plan** out) {
+  return guarded([&] {
+    if (!like || !n || !out) fail(QTC_ERR_INVALID, "null argument");
+    const Network& a = like->plan.net;
+    const Network& b = n->net;
+    if (a.n_labels != b.n_labels || a.leaves.size() != b.leaves.size())
+      fail(QTC_ERR_INVALID, "networks differ in structure (%zu vs %zu leaves)", a.leaves.size(),
+           b.leaves.size());
+    for (size_t i = 0; i < a.leaves.size(); ++i)
+      if (a.leaves[i].labels != b.leaves[i].labels)
+        fail(QTC_ERR_INVALID, "networks differ in structure at leaf %zu", i);
+    auto p = std::make_unique<qtc_plan>();
+    p->plan = like->plan;
+    p->plan.net = b;   // same labels, the new tensor values
+    *out = p.release();
+  });
+}
+
 extern "C" qtc_status qtc_plan_stats(const qtc_plan* p, qtc_plan_info* info) {
   return guarded([&] {
     if (!p || !info) fail(QTC_ERR_INVALID, "null argument");

@@ -32,13 +32,15 @@ enum LeafKind : uint8_t {
   LK_DEPOL = 18, LK_DEPHASE = 19, LK_AMPDAMP = 20,
   LK_OBS_I = 21,          // [bra, ket] identity: closes a wire explicitly
   LK_CNOTX = 22,          // CNOT as XOR [t_out, c, t_in]; the control is a hyperedge
-  LK_COUNT = 23
+  LK_ONES = 23,           // [a] = (1, 1): closes a shared ket/bra wire (trace)
+  LK_OBS_P0 = 24, LK_OBS_P1 = 25,   // [bra, ket] projectors |0><0|, |1><1|
+  LK_COUNT = 26
 };
 
 QTC_HD inline int leaf_rank_of(int kind) {
   switch (kind) {
     case LK_ZERO: case LK_PLUS: case LK_PROJ0: case LK_PROJ1:
-    case LK_ZDIAG: case LK_RZDIAG:
+    case LK_ZDIAG: case LK_RZDIAG: case LK_ONES:
       return 1;
     case LK_ZZ: case LK_CNOT: case LK_DEPOL: case LK_DEPHASE: case LK_AMPDAMP:
       return 4;

@@ -76,6 +76,9 @@ __device__ inline void gate_tensor(const GateSpec& s, const double* params, T* v
       break;
     case LK_Z: case LK_OBS_Z: val[0].x = R(1); val[3].x = R(-1); break;
     case LK_OBS_I: val[0].x = R(1); val[3].x = R(1); break;
+    case LK_ONES: val[0].x = R(1); val[1].x = R(1); break;
+    case LK_OBS_P0: val[0].x = R(1); break;
+    case LK_OBS_P1: val[3].x = R(1); break;
     case LK_CNOTX:
       for (int c = 0; c < 2; ++c)
         for (int t = 0; t < 2; ++t) val[(t ^ c) | c << 1 | t << 2].x = R(1);

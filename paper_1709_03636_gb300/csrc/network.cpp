@@ -68,8 +68,8 @@ GateSpec plain(uint8_t kind, bool conj) { return spec_of(kind, conj, nullptr); }
 Network build_network(const Circuit& c, const qtc_observable& obs, bool lightcone,
                       bool diag) {
   const int n = c.n;
-  std::vector<char> op(n, 'I');
-  bool amplitude = false;
+  std::vector<char> op(n, 'I');   // 'I', 'X', 'Y', 'Z', or '0'/'1' (projector)
+  bool amplitude = false, projector = false;
   std::vector<int> bits(n, 0);
   switch (obs.kind) {
     case QTC_OBS_ZZ:
@@ -101,6 +101,18 @@ Network build_network(const Circuit& c, const qtc_observable& obs, bool lightcon
         bits[q] = obs.bits[q];
       }
       break;
+    case QTC_OBS_PROJECTOR: {
+      if (!obs.bits) fail(QTC_ERR_INVALID, "projector observable without bits");
+      projector = true;
+      bool any = false;
+      for (int q = 0; q < n; ++q) {
+        if (obs.bits[q] > 2) fail(QTC_ERR_INVALID, "projector entry %d at qubit %d", obs.bits[q], q);
+        op[q] = obs.bits[q] == 2 ? 'I' : (obs.bits[q] ? '1' : '0');
+        any |= obs.bits[q] != 2;
+      }
+      if (lightcone && !any) fail(QTC_ERR_INVALID, "no measured qubit: empty light cone");
+      break;
+    }
     default:
       fail(QTC_ERR_INVALID, "unknown observable kind %d", obs.kind);
   }
@@ -112,7 +124,7 @@ Network build_network(const Circuit& c, const qtc_observable& obs, bool lightcon
     std::vector<char> in_d(n, 0);
     for (int q = 0; q < n; ++q) {
       in_s[q] = op[q] != 'I';
-      in_d[q] = op[q] == 'Z';
+      in_d[q] = op[q] == 'Z' || op[q] == '0' || op[q] == '1';  // diagonal operators
     }
     for (int gi = G - 1; gi >= 0; --gi) {
       const Gate& g = c.gates[gi];
@@ -220,10 +232,12 @@ Network build_network(const Circuit& c, const qtc_observable& obs, bool lightcon
   for (int gi = 0; gi < G; ++gi) channels |= keep[gi] && gate_is_channel(c.gates[gi].kind);
   if (channels && amplitude)
     fail(QTC_ERR_INVALID, "a circuit with noise channels has no amplitude network");
-  if (channels) {
+  if (channels && !projector) {
     // A channel that is the last operation on a qubit closed by the trace
     // (identity observable) is the identity there (trace preserving): drop
-    // it, and any channels it uncovers.
+    // it, and any channels it uncovers.  (Projector networks keep it: their
+    // wires close with explicit tensors, and every projector network of a
+    // circuit keeps one structure.)
     for (int q = 0; q < n; ++q) {
       if (!in_s[q] || op[q] != 'I') continue;
       for (int gi = G - 1; gi >= 0; --gi) {
@@ -274,7 +288,28 @@ Network build_network(const Circuit& c, const qtc_observable& obs, bool lightcon
     for (int q = 0; q < n; ++q) {
       if (!in_s[q]) continue;
       switch (op[q]) {
+        case '0':
+        case '1':
+          if (diag && !channels) {
+            unite.push_back({bra[q], ket[q]});
+            net.leaves.push_back({plain(op[q] == '1' ? LK_PROJ1 : LK_PROJ0, false), {ket[q]}});
+          } else {
+            net.leaves.push_back({plain(op[q] == '1' ? LK_OBS_P1 : LK_OBS_P0, false),
+                                  {bra[q], ket[q]}});
+          }
+          break;
         case 'I':
+          // projector networks close unmeasured qubits with a tensor too, so
+          // that every projector network of a circuit has one structure
+          if (projector && diag && !channels) {
+            unite.push_back({bra[q], ket[q]});
+            net.leaves.push_back({plain(LK_ONES, false), {ket[q]}});
+            break;
+          }
+          if (projector) {
+            net.leaves.push_back({plain(LK_OBS_I, false), {bra[q], ket[q]}});
+            break;
+          }
           // with channels a wire is closed by an explicit identity tensor: a
           // merged label could repeat an index of a channel tensor
           if (channels)

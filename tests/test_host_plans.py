@@ -61,6 +61,10 @@ def leaf_tensor(kind, conj, slot, coeff, constant, params):
         return v
     if kind == 21:
         return np.eye(2, dtype=complex)
+    if kind == 23:  # (1, 1): closes a shared ket/bra wire
+        return np.array([1, 1], dtype=complex)
+    if kind in (24, 25):  # [bra, ket] projector
+        return np.diag([1, 0] if kind == 24 else [0, 1]).astype(complex)
     if kind == 22:  # sparse CNOT [t_out, c, t_in]
         v = np.zeros((2, 2, 2), dtype=complex)
         for cc in range(2):
@@ -158,6 +162,34 @@ def test_channel_arguments_are_checked():
     c.add_gate("h", [0]).add_gate("ampdamp", [0], constant=0.3)
     with pytest.raises(q.QtcError):
         q.Network(c, "amplitude", bits=[0, 0], lightcone=False)
+
+
+@pytest.mark.parametrize("diag", [True, False])
+@pytest.mark.parametrize("lightcone", [True, False])
+def test_projector_networks_give_prefix_probabilities(diag, lightcone):
+    """<psi| prod P |psi> (Section 3.3) for projector patterns, against sums of
+    |psi|^2; with lightcone = 0 the networks of all patterns share one
+    structure, and one plan serves them all."""
+    n = 8
+    edges = random_regular_graph(n, 3, 12)
+    g, b = [0.52, 1.17], [0.93, 0.31]
+    p = np.abs(sv.qaoa_state(n, edges, g, b).reshape(-1)) ** 2
+    idx = np.arange(1 << n)
+    circ = q.Circuit.qaoa(n, edges, 2)
+    first = None
+    for bits in ([0, 2, 2, 2, 2, 2, 2, 2], [1, 0, 2, 1, 2, 2, 2, 2], [1, 0, 1, 1, 0, 0, 1, 0],
+                 [2, 2, 2, 2, 2, 1, 2, 2]):
+        mask = sum(1 << k for k in range(n) if bits[k] != 2)
+        pat = sum(bits[k] << k for k in range(n) if bits[k] != 2)
+        ref = p[(idx & mask) == pat].sum()
+        net = q.Network(circ, "projector", bits=bits, lightcone=lightcone, diag=diag)
+        if lightcone:
+            plan = q.Plan(net, "lg", seed=2)
+        else:
+            plan = q.Plan(net, like=first) if first else q.Plan(net, "lg", seed=2)
+            first = first or plan
+        val = run_plan(net, plan, g + b)
+        assert abs(val - ref) < 1e-12
 
 
 def test_plans_are_binary_trees():
