@@ -75,14 +75,6 @@ __device__ inline void gate_tensor(const GateSpec& s, const double* params, T* v
       val[1].y = R(1);   // [1][0] = +i
       break;
     case LK_Z: case LK_OBS_Z: val[0].x = R(1); val[3].x = R(-1); break;
-    case LK_OBS_I: val[0].x = R(1); val[3].x = R(1); break;
-    case LK_ONES: val[0].x = R(1); val[1].x = R(1); break;
-    case LK_OBS_P0: val[0].x = R(1); break;
-    case LK_OBS_P1: val[3].x = R(1); break;
-    case LK_CNOTX:
-      for (int c = 0; c < 2; ++c)
-        for (int t = 0; t < 2; ++t) val[(t ^ c) | c << 1 | t << 2].x = R(1);
-      break;
     case LK_RX:  // cos(t/2) I - i sin(t/2) X, [out, in]
       val[0].x = ch; val[3].x = ch; val[1].y = -sh; val[2].y = -sh;
       der[0].x = -half * sh * dth; der[3].x = -half * sh * dth;
@@ -111,40 +103,38 @@ __device__ inline void gate_tensor(const GateSpec& s, const double* params, T* v
       for (int c = 0; c < 2; ++c)
         for (int t = 0; t < 2; ++t) val[c | (t ^ c) << 1 | c << 2 | t << 3].x = R(1);
       break;
+    case LK_OBS_I: val[0].x = R(1); val[3].x = R(1); break;
+    case LK_ONES: val[0].x = R(1); val[1].x = R(1); break;
+    case LK_OBS_P0: val[0].x = R(1); break;
+    case LK_OBS_P1: val[3].x = R(1); break;
+    case LK_CNOTX:  // [t_out, c, t_in]: 1 where t_out = t_in xor c
+      for (int i = 0; i < 8; ++i) val[i].x = ((i & 1) == (((i >> 1) ^ (i >> 2)) & 1)) ? R(1) : R(0);
+      break;
     case LK_DEPOL: case LK_DEPHASE: case LK_AMPDAMP: {
-      // Kraus operators K[k][row][col] of the channel, then
-      // value[ko | bo<<1 | ki<<2 | bi<<3] = sum_k K[ko][ki] conj(K[bo][bi])
+      // sum_k K[ko][ki] conj(K[bo][bi]) at index ko | bo<<1 | ki<<2 | bi<<3, in
+      // closed form (all real): depolarizing (1-s) I(x)I + s/3 (XX* + YY* + ZZ*),
+      // dephasing (1-s) I(x)I + s ZZ*, amplitude damping K0 K0* + K1 K1*
       const R st = (R)s.constant;
-      T K[4][2][2];
-      for (int k = 0; k < 4; ++k)
-        for (int r = 0; r < 2; ++r)
-          for (int c = 0; c < 2; ++c) K[k][r][c] = T{R(0), R(0)};
-      int nk = 2;
-      if (s.kind == LK_DEPOL) {
-        const R a = sqrt(R(1) - st), b = sqrt(st / R(3));
-        K[0][0][0].x = a; K[0][1][1].x = a;
-        K[1][0][1].x = b; K[1][1][0].x = b;                  // X
-        K[2][0][1].y = -b; K[2][1][0].y = b;                 // Y = [[0, -i], [i, 0]]
-        K[3][0][0].x = b; K[3][1][1].x = -b;                 // Z
-        nk = 4;
-      } else if (s.kind == LK_DEPHASE) {
-        const R a = sqrt(R(1) - st), b = sqrt(st);
-        K[0][0][0].x = a; K[0][1][1].x = a;
-        K[1][0][0].x = b; K[1][1][1].x = -b;
-      } else {
-        K[0][0][0].x = R(1); K[0][1][1].x = sqrt(R(1) - st);
-        K[1][0][1].x = sqrt(st);
-      }
-      for (int k = 0; k < nk; ++k)
-        for (int i = 0; i < 16; ++i) {
-          const T a = K[k][i & 1][(i >> 2) & 1];         // K[ko][ki]
-          const T b = K[k][(i >> 1) & 1][(i >> 3) & 1];  // K[bo][bi]
-          val[i].x += a.x * b.x + a.y * b.y;
-          val[i].y += a.y * b.x - a.x * b.y;
+      for (int i = 0; i < 16; ++i) {
+        const int ko = i & 1, bo = (i >> 1) & 1, ki = (i >> 2) & 1, bi = (i >> 3) & 1;
+        const bool keep = ko == ki && bo == bi;
+        const R zz = (ko ^ bo) ? R(-1) : R(1);   // Z[ko][ko] Z[bo][bo]
+        R v = R(0);
+        if (s.kind == LK_DEPOL) {
+          if (keep) v = (R(1) - st) + st / R(3) * zz;
+          else if (ko != ki && bo != bi && ko == bo) v = R(2) * st / R(3);  // XX* + YY*
+        } else if (s.kind == LK_DEPHASE) {
+          if (keep) v = (R(1) - st) + st * zz;
+        } else {
+          if (keep) v = (ko ? sqrt(R(1) - st) : R(1)) * (bo ? sqrt(R(1) - st) : R(1));
+          else if (ko == 0 && bo == 0 && ki == 1 && bi == 1) v = st;
         }
+        val[i].x = v;
+      }
       break;
     }
-    default: break;
+    default:
+      break;
   }
   if (s.conj)
     for (int i = 0; i < n; ++i) {
