@@ -49,7 +49,7 @@ KERNEL_SOURCES = {
 NCU_TRAFFIC = {
     # (workload, kernel, dtype, want_grad): (bytes per launch, source hash, profile summary)
     ("qaoa_p1_n50_d3", "smem_exec_kernel", "c64", True):
-        (1823232, "c034b83b090c494f", "profiles/smem_exec_kernel_qaoa_p1_n50_d3.md"),
+        (1822976, "79f8dc77ece812cf", "profiles/smem_exec_kernel_qaoa_p1_n50_d3.md"),
 }
 
 
