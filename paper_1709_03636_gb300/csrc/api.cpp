@@ -645,18 +645,25 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
   for (const TaskDev& t : hp->tasks) max_ops = std::max(max_ops, t.op_count);
   for (const Plan& pl : b->plans) max_rank = std::max(max_rank, pl.max_rank);
   auto round16 = [](size_t x) { return (uint32_t)((x + 15) & ~size_t(15)); };
-  hp->table_bytes = round16((size_t)table_elems * elem);
-  // warp teams need every op within the pre-expanded tables
-  bool warp_ok = max_rank <= kWarpMaxRank;
+  // warp teams need every op within the pre-expanded tables, and every
+  // element of the table copy and arena within a 16-bit lane offset
+  bool warp_ok = max_rank <= kWarpMaxRank && (size_t)table_elems + hp->max_arena <= 0xffffu;
   for (const SOp& op : hp->ops)
     if (op.code == SOP_CONTRACT && (op.rc > kWarpMaxRank || op.ry > kWarpMaxSummed))
       warp_ok = false;
+  // CTA teams share one gate table at the start of shared memory; a warp team
+  // keeps its own copy right before its arena ([steps | lane gradient
+  // accumulators | table | arena]), so every operand of a warp step is an
+  // offset from one base.
   auto layout = [&](bool warp, uint32_t stage) {
     hp->warp_teams = warp;
     hp->n_teams = warp ? kExecBlock / 32 : 1;
     hp->stage_ops = stage;
     const size_t op_bytes = warp ? sizeof(WStep) : sizeof(SOp);
-    hp->team_bytes = round16((size_t)stage * op_bytes + (size_t)hp->max_arena * elem);
+    hp->table_bytes = warp ? 0 : round16((size_t)table_elems * elem);
+    const size_t lane_grad = (warp && want_grad && P <= kWarpLaneGradSlots) ? (size_t)P * 32 : 0;
+    hp->team_bytes = round16((size_t)stage * op_bytes +
+                             (lane_grad + hp->max_arena + (warp ? table_elems : 0)) * elem);
     hp->smem = hp->table_bytes + (size_t)hp->n_teams * hp->team_bytes;
     return hp->smem <= max_dynamic;
   };

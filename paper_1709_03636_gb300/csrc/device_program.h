@@ -110,6 +110,10 @@ struct alignas(16) SOp {
 // leaf-gradient dot fused into the op that produces it).
 constexpr int kWarpMaxRank = 7;
 constexpr int kWarpMaxSummed = 4;
+// With at most this many parameters a warp team keeps one complex gradient
+// accumulator per (parameter, lane) in shared memory, right after its staged
+// steps; each lane adds its own leaf-gradient terms there without shuffles.
+constexpr int kWarpLaneGradSlots = 8;
 
 enum WOpFlag : uint8_t { WOPF_LEAFGRAD = 1 };
 
@@ -137,14 +141,14 @@ enum WLaneFlag : uint8_t {
   WLF_LG_MUL = 4,   // leaf gradient: group-sum of out * d(leaf)/dparam into slot
   WLF_LG_ADD = 8    // leaf gradient: group-sum of the product itself into slot
 };
-// Lane operand offsets: bit 15 set = gate table element, else team arena.
-constexpr uint16_t kWTable = 0x8000;
+// Lane offsets count elements from the start of the warp's gate-table copy
+// (the table, then the warp's arena).
 // WStep::rounds bit 7: some lane adds a leaf gradient (low bits: rounds).
 constexpr uint8_t kWHasLeafGrad = 0x80;
 
 struct alignas(16) WLane {
   uint8_t kind, flags, gw, slot;   // gw: log2 of the op's lane-group width
-  uint16_t c_off, a_off, b_off;    // output (arena), first-term operands
+  uint16_t c_off, a_off, b_off;    // output, first-term operands
   uint16_t der_off;                // WLF_LG_MUL: table offset of d(leaf)/dparam
   uint16_t ya1, yb1;               // WLF_Y1: element deltas of the second term
 };

@@ -73,33 +73,28 @@ __device__ __forceinline__ void warp_contract(const WOp& op, const uint4 head, T
   }
 }
 
-// Parameter slots whose leaf-gradient terms a warp team accumulates in
-// registers (per lane; summed over the warp once per network).
-constexpr int kRegSlots = 8;
-
 // One bundle step of a warp program: every lane computes its own output
 // element (one or two summed terms, Eq. 1) of the op its lane group belongs
 // to.  Leaf-gradient lanes form out * d(leaf)/dparam (or the plain product);
-// with few parameters each lane adds its term to its own register
-// accumulator of the slot, otherwise the lane group sums with shuffles and
-// its first lane adds the sum to the slot in shared memory.
+// with few parameters each lane adds its term to its own accumulator of the
+// slot (lacc_s: this lane's column, one row of 32 per slot), otherwise the
+// lane group sums with shuffles and its first lane adds the sum to the slot.
+// Every offset counts elements from base_s, the warp's gate-table copy, which
+// its arena follows.
 template <typename T>
-__device__ __forceinline__ void warp_bundle(const uint4 L, uint32_t rounds, uint32_t table_s,
-                                            uint32_t arena_s, decltype(T::x)* grad,
-                                            decltype(T::x) (&racc)[2 * kRegSlots], bool reg_grad,
-                                            double* res_row, uint32_t lane) {
+__device__ __forceinline__ void warp_bundle(const uint4 L, uint32_t rounds, uint32_t base_s,
+                                            decltype(T::x)* grad, uint32_t lacc_s,
+                                            bool lane_grad, double* res_row, uint32_t lane) {
   constexpr uint32_t kE = sizeof(T);
   const uint32_t kind = L.x & 0xffu, flags = (L.x >> 8) & 0xffu;
   const uint32_t gw = (L.x >> 16) & 0xffu, slot = L.x >> 24;
-  const uint32_t a_off = L.y >> 16, b_off = L.z & 0xffffu;
-  const uint32_t pa = ((a_off & kWTable) ? table_s : arena_s) + (a_off & 0x7fffu) * kE;
-  const uint32_t pb = ((b_off & kWTable) ? table_s : arena_s) + (b_off & 0x7fffu) * kE;
+  const uint32_t pa = base_s + (L.y >> 16) * kE, pb = base_s + (L.z & 0xffffu) * kE;
   const T a0 = lds_c<T>(pa), b0 = lds_c<T>(pb);
   T acc = cfma(a0, b0, czero<T>());
   if (flags & WLF_Y1)
     acc = cfma(lds_c<T>(pa + (L.w & 0xffffu) * kE), lds_c<T>(pb + (L.w >> 16) * kE), acc);
   if (kind == WL_SEED) acc = from_d2<T>(make_double2(1.0, 0.0));
-  if (flags & WLF_STORE) sts_c(arena_s + (L.y & 0xffffu) * kE, acc);
+  if (flags & WLF_STORE) sts_c(base_s + (L.y & 0xffffu) * kE, acc);
   if (kind == WL_RESULT) {
     const double2 v = to_d2(a0);
     res_row[0] = v.x;
@@ -107,15 +102,16 @@ __device__ __forceinline__ void warp_bundle(const uint4 L, uint32_t rounds, uint
   }
   if (rounds & kWHasLeafGrad) {
     T v = czero<T>();
-    if (flags & WLF_LG_MUL) v = cfma(acc, lds_c<T>(table_s + (L.z >> 16) * kE), v);
+    if (flags & WLF_LG_MUL) v = cfma(acc, lds_c<T>(base_s + (L.z >> 16) * kE), v);
     else if (flags & WLF_LG_ADD) v = acc;
-    if (reg_grad) {
-#pragma unroll
-      for (uint32_t q = 0; q < (uint32_t)kRegSlots; ++q)
-        if (q == slot) {
-          racc[2 * q] += v.x;
-          racc[2 * q + 1] += v.y;
-        }
+    if (lane_grad) {
+      if (flags & (WLF_LG_MUL | WLF_LG_ADD)) {
+        const uint32_t p = lacc_s + slot * (32u * kE);
+        T s = lds_c<T>(p);
+        s.x += v.x;
+        s.y += v.y;
+        sts_c(p, s);
+      }
       return;
     }
     for (uint32_t r = 0; r < (rounds & 0x7fu); ++r) {
@@ -133,6 +129,17 @@ __device__ __forceinline__ void warp_bundle(const uint4 L, uint32_t rounds, uint
   }
 }
 
+// A warp team's own copy of the gate table (its lanes stride over the gates).
+template <typename T>
+__device__ __forceinline__ void build_warp_gate_table(const ProgramDev& prog, T* table,
+                                                      uint32_t lane) {
+  for (int e = (int)lane; e < prog.n_gates; e += 32) {
+    const GateEntryDev g = e < kInlineGates ? prog.gates_inline[e] : prog.gates[e];
+    gate_tensor<T>(g.spec, prog.params, table + g.val_off,
+                   g.spec.slot >= 0 ? table + g.der_off : nullptr);
+  }
+}
+
 template <typename T, bool kWarp>
 __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
   using R = decltype(T::x);
@@ -142,21 +149,27 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
   __shared__ unsigned int s_task[kMaxTeams];
   __shared__ int s_last;
   __shared__ double s_part[(1 + kMaxParams) * kReduceThreads / 32];
-  T* table = reinterpret_cast<T*>(smem_raw);
 
+  // A CTA team reads the gate table at the start of shared memory; a warp
+  // team keeps its own copy between its staged steps and its arena, so its
+  // table and arena offsets run on from one another.
   using OpT = typename std::conditional<kWarp, WStep, SOp>::type;
   const Team<kWarp> team;
+  const int P = prog.n_params;
   const int teams_per_cta = blockDim.x / team.size;
   unsigned char* team_base = smem_raw + prog.table_bytes + (size_t)team.id * prog.team_bytes;
   OpT* stage = reinterpret_cast<OpT*>(team_base);
-  T* arena = reinterpret_cast<T*>(team_base + (size_t)prog.stage_ops * sizeof(OpT));
+  T* after_stage = reinterpret_cast<T*>(team_base + (size_t)prog.stage_ops * sizeof(OpT));
+  const bool lane_grad = kWarp && prog.want_grad && P <= kWarpLaneGradSlots;
+  T* table = kWarp ? after_stage + (lane_grad ? 32 * P : 0) : reinterpret_cast<T*>(smem_raw);
+  T* arena = kWarp ? table + prog.table_elems : after_stage;
   const OpT* ops = kWarp ? reinterpret_cast<const OpT*>(prog.wsteps)
                          : reinterpret_cast<const OpT*>(prog.ops);
   R* grad = s_grad[team.id];
-  const int P = prog.n_params;
   const int stride = 2 + 2 * P;
   constexpr int kWords = sizeof(OpT) / sizeof(uint4);
-  const uint32_t stage_s = smem_u32(stage), table_s = smem_u32(table), arena_s = smem_u32(arena);
+  const uint32_t stage_s = smem_u32(stage), table_s = smem_u32(table);
+  const uint32_t lacc_s = smem_u32(after_stage) + team.tid * (uint32_t)sizeof(T);
 
   // Each team's first network is fixed by its position (no queue round
   // trip); its first op chunk is copied asynchronously while the gate table
@@ -171,17 +184,18 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
     uint4* dst = reinterpret_cast<uint4*>(stage);
     for (uint32_t w = team.tid; w < n * kWords; w += team.size) cp_async16(dst + w, src + w);
   }
-  build_gate_table<T>(prog.gates, prog.n_gates, prog.params, table, prog.gates_inline,
-                      kInlineGates);
+  if (kWarp)
+    build_warp_gate_table<T>(prog, table, team.tid);
+  else
+    build_gate_table<T>(prog.gates, prog.n_gates, prog.params, table, prog.gates_inline,
+                        kInlineGates);
   cp_async_wait_all();
   __syncthreads();
   bool staged = true;
-  const bool reg_grad = kWarp && P <= kRegSlots;
-  R racc[2 * kRegSlots];
   while (t < (unsigned)prog.n_tasks) {
     for (int i = team.tid; i < 2 * P; i += team.size) grad[i] = R(0);
-#pragma unroll
-    for (int i = 0; i < 2 * kRegSlots; ++i) racc[i] = R(0);
+    if (lane_grad)
+      for (int q = 0; q < P; ++q) sts_c(lacc_s + q * 32u * (uint32_t)sizeof(T), czero<T>());
     for (uint32_t base = 0; base < task.op_count; base += prog.stage_ops) {
       const uint32_t n = min(prog.stage_ops, task.op_count - base);
       if (!staged) {
@@ -212,7 +226,7 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
             l_next = lds_u4(nxt + 16 + 16 * team.tid);
           }
           if (!(h & 0xffu)) {
-            warp_bundle<T>(L, (h >> 8) & 0xffu, table_s, arena_s, grad, racc, reg_grad,
+            warp_bundle<T>(L, (h >> 8) & 0xffu, table_s, grad, lacc_s, lane_grad,
                            prog.results + (size_t)task.net * stride, team.tid);
           } else {
             // solo step; header word: code, rc, ry, flags | out, in1 | in2, slot | der
@@ -269,14 +283,14 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
         team.sync();
       }
     }
-    if (reg_grad) {
-      // sum the lanes' register accumulators into the network's slots
-#pragma unroll
-      for (int i = 0; i < 2 * kRegSlots; ++i) {
-        if (i >= 2 * P) break;
-        R v = racc[i];
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (team.tid == 0) grad[i] += v;
+    if (lane_grad) {
+      // sum the lanes' accumulators into the network's slots
+      for (int q = 0; q < P; ++q) {
+        T v = warp_csum(lds_c<T>(lacc_s + q * 32u * (uint32_t)sizeof(T)), 32u);
+        if (team.tid == 0) {
+          grad[2 * q] += v.x;
+          grad[2 * q + 1] += v.y;
+        }
       }
       team.sync();
     }

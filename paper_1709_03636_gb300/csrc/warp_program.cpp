@@ -94,9 +94,9 @@ Access accesses(const WOp& w, uint32_t table_elems) {
   return acc;
 }
 
-uint16_t lane_operand(uint32_t off, uint32_t table_elems) {
-  return off < table_elems ? (uint16_t)(kWTable | off) : (uint16_t)(off - table_elems);
-}
+// Lane offsets are team relative: the warp's own gate-table copy first, then
+// its arena (the same numbering as the shared-memory ops).
+uint16_t lane_operand(uint32_t off, uint32_t) { return (uint16_t)off; }
 
 struct Slotted {
   uint32_t mask = 0;   // lanes in use
@@ -172,7 +172,7 @@ void build_warp_steps(const std::vector<SOp>& ops, uint32_t table_elems, uint32_
         if (w.code == SOP_CONTRACT) {
           l.kind = WL_CONTRACT;
           l.flags = WLF_STORE;
-          l.c_off = (uint16_t)(w.out - table_elems + c);
+          l.c_off = (uint16_t)(w.out + c);
           l.a_off = (uint16_t)(lane_operand(w.in1, table_elems) + w.a_lo[c]);
           l.b_off = (uint16_t)(lane_operand(w.in2, table_elems) + w.b_lo[c]);
           if (w.ry == 1) {
@@ -195,7 +195,7 @@ void build_warp_steps(const std::vector<SOp>& ops, uint32_t table_elems, uint32_
         } else {
           l.kind = WL_SEED;
           l.flags = WLF_STORE;
-          l.c_off = (uint16_t)(w.out - table_elems);
+          l.c_off = (uint16_t)w.out;
         }
         if (l.flags & (WLF_LG_MUL | WLF_LG_ADD))
           st.step.rounds = (uint8_t)(kWHasLeafGrad |
@@ -211,8 +211,6 @@ void build_warp_steps(const std::vector<SOp>& ops, uint32_t table_elems, uint32_
         if (!(st.mask & (1u << l))) {
           // idle lanes read table element 0 and write nothing
           st.step.lane[l] = WLane{};
-          st.step.lane[l].a_off = kWTable;
-          st.step.lane[l].b_off = kWTable;
         }
     out.push_back(st.step);
   }
