@@ -674,25 +674,48 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
     }
   };
   bool ok = false;
-  if (warp_ok) {
-    // schedule each network's ops into warp steps (lane-packed bundles)
+  // Schedule each network's ops into warp steps (lane-packed bundles).  First
+  // with an arena buffer per intermediate and adjoint: ops that would reuse
+  // memory no longer wait for its last reader, so independent subtrees share
+  // steps.  That layout is taken when it fits with the whole step list staged
+  // at once; otherwise the reused arena.
+  for (int pass = 0; warp_ok && pass < 2 && !ok; ++pass) {
+    const bool reuse = pass == 1;
     std::vector<TaskDev> wtasks = hp->tasks;
     std::vector<WStep> wsteps;
-    uint32_t max_steps = 1;
+    uint32_t max_steps = 1, max_arena = 0;
+    bool fit = true;
     for (TaskDev& t : wtasks) {
-      const std::vector<SOp> net_ops(hp->ops.begin() + t.op_begin,
-                                     hp->ops.begin() + t.op_begin + t.op_count);
+      std::vector<SOp> net_ops(hp->ops.begin() + t.op_begin,
+                               hp->ops.begin() + t.op_begin + t.op_count);
+      if (!reuse) {
+        LoweredNet ln = lower_smem(b->plans[t.net], leaf_gate[t.net], val_off, der_off,
+                                   table_elems, want_grad != 0, max_elems, false);
+        if (!ln.fits || (size_t)table_elems + ln.arena_elems > 0xffffu) {
+          fit = false;
+          break;
+        }
+        net_ops = std::move(ln.ops);
+        t.arena_elems = ln.arena_elems;
+      }
+      max_arena = std::max(max_arena, t.arena_elems);
       const uint32_t begin = (uint32_t)wsteps.size();
       build_warp_steps(net_ops, table_elems, t.arena_elems, wsteps);
       t.op_begin = begin;
       t.op_count = (uint32_t)wsteps.size() - begin;
       max_steps = std::max(max_steps, t.op_count);
     }
-    ok = try_layout(true, std::min<uint32_t>(max_steps, 128));
+    if (!fit) continue;
+    const uint32_t shared_arena = hp->max_arena;
+    hp->max_arena = max_arena;
+    const uint32_t stage = std::min<uint32_t>(max_steps, 128);
+    ok = reuse ? try_layout(true, stage) : layout(true, stage);
     if (ok) {
       hp->tasks = std::move(wtasks);
       hp->wsteps = std::move(wsteps);
       hp->ops.clear();
+    } else {
+      hp->max_arena = shared_arena;
     }
   }
   if (!ok) ok = try_layout(false, std::min<uint32_t>(max_ops, 64));

@@ -71,9 +71,10 @@ struct Pending {
 
 // Places the arena buffers referenced by `ops` (first-fit decreasing over op
 // index live ranges; a buffer written by op i and one read last by op i never
-// share memory) and writes the resolved ops.  Returns the arena size.
+// share memory; with reuse off every buffer gets memory of its own) and
+// writes the resolved ops.  Returns the arena size.
 uint32_t place_arena(const std::vector<Pending>& ops, const std::vector<uint32_t>& buf_size,
-                     uint32_t table_elems, std::vector<SOp>& out) {
+                     uint32_t table_elems, std::vector<SOp>& out, bool reuse = true) {
   const int B = (int)buf_size.size();
   std::vector<int> first(B, -1), last(B, -1);
   for (int i = 0; i < (int)ops.size(); ++i) {
@@ -98,7 +99,7 @@ uint32_t place_arena(const std::vector<Pending>& ops, const std::vector<uint32_t
     const uint32_t size = rounded(b);
     std::vector<std::pair<uint32_t, uint32_t>> busy;
     for (int q : placed)
-      if (!(last[q] < first[b] || last[b] < first[q]))
+      if (!reuse || !(last[q] < first[b] || last[b] < first[q]))
         busy.push_back({offset[q], offset[q] + rounded(q)});
     std::sort(busy.begin(), busy.end());
     uint32_t at = 0;
@@ -137,7 +138,7 @@ std::vector<char> needs_grad(const Plan& plan) {
 LoweredNet lower_smem(const Plan& plan, const std::vector<int>& leaf_gate,
                       const std::vector<uint32_t>& gate_val_off,
                       const std::vector<uint32_t>& gate_der_off, uint32_t table_elems,
-                      bool want_grad, uint32_t max_elems) {
+                      bool want_grad, uint32_t max_elems, bool reuse_arena) {
   LoweredNet out;
   const int L = (int)plan.net.leaves.size();
   const int S = (int)plan.steps.size();
@@ -225,7 +226,7 @@ LoweredNet lower_smem(const Plan& plan, const std::vector<int>& leaf_gate,
       }
     }
   }
-  out.arena_elems = place_arena(ops, buf_size, table_elems, out.ops);
+  out.arena_elems = place_arena(ops, buf_size, table_elems, out.ops, reuse_arena);
   out.fits = table_elems + out.arena_elems <= max_elems;
   return out;
 }

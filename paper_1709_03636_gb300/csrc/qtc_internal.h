@@ -144,17 +144,20 @@ struct LoweredNet {
   bool fits = false;
 };
 
-// Lowers one plan to a shared-memory op program.  table_elems: size of the
-// gate value + derivative region that precedes the arena.
 // One network's shared-memory ops as warp steps (lane-packed bundles of
 // independent small ops, solo steps for the rest), appended to `out`.
 void build_warp_steps(const std::vector<SOp>& ops, uint32_t table_elems, uint32_t arena_elems,
                       std::vector<WStep>& out);
 
+// Lowers one plan to a shared-memory op program.  table_elems: size of the
+// gate value + derivative region that precedes the arena.  With reuse_arena
+// off every intermediate and adjoint keeps its own arena buffer (no
+// write-after-read ordering between ops that reuse memory).
 LoweredNet lower_smem(const Plan& plan, const std::vector<int>& leaf_gate,
                       const std::vector<uint32_t>& gate_val_off,
                       const std::vector<uint32_t>& gate_der_off,
-                      uint32_t table_elems, bool want_grad, uint32_t max_elems);
+                      uint32_t table_elems, bool want_grad, uint32_t max_elems,
+                      bool reuse_arena = true);
 
 // ---- graph lowering (networks larger than one CTA's shared memory) ---------
 
