@@ -143,6 +143,7 @@ typedef struct qtc_program_info {
   int n_ops;              /* shared-memory ops over all networks (CTA teams) */
   int n_warp_steps;       /* warp steps over all networks (warp teams)       */
   int max_warp_steps;     /* warp steps of the longest network               */
+  int n_solo_steps;       /* of the warp steps, those one op runs alone      */
 } qtc_program_info;
 
 typedef struct qtc_engine qtc_engine;

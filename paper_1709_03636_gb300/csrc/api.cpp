@@ -677,8 +677,8 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
   // Schedule each network's ops into warp steps (lane-packed bundles).  First
   // with an arena buffer per intermediate and adjoint: ops that would reuse
   // memory no longer wait for its last reader, so independent subtrees share
-  // steps.  That layout is taken when it fits with the whole step list staged
-  // at once; otherwise the reused arena.
+  // steps.  That layout is taken when it fits with the whole step list
+  // staged at once; otherwise the reused arena.
   for (int pass = 0; warp_ok && pass < 2 && !ok; ++pass) {
     const bool reuse = pass == 1;
     std::vector<TaskDev> wtasks = hp->tasks;
@@ -688,6 +688,7 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
     for (TaskDev& t : wtasks) {
       std::vector<SOp> net_ops(hp->ops.begin() + t.op_begin,
                                hp->ops.begin() + t.op_begin + t.op_count);
+      const uint32_t begin = (uint32_t)wsteps.size();
       if (!reuse) {
         LoweredNet ln = lower_smem(b->plans[t.net], leaf_gate[t.net], val_off, der_off,
                                    table_elems, want_grad != 0, max_elems, false);
@@ -695,12 +696,11 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
           fit = false;
           break;
         }
-        net_ops = std::move(ln.ops);
         t.arena_elems = ln.arena_elems;
+        net_ops = std::move(ln.ops);
       }
-      max_arena = std::max(max_arena, t.arena_elems);
-      const uint32_t begin = (uint32_t)wsteps.size();
       build_warp_steps(net_ops, table_elems, t.arena_elems, wsteps);
+      max_arena = std::max(max_arena, t.arena_elems);
       t.op_begin = begin;
       t.op_count = (uint32_t)wsteps.size() - begin;
       max_steps = std::max(max_steps, t.op_count);
@@ -711,6 +711,21 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
     const uint32_t stage = std::min<uint32_t>(max_steps, 128);
     ok = reuse ? try_layout(true, stage) : layout(true, stage);
     if (ok) {
+      // With a fixed stride per task a team starts copying its first task's
+      // steps without first reading the task record; taken when the padding
+      // costs little.
+      const size_t padded = (size_t)wtasks.size() * max_steps;
+      if (padded <= wsteps.size() + wsteps.size() / 2 || padded * sizeof(WStep) <= (16u << 20)) {
+        std::vector<WStep> fixed(padded);
+        for (size_t i = 0; i < wtasks.size(); ++i) {
+          std::copy(wsteps.begin() + wtasks[i].op_begin,
+                    wsteps.begin() + wtasks[i].op_begin + wtasks[i].op_count,
+                    fixed.begin() + i * max_steps);
+          wtasks[i].op_begin = (uint32_t)(i * max_steps);
+        }
+        wsteps = std::move(fixed);
+        hp->task_stride = max_steps;
+      }
       hp->tasks = std::move(wtasks);
       hp->wsteps = std::move(wsteps);
       hp->ops.clear();
@@ -843,7 +858,8 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   auto* dwsteps = (WStep*)e->alloc(sizeof(WStep) * std::max<size_t>(1, hp.wsteps.size()));
   auto* dw = (double*)e->alloc(sizeof(double) * N);
   auto* dparams = (double*)e->alloc(sizeof(double) * std::max(P, 1));
-  auto* dres = (double*)e->alloc(sizeof(double) * (size_t)N * (2 + 2 * P));
+  // per network: the result row, then (after all rows) its weighted terms
+  auto* dres = (double*)e->alloc(sizeof(double) * (size_t)N * ((2 + 2 * P) + (1 + P)));
   auto* dout = (double*)e->alloc(sizeof(double) * (2 + P + N));
   auto* dcnt = (unsigned int*)e->alloc(sizeof(unsigned int) * 4);
   cuda_check(cudaMemcpyAsync(dg, hp.gates.data(), sizeof(GateEntryDev) * G, cudaMemcpyHostToDevice, stream), "upload gates");
@@ -864,6 +880,7 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   d.table_bytes = hp.table_bytes;
   d.team_bytes = hp.team_bytes;
   d.stage_ops = hp.stage_ops;
+  d.task_stride = hp.task_stride;
   d.tasks = dt;
   d.n_tasks = (int)hp.tasks.size();
   d.ops = dops;
@@ -873,6 +890,7 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   d.weights = dw;
   d.params = dparams;
   d.results = dres;
+  d.contrib = dres + (size_t)N * (2 + 2 * P);
   d.out = dout;
   d.counters = dcnt;
   d.want_grad = want_grad;
@@ -950,9 +968,13 @@ extern "C" qtc_status qtc_batch_program_info(qtc_batch* b, int dtype, int want_g
                 sizeof(WStep) * hp.wsteps.size();
       info->warp_teams = hp.warp_teams ? 1 : 0;
       info->n_ops = (int)hp.ops.size();
-      info->n_warp_steps = (int)hp.wsteps.size();
       for (const TaskDev& t : hp.tasks)
-        if (hp.warp_teams) info->max_warp_steps = std::max(info->max_warp_steps, (int)t.op_count);
+        if (hp.warp_teams) {
+          info->n_warp_steps += (int)t.op_count;
+          info->max_warp_steps = std::max(info->max_warp_steps, (int)t.op_count);
+          for (uint32_t k = 0; k < t.op_count; ++k)
+            info->n_solo_steps += hp.wsteps[t.op_begin + k].solo ? 1 : 0;
+        }
     }
     info->table_bytes = tables;
   });

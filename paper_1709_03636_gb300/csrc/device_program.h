@@ -146,8 +146,10 @@ enum WLaneFlag : uint8_t {
 // WStep::rounds bit 7: some lane adds a leaf gradient (low bits: rounds).
 constexpr uint8_t kWHasLeafGrad = 0x80;
 
+// Unused fields are zero: every lane's loads stay at valid offsets.
 struct alignas(16) WLane {
-  uint8_t kind, flags, gw, slot;   // gw: log2 of the op's lane-group width
+  uint8_t kind, flags, gw, slot;   // gw: log2 of the op's lane-group width;
+                                   // slot: parameter of a leaf-gradient lane
   uint16_t c_off, a_off, b_off;    // output, first-term operands
   uint16_t der_off;                // WLF_LG_MUL: table offset of d(leaf)/dparam
   uint16_t ya1, yb1;               // WLF_Y1: element deltas of the second term
@@ -184,6 +186,8 @@ struct ProgramDev {
   uint32_t table_bytes;        // table region, rounded to 16 bytes
   uint32_t team_bytes;         // per team: staged ops, then its arena
   uint32_t stage_ops;          // ops staged per team at a time
+  uint32_t task_stride;        // warp teams: task t's steps start at t * task_stride
+                               // (0: at tasks[t].op_begin)
   const TaskDev* tasks;
   int n_tasks;
   const SOp* ops;              // CTA teams
@@ -193,6 +197,7 @@ struct ProgramDev {
   const double* weights;       // per network, for <C>
   const double* params;        // device, n_params
   double* results;             // per network: Re s, Im s, (Re, Im) ds/dparam_k
+  double* contrib;             // per network: w (1 - Re s)/2, -w/2 Re ds/dparam_k
   double* out;                 // [<C>, d<C>/dparam (n_params), Re s per network]
   unsigned int* counters;      // [0] task queue, [1] finished blocks, [2] error
   int want_grad;

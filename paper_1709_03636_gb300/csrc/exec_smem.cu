@@ -80,37 +80,40 @@ __device__ __forceinline__ void warp_contract(const WOp& op, const uint4 head, T
 // slot (lacc_s: this lane's column, one row of 32 per slot), otherwise the
 // lane group sums with shuffles and its first lane adds the sum to the slot.
 // Every offset counts elements from base_s, the warp's gate-table copy, which
-// its arena follows.
+// its arena follows.  All shared-memory loads of the step issue before any
+// arithmetic (one round trip per step): lanes without a second term read
+// their first operands again (ya1 = yb1 = 0), lanes without a leaf
+// derivative read table element 0, and lanes that add no leaf-gradient term
+// read the accumulator of slot 0.
 template <typename T>
 __device__ __forceinline__ void warp_bundle(const uint4 L, uint32_t rounds, uint32_t base_s,
                                             decltype(T::x)* grad, uint32_t lacc_s,
-                                            bool lane_grad, double* res_row, uint32_t lane) {
+                                            bool lane_grad, uint32_t n_params, uint32_t res_s,
+                                            uint32_t lane) {
   constexpr uint32_t kE = sizeof(T);
   const uint32_t kind = L.x & 0xffu, flags = (L.x >> 8) & 0xffu;
   const uint32_t gw = (L.x >> 16) & 0xffu, slot = L.x >> 24;
   const uint32_t pa = base_s + (L.y >> 16) * kE, pb = base_s + (L.z & 0xffffu) * kE;
+  const uint32_t pl = lacc_s + (slot < n_params ? slot : 0u) * (32u * kE);
   const T a0 = lds_c<T>(pa), b0 = lds_c<T>(pb);
+  const T a1 = lds_c<T>(pa + (L.w & 0xffffu) * kE), b1 = lds_c<T>(pb + (L.w >> 16) * kE);
+  const T d = lds_c<T>(base_s + (L.z >> 16) * kE);
+  T s = czero<T>();
+  if (lane_grad) s = lds_c<T>(pl);
   T acc = cfma(a0, b0, czero<T>());
-  if (flags & WLF_Y1)
-    acc = cfma(lds_c<T>(pa + (L.w & 0xffffu) * kE), lds_c<T>(pb + (L.w >> 16) * kE), acc);
+  if (flags & WLF_Y1) acc = cfma(a1, b1, acc);
   if (kind == WL_SEED) acc = from_d2<T>(make_double2(1.0, 0.0));
   if (flags & WLF_STORE) sts_c(base_s + (L.y & 0xffffu) * kE, acc);
-  if (kind == WL_RESULT) {
-    const double2 v = to_d2(a0);
-    res_row[0] = v.x;
-    res_row[1] = v.y;
-  }
+  if (kind == WL_RESULT) sts_c(res_s, to_d2(a0));
   if (rounds & kWHasLeafGrad) {
     T v = czero<T>();
-    if (flags & WLF_LG_MUL) v = cfma(acc, lds_c<T>(base_s + (L.z >> 16) * kE), v);
+    if (flags & WLF_LG_MUL) v = cfma(acc, d, v);
     else if (flags & WLF_LG_ADD) v = acc;
     if (lane_grad) {
       if (flags & (WLF_LG_MUL | WLF_LG_ADD)) {
-        const uint32_t p = lacc_s + slot * (32u * kE);
-        T s = lds_c<T>(p);
         s.x += v.x;
         s.y += v.y;
-        sts_c(p, s);
+        sts_c(pl, s);
       }
       return;
     }
@@ -125,6 +128,38 @@ __device__ __forceinline__ void warp_bundle(const uint4 L, uint32_t rounds, uint
     if ((flags & (WLF_LG_MUL | WLF_LG_ADD)) && (lane & ((1u << gw) - 1u)) == 0) {
       atomicAdd(&grad[2 * slot], v.x);
       atomicAdd(&grad[2 * slot + 1], v.y);
+    }
+  }
+}
+
+// One warp: out[q] = sum over networks of contrib[e * (1 + P) + q] for
+// q = 0..P (<C> and its gradient), in FP64, in a fixed order (rows e0 + lane,
+// + 32, + 64, + 96 loaded together and added pairwise into the lane's partial
+// sum, then a shuffle tree); zeros when the batch is not reduced to the
+// Max-Cut objective.
+__device__ __forceinline__ void reduce_contrib_rows(const volatile double* contrib, int N, int P,
+                                                    bool qaoa_reduce, double* out,
+                                                    uint32_t lane) {
+  const int nq = 1 + P;
+  for (int q0 = 0; q0 < nq; q0 += 4) {
+    double part[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int e0 = 0; e0 < N; e0 += 128) {
+      double v[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int e = e0 + 32 * r + (int)lane;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          v[r][i] = (e < N && q0 + i < nq) ? contrib[(size_t)e * nq + q0 + i] : 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) part[i] += (v[0][i] + v[1][i]) + (v[2][i] + v[3][i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      double v = part[i];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0 && q0 + i < nq) out[q0 + i] = qaoa_reduce ? v : 0.0;
     }
   }
 }
@@ -147,8 +182,8 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
   // one network's partial derivatives per team, in the element precision
   __shared__ R s_grad[kMaxTeams][2 * kMaxParams];
   __shared__ unsigned int s_task[kMaxTeams];
+  __shared__ double2 s_res[kMaxTeams];   // the network's scalar, per team
   __shared__ int s_last;
-  __shared__ double s_part[(1 + kMaxParams) * kReduceThreads / 32];
 
   // A CTA team reads the gate table at the start of shared memory; a warp
   // team keeps its own copy between its staged steps and its arena, so its
@@ -170,6 +205,7 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
   constexpr int kWords = sizeof(OpT) / sizeof(uint4);
   const uint32_t stage_s = smem_u32(stage), table_s = smem_u32(table);
   const uint32_t lacc_s = smem_u32(after_stage) + team.tid * (uint32_t)sizeof(T);
+  const uint32_t res_s = smem_u32(&s_res[team.id]);
 
   // Each team's first network is fixed by its position (no queue round
   // trip); its first op chunk is copied asynchronously while the gate table
@@ -178,11 +214,19 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
   unsigned int t = blockIdx.x * teams_per_cta + team.id;
   TaskDev task{};
   if (t < (unsigned)prog.n_tasks) {
-    task = prog.tasks[t];
-    const uint32_t n = min(prog.stage_ops, task.op_count);
-    const uint4* src = reinterpret_cast<const uint4*>(ops + task.op_begin);
     uint4* dst = reinterpret_cast<uint4*>(stage);
-    for (uint32_t w = team.tid; w < n * kWords; w += team.size) cp_async16(dst + w, src + w);
+    if (kWarp && prog.task_stride) {
+      // fixed stride: the copy starts before the task record arrives
+      const uint4* src = reinterpret_cast<const uint4*>(ops + (size_t)t * prog.task_stride);
+      for (uint32_t w = team.tid; w < prog.stage_ops * kWords; w += team.size)
+        cp_async16(dst + w, src + w);
+      task = prog.tasks[t];
+    } else {
+      task = prog.tasks[t];
+      const uint32_t n = min(prog.stage_ops, task.op_count);
+      const uint4* src = reinterpret_cast<const uint4*>(ops + task.op_begin);
+      for (uint32_t w = team.tid; w < n * kWords; w += team.size) cp_async16(dst + w, src + w);
+    }
   }
   if (kWarp)
     build_warp_gate_table<T>(prog, table, team.tid);
@@ -190,9 +234,10 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
     build_gate_table<T>(prog.gates, prog.n_gates, prog.params, table, prog.gates_inline,
                         kInlineGates);
   cp_async_wait_all();
-  __syncthreads();
+  team.sync();  // a warp team's table and steps are its own
   bool staged = true;
   while (t < (unsigned)prog.n_tasks) {
+    const double w_net = prog.weights[task.net];  // used once the network is done
     for (int i = team.tid; i < 2 * P; i += team.size) grad[i] = R(0);
     if (lane_grad)
       for (int q = 0; q < P; ++q) sts_c(lacc_s + q * 32u * (uint32_t)sizeof(T), czero<T>());
@@ -226,8 +271,8 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
             l_next = lds_u4(nxt + 16 + 16 * team.tid);
           }
           if (!(h & 0xffu)) {
-            warp_bundle<T>(L, (h >> 8) & 0xffu, table_s, grad, lacc_s, lane_grad,
-                           prog.results + (size_t)task.net * stride, team.tid);
+            warp_bundle<T>(L, (h >> 8) & 0xffu, table_s, grad, lacc_s, lane_grad, (uint32_t)P,
+                           res_s, team.tid);
           } else {
             // solo step; header word: code, rc, ry, flags | out, in1 | in2, slot | der
             const WOp& w = op.op;
@@ -242,11 +287,7 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
               warp_leaf_dot<T>(in1, in2, 1u << ((head.x >> 8) & 0xffu), team.tid, grad,
                                head.z >> 16);
             } else if (code == SOP_RESULT) {
-              if (team.tid == 0) {
-                const double2 v = to_d2(*in1);
-                prog.results[(size_t)task.net * stride] = v.x;
-                prog.results[(size_t)task.net * stride + 1] = v.y;
-              }
+              if (team.tid == 0) s_res[team.id] = to_d2(*in1);
             } else if (code == SOP_SEED) {
               if (team.tid == 0) *out = from_d2<T>(make_double2(1.0, 0.0));
             }
@@ -265,11 +306,8 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
                                  team.tid, grad, op.out);
               break;
             case SOP_RESULT:
-              if (team.tid == 0) {
-                const double2 v = to_d2(*resolve(op.in1, table, arena, prog.table_elems));
-                prog.results[(size_t)task.net * stride] = v.x;
-                prog.results[(size_t)task.net * stride + 1] = v.y;
-              }
+              if (team.tid == 0) s_res[team.id] = to_d2(*resolve(op.in1, table, arena,
+                                                                prog.table_elems));
               break;
             case SOP_SEED:
               if (team.tid == 0)
@@ -294,8 +332,21 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
       }
       team.sync();
     }
+    // the network's row (scalar and derivatives), its weighted terms of <C>
+    // and of the gradient (Section 4.1), and its entry of the output
+    double* row = prog.results + (size_t)task.net * stride;
+    double* crow = prog.contrib + (size_t)task.net * (1 + P);
+    if (team.tid == 0) {
+      const double2 sv = s_res[team.id];
+      row[0] = sv.x;
+      row[1] = sv.y;
+      crow[0] = 0.5 * w_net * (1.0 - sv.x);
+      prog.out[1 + P + task.net] = sv.x;
+    }
     for (int i = team.tid; i < 2 * P; i += team.size)
-      prog.results[(size_t)task.net * stride + 2 + i] = prog.want_grad ? (double)grad[i] : 0.0;
+      row[2 + i] = prog.want_grad ? (double)grad[i] : 0.0;
+    for (int q = team.tid; q < P; q += team.size)
+      crow[1 + q] = prog.want_grad ? -0.5 * w_net * (double)grad[2 * q] : 0.0;
     // networks beyond the statically assigned ones come from the queue
     const unsigned int n_static = gridDim.x * teams_per_cta;
     if (n_static >= (unsigned)prog.n_tasks) break;
@@ -305,14 +356,24 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
     if (t < (unsigned)prog.n_tasks) task = prog.tasks[t];
   }
 
-  // the last CTA reduces in FP64 and re-arms the counters
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomic_add_acq_rel(&prog.counters[1], 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!s_last) return;
-  reduce_network_rows(prog.results, prog.weights, prog.n_nets, P, prog.qaoa_reduce != 0,
-                      prog.out, s_part);
-  if (threadIdx.x == 0) {
+  // A team counts itself out after its last queue fetch (its first thread's
+  // release, after the team barrier, covers the team's row writes); the last
+  // team out sums the weighted rows in FP64 and re-arms the counters (no team
+  // touches them afterwards).
+  team.sync();
+  bool last = false;
+  if (team.tid == 0)
+    last = atomic_add_acq_rel(&prog.counters[1], 1u) == gridDim.x * teams_per_cta - 1;
+  if (kWarp) {
+    last = __shfl_sync(0xffffffffu, last, 0);
+  } else {
+    if (team.tid == 0) s_last = last;
+    team.sync();
+    last = s_last;
+  }
+  if (!last || team.tid >= 32) return;
+  reduce_contrib_rows(prog.contrib, prog.n_nets, P, prog.qaoa_reduce != 0, prog.out, team.tid);
+  if (team.tid == 0) {
     prog.out[1 + P + prog.n_nets] = 0.0;  // status: this executor never waits
     prog.counters[0] = 0;
     prog.counters[1] = 0;

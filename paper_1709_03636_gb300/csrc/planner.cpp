@@ -288,6 +288,42 @@ std::vector<Step> eliminate(const Network& net, const std::vector<int>& order) {
   return st.steps;
 }
 
+// Per-step label layout.  A label's death is the step that sums it; every
+// intermediate stores its labels by decreasing death step (the label that
+// survives longest is bit 0), so operands of later steps share low bits.
+void layout_labels(Plan& plan) {
+  const Network& net = plan.net;
+  const int L = (int)net.leaves.size();
+  const int S = (int)plan.steps.size();
+  TNState st(net);
+  std::vector<int> death(net.n_labels, S);
+  std::vector<std::vector<int>> result_sets;
+  for (int s = 0; s < S; ++s) {
+    const Step& stp = plan.steps[s];
+    std::vector<int> u;
+    std::set_union(st.lab[stp.a].begin(), st.lab[stp.a].end(), st.lab[stp.b].begin(),
+                   st.lab[stp.b].end(), std::back_inserter(u));
+    int id = st.contract(stp.a, stp.b);
+    for (int l : u)
+      if (!std::binary_search(st.lab[id].begin(), st.lab[id].end(), l)) death[l] = s;
+    result_sets.push_back(st.lab[id]);
+  }
+  plan.labels.assign(L + S, {});
+  for (int i = 0; i < L; ++i) plan.labels[i] = net.leaves[i].labels;
+  for (int s = 0; s < S; ++s) {
+    std::vector<int> r = result_sets[s];
+    std::sort(r.begin(), r.end(), [&](int x, int y) {
+      if (death[x] != death[y]) return death[x] > death[y];
+      return x < y;
+    });
+    plan.labels[L + s] = r;
+  }
+  Cost c = cost_of(net, plan.steps);
+  plan.max_rank = c.max_rank;
+  plan.cmacs = c.flops;
+  plan.bytes_c64 = 8.0 * c.elems;
+}
+
 }  // namespace
 
 Plan make_plan(const Network& net, const qtc_plan_opts& o) {
@@ -327,38 +363,7 @@ Plan make_plan(const Network& net, const qtc_plan_opts& o) {
     fail(QTC_ERR_UNSUPPORTED, "a single-leaf network needs no contraction");
   }
 
-  // Per-step label layout.  A label's death is the step that sums it; every
-  // intermediate stores its labels by decreasing death step (the label that
-  // survives longest is bit 0), so operands of later steps share low bits.
-  const int L = (int)net.leaves.size();
-  const int S = (int)plan.steps.size();
-  TNState st(net);
-  std::vector<int> death(net.n_labels, S);
-  std::vector<std::vector<int>> result_sets;
-  for (int s = 0; s < S; ++s) {
-    const Step& stp = plan.steps[s];
-    std::vector<int> u;
-    std::set_union(st.lab[stp.a].begin(), st.lab[stp.a].end(), st.lab[stp.b].begin(),
-                   st.lab[stp.b].end(), std::back_inserter(u));
-    int id = st.contract(stp.a, stp.b);
-    for (int l : u)
-      if (!std::binary_search(st.lab[id].begin(), st.lab[id].end(), l)) death[l] = s;
-    result_sets.push_back(st.lab[id]);
-  }
-  plan.labels.resize(L + S);
-  for (int i = 0; i < L; ++i) plan.labels[i] = net.leaves[i].labels;
-  for (int s = 0; s < S; ++s) {
-    std::vector<int> r = result_sets[s];
-    std::sort(r.begin(), r.end(), [&](int x, int y) {
-      if (death[x] != death[y]) return death[x] > death[y];
-      return x < y;
-    });
-    plan.labels[L + s] = r;
-  }
-  Cost c = cost_of(net, plan.steps);
-  plan.max_rank = c.max_rank;
-  plan.cmacs = c.flops;
-  plan.bytes_c64 = 8.0 * c.elems;
+  layout_labels(plan);
   return plan;
 }
 

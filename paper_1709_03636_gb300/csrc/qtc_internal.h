@@ -237,6 +237,7 @@ struct HostProgram {
   uint32_t table_bytes = 0;        // gate table region, 16-byte rounded
   uint32_t team_bytes = 0;         // per team: staged ops + arena
   uint32_t stage_ops = 0;          // ops staged per team at a time
+  uint32_t task_stride = 0;        // warp steps of task t start at t * task_stride (0: packed)
   bool warp_teams = false;         // one network per warp (small networks)
   int n_teams = 1;                 // teams per CTA
   size_t smem = 0;                 // dynamic shared memory per CTA, bytes

@@ -77,7 +77,8 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
     const size_t o_wsteps = align256(o_ops + sizeof(SOp) * hp.ops.size());
     const size_t o_weights = align256(o_wsteps + sizeof(WStep) * hp.wsteps.size());
     const size_t o_results = align256(o_weights + sizeof(double) * N);
-    const size_t o_counters = align256(o_results + sizeof(double) * (size_t)N * (2 + 2 * P));
+    const size_t o_contrib = align256(o_results + sizeof(double) * (size_t)N * (2 + 2 * P));
+    const size_t o_counters = align256(o_contrib + sizeof(double) * (size_t)N * (1 + P));
     const size_t total = o_counters + sizeof(unsigned int) * 4;
     if (total > kScratchBytes)
       fail(QTC_ERR_ARENA,
@@ -121,6 +122,7 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
     d.table_bytes = hp.table_bytes;
     d.team_bytes = hp.team_bytes;
     d.stage_ops = hp.stage_ops;
+    d.task_stride = hp.task_stride;
     d.tasks = (const TaskDev*)(base + o_tasks);
     d.n_tasks = (int)hp.tasks.size();
     d.ops = (const SOp*)(base + o_ops);
@@ -130,6 +132,7 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
     d.weights = (const double*)(base + o_weights);
     d.params = params_dev;
     d.results = (double*)(base + o_results);
+    d.contrib = (double*)(base + o_contrib);
     d.out = out_dev;
     d.counters = (unsigned int*)(base + o_counters);
     d.want_grad = hp.want_grad;

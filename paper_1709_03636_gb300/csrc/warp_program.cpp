@@ -168,7 +168,10 @@ void build_warp_steps(const std::vector<SOp>& ops, uint32_t table_elems, uint32_
       for (uint32_t c = 0; c < width; ++c) {
         WLane& l = st.step.lane[pos + c];
         l.gw = (uint8_t)gw;
-        l.slot = (uint8_t)w.slot;
+        // the parameter slot of a leaf-gradient lane; 0 for the others
+        const bool leaf = (w.code == SOP_CONTRACT && (w.flags & WOPF_LEAFGRAD)) ||
+                          w.code == SOP_LEAFGRAD;
+        l.slot = leaf ? (uint8_t)w.slot : (uint8_t)0;
         if (w.code == SOP_CONTRACT) {
           l.kind = WL_CONTRACT;
           l.flags = WLF_STORE;
