@@ -276,7 +276,10 @@ qtc_status qtc_batch_prepare(qtc_engine* e, qtc_batch* b, int dtype,
  * gammas, betas: host, p values each.  C_out: host, 1 double.
  * per_edge_out: host, nullable, m doubles <Z_u Z_v>_i.
  * grad_out: host, nullable (needs want_grad), 2p doubles
- * d<C>/d(gamma_1..p, beta_1..p).  Synchronises `stream`. */
+ * d<C>/d(gamma_1..p, beta_1..p).  Synchronises `stream`.  <C> and the
+ * gradient are FP64 sums over the edge networks; with the shared-memory
+ * executor the terms are added in no fixed order (atomics), so repeated
+ * calls can differ in the last bits. */
 qtc_status qtc_qaoa_expectation(qtc_engine* e, qtc_batch* b,
                                 const double* gammas, const double* betas,
                                 int dtype, int want_grad, void* stream,

@@ -858,8 +858,8 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   auto* dwsteps = (WStep*)e->alloc(sizeof(WStep) * std::max<size_t>(1, hp.wsteps.size()));
   auto* dw = (double*)e->alloc(sizeof(double) * N);
   auto* dparams = (double*)e->alloc(sizeof(double) * std::max(P, 1));
-  // per network: the result row, then (after all rows) its weighted terms
-  auto* dres = (double*)e->alloc(sizeof(double) * (size_t)N * ((2 + 2 * P) + (1 + P)));
+  auto* dres = (double*)e->alloc(sizeof(double) * (size_t)N * (2 + 2 * P));
+  auto* dacc = (double*)e->alloc(sizeof(double) * (1 + P));
   auto* dout = (double*)e->alloc(sizeof(double) * (2 + P + N));
   auto* dcnt = (unsigned int*)e->alloc(sizeof(unsigned int) * 4);
   cuda_check(cudaMemcpyAsync(dg, hp.gates.data(), sizeof(GateEntryDev) * G, cudaMemcpyHostToDevice, stream), "upload gates");
@@ -872,6 +872,7 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
                "upload warp steps");
   cuda_check(cudaMemcpyAsync(dw, hp.weights.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream), "upload weights");
   cuda_check(cudaMemsetAsync(dcnt, 0, sizeof(unsigned int) * 4, stream), "clear counters");
+  cuda_check(cudaMemsetAsync(dacc, 0, sizeof(double) * (1 + P), stream), "clear sums");
   cuda_check(cudaStreamSynchronize(stream), "prepare sync");
   d.gates = dg;
   d.n_gates = G;
@@ -890,7 +891,7 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   d.weights = dw;
   d.params = dparams;
   d.results = dres;
-  d.contrib = dres + (size_t)N * (2 + 2 * P);
+  d.acc = dacc;
   d.out = dout;
   d.counters = dcnt;
   d.want_grad = want_grad;

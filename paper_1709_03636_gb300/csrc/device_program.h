@@ -197,7 +197,8 @@ struct ProgramDev {
   const double* weights;       // per network, for <C>
   const double* params;        // device, n_params
   double* results;             // per network: Re s, Im s, (Re, Im) ds/dparam_k
-  double* contrib;             // per network: w (1 - Re s)/2, -w/2 Re ds/dparam_k
+  double* acc;                 // [1 + n_params]: sums over networks of w (1 - Re s)/2 and
+                               // -w/2 Re ds/dparam_k; zero between launches
   double* out;                 // [<C>, d<C>/dparam (n_params), Re s per network]
   unsigned int* counters;      // [0] task queue, [1] finished blocks, [2] error
   int want_grad;

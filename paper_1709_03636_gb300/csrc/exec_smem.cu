@@ -132,38 +132,6 @@ __device__ __forceinline__ void warp_bundle(const uint4 L, uint32_t rounds, uint
   }
 }
 
-// One warp: out[q] = sum over networks of contrib[e * (1 + P) + q] for
-// q = 0..P (<C> and its gradient), in FP64, in a fixed order (rows e0 + lane,
-// + 32, + 64, + 96 loaded together and added pairwise into the lane's partial
-// sum, then a shuffle tree); zeros when the batch is not reduced to the
-// Max-Cut objective.
-__device__ __forceinline__ void reduce_contrib_rows(const volatile double* contrib, int N, int P,
-                                                    bool qaoa_reduce, double* out,
-                                                    uint32_t lane) {
-  const int nq = 1 + P;
-  for (int q0 = 0; q0 < nq; q0 += 4) {
-    double part[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int e0 = 0; e0 < N; e0 += 128) {
-      double v[4][4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int e = e0 + 32 * r + (int)lane;
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          v[r][i] = (e < N && q0 + i < nq) ? contrib[(size_t)e * nq + q0 + i] : 0.0;
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) part[i] += (v[0][i] + v[1][i]) + (v[2][i] + v[3][i]);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      double v = part[i];
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      if (lane == 0 && q0 + i < nq) out[q0 + i] = qaoa_reduce ? v : 0.0;
-    }
-  }
-}
-
 // A warp team's own copy of the gate table (its lanes stride over the gates).
 template <typename T>
 __device__ __forceinline__ void build_warp_gate_table(const ProgramDev& prog, T* table,
@@ -183,7 +151,7 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
   __shared__ R s_grad[kMaxTeams][2 * kMaxParams];
   __shared__ unsigned int s_task[kMaxTeams];
   __shared__ double2 s_res[kMaxTeams];   // the network's scalar, per team
-  __shared__ int s_last;
+  __shared__ int s_last[kMaxTeams];
 
   // A CTA team reads the gate table at the start of shared memory; a warp
   // team keeps its own copy between its staged steps and its arena, so its
@@ -332,21 +300,24 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
       }
       team.sync();
     }
-    // the network's row (scalar and derivatives), its weighted terms of <C>
-    // and of the gradient (Section 4.1), and its entry of the output
+    // the network's row (scalar and derivatives), its entry of the output,
+    // and its weighted terms of <C> and of the gradient (Section 4.1) added
+    // into the FP64 sums (atomics carried out in L2: the order of the terms
+    // over networks is not fixed, so sums can differ in the last bits
+    // between runs)
     double* row = prog.results + (size_t)task.net * stride;
-    double* crow = prog.contrib + (size_t)task.net * (1 + P);
     if (team.tid == 0) {
       const double2 sv = s_res[team.id];
       row[0] = sv.x;
       row[1] = sv.y;
-      crow[0] = 0.5 * w_net * (1.0 - sv.x);
       prog.out[1 + P + task.net] = sv.x;
+      atomicAdd(&prog.acc[0], 0.5 * w_net * (1.0 - sv.x));
     }
     for (int i = team.tid; i < 2 * P; i += team.size)
       row[2 + i] = prog.want_grad ? (double)grad[i] : 0.0;
-    for (int q = team.tid; q < P; q += team.size)
-      crow[1 + q] = prog.want_grad ? -0.5 * w_net * (double)grad[2 * q] : 0.0;
+    if (prog.want_grad)
+      for (int q = team.tid; q < P; q += team.size)
+        atomicAdd(&prog.acc[1 + q], -0.5 * w_net * (double)grad[2 * q]);
     // networks beyond the statically assigned ones come from the queue
     const unsigned int n_static = gridDim.x * teams_per_cta;
     if (n_static >= (unsigned)prog.n_tasks) break;
@@ -357,22 +328,19 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
   }
 
   // A team counts itself out after its last queue fetch (its first thread's
-  // release, after the team barrier, covers the team's row writes); the last
-  // team out sums the weighted rows in FP64 and re-arms the counters (no team
-  // touches them afterwards).
+  // release, after the team barrier, covers the team's writes and sums); the
+  // last team out copies the sums to the output, clears them and re-arms the
+  // counters (no team touches them afterwards).
   team.sync();
-  bool last = false;
   if (team.tid == 0)
-    last = atomic_add_acq_rel(&prog.counters[1], 1u) == gridDim.x * teams_per_cta - 1;
-  if (kWarp) {
-    last = __shfl_sync(0xffffffffu, last, 0);
-  } else {
-    if (team.tid == 0) s_last = last;
-    team.sync();
-    last = s_last;
+    s_last[team.id] = atomic_add_acq_rel(&prog.counters[1], 1u) == gridDim.x * teams_per_cta - 1;
+  team.sync();
+  if (!s_last[team.id]) return;
+  for (int q = team.tid; q <= P; q += team.size) {
+    const double v = reinterpret_cast<volatile double*>(prog.acc)[q];
+    prog.out[q] = prog.qaoa_reduce ? v : 0.0;
+    prog.acc[q] = 0.0;
   }
-  if (!last || team.tid >= 32) return;
-  reduce_contrib_rows(prog.contrib, prog.n_nets, P, prog.qaoa_reduce != 0, prog.out, team.tid);
   if (team.tid == 0) {
     prog.out[1 + P + prog.n_nets] = 0.0;  // status: this executor never waits
     prog.counters[0] = 0;

@@ -77,8 +77,9 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
     const size_t o_wsteps = align256(o_ops + sizeof(SOp) * hp.ops.size());
     const size_t o_weights = align256(o_wsteps + sizeof(WStep) * hp.wsteps.size());
     const size_t o_results = align256(o_weights + sizeof(double) * N);
-    const size_t o_contrib = align256(o_results + sizeof(double) * (size_t)N * (2 + 2 * P));
-    const size_t o_counters = align256(o_contrib + sizeof(double) * (size_t)N * (1 + P));
+    // the FP64 sums and the counters sit together: one clear per call
+    const size_t o_acc = align256(o_results + sizeof(double) * (size_t)N * (2 + 2 * P));
+    const size_t o_counters = o_acc + ((sizeof(double) * (1 + P) + 15) & ~size_t(15));
     const size_t total = o_counters + sizeof(unsigned int) * 4;
     if (total > kScratchBytes)
       fail(QTC_ERR_ARENA,
@@ -105,9 +106,9 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
                                  cudaMemcpyHostToDevice, s), "upload weights");
       setup.resident = hp.serial;
     }
-    // the queue and block counters must start at zero; the array keeps
-    // whatever the previous call left there
-    cuda_check(cudaMemsetAsync(base + o_counters, 0, sizeof(unsigned int) * 4, s),
+    // the sums, the queue and the team counter must start at zero; the array
+    // keeps whatever the previous call left there
+    cuda_check(cudaMemsetAsync(base + o_acc, 0, o_counters - o_acc + sizeof(unsigned int) * 4, s),
                "clear counters");
 
     int per_sm = 0;
@@ -132,7 +133,7 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
     d.weights = (const double*)(base + o_weights);
     d.params = params_dev;
     d.results = (double*)(base + o_results);
-    d.contrib = (double*)(base + o_contrib);
+    d.acc = (double*)(base + o_acc);
     d.out = out_dev;
     d.counters = (unsigned int*)(base + o_counters);
     d.want_grad = hp.want_grad;
