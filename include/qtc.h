@@ -212,6 +212,14 @@ qtc_status qtc_network_build(const qtc_circuit* c, const qtc_observable* obs,
  * kind (LeafKind code, see device_program.h), conj (1 = bra side, values
  * complex-conjugated), slot/coeff/constant (angle = coeff*params[slot] +
  * constant), labels in storage order (label k = bit k of the element index). */
+/* Leaf `leaf` of a network evaluated on the host at `params` (host,
+ * n_params doubles): the tensor of the gate, state, observable or channel of
+ * Section 2 that the executors build, 2^rank complex elements as interleaved
+ * (re, im) doubles in val (host), and d/dparams[slot] of each in der (host,
+ * nullable; zeros for a leaf without a parameter).  Element index bit k is
+ * label k of qtc_network_leaves.  QTC_ERR_INVALID for a leaf out of range. */
+qtc_status qtc_network_leaf_values(const qtc_network* n, int leaf, const double* params,
+                                   double* val, double* der);
 qtc_status qtc_network_leaves(const qtc_network* n, int32_t* counts, int32_t* kind,
                               int32_t* conj, int32_t* slot, double* coeff,
                               double* constant, int32_t* labels);

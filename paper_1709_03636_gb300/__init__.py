@@ -181,6 +181,21 @@ class Network(_Handle):
                 for i in range(n)], counts[1]
 
 
+    def leaf_values(self, leaf: int, params=()):
+        """Leaf `leaf` as the executors build it, at `params` (host): its 2^rank
+        elements and their derivatives with respect to its parameter, complex
+        numpy arrays indexed like the element index (bit k = label k)."""
+        import numpy as np
+        val = (ctypes.c_double * (2 * 16))()
+        der = (ctypes.c_double * (2 * 16))()
+        p = _f64(list(params) + [0.0]) if len(params) else None
+        check(lib.qtc_network_leaf_values(self.ptr, int(leaf), p, val, der))
+        n = 1 << len(self.leaves()[0][leaf]["labels"])
+        v = np.array(val[:2 * n]).view(np.complex128)
+        d = np.array(der[:2 * n]).view(np.complex128)
+        return v, d
+
+
 def plan_opts(ordering="lg", seed=0, max_rejections=10, restarts=8, budget_ms=0.0):
     o = qtc_plan_opts()
     o.kind = ORDERINGS[ordering] if isinstance(ordering, str) else int(ordering)

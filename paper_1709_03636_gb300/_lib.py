@@ -66,6 +66,7 @@ SIGNATURES = {
     "qtc_network_build": (c_int, [c_void_p, P(qtc_observable), c_int, c_int, P(c_void_p)]),
     "qtc_network_leaves": (c_int, [c_void_p, P(c_int32), P(c_int32), P(c_int32), P(c_int32),
                                    P(c_double), P(c_double), P(c_int32)]),
+    "qtc_network_leaf_values": (c_int, [c_void_p, c_int, P(c_double), P(c_double), P(c_double)]),
     "qtc_network_destroy": (None, [c_void_p]),
     "qtc_plan_create": (c_int, [c_void_p, P(qtc_plan_opts), P(c_void_p)]),
     "qtc_plan_stats": (c_int, [c_void_p, P(qtc_plan_info)]),

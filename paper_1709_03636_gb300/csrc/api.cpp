@@ -376,6 +376,18 @@ extern "C" qtc_status qtc_network_build(const qtc_circuit* c, const qtc_observab
   });
 }
 
+extern "C" qtc_status qtc_network_leaf_values(const qtc_network* n, int leaf,
+                                              const double* params, double* val, double* der) {
+  return guarded([&] {
+    if (!n || !val) fail(QTC_ERR_INVALID, "null argument");
+    if (leaf < 0 || leaf >= (int)n->net.leaves.size())
+      fail(QTC_ERR_INVALID, "leaf %d of %zu", leaf, n->net.leaves.size());
+    const GateSpec& s = n->net.leaves[leaf].spec;
+    if (s.slot >= 0 && !params) fail(QTC_ERR_INVALID, "leaf %d needs params", leaf);
+    leaf_values(s, params, val, der);
+  });
+}
+
 extern "C" qtc_status qtc_network_leaves(const qtc_network* n, int32_t* counts, int32_t* kind,
                                          int32_t* conj, int32_t* slot, double* coeff,
                                          double* constant, int32_t* labels) {
@@ -728,6 +740,7 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
       }
       hp->tasks = std::move(wtasks);
       hp->wsteps = std::move(wsteps);
+      hp->coef = coefficient_table(hp->gates, table_elems, dtype);
       hp->ops.clear();
     } else {
       hp->max_arena = shared_arena;
@@ -856,6 +869,7 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   auto* dt = (TaskDev*)e->alloc(sizeof(TaskDev) * hp.tasks.size());
   auto* dops = (SOp*)e->alloc(sizeof(SOp) * std::max<size_t>(1, hp.ops.size()));
   auto* dwsteps = (WStep*)e->alloc(sizeof(WStep) * std::max<size_t>(1, hp.wsteps.size()));
+  auto* dcoef = e->alloc(std::max<size_t>(16, hp.coef.size()));
   auto* dw = (double*)e->alloc(sizeof(double) * N);
   auto* dparams = (double*)e->alloc(sizeof(double) * std::max(P, 1));
   auto* dres = (double*)e->alloc(sizeof(double) * (size_t)N * (2 + 2 * P));
@@ -870,6 +884,10 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
     cuda_check(cudaMemcpyAsync(dwsteps, hp.wsteps.data(), sizeof(WStep) * hp.wsteps.size(),
                                cudaMemcpyHostToDevice, stream),
                "upload warp steps");
+  if (!hp.coef.empty())
+    cuda_check(cudaMemcpyAsync(dcoef, hp.coef.data(), hp.coef.size(), cudaMemcpyHostToDevice,
+                               stream),
+               "upload gate coefficients");
   cuda_check(cudaMemcpyAsync(dw, hp.weights.data(), sizeof(double) * N, cudaMemcpyHostToDevice, stream), "upload weights");
   cuda_check(cudaMemsetAsync(dcnt, 0, sizeof(unsigned int) * 4, stream), "clear counters");
   cuda_check(cudaMemsetAsync(dacc, 0, sizeof(double) * (1 + P), stream), "clear sums");
@@ -882,6 +900,7 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   d.team_bytes = hp.team_bytes;
   d.stage_ops = hp.stage_ops;
   d.task_stride = hp.task_stride;
+  d.coef = dcoef;
   d.tasks = dt;
   d.n_tasks = (int)hp.tasks.size();
   d.ops = dops;

@@ -62,6 +62,21 @@ struct GateSpec {
   double constant;
 };
 
+// One element of the gate table as coefficients (see gate_coef.cpp):
+// value = (a0 + i a1) cos(t/2) + (a2 + i a3) sin(t/2) + (a4 + i a5), with
+// t the angle of gate `gate`; derivative elements carry their own
+// coefficients.  One record per table element (padding: zeros).
+struct alignas(16) TabCoef32 {
+  float a[6];
+  uint32_t gate;
+  uint32_t pad;
+};
+struct alignas(16) TabCoef64 {
+  double a[6];
+  uint32_t gate;
+  uint32_t pad[3];
+};
+
 struct GateEntryDev {
   GateSpec spec;
   uint32_t val_off;    // element offset of the values in the table region
@@ -182,6 +197,8 @@ struct ProgramDev {
   const GateEntryDev* gates;
   int n_gates;
   GateEntryDev gates_inline[kInlineGates];   // the first min(n_gates, 16) entries
+  const void* coef;            // warp teams: TabCoef32 (complex64) or TabCoef64 per
+                               // table element
   uint32_t table_elems;        // gate values + derivatives, in elements
   uint32_t table_bytes;        // table region, rounded to 16 bytes
   uint32_t team_bytes;         // per team: staged ops, then its arena

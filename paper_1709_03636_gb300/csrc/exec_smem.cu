@@ -132,14 +132,52 @@ __device__ __forceinline__ void warp_bundle(const uint4 L, uint32_t rounds, uint
   }
 }
 
-// A warp team's own copy of the gate table (its lanes stride over the gates).
+// A warp team's own copy of the gate table.  With at most 32 gates, lane g
+// takes the sine and cosine of gate g's half angle; every element is then one
+// complex multiply-add of its coefficient record with its gate's pair,
+// shuffled from that lane (the same code for every kind; the records of 128
+// elements are loaded before any is used).  Otherwise the lanes stride over
+// the gates in closed form.
 template <typename T>
 __device__ __forceinline__ void build_warp_gate_table(const ProgramDev& prog, T* table,
-                                                      uint32_t lane) {
-  for (int e = (int)lane; e < prog.n_gates; e += 32) {
-    const GateEntryDev g = e < kInlineGates ? prog.gates_inline[e] : prog.gates[e];
-    gate_tensor<T>(g.spec, prog.params, table + g.val_off,
-                   g.spec.slot >= 0 ? table + g.der_off : nullptr);
+                                                      uint32_t table_s, uint32_t lane) {
+  using R = decltype(T::x);
+  using Rec = typename std::conditional<sizeof(R) == 4, TabCoef32, TabCoef64>::type;
+  if (prog.n_gates > 32 || prog.coef == nullptr) {
+    for (int e = (int)lane; e < prog.n_gates; e += 32) {
+      const GateEntryDev g = e < kInlineGates ? prog.gates_inline[e] : prog.gates[e];
+      gate_tensor<T>(g.spec, prog.params, table + g.val_off,
+                     g.spec.slot >= 0 ? table + g.der_off : nullptr);
+    }
+    return;
+  }
+  const Rec* rec = static_cast<const Rec*>(prog.coef);
+  const uint32_t ne = prog.table_elems;
+  R c = R(1), s = R(0);
+  if ((int)lane < prog.n_gates) {
+    const GateEntryDev g =
+        (int)lane < kInlineGates ? prog.gates_inline[lane] : prog.gates[lane];
+    const double theta =
+        g.spec.constant + (g.spec.slot >= 0 ? g.spec.coeff * prog.params[g.spec.slot] : 0.0);
+    sincos_r((R)(0.5 * theta), &s, &c);
+  }
+  for (uint32_t j0 = 0; j0 < ne; j0 += 128) {
+    Rec r[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t j = j0 + 32 * k + lane;
+      r[k] = j < ne ? rec[j] : Rec{};
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t j = j0 + 32 * k + lane;
+      const R cj = __shfl_sync(0xffffffffu, c, r[k].gate & 31u);
+      const R sj = __shfl_sync(0xffffffffu, s, r[k].gate & 31u);
+      T v;
+      v.x = fma((R)r[k].a[0], cj, fma((R)r[k].a[2], sj, (R)r[k].a[4]));
+      v.y = fma((R)r[k].a[1], cj, fma((R)r[k].a[3], sj, (R)r[k].a[5]));
+      if (j < ne) sts_c(table_s + j * (uint32_t)sizeof(T), v);
+    }
   }
 }
 
@@ -197,7 +235,7 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
     }
   }
   if (kWarp)
-    build_warp_gate_table<T>(prog, table, team.tid);
+    build_warp_gate_table<T>(prog, table, table_s, team.tid);
   else
     build_gate_table<T>(prog.gates, prog.n_gates, prog.params, table, prog.gates_inline,
                         kInlineGates);

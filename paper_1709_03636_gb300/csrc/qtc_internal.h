@@ -1,6 +1,7 @@
 // Internal host-side structures of the contraction engine.
 #pragma once
 
+#include <complex>
 #include <cstdint>
 #include <string>
 #include <utility>
@@ -131,6 +132,16 @@ struct Plan {
 
 Plan make_plan(const Network& net, const qtc_plan_opts& opts);
 
+// ---- leaf tensors as coefficients (gate_coef.cpp) ---------------------------
+// A, B, C (2^rank each) with element = A cos(t/2) + B sin(t/2) + C.
+void gate_coefficients(const GateSpec& s, std::complex<double>* A, std::complex<double>* B,
+                       std::complex<double>* C);
+// The warp executor's coefficient records, one per table element.
+std::vector<uint8_t> coefficient_table(const std::vector<GateEntryDev>& gates,
+                                       uint32_t table_elems, int dtype);
+// Host evaluation: val and der (nullable) as interleaved complex doubles.
+void leaf_values(const GateSpec& s, const double* params, double* val, double* der);
+
 // ---- lowering --------------------------------------------------------------
 // Deduplicated gate table shared by every network of a batch.
 struct GateTable {
@@ -232,6 +243,7 @@ struct HostProgram {
   std::vector<TaskDev> tasks;
   std::vector<SOp> ops;            // CTA teams (empty for warp teams)
   std::vector<WStep> wsteps;       // warp teams
+  std::vector<uint8_t> coef;       // warp teams: gate table coefficient records
   std::vector<double> weights;
   uint32_t table_elems = 0, max_arena = 0;
   uint32_t table_bytes = 0;        // gate table region, 16-byte rounded

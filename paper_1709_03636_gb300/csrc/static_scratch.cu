@@ -75,7 +75,8 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
     const size_t o_tasks = align256(o_gates + sizeof(GateEntryDev) * G);
     const size_t o_ops = align256(o_tasks + sizeof(TaskDev) * hp.tasks.size());
     const size_t o_wsteps = align256(o_ops + sizeof(SOp) * hp.ops.size());
-    const size_t o_weights = align256(o_wsteps + sizeof(WStep) * hp.wsteps.size());
+    const size_t o_coef = align256(o_wsteps + sizeof(WStep) * hp.wsteps.size());
+    const size_t o_weights = align256(o_coef + hp.coef.size());
     const size_t o_results = align256(o_weights + sizeof(double) * N);
     // the FP64 sums and the counters sit together: one clear per call
     const size_t o_acc = align256(o_results + sizeof(double) * (size_t)N * (2 + 2 * P));
@@ -102,6 +103,9 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
         cuda_check(cudaMemcpyAsync(base + o_wsteps, hp.wsteps.data(),
                                    sizeof(WStep) * hp.wsteps.size(),
                                    cudaMemcpyHostToDevice, s), "upload warp ops");
+      if (!hp.coef.empty())
+        cuda_check(cudaMemcpyAsync(base + o_coef, hp.coef.data(), hp.coef.size(),
+                                   cudaMemcpyHostToDevice, s), "upload gate coefficients");
       cuda_check(cudaMemcpyAsync(base + o_weights, hp.weights.data(), sizeof(double) * N,
                                  cudaMemcpyHostToDevice, s), "upload weights");
       setup.resident = hp.serial;
@@ -124,6 +128,7 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
     d.team_bytes = hp.team_bytes;
     d.stage_ops = hp.stage_ops;
     d.task_stride = hp.task_stride;
+    d.coef = base + o_coef;
     d.tasks = (const TaskDev*)(base + o_tasks);
     d.n_tasks = (int)hp.tasks.size();
     d.ops = (const SOp*)(base + o_ops);

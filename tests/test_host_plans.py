@@ -401,3 +401,63 @@ def test_library_exports_every_declared_symbol():
     so = ctypes.CDLL(_lib.LIB_PATH)
     missing = [n for n in sorted(names) if not hasattr(so, n)]
     assert not missing, missing
+
+
+def _leaf_cases():
+    rng = np.random.default_rng(11)
+    edges = [(0, 1), (1, 2), (2, 3), (3, 0), (0, 2)]
+    out = []
+    circ = q.Circuit.qaoa(4, edges, 2)
+    out.append((q.Network(circ, edge=(0, 1)), 4))
+    out.append((q.Network(circ, edge=(0, 1), diag=False), 4))
+    for ch in ("depolarize", "dephase", "ampdamp"):
+        out.append((q.Network(q.Circuit.qaoa(4, edges, 1, noise=(ch, 0.13)), edge=(1, 2)), 2))
+    out.append((q.Network(circ, "pauli", pauli="XYZI", lightcone=False), 4))
+    out.append((q.Network(circ, "amplitude", bits=[1, 0, 1, 1], lightcone=False), 4))
+    out.append((q.Network(circ, "projector", bits=[1, 0, 2, 2], lightcone=False), 4))
+    # generic gates, with parameters: slot, coefficient and constant angle
+    cn = q.Circuit(4, 3)
+    for g, qs, t in random_cnot_circuit(4, 12, 3) + [("h", (1,), 0.0), ("x", (2,), 0.0),
+                                                    ("y", (3,), 0.0), ("z", (0,), 0.0),
+                                                    ("zz", (0, 3), 0.4)]:
+        slot = int(rng.integers(3)) if g in ("rx", "rz", "zz") else -1
+        cn.add_gate(g, list(qs), slot, float(rng.uniform(-2, 2)) if slot >= 0 else 0.0, t)
+    out.append((q.Network(cn, "pauli", pauli="ZZXY", lightcone=False), 3))
+    out.append((q.Network(cn, "pauli", pauli="ZIZI", lightcone=False, diag=False), 3))
+    return out, rng
+
+
+def test_leaf_values_match_closed_forms():
+    """Every leaf kind as the executors build it (coefficients A cos(t/2) +
+    B sin(t/2) + C) against the closed forms above; derivatives against
+    central differences of those closed forms."""
+    cases, rng = _leaf_cases()
+    kinds = set()
+    for net, n_params in cases:
+        params = rng.uniform(-2, 2, size=max(n_params, 1))
+        leaves, _ = net.leaves()
+        for i, l in enumerate(leaves):
+            kinds.add(l["kind"])
+            val, der = net.leaf_values(i, params)
+            ref = leaf_tensor(l["kind"], l["conj"], l["slot"], l["coeff"], l["constant"], params)
+            ref = np.asarray(ref, dtype=complex).flatten(order="F")
+            assert np.max(np.abs(val - ref)) < 1e-14, (l, val, ref)
+            if l["slot"] >= 0:
+                h = 1e-5
+                pp, pm = params.copy(), params.copy()
+                pp[l["slot"]] += h
+                pm[l["slot"]] -= h
+                fd = (np.asarray(leaf_tensor(l["kind"], l["conj"], l["slot"], l["coeff"],
+                                             l["constant"], pp), complex).flatten(order="F")
+                      - np.asarray(leaf_tensor(l["kind"], l["conj"], l["slot"], l["coeff"],
+                                               l["constant"], pm), complex).flatten(order="F"))
+                assert np.max(np.abs(der - fd / (2 * h))) < 1e-8
+            else:
+                assert np.max(np.abs(der)) == 0
+    assert len(kinds) >= 15, sorted(kinds)
+
+
+def test_leaf_values_rejects_bad_leaf():
+    net = q.Network(q.Circuit.qaoa(4, [(0, 1), (1, 2)], 1), edge=(0, 1))
+    with pytest.raises(q.QtcError):
+        net.leaf_values(10 ** 6, [0.1, 0.2])
