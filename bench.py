@@ -42,14 +42,14 @@ DEFAULT_WORKLOAD = "qaoa_p1_n50_d3"
 # (otherwise null: the figure would describe another kernel).
 KERNEL_SOURCES = {
     "smem_exec_kernel": ["exec_smem.cu", "exec_common.cuh", "device_program.h",
-                         "warp_program.cpp"],
+                         "warp_program.cpp", "api.cpp", "gate_coef.cpp", "lower.cpp"],
     "graph_exec_kernel": ["exec_graph.cu", "exec_common.cuh", "device_program.h", "lower.cpp",
                           "graph_host.cpp"],
 }
 NCU_TRAFFIC = {
     # (workload, kernel, dtype, want_grad): (bytes per launch, source hash, profile summary)
     ("qaoa_p1_n50_d3", "smem_exec_kernel", "c64", True):
-        (1822976, "79f8dc77ece812cf", "profiles/smem_exec_kernel_qaoa_p1_n50_d3.md"),
+        (698880, "44995556479c5a6e", "profiles/smem_exec_kernel_qaoa_p1_n50_d3.md"),
 }
 
 
