@@ -49,7 +49,7 @@ KERNEL_SOURCES = {
 NCU_TRAFFIC = {
     # (workload, kernel, dtype, want_grad): (bytes per launch, source hash, profile summary)
     ("qaoa_p1_n50_d3", "smem_exec_kernel", "c64", True):
-        (698880, "44995556479c5a6e", "profiles/smem_exec_kernel_qaoa_p1_n50_d3.md"),
+        (698880, "0a36dd11d0e5b6fa", "profiles/smem_exec_kernel_qaoa_p1_n50_d3.md"),
 }
 
 
@@ -348,14 +348,13 @@ def run_ours(args):
     h_grad = torch.zeros(P, dtype=torch.float64).pin_memory()
     vp = lambda t: q.ctypes.c_void_p(t.data_ptr())  # noqa: E731
 
+    dptr = lambda t: q.ctypes.cast(vp(t), q.ctypes.POINTER(q.ctypes.c_double))  # noqa: E731
+    e2e_args = (engine.ptr, batch.ptr, dptr(h_gam), dptr(h_bet), q.DTYPES[dtype], 1,
+                q.ctypes.c_void_p(stream.cuda_stream), dptr(h_C), dptr(h_edge), dptr(h_grad))
+    e2e_call = _lib.lib.qtc_qaoa_expectation
+
     def e2e_step():
-        _lib.check(_lib.lib.qtc_qaoa_expectation(
-            engine.ptr, batch.ptr, q.ctypes.cast(vp(h_gam), q.ctypes.POINTER(q.ctypes.c_double)),
-            q.ctypes.cast(vp(h_bet), q.ctypes.POINTER(q.ctypes.c_double)),
-            q.DTYPES[dtype], 1, q.ctypes.c_void_p(stream.cuda_stream),
-            q.ctypes.cast(vp(h_C), q.ctypes.POINTER(q.ctypes.c_double)),
-            q.ctypes.cast(vp(h_edge), q.ctypes.POINTER(q.ctypes.c_double)),
-            q.ctypes.cast(vp(h_grad), q.ctypes.POINTER(q.ctypes.c_double))))
+        _lib.check(e2e_call(*e2e_args))
 
     for _ in range(args.warmup):
         e2e_step()

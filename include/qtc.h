@@ -17,7 +17,11 @@
  *  - "device" pointers are CUDA global-memory addresses on the engine's
  *    device; "host" pointers are ordinary (pageable or pinned) host memory.
  *  - Device memory is never allocated by the library: every device buffer it
- *    uses lives in the arena the caller hands to qtc_engine_create.
+ *    uses lives in the arena the caller hands to qtc_engine_create.  The one
+ *    allocation it makes is a small pinned, device-mapped host buffer per
+ *    engine (allocated by the first host-pointer expectation call, freed by
+ *    qtc_engine_destroy) through which such calls pass parameters and
+ *    results without copies.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Calls with host outputs synchronise that stream before they
  *    return; calls with device outputs are asynchronous on it.
@@ -284,7 +288,9 @@ qtc_status qtc_batch_prepare(qtc_engine* e, qtc_batch* b, int dtype,
  * gammas, betas: host, p values each.  C_out: host, 1 double.
  * per_edge_out: host, nullable, m doubles <Z_u Z_v>_i.
  * grad_out: host, nullable (needs want_grad), 2p doubles
- * d<C>/d(gamma_1..p, beta_1..p).  Synchronises `stream`.  <C> and the
+ * d<C>/d(gamma_1..p, beta_1..p).  One launch per wave and one stream
+ * synchronisation: the kernel reads the parameters from and writes the
+ * results to the engine's mapped host buffer.  Synchronises `stream`.  <C> and the
  * gradient are FP64 sums over the edge networks; with the shared-memory
  * executor the terms are added in no fixed order (atomics), so repeated
  * calls can differ in the last bits. */

@@ -86,6 +86,34 @@ struct qtc_engine {
   }
 
   char* work_base() const { return arena + bytes - work; }
+
+  // Host-pointer calls pass parameters and results through a small pinned,
+  // device-mapped host buffer: the kernel reads and writes it in place, so a
+  // call is one launch and one stream synchronisation with no copies.
+  double* staging_host = nullptr;
+  double* staging_dev = nullptr;
+  size_t staging_elems = 0;
+
+  double* staging(size_t n) {
+    if (n > staging_elems) {
+      if (staging_host) cuda_check(cudaFreeHost(staging_host), "free staging buffer");
+      staging_host = nullptr;
+      staging_elems = 0;
+      void* h = nullptr;
+      cuda_check(cudaHostAlloc(&h, sizeof(double) * n, cudaHostAllocMapped),
+                 "allocate staging buffer");
+      staging_host = (double*)h;
+      staging_elems = n;
+      void* d = nullptr;
+      cuda_check(cudaHostGetDevicePointer(&d, h, 0), "map staging buffer");
+      staging_dev = (double*)d;
+    }
+    return staging_host;
+  }
+
+  ~qtc_engine() {
+    if (staging_host) cudaFreeHost(staging_host);
+  }
 };
 
 // Device tables of the state-vector reference for one circuit and engine.
@@ -1048,16 +1076,14 @@ extern "C" qtc_status qtc_qaoa_expectation(qtc_engine* e, qtc_batch* b, const do
     const Prepared& pr = prepare(e, b, dtype, want_grad, s);
     const int P = 2 * p;
     const int N = (int)b->plans.size();
-    std::vector<double> params(P), host_out(2 + P + N);
+    // parameters and results in the engine's mapped staging buffer
+    double* params = e->staging((size_t)P + 2 + P + N);
+    double* host_out = params + P;
     for (int k = 0; k < p; ++k) {
       params[k] = gammas[k];
       params[p + k] = betas[k];
     }
-    cuda_check(cudaMemcpyAsync((void*)pr.prog.params, params.data(), sizeof(double) * P,
-                               cudaMemcpyHostToDevice, s), "upload parameters");
-    launch(e, pr, pr.prog.params, pr.prog.out, s);
-    cuda_check(cudaMemcpyAsync(host_out.data(), pr.prog.out, sizeof(double) * host_out.size(),
-                               cudaMemcpyDeviceToHost, s), "download results");
+    launch(e, pr, e->staging_dev, e->staging_dev + P, s);
     cuda_check(cudaStreamSynchronize(s), "synchronise stream");
     if (host_out[1 + P + N] != 0.0)
       fail(QTC_ERR_TIMEOUT, "a device-side dependency wait expired (status %g)",
