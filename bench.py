@@ -397,6 +397,10 @@ def run_ours(args):
                      "algorithmic_bytes_per_step": alg_bytes},
         "e2e": {"value": world * n_nets / e2e_s, "unit": "networks/s",
                 "h2d_bytes_per_step": 8 * P, "d2h_bytes_per_step": 8 * (2 + P + n_nets)},
+        "complex_gflops": {"value": 8.0 * (stats["cmacs"] + (stats["grad_cmacs"] if want_grad
+                                                                else 0.0)) / (ms * 1e-3) / 1e9,
+                           "unit": "GFLOP/s", "count": "algorithmic, 8 real flops per complex "
+                           "multiply-add (forward and adjoint contractions)"},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "step_ms_min_median_max": [min(step_ms), statistics.median(step_ms), max(step_ms)],
