@@ -697,7 +697,8 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
   // offset from one base.
   auto layout = [&](bool warp, uint32_t stage) {
     hp->warp_teams = warp;
-    hp->n_teams = warp ? kExecBlock / 32 : 1;
+    hp->n_teams = warp ? kWarpTeamsPerCta : 1;
+    hp->block = warp ? 32 * kWarpTeamsPerCta : kExecBlock;
     hp->stage_ops = stage;
     const size_t op_bytes = warp ? sizeof(WStep) : sizeof(SOp);
     hp->table_bytes = warp ? 0 : round16((size_t)table_elems * elem);
@@ -943,7 +944,7 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   d.counters = dcnt;
   d.want_grad = want_grad;
   d.qaoa_reduce = hp.qaoa_reduce;
-  pr.block = kExecBlock;
+  pr.block = hp.block;
   pr.smem = hp.smem;
   int per_sm = 0;
   pr.warp_teams = hp.warp_teams;

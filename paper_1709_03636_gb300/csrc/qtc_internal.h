@@ -14,6 +14,11 @@
 
 namespace qtc {
 
+// Threads per CTA of the shared-memory executor (CTA teams), and networks per
+// CTA when one warp runs one network.
+constexpr int kExecBlock = 128;
+constexpr int kWarpTeamsPerCta = 4;
+
 // ---- errors ---------------------------------------------------------------
 // Internal code throws Error; every C-ABI entry point catches it, stores the
 // message in the thread-local buffer and returns the status.
@@ -252,6 +257,7 @@ struct HostProgram {
   uint32_t task_stride = 0;        // warp steps of task t start at t * task_stride (0: packed)
   bool warp_teams = false;         // one network per warp (small networks)
   int n_teams = 1;                 // teams per CTA
+  int block = kExecBlock;          // threads per CTA
   size_t smem = 0;                 // dynamic shared memory per CTA, bytes
   int n_nets = 0, n_params = 0;
   int qaoa_reduce = 1;
@@ -283,6 +289,5 @@ inline size_t elem_bytes(int dtype) { return dtype == QTC_C128 ? 16 : 8; }
 // minus 16 KB for the kernel's static shared memory (about 10 KB).
 inline size_t max_dynamic_smem(size_t optin) { return optin > 16384 ? optin - 16384 : 0; }
 
-constexpr int kExecBlock = 128;
 
 }  // namespace qtc

@@ -117,7 +117,7 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
 
     int per_sm = 0;
     cuda_check(smem_exec_configure(dtype == QTC_C128 ? 0 : 1, hp.warp_teams, hp.smem, max_dyn,
-                                   kExecBlock, &per_sm), "configure executor");
+                                   hp.block, &per_sm), "configure executor");
     if (per_sm < 1) fail(QTC_ERR_UNSUPPORTED, "executor does not fit on an SM");
     ProgramDev d{};
     d.gates = (const GateEntryDev*)(base + o_gates);
@@ -145,7 +145,7 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
     d.qaoa_reduce = hp.qaoa_reduce;
     const int ctas = ((int)hp.tasks.size() + hp.n_teams - 1) / hp.n_teams;
     const int grid = std::max(1, std::min(ctas, setup.sm_count * per_sm));
-    cuda_check(smem_exec_launch(d, dtype == QTC_C128 ? 0 : 1, hp.warp_teams, grid, kExecBlock,
+    cuda_check(smem_exec_launch(d, dtype == QTC_C128 ? 0 : 1, hp.warp_teams, grid, hp.block,
                                 hp.smem, s),
                "launch executor");
   });
