@@ -162,7 +162,8 @@ const char* qtc_last_error(void);
 
 /* ---- engine -------------------------------------------------------------
  * An engine binds one CUDA device and one caller-owned device arena
- * [arena, arena + arena_bytes), 256-byte aligned.  Plans, intermediates,
+ * [arena, arena + arena_bytes), 256-byte aligned (an arena_bytes that is not
+ * a multiple of 256 is rounded down to one).  Plans, intermediates,
  * counters and results are carved from it; the library never calls
  * cudaMalloc.  Program tables grow from the front; the global-memory
  * intermediates of the graph executor use one work buffer at the back,
@@ -331,6 +332,13 @@ qtc_status qtc_engine_set_limits(qtc_engine* e, size_t max_wave_bytes, double wa
  * memory; small_rank > 0 moves every tensor of higher rank to global memory
  * (default 10).  Invalidates prepared programs. */
 qtc_status qtc_engine_set_graph_options(qtc_engine* e, int force_graph, int small_rank);
+
+/* Task sizes of the graph executor (tuning; see the autotuner of the Python
+ * package): a chunk task of a global step covers about 2^task_terms_log2
+ * multiply-adds (12..20, default 16); a shared-memory subtree task holds at
+ * most subtree_bytes of values (4096..32768, default 32768).  Invalidates
+ * prepared programs.  QTC_ERR_INVALID outside those ranges. */
+qtc_status qtc_engine_set_task_options(qtc_engine* e, int task_terms_log2, int subtree_bytes);
 
 /* Launches a one-task program whose task waits for a counter nothing ever
  * signals, so that the bounded wait expires after the engine's wait limit and

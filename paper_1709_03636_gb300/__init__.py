@@ -17,7 +17,7 @@ __all__ = [
     "QtcError", "Engine", "Circuit", "Network", "Plan", "Batch", "DTYPES", "ORDERINGS",
     "contract", "qaoa_expectation", "qaoa_expectation_device", "QAOAExpectation",
     "statevector_expectation", "statevector_expectation_device", "optimize_angles",
-    "answer_string",
+    "answer_string", "autotune",
     "GATES",
 ]
 
@@ -87,6 +87,8 @@ class Engine(_Handle):
                                     arena.numel() * arena.element_size(), ctypes.byref(h)))
         super().__init__(h)
         self.device = device
+        self.graph_options = (False, 0)
+        self.task_options = (16, 32768)
 
     def reset(self):
         check(lib.qtc_engine_reset(self.ptr))
@@ -99,6 +101,14 @@ class Engine(_Handle):
         """Run small networks through the graph executor / move tensors of
         rank > small_rank to global memory (0: default)."""
         check(lib.qtc_engine_set_graph_options(self.ptr, int(force_graph), int(small_rank)))
+        self.graph_options = (bool(force_graph), int(small_rank))
+
+    def set_task_options(self, task_terms_log2=16, subtree_bytes=32768):
+        """Graph-executor task sizes: about 2^task_terms_log2 multiply-adds per
+        chunk task, at most subtree_bytes of values per shared-memory subtree."""
+        check(lib.qtc_engine_set_task_options(self.ptr, int(task_terms_log2),
+                                              int(subtree_bytes)))
+        self.task_options = (int(task_terms_log2), int(subtree_bytes))
 
     @property
     def last_launches(self) -> int:
@@ -435,3 +445,6 @@ class _LazyAutograd:
 
 
 QAOAExpectation = _LazyAutograd()
+
+
+from .tuning import autotune  # noqa: E402  (graph-executor task shapes)

@@ -172,7 +172,9 @@ extern "C" qtc_status qtc_engine_create(int device, void* arena, size_t arena_by
     auto e = std::make_unique<qtc_engine>();
     e->device = device;
     e->arena = (char*)arena;
-    e->bytes = arena_bytes;
+    // the work buffer sits at the back of the arena: a length that is a
+    // multiple of 256 keeps its start (and every element in it) aligned
+    e->bytes = arena_bytes & ~size_t(255);
     int v = 0;
     cuda_check(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device), "SM count");
     e->sm_count = v;
@@ -217,6 +219,22 @@ extern "C" qtc_status qtc_engine_set_graph_options(qtc_engine* e, int force_grap
     if (small_rank < 0 || small_rank > 16) fail(QTC_ERR_INVALID, "small rank %d", small_rank);
     e->options.force_graph = force_graph != 0;
     e->options.small_rank = small_rank;
+    e->generation += 1;
+    e->used = 0;
+    e->work = 0;
+  });
+}
+
+extern "C" qtc_status qtc_engine_set_task_options(qtc_engine* e, int task_terms_log2,
+                                                  int subtree_bytes) {
+  return guarded([&] {
+    if (!e) fail(QTC_ERR_INVALID, "null engine");
+    if (task_terms_log2 < 12 || task_terms_log2 > 20)
+      fail(QTC_ERR_INVALID, "task size 2^%d multiply-adds (12..20)", task_terms_log2);
+    if (subtree_bytes < 4096 || subtree_bytes > 32768)
+      fail(QTC_ERR_INVALID, "subtree of %d bytes (4096..32768)", subtree_bytes);
+    e->options.task_terms_log2 = task_terms_log2;
+    e->options.subtree_bytes = subtree_bytes;
     e->generation += 1;
     e->used = 0;
     e->work = 0;

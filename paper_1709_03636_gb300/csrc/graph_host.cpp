@@ -245,7 +245,8 @@ void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
   const int N = (int)plans.size();
   GraphLimits lim;
   lim.arena_elems = (uint32_t)(49152 / elem);
-  lim.subtree_elems = 32768 / elem;
+  lim.subtree_elems = (uint64_t)opts.subtree_bytes / elem;
+  lim.task_terms_log2 = opts.task_terms_log2;
   if (opts.small_rank > 0) lim.small_rank = opts.small_rank;
   lim.tensor_cores = hp.dtype == QTC_SPLIT_BF16;
   // with tensor cores four teams share one CTA's shared memory

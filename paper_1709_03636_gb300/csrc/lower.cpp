@@ -271,8 +271,10 @@ uint32_t log2_floor(uint64_t x) {
 
 // Fills the bit maps and chunking of C = sum over (A u B) - C of A * B.
 // force_split: always reduce over chunks of the summed index (leaf adjoints).
+// A chunk task covers about 2^task_terms_log2 multiply-adds.
 bool encode_gstep(GStep& g, const std::vector<int>& lc, const std::vector<int>& la,
-                  const std::vector<int>& lb, bool force_split, std::string* why) {
+                  const std::vector<int>& lb, bool force_split, int task_terms_log2,
+                  std::string* why) {
   std::vector<int> pa, pb, ya, yb;
   for (int x : lc) {
     pa.push_back(pos_in(la, x));
@@ -301,7 +303,7 @@ bool encode_gstep(GStep& g, const std::vector<int>& lc, const std::vector<int>& 
   const uint64_t nout = 1ull << g.rc, ny = 1ull << g.ry;
   if (nout <= kGRow && (force_split || nout * ny >= (1ull << 14))) {
     // small output, long sums: split the summed index over chunks
-    uint64_t per = std::max<uint64_t>(256, (1ull << 16) / nout);
+    uint64_t per = std::max<uint64_t>(256, (1ull << task_terms_log2) / nout);
     per = std::min<uint64_t>(per, kYTab);
     per = std::min<uint64_t>(per, ny);
     g.flags |= GSF_SPLIT;
@@ -312,7 +314,7 @@ bool encode_gstep(GStep& g, const std::vector<int>& lc, const std::vector<int>& 
     const uint64_t rows = nout / rowlen;
     uint64_t per = 1;
     if (ny <= kYTab) {
-      per = std::max<uint64_t>(1, (1ull << 16) / (rowlen * ny));
+      per = std::max<uint64_t>(1, (1ull << task_terms_log2) / (rowlen * ny));
       per = std::min<uint64_t>(per, kMaxChunkRows);
       per = std::min<uint64_t>(per, rows);
     }
@@ -571,7 +573,7 @@ NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
     u.kind = GT_CHUNK;
     std::memset(&u.step, 0, sizeof u.step);
     std::string why;
-    if (!encode_gstep(u.step, lc, la, lb, leaf_for_grad >= 0, &why)) {
+    if (!encode_gstep(u.step, lc, la, lb, leaf_for_grad >= 0, lim.task_terms_log2, &why)) {
       ng.fits = false;
       ng.why = why;
       return -1;

@@ -180,6 +180,7 @@ LoweredNet lower_smem(const Plan& plan, const std::vector<int>& leaf_gate,
 
 struct GraphLimits {
   int small_rank = 10;               // tensors of higher rank live in global memory
+  int task_terms_log2 = 16;          // multiply-adds per chunk task of a global step
   uint64_t subtree_elems = 4096;     // elements of all values of one subtree
   uint32_t arena_elems = 8192;       // shared-memory arena of one subtree task
   bool tensor_cores = false;         // split-BF16 GEMM tasks for GEMM-shaped steps
@@ -219,9 +220,12 @@ struct ProgramOptions {
   size_t wave_cap_bytes = (size_t)8 << 30;
   bool force_graph = false;
   int small_rank = 0;
+  int task_terms_log2 = 16;        // multiply-adds per chunk task of a global step
+  int subtree_bytes = 32768;       // values of one shared-memory subtree task
   bool operator==(const ProgramOptions& o) const {
     return wave_cap_bytes == o.wave_cap_bytes && force_graph == o.force_graph &&
-           small_rank == o.small_rank;
+           small_rank == o.small_rank && task_terms_log2 == o.task_terms_log2 &&
+           subtree_bytes == o.subtree_bytes;
   }
 };
 
