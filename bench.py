@@ -92,6 +92,9 @@ def parse():
                     help="tensor network vs state vector over regularities 3..7 (table)")
     ap.add_argument("--width-sweep", action="store_true",
                     help="time per <C> against the ordering's width, 18-qubit circuits (table)")
+    ap.add_argument("--autotune", default=None, metavar="CACHE.json",
+                    help="tune the graph executor's task shapes on this workload first "
+                         "(cache file, created if missing; no effect on shared-memory batches)")
     ap.add_argument("--noise", default=None, metavar="CHANNEL:STRENGTH",
                     help="noisy QAOA: depolarize|dephase|ampdamp channel of that strength on "
                          "every qubit after each mixer (density-matrix networks)")
@@ -291,6 +294,11 @@ def run_ours(args):
         info = batch.program_info(dtype, grad)
         need += info["work_bytes"] + 2 * info["table_bytes"]
     engine = q.Engine(local, arena_bytes=int(need) + (256 << 20))
+    tuned = None
+    if args.autotune:
+        tuned = q.autotune(engine, batch, dtype, want_grad, cache_path=args.autotune)
+        tuned = {k: tuned[k] for k in ("small_rank", "task_terms_log2", "subtree_bytes",
+                                       "cached")}
     batch.prepare(engine, dtype, want_grad=want_grad)
     batch.prepare(engine, dtype, want_grad=False)
     P = 2 * w.p
@@ -402,6 +410,7 @@ def run_ours(args):
                            "unit": "GFLOP/s", "count": "algorithmic, 8 real flops per complex "
                            "multiply-add (forward and adjoint contractions)"},
         "gpu_launches": launches,
+        "autotuned": tuned,
         "clocks": clocks.summary(),
         "step_ms_min_median_max": [min(step_ms), statistics.median(step_ms), max(step_ms)],
         "forward_only": {"value": world * n_nets / (fwd * 1e-3), "unit": "networks/s",
