@@ -7,8 +7,9 @@ pass) and swept backwards (adjoint), and the per-edge scalars are reduced to
 <C> and d<C>/d(gamma, beta) in FP64 - all in one launch of the executor.
 The planner (host) runs once before timing, as the paper excludes ordering
 time.  `value` is edge networks per second with inputs resident in device
-memory; `e2e` is the same through the host-pointer C call (pinned inputs
-copied in, results copied out, every step).
+memory; `e2e` is the same through the host-pointer C call (every step, the
+parameters go in and the results come out through the engine's pinned,
+device-mapped host buffer).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference   # the FP64 CPU oracle on the same metric
@@ -219,6 +220,41 @@ def oracle_networks_per_s(w, edges, g, b, want_grad, seconds):
             el = time.perf_counter() - t0
             if el >= seconds:
                 return done / el, done, el
+
+
+def _oracle_share(job):
+    """One worker of the all-cores oracle timing: edges k, k + n, ... of the
+    workload, repeated for `seconds`."""
+    name, k, n, seconds, want_grad = job
+    w = WORKLOADS[name]
+    edges = w.graph()
+    g, b = w.angles()
+    from oracle import tensornet as tn
+    mine = edges[k::n] or edges[:1]
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        for e in mine:
+            if want_grad:
+                tn.edge_value_grad(w.n, edges, g, b, e, lightcone=w.lightcone, dense=not w.diag)
+            else:
+                tn.edge_value(w.n, edges, g, b, e, lightcone=w.lightcone, dense=not w.diag)
+            done += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                return done, el
+
+
+def oracle_all_cores(w, want_grad, seconds):
+    """The same oracle on every host core: one process per core (spawned, so
+    that no child inherits the parent's CUDA context), edges dealt round
+    robin; the rate is the sum of the workers' rates."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    jobs = [(w.name, k, n, seconds, want_grad) for k in range(n)]
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_oracle_share, jobs)
+    return sum(d / el for d, el in res), n, sum(d for d, _ in res)
 
 
 def run_reference(args):
@@ -462,6 +498,11 @@ def run_ours(args):
             "value": rate, "unit": "networks/s", "cores": 1, "kind": "oracle",
             "sample": f"{done} edge networks of {w.name} with gradient in {el:.1f} s "
                       "(FP64 tensor-network oracle, numpy einsum, one thread)"}
+        rate_all, cores, done_all = oracle_all_cores(w, want_grad, 10.0)
+        line["cpu_baseline_all_cores"] = {
+            "value": rate_all, "unit": "networks/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done_all} edge networks of {w.name} with gradient, 10 s on each of "
+                      f"{cores} processes (one per core, edges dealt round robin)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
