@@ -736,10 +736,12 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
   // Schedule each network's ops into warp steps (lane-packed bundles).  First
   // with an arena buffer per intermediate and adjoint: ops that would reuse
   // memory no longer wait for its last reader, so independent subtrees share
-  // steps.  That layout is taken when it fits with the whole step list
-  // staged at once; otherwise the reused arena.
-  for (int pass = 0; warp_ok && pass < 2 && !ok; ++pass) {
-    const bool reuse = pass == 1;
+  // steps; then with buffers of their own for the small tensors only (<= 32
+  // elements: the lane-packed ops); each taken when it fits with the whole
+  // step list staged at once.  Otherwise the reused arena.
+  for (int pass = 0; warp_ok && pass < 3 && !ok; ++pass) {
+    const bool reuse = pass == 2;
+    const uint32_t private_below = pass == 0 ? UINT32_MAX : 32u;
     std::vector<TaskDev> wtasks = hp->tasks;
     std::vector<WStep> wsteps;
     uint32_t max_steps = 1, max_arena = 0;
@@ -750,7 +752,7 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
       const uint32_t begin = (uint32_t)wsteps.size();
       if (!reuse) {
         LoweredNet ln = lower_smem(b->plans[t.net], leaf_gate[t.net], val_off, der_off,
-                                   table_elems, want_grad != 0, max_elems, false);
+                                   table_elems, want_grad != 0, max_elems, private_below);
         if (!ln.fits || (size_t)table_elems + ln.arena_elems > 0xffffu) {
           fit = false;
           break;

@@ -116,14 +116,14 @@ struct alignas(16) SOp {
   uint8_t y1[kMaxSmemRank], y2[kMaxSmemRank];
 };
 
-// The same ops for networks run one per warp (every tensor of rank <= 7,
-// at most 4 summed bits per op): the bit maps are pre-expanded into byte
-// offset tables.  Output element c = 32 j + lane of a CONTRACT reads
+// The same ops for networks run one per warp (every tensor of rank <= 11,
+// at most 4 summed bits per op): the bit maps are pre-expanded into offset
+// tables.  Output element c = 32 j + lane of a CONTRACT reads
 // in1[a_lo[lane] | a_hi[j] | ya[y]] and in2[b_lo[lane] | b_hi[j] | yb[y]].
 // A CONTRACT flagged WOPF_LEAFGRAD produces dS/dleaf and also adds
 // sum_c out[c] * table[der + c] to the parameter gradient slot `slot` (the
 // leaf-gradient dot fused into the op that produces it).
-constexpr int kWarpMaxRank = 7;
+constexpr int kWarpMaxRank = 11;
 constexpr int kWarpMaxSummed = 4;
 // With at most this many parameters a warp team keeps one complex gradient
 // accumulator per (parameter, lane) in shared memory, right after its staged
@@ -136,12 +136,11 @@ struct alignas(16) WOp {
   uint8_t code, rc, ry, flags;
   uint16_t out, in1, in2, slot;   // element offsets (team relative), gradient slot
   uint16_t der, pad0;             // WOPF_LEAFGRAD: table offset of d(leaf)/dparam
-  uint8_t a_hi[4], b_hi[4];
-  uint8_t ya[16], yb[16];
-  uint8_t a_lo[32], b_lo[32];
-  uint8_t pad1[8];
+  uint16_t a_lo[32], b_lo[32];    // output bits 0..4
+  uint16_t ya[16], yb[16];        // summed bits
+  uint16_t a_hi[64], b_hi[64];    // output bits 5..10
 };
-static_assert(sizeof(WOp) == 128, "WOp is staged as eight 16-byte words");
+static_assert(sizeof(WOp) == 464, "WOp is staged as 29 16-byte words");
 
 // Warp programs are sequences of steps.  A bundle step packs mutually
 // independent small ops into aligned lane groups of one warp (the host

@@ -21,10 +21,11 @@ namespace qtc {
 constexpr int kMaxTeams = 8;
 
 // One CONTRACT op of a warp team from its pre-expanded offset tables: lane
-// handles outputs c = 32 j + lane.  The op's tables are read with 16-byte
-// loads up front; ops with zero or one summed bit (most of them) take
-// straight-line paths whose operand loads issue together.  With WOPF_LEAFGRAD the op also adds sum_c out[c] * der[c] to the
-// parameter gradient (the leaf-gradient dot of the adjoint, fused).
+// handles outputs c = 32 j + lane (j < 2^(rc - 5), up to 64 for rank 11).
+// Ops with zero or one summed bit (most of them) take straight-line paths
+// whose operand loads issue together.  With WOPF_LEAFGRAD the op also adds
+// sum_c out[c] * der[c] to the parameter gradient (the leaf-gradient dot of
+// the adjoint, fused).
 template <typename T>
 __device__ __forceinline__ void warp_contract(const WOp& op, const uint4 head, T* out,
                                               const T* a, const T* b, const T* table,
@@ -32,31 +33,22 @@ __device__ __forceinline__ void warp_contract(const WOp& op, const uint4 head, T
   const uint32_t rc = (head.x >> 8) & 0xffu, ry = (head.x >> 16) & 0xffu;
   const bool leafgrad = ((head.x >> 24) & WOPF_LEAFGRAD) != 0;
   const uint32_t nout = 1u << rc, ny = 1u << ry;
-  const uint4 hy = *reinterpret_cast<const uint4*>(&op.a_hi[0]);  // a_hi, b_hi, ya[0..7]
-  const uint4 hy2 = *reinterpret_cast<const uint4*>(&op.ya[8]);   // ya[8..15], yb[0..7]
-  const uint2 hy3 = *reinterpret_cast<const uint2*>(&op.yb[8]);   // yb[8..15]
   const uint32_t alo = op.a_lo[lane], blo = op.b_lo[lane];
+  const uint32_t ay1 = op.ya[1], by1 = op.yb[1];
   T dot = czero<T>();
   for (uint32_t j = 0; 32 * j < nout; ++j) {
     const uint32_t c = 32 * j + lane;
-    const uint32_t oa = alo | ((hy.x >> (8 * j)) & 0xffu);
-    const uint32_t ob = blo | ((hy.y >> (8 * j)) & 0xffu);
+    const uint32_t oa = alo | op.a_hi[j];
+    const uint32_t ob = blo | op.b_hi[j];
     T acc;
     if (ry == 0) {  // a product (batch and free labels only)
       acc = cfma(a[oa], b[ob], czero<T>());
     } else if (ry == 1) {
-      const uint32_t ay = (hy.z >> 8) & 0xffu, by = (hy2.z >> 8) & 0xffu;
-      const T a0 = a[oa], b0 = b[ob], a1 = a[oa | ay], b1 = b[ob | by];
+      const T a0 = a[oa], b0 = b[ob], a1 = a[oa | ay1], b1 = b[ob | by1];
       acc = cfma(a1, b1, cfma(a0, b0, czero<T>()));
     } else {
-      const uint64_t yal = ((uint64_t)hy.w << 32) | hy.z, yah = ((uint64_t)hy2.y << 32) | hy2.x;
-      const uint64_t ybl = ((uint64_t)hy2.w << 32) | hy2.z, ybh = ((uint64_t)hy3.y << 32) | hy3.x;
       acc = czero<T>();
-      for (uint32_t y = 0; y < ny; ++y) {
-        const uint32_t ay = (uint32_t)(((y < 8 ? yal : yah) >> (8 * (y & 7))) & 0xffu);
-        const uint32_t by = (uint32_t)(((y < 8 ? ybl : ybh) >> (8 * (y & 7))) & 0xffu);
-        acc = cfma(a[oa | ay], b[ob | by], acc);
-      }
+      for (uint32_t y = 0; y < ny; ++y) acc = cfma(a[oa | op.ya[y]], b[ob | op.yb[y]], acc);
     }
     if (c < nout) {
       out[c] = acc;

@@ -71,10 +71,11 @@ struct Pending {
 
 // Places the arena buffers referenced by `ops` (first-fit decreasing over op
 // index live ranges; a buffer written by op i and one read last by op i never
-// share memory; with reuse off every buffer gets memory of its own) and
-// writes the resolved ops.  Returns the arena size.
+// share memory) and writes the resolved ops.  Buffers of at most
+// `private_below` elements get memory of their own (no reuse at all with
+// UINT32_MAX).  Returns the arena size.
 uint32_t place_arena(const std::vector<Pending>& ops, const std::vector<uint32_t>& buf_size,
-                     uint32_t table_elems, std::vector<SOp>& out, bool reuse = true) {
+                     uint32_t table_elems, std::vector<SOp>& out, uint32_t private_below = 0) {
   const int B = (int)buf_size.size();
   std::vector<int> first(B, -1), last(B, -1);
   for (int i = 0; i < (int)ops.size(); ++i) {
@@ -99,7 +100,8 @@ uint32_t place_arena(const std::vector<Pending>& ops, const std::vector<uint32_t
     const uint32_t size = rounded(b);
     std::vector<std::pair<uint32_t, uint32_t>> busy;
     for (int q : placed)
-      if (!reuse || !(last[q] < first[b] || last[b] < first[q]))
+      if (buf_size[b] <= private_below || buf_size[q] <= private_below ||
+          !(last[q] < first[b] || last[b] < first[q]))
         busy.push_back({offset[q], offset[q] + rounded(q)});
     std::sort(busy.begin(), busy.end());
     uint32_t at = 0;
@@ -138,7 +140,7 @@ std::vector<char> needs_grad(const Plan& plan) {
 LoweredNet lower_smem(const Plan& plan, const std::vector<int>& leaf_gate,
                       const std::vector<uint32_t>& gate_val_off,
                       const std::vector<uint32_t>& gate_der_off, uint32_t table_elems,
-                      bool want_grad, uint32_t max_elems, bool reuse_arena) {
+                      bool want_grad, uint32_t max_elems, uint32_t private_below) {
   LoweredNet out;
   const int L = (int)plan.net.leaves.size();
   const int S = (int)plan.steps.size();
@@ -226,7 +228,7 @@ LoweredNet lower_smem(const Plan& plan, const std::vector<int>& leaf_gate,
       }
     }
   }
-  out.arena_elems = place_arena(ops, buf_size, table_elems, out.ops, reuse_arena);
+  out.arena_elems = place_arena(ops, buf_size, table_elems, out.ops, private_below);
   out.fits = table_elems + out.arena_elems <= max_elems;
   return out;
 }

@@ -166,14 +166,15 @@ void build_warp_steps(const std::vector<SOp>& ops, uint32_t table_elems, uint32_
                       std::vector<WStep>& out);
 
 // Lowers one plan to a shared-memory op program.  table_elems: size of the
-// gate value + derivative region that precedes the arena.  With reuse_arena
-// off every intermediate and adjoint keeps its own arena buffer (no
-// write-after-read ordering between ops that reuse memory).
+// gate value + derivative region that precedes the arena.  Intermediates and
+// adjoints of at most private_below elements keep arena buffers of their own
+// (no write-after-read ordering between ops that would reuse that memory);
+// UINT32_MAX: every buffer.
 LoweredNet lower_smem(const Plan& plan, const std::vector<int>& leaf_gate,
                       const std::vector<uint32_t>& gate_val_off,
                       const std::vector<uint32_t>& gate_der_off,
                       uint32_t table_elems, bool want_grad, uint32_t max_elems,
-                      bool reuse_arena = true);
+                      uint32_t private_below = 0);
 
 // ---- graph lowering (networks larger than one CTA's shared memory) ---------
 

@@ -20,11 +20,11 @@ namespace qtc {
 
 namespace {
 
-uint8_t deposit(const uint8_t* pos, int first, int count, uint32_t idx) {
+uint16_t deposit(const uint8_t* pos, int first, int count, uint32_t idx) {
   uint32_t off = 0;
   for (int i = 0; i < count; ++i)
     if (((idx >> i) & 1u) && pos[first + i] != kAbsent) off |= 1u << pos[first + i];
-  return (uint8_t)off;
+  return (uint16_t)off;
 }
 
 WOp expand(const SOp& op) {
@@ -42,7 +42,7 @@ WOp expand(const SOp& op) {
       w.a_lo[c] = deposit(op.p1, 0, lo, c);
       w.b_lo[c] = deposit(op.p2, 0, lo, c);
     }
-    for (uint32_t j = 0; j < 4; ++j) {
+    for (uint32_t j = 0; j < 64; ++j) {
       w.a_hi[j] = deposit(op.p1, 5, hi, j);
       w.b_hi[j] = deposit(op.p2, 5, hi, j);
     }

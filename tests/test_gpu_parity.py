@@ -83,6 +83,11 @@ def test_qaoa_p2_n100_batched_matches_oracle(engine):
     assert np.max(np.abs(np.array(per_edge) - ref)) < 2e-6
     assert _rel(C, ref_C) < C_REL
     _grad_close(grad, ref_grad)
+    # the forward-only program (one warp per network, tensors up to rank 11)
+    assert batch.program_info("c64", False)["warp_teams"] == 1
+    C_f, per_edge_f, _ = q.qaoa_expectation(engine, batch, g, b, "c64", want_grad=False)
+    assert np.max(np.abs(np.array(per_edge_f) - ref)) < 2e-6
+    assert _rel(C_f, ref_C) < C_REL
 
 
 def test_qaoa_dense_and_diagonal_forms_agree(engine):
