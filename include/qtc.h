@@ -148,6 +148,7 @@ typedef struct qtc_program_info {
   int n_warp_steps;       /* warp steps over all networks (warp teams)       */
   int max_warp_steps;     /* warp steps of the longest network               */
   int n_solo_steps;       /* of the warp steps, those one op runs alone      */
+  int stage_ops;          /* ops or warp steps a team stages at a time       */
 } qtc_program_info;
 
 typedef struct qtc_engine qtc_engine;
@@ -333,12 +334,15 @@ qtc_status qtc_engine_set_limits(qtc_engine* e, size_t max_wave_bytes, double wa
  * (default 10).  Invalidates prepared programs. */
 qtc_status qtc_engine_set_graph_options(qtc_engine* e, int force_graph, int small_rank);
 
-/* Task sizes of the graph executor (tuning; see the autotuner of the Python
- * package): a chunk task of a global step covers about 2^task_terms_log2
- * multiply-adds (12..20, default 16); a shared-memory subtree task holds at
- * most subtree_bytes of values (4096..32768, default 32768).  Invalidates
- * prepared programs.  QTC_ERR_INVALID outside those ranges. */
-qtc_status qtc_engine_set_task_options(qtc_engine* e, int task_terms_log2, int subtree_bytes);
+/* Task shapes (tuning; see the autotuner of the Python package): a chunk
+ * task of a global step of the graph executor covers about
+ * 2^task_terms_log2 multiply-adds (12..20, default 16); a shared-memory
+ * subtree task holds at most subtree_bytes of values (4096..32768, default
+ * 32768); warp_teams = 0 keeps the shared-memory executor at one network per
+ * CTA (default 1: one per warp where the network's program fits).
+ * Invalidates prepared programs.  QTC_ERR_INVALID outside those ranges. */
+qtc_status qtc_engine_set_task_options(qtc_engine* e, int task_terms_log2, int subtree_bytes,
+                                       int warp_teams);
 
 /* Launches a one-task program whose task waits for a counter nothing ever
  * signals, so that the bounded wait expires after the engine's wait limit and

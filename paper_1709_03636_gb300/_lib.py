@@ -46,7 +46,7 @@ class qtc_program_info(ctypes.Structure):
                 ("n_global_steps", c_int), ("n_smem_tasks", c_int), ("smem_bytes", c_int),
                 ("work_bytes", c_double), ("table_bytes", c_double), ("n_gemm_steps", c_int),
                 ("warp_teams", c_int), ("n_ops", c_int), ("n_warp_steps", c_int),
-                ("max_warp_steps", c_int), ("n_solo_steps", c_int)]
+                ("max_warp_steps", c_int), ("n_solo_steps", c_int), ("stage_ops", c_int)]
 
 
 # name -> (restype, argtypes)
@@ -88,7 +88,7 @@ SIGNATURES = {
     "qtc_engine_set_limits": (c_int, [c_void_p, c_size_t, c_double]),
     "qtc_selftest_wait_timeout": (c_int, [c_void_p, c_void_p]),
     "qtc_engine_set_graph_options": (c_int, [c_void_p, c_int, c_int]),
-    "qtc_engine_set_task_options": (c_int, [c_void_p, c_int, c_int]),
+    "qtc_engine_set_task_options": (c_int, [c_void_p, c_int, c_int, c_int]),
     "qtc_batch_launch_info": (c_int, [c_void_p, c_void_p, c_int, c_int, P(c_int32)]),
     "qtc_statevector_qaoa": (c_int, [c_void_p, c_void_p, P(c_double), P(c_double), c_int, c_int,
                                      c_void_p, P(c_double), P(c_double)]),

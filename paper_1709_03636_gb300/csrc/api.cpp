@@ -40,6 +40,7 @@ struct Prepared {
   int grid = 0, block = 0;
   size_t smem = 0;
   bool warp_teams = false;
+  bool stream = false;               // warp teams: steps streamed from global memory
   bool graph = false;
   int per_sm = 0;                    // resident CTAs per SM reported by the runtime
   std::vector<GraphProgDev> waves;   // graph form: one launch each
@@ -226,7 +227,7 @@ extern "C" qtc_status qtc_engine_set_graph_options(qtc_engine* e, int force_grap
 }
 
 extern "C" qtc_status qtc_engine_set_task_options(qtc_engine* e, int task_terms_log2,
-                                                  int subtree_bytes) {
+                                                  int subtree_bytes, int warp_teams) {
   return guarded([&] {
     if (!e) fail(QTC_ERR_INVALID, "null engine");
     if (task_terms_log2 < 12 || task_terms_log2 > 20)
@@ -235,6 +236,7 @@ extern "C" qtc_status qtc_engine_set_task_options(qtc_engine* e, int task_terms_
       fail(QTC_ERR_INVALID, "subtree of %d bytes (4096..32768)", subtree_bytes);
     e->options.task_terms_log2 = task_terms_log2;
     e->options.subtree_bytes = subtree_bytes;
+    e->options.warp_teams = warp_teams != 0;
     e->generation += 1;
     e->used = 0;
     e->work = 0;
@@ -705,7 +707,8 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
   auto round16 = [](size_t x) { return (uint32_t)((x + 15) & ~size_t(15)); };
   // warp teams need every op within the pre-expanded tables, and every
   // element of the table copy and arena within a 16-bit lane offset
-  bool warp_ok = max_rank <= kWarpMaxRank && (size_t)table_elems + hp->max_arena <= 0xffffu;
+  bool warp_ok = opts.warp_teams && max_rank <= kWarpMaxRank &&
+                 (size_t)table_elems + hp->max_arena <= 0xffffu;
   for (const SOp& op : hp->ops)
     if (op.code == SOP_CONTRACT && (op.rc > kWarpMaxRank || op.ry > kWarpMaxSummed))
       warp_ok = false;
@@ -713,10 +716,12 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
   // keeps its own copy right before its arena ([steps | lane gradient
   // accumulators | table | arena]), so every operand of a warp step is an
   // offset from one base.
-  auto layout = [&](bool warp, uint32_t stage) {
+  // stage 0 (warp teams): steps streamed from global memory, no stage region
+  auto layout = [&](bool warp, uint32_t stage, int teams = kWarpTeamsPerCta) {
     hp->warp_teams = warp;
-    hp->n_teams = warp ? kWarpTeamsPerCta : 1;
-    hp->block = warp ? 32 * kWarpTeamsPerCta : kExecBlock;
+    hp->stream_steps = warp && stage == 0;
+    hp->n_teams = warp ? teams : 1;
+    hp->block = warp ? 32 * teams : kExecBlock;
     hp->stage_ops = stage;
     const size_t op_bytes = warp ? sizeof(WStep) : sizeof(SOp);
     hp->table_bytes = warp ? 0 : round16((size_t)table_elems * elem);
@@ -737,8 +742,10 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
   // with an arena buffer per intermediate and adjoint: ops that would reuse
   // memory no longer wait for its last reader, so independent subtrees share
   // steps; then with buffers of their own for the small tensors only (<= 32
-  // elements: the lane-packed ops); each taken when it fits with the whole
-  // step list staged at once.  Otherwise the reused arena.
+  // elements: the lane-packed ops); then the reused arena.  Each is taken
+  // when it fits with the whole step list staged at once, or else with the
+  // steps streamed from global memory (no stage region), with 4, 2 or 1
+  // warp teams per CTA; the reused arena last tries smaller stages.
   for (int pass = 0; warp_ok && pass < 3 && !ok; ++pass) {
     const bool reuse = pass == 2;
     const uint32_t private_below = pass == 0 ? UINT32_MAX : 32u;
@@ -770,7 +777,12 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
     const uint32_t shared_arena = hp->max_arena;
     hp->max_arena = max_arena;
     const uint32_t stage = std::min<uint32_t>(max_steps, 128);
-    ok = reuse ? try_layout(true, stage) : layout(true, stage);
+    // (complex128 measured slower on one warp than on a CTA per network with a
+    // single warp team per CTA)
+    const int min_teams = dtype == QTC_C128 ? 2 : 1;
+    for (int teams = kWarpTeamsPerCta; teams >= min_teams && !ok; teams /= 2)
+      ok = layout(true, stage, teams) || layout(true, 0, teams);
+    if (!ok && reuse) ok = try_layout(true, stage);
     if (ok) {
       // With a fixed stride per task a team starts copying its first task's
       // steps without first reading the task record; taken when the padding
@@ -968,7 +980,9 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
   pr.smem = hp.smem;
   int per_sm = 0;
   pr.warp_teams = hp.warp_teams;
-  cuda_check(smem_exec_configure(dtype == QTC_C128 ? 0 : 1, pr.warp_teams, pr.smem, max_dyn,
+  pr.stream = hp.stream_steps;
+  cuda_check(smem_exec_configure(dtype == QTC_C128 ? 0 : 1,
+                                 pr.warp_teams ? (pr.stream ? 2 : 1) : 0, pr.smem, max_dyn,
                                  pr.block, &per_sm),
              "configure executor");
   if (per_sm < 1) fail(QTC_ERR_UNSUPPORTED, "executor does not fit on an SM (%zu bytes)", pr.smem);
@@ -996,7 +1010,8 @@ static void launch(qtc_engine* e, const Prepared& pr, const double* params_dev, 
   ProgramDev d = pr.prog;
   d.params = params_dev;
   d.out = out_dev;
-  cuda_check(smem_exec_launch(d, pr.dtype == QTC_C128 ? 0 : 1, pr.warp_teams, pr.grid, pr.block,
+  cuda_check(smem_exec_launch(d, pr.dtype == QTC_C128 ? 0 : 1,
+                              pr.warp_teams ? (pr.stream ? 2 : 1) : 0, pr.grid, pr.block,
                               pr.smem, stream),
              "launch executor");
   e->last_launches = 1;
@@ -1017,6 +1032,7 @@ extern "C" qtc_status qtc_batch_program_info(qtc_batch* b, int dtype, int want_g
     std::memset(info, 0, sizeof *info);
     info->graph = hp.graph ? 1 : 0;
     info->smem_bytes = (int)hp.smem;
+    info->stage_ops = (int)hp.stage_ops;
     double tables = sizeof(GateEntryDev) * hp.gates.size();
     if (hp.graph) {
       info->n_waves = (int)hp.waves.size();

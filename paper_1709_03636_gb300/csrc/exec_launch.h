@@ -8,12 +8,13 @@
 namespace qtc {
 
 // dtype: 0 = complex double, otherwise complex float.
-// warp_teams: each warp of a CTA runs its own network (small networks);
-// otherwise the whole CTA runs one network at a time.
-cudaError_t smem_exec_configure(int dtype, bool warp_teams, size_t smem_bytes, size_t max_dynamic,
+// mode: 0 = the whole CTA runs one network at a time; 1 = each warp of a CTA
+// runs its own network from steps staged in shared memory; 2 = the same with
+// steps streamed from global memory (step lists too long to stage).
+cudaError_t smem_exec_configure(int dtype, int mode, size_t smem_bytes, size_t max_dynamic,
                                 int block, int* blocks_per_sm);
-cudaError_t smem_exec_launch(const ProgramDev& prog, int dtype, bool warp_teams, int grid,
-                             int block, size_t smem_bytes, cudaStream_t stream);
+cudaError_t smem_exec_launch(const ProgramDev& prog, int dtype, int mode, int grid, int block,
+                             size_t smem_bytes, cudaStream_t stream);
 
 // Graph executor (networks larger than one CTA's shared memory); one launch
 // per wave.

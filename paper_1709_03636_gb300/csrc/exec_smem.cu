@@ -173,7 +173,27 @@ __device__ __forceinline__ void build_warp_gate_table(const ProgramDev& prog, T*
   }
 }
 
-template <typename T, bool kWarp>
+// Read-only loads of streamed warp steps (global memory, not written while
+// the kernel runs).
+__device__ __forceinline__ uint4 ldg_u4(const void* p) {
+  return __ldg(reinterpret_cast<const uint4*>(p));
+}
+__device__ __forceinline__ uint32_t ldg_u32(const void* p) {
+  return __ldg(reinterpret_cast<const unsigned int*>(p));
+}
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Streamed steps: the queue holds steps k .. k + 3 in registers; step
+// k + kStreamAhead is prefetched into L2 so that the queue's loads hit it.
+constexpr uint32_t kStreamAhead = 16;
+
+// kStream (warp teams whose step lists do not fit shared memory beside their
+// arenas): steps are read from global memory through a four-deep register
+// queue per lane (header word and the lane's descriptor) instead of being
+// staged; a solo step's op is read where it lies.
+template <typename T, bool kWarp, bool kStream = false>
 __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
   using R = decltype(T::x);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -211,7 +231,24 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
   // queue, numbered after the statically assigned ones.
   unsigned int t = blockIdx.x * teams_per_cta + team.id;
   TaskDev task{};
-  if (t < (unsigned)prog.n_tasks) {
+  // streamed steps: the register queue (steps k .. k + 3 of the current task)
+  uint32_t h0 = 0, h1 = 0, h2 = 0, h3 = 0;
+  uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0, q2 = q0, q3 = q0;
+  bool primed = false;
+  if (kStream && t < (unsigned)prog.n_tasks) {
+    // with a fixed stride the first steps are read before the task record
+    // arrives (only within the task's own stride)
+    if (prog.task_stride) {
+      const WStep* gs = prog.wsteps + (size_t)t * prog.task_stride;
+      const uint32_t m = min(prog.task_stride, 4u);
+      if (m > 0) { h0 = ldg_u32(&gs[0]); q0 = ldg_u4(&gs[0].lane[team.tid]); }
+      if (m > 1) { h1 = ldg_u32(&gs[1]); q1 = ldg_u4(&gs[1].lane[team.tid]); }
+      if (m > 2) { h2 = ldg_u32(&gs[2]); q2 = ldg_u4(&gs[2].lane[team.tid]); }
+      if (m > 3) { h3 = ldg_u32(&gs[3]); q3 = ldg_u4(&gs[3].lane[team.tid]); }
+      primed = true;
+    }
+    task = prog.tasks[t];
+  } else if (t < (unsigned)prog.n_tasks) {
     uint4* dst = reinterpret_cast<uint4*>(stage);
     if (kWarp && prog.task_stride) {
       // fixed stride: the copy starts before the task record arrives
@@ -239,7 +276,54 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
     for (int i = team.tid; i < 2 * P; i += team.size) grad[i] = R(0);
     if (lane_grad)
       for (int q = 0; q < P; ++q) sts_c(lacc_s + q * 32u * (uint32_t)sizeof(T), czero<T>());
-    for (uint32_t base = 0; base < task.op_count; base += prog.stage_ops) {
+    if constexpr (kStream) {
+      const WStep* gs = prog.wsteps + task.op_begin;
+      const uint32_t n = task.op_count;
+      if (!primed) {
+        if (n > 0) { h0 = ldg_u32(&gs[0]); q0 = ldg_u4(&gs[0].lane[team.tid]); }
+        if (n > 1) { h1 = ldg_u32(&gs[1]); q1 = ldg_u4(&gs[1].lane[team.tid]); }
+        if (n > 2) { h2 = ldg_u32(&gs[2]); q2 = ldg_u4(&gs[2].lane[team.tid]); }
+        if (n > 3) { h3 = ldg_u32(&gs[3]); q3 = ldg_u4(&gs[3].lane[team.tid]); }
+      }
+      primed = false;
+      for (uint32_t k = 4; k < min(n, kStreamAhead); ++k) prefetch_l2(&gs[k].lane[team.tid]);
+      for (uint32_t k = 0; k < n; ++k) {
+        const uint32_t h = h0;  // solo | rounds << 8
+        const uint4 L = q0;
+        h0 = h1; q0 = q1;
+        h1 = h2; q1 = q2;
+        h2 = h3; q2 = q3;
+        if (k + 4 < n) {
+          h3 = ldg_u32(&gs[k + 4]);
+          q3 = ldg_u4(&gs[k + 4].lane[team.tid]);
+        }
+        if (k + kStreamAhead < n) prefetch_l2(&gs[k + kStreamAhead].lane[team.tid]);
+        if (!(h & 0xffu)) {
+          warp_bundle<T>(L, (h >> 8) & 0xffu, table_s, grad, lacc_s, lane_grad, (uint32_t)P,
+                         res_s, team.tid);
+        } else {
+          // solo step, its op read in place
+          const WOp& w = gs[k].op;
+          const uint4 head = ldg_u4(&w);
+          const uint32_t code = head.x & 0xffu;
+          T* out = resolve<T>(head.y & 0xffffu, table, arena, prog.table_elems);
+          T* in1 = resolve<T>(head.y >> 16, table, arena, prog.table_elems);
+          T* in2 = resolve<T>(head.z & 0xffffu, table, arena, prog.table_elems);
+          if (code == SOP_CONTRACT) {
+            warp_contract<T>(w, head, out, in1, in2, table, grad, team.tid);
+          } else if (code == SOP_LEAFGRAD) {
+            warp_leaf_dot<T>(in1, in2, 1u << ((head.x >> 8) & 0xffu), team.tid, grad,
+                             head.z >> 16);
+          } else if (code == SOP_RESULT) {
+            if (team.tid == 0) s_res[team.id] = to_d2(*in1);
+          } else if (code == SOP_SEED) {
+            if (team.tid == 0) *out = from_d2<T>(make_double2(1.0, 0.0));
+          }
+        }
+        team.sync();
+      }
+    }
+    for (uint32_t base = 0; !kStream && base < task.op_count; base += prog.stage_ops) {
       const uint32_t n = min(prog.stage_ops, task.op_count - base);
       if (!staged) {
         // stage a chunk of the op list with one cooperative copy
@@ -378,19 +462,26 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
   }
 }
 
-template <typename T, bool kWarp>
+template <typename T, bool kWarp, bool kStream>
 static const void* kernel_ptr() {
-  return (const void*)smem_exec_kernel<T, kWarp>;
+  return (const void*)smem_exec_kernel<T, kWarp, kStream>;
 }
 
-static const void* select_kernel(int dtype, bool warp) {
-  if (dtype == 0) return warp ? kernel_ptr<double2, true>() : kernel_ptr<double2, false>();
-  return warp ? kernel_ptr<float2, true>() : kernel_ptr<float2, false>();
+// mode: 0 CTA teams, 1 warp teams with staged steps, 2 warp teams with
+// streamed steps
+template <typename T>
+static const void* select_mode(int mode) {
+  if (mode == 2) return kernel_ptr<T, true, true>();
+  return mode == 1 ? kernel_ptr<T, true, false>() : kernel_ptr<T, false, false>();
 }
 
-cudaError_t smem_exec_configure(int dtype, bool warp_teams, size_t smem_bytes, size_t max_dynamic,
+static const void* select_kernel(int dtype, int mode) {
+  return dtype == 0 ? select_mode<double2>(mode) : select_mode<float2>(mode);
+}
+
+cudaError_t smem_exec_configure(int dtype, int mode, size_t smem_bytes, size_t max_dynamic,
                                 int block, int* blocks_per_sm) {
-  const void* fn = select_kernel(dtype, warp_teams);
+  const void* fn = select_kernel(dtype, mode);
   // the attribute is per kernel, shared by every prepared program: always
   // raise it to the device limit so a smaller program never lowers it below
   // what a larger one needs
@@ -401,15 +492,19 @@ cudaError_t smem_exec_configure(int dtype, bool warp_teams, size_t smem_bytes, s
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem_bytes);
 }
 
-cudaError_t smem_exec_launch(const ProgramDev& prog, int dtype, bool warp_teams, int grid,
-                             int block, size_t smem_bytes, cudaStream_t stream) {
+cudaError_t smem_exec_launch(const ProgramDev& prog, int dtype, int mode, int grid, int block,
+                             size_t smem_bytes, cudaStream_t stream) {
   if (dtype == 0) {
-    if (warp_teams)
+    if (mode == 2)
+      smem_exec_kernel<double2, true, true><<<grid, block, smem_bytes, stream>>>(prog);
+    else if (mode == 1)
       smem_exec_kernel<double2, true><<<grid, block, smem_bytes, stream>>>(prog);
     else
       smem_exec_kernel<double2, false><<<grid, block, smem_bytes, stream>>>(prog);
   } else {
-    if (warp_teams)
+    if (mode == 2)
+      smem_exec_kernel<float2, true, true><<<grid, block, smem_bytes, stream>>>(prog);
+    else if (mode == 1)
       smem_exec_kernel<float2, true><<<grid, block, smem_bytes, stream>>>(prog);
     else
       smem_exec_kernel<float2, false><<<grid, block, smem_bytes, stream>>>(prog);

@@ -223,10 +223,11 @@ struct ProgramOptions {
   int small_rank = 0;
   int task_terms_log2 = 16;        // multiply-adds per chunk task of a global step
   int subtree_bytes = 32768;       // values of one shared-memory subtree task
+  bool warp_teams = true;          // networks may run one per warp
   bool operator==(const ProgramOptions& o) const {
     return wave_cap_bytes == o.wave_cap_bytes && force_graph == o.force_graph &&
            small_rank == o.small_rank && task_terms_log2 == o.task_terms_log2 &&
-           subtree_bytes == o.subtree_bytes;
+           subtree_bytes == o.subtree_bytes && warp_teams == o.warp_teams;
   }
 };
 
@@ -261,6 +262,7 @@ struct HostProgram {
   uint32_t stage_ops = 0;          // ops staged per team at a time
   uint32_t task_stride = 0;        // warp steps of task t start at t * task_stride (0: packed)
   bool warp_teams = false;         // one network per warp (small networks)
+  bool stream_steps = false;       // warp teams read their steps from global memory
   int n_teams = 1;                 // teams per CTA
   int block = kExecBlock;          // threads per CTA
   size_t smem = 0;                 // dynamic shared memory per CTA, bytes

@@ -116,7 +116,8 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
                "clear counters");
 
     int per_sm = 0;
-    cuda_check(smem_exec_configure(dtype == QTC_C128 ? 0 : 1, hp.warp_teams, hp.smem, max_dyn,
+    const int mode = hp.warp_teams ? (hp.stream_steps ? 2 : 1) : 0;
+    cuda_check(smem_exec_configure(dtype == QTC_C128 ? 0 : 1, mode, hp.smem, max_dyn,
                                    hp.block, &per_sm), "configure executor");
     if (per_sm < 1) fail(QTC_ERR_UNSUPPORTED, "executor does not fit on an SM");
     ProgramDev d{};
@@ -145,7 +146,7 @@ extern "C" qtc_status qtc_qaoa_expectation_static(qtc_batch* b, const double* pa
     d.qaoa_reduce = hp.qaoa_reduce;
     const int ctas = ((int)hp.tasks.size() + hp.n_teams - 1) / hp.n_teams;
     const int grid = std::max(1, std::min(ctas, setup.sm_count * per_sm));
-    cuda_check(smem_exec_launch(d, dtype == QTC_C128 ? 0 : 1, hp.warp_teams, grid, hp.block,
+    cuda_check(smem_exec_launch(d, dtype == QTC_C128 ? 0 : 1, mode, grid, hp.block,
                                 hp.smem, s),
                "launch executor");
   });

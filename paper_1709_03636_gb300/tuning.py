@@ -1,19 +1,17 @@
-"""Autotuner for the graph executor's task shapes.
+"""Autotuner for the executors' task shapes.
 
 Networks too large for one CTA's shared memory run on the persistent graph
 executor (one launch per wave).  How its work is cut into tasks decides how
 well the tasks fill the GPU: the rank above which tensors live in global
 memory (`small_rank`), the multiply-adds per chunk task of a global step
 (`task_terms_log2`) and the size of a shared-memory subtree task
-(`subtree_bytes`).  `autotune` times each candidate on the batch itself (the
+(`subtree_bytes`).  Batches whose networks fit one CTA's shared memory run on
+the shared-memory executor, one network per warp or one per CTA
+(`warp_teams`).  `autotune` times each candidate on the batch itself (the
 device call, L2 flushed between evaluations, CUDA events), applies the
 fastest to the engine and can persist the choice in a JSON cache keyed by the
 batch's structure, the dtype, the gradient flag and the GPU, so a later run
 applies it without timing.
-
-Batches whose networks all fit one CTA's shared memory run on the
-shared-memory executor, which has nothing to tune; `autotune` then returns
-the defaults unchanged.
 """
 
 from __future__ import annotations
@@ -22,16 +20,20 @@ import hashlib
 import json
 import os
 
-DEFAULTS = {"small_rank": 10, "task_terms_log2": 16, "subtree_bytes": 32768}
+DEFAULTS = {"small_rank": 10, "task_terms_log2": 16, "subtree_bytes": 32768,
+            "warp_teams": True}
 
 
-def default_candidates():
-    """small_rank x task size x subtree size around the defaults."""
+def default_candidates(graph: bool = True):
+    """Graph programs: small_rank x task size x subtree size around the
+    defaults.  Shared-memory programs: one network per warp or per CTA."""
+    if not graph:
+        return [dict(DEFAULTS), dict(DEFAULTS, warp_teams=False)]
     out = []
     for sr in (9, 10, 11):
         for tt in (15, 16, 17):
             for sb in (16384, 32768):
-                out.append({"small_rank": sr, "task_terms_log2": tt, "subtree_bytes": sb})
+                out.append(dict(DEFAULTS, small_rank=sr, task_terms_log2=tt, subtree_bytes=sb))
     return out
 
 
@@ -68,7 +70,8 @@ def apply(engine, choice: dict):
     """Set the engine's graph-executor options to `choice` (invalidates its
     prepared programs)."""
     engine.set_graph_options(False, int(choice["small_rank"]))
-    engine.set_task_options(int(choice["task_terms_log2"]), int(choice["subtree_bytes"]))
+    engine.set_task_options(int(choice["task_terms_log2"]), int(choice["subtree_bytes"]),
+                            bool(choice.get("warp_teams", True)))
 
 
 def _device_timer(engine, batch, dtype, want_grad, steps, warmup):
@@ -112,18 +115,17 @@ def autotune(engine, batch, dtype: str = "c64", want_grad: bool = True, *, cache
     key = signature(batch, dtype, want_grad, device_name)
     table = _load(cache_path)
     if key in table:
-        choice = dict(table[key])
+        choice = dict(DEFAULTS, **table[key])
         apply(engine, choice)
         choice.update(cached=True, trials=[])
         return choice
-    if not batch.program_info(dtype, want_grad)["graph"]:
-        apply(engine, DEFAULTS)
-        return dict(DEFAULTS, ms=None, cached=False, trials=[], graph=False)
+    graph = bool(batch.program_info(dtype, want_grad)["graph"])
     from . import QtcError
     if timer is None:
         timer = _device_timer(engine, batch, dtype, want_grad, steps, warmup)
     trials = []
-    for cand in candidates or default_candidates():
+    for cand in candidates or default_candidates(graph):
+        cand = dict(DEFAULTS, **cand)
         try:
             apply(engine, cand)
             batch.prepare(engine, dtype, want_grad=want_grad)
@@ -142,4 +144,4 @@ def autotune(engine, batch, dtype: str = "c64", want_grad: bool = True, *, cache
     apply(engine, choice)
     table[key] = dict(choice, ms=best["ms"])
     _store(cache_path, table)
-    return dict(choice, ms=best["ms"], cached=False, trials=trials)
+    return dict(choice, ms=best["ms"], cached=False, trials=trials, graph=graph)

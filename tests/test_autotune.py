@@ -20,9 +20,10 @@ class FakeEngine:
         self.calls.append(("graph", force_graph, small_rank))
         self.sr = small_rank
 
-    def set_task_options(self, task_terms_log2=16, subtree_bytes=32768):
-        self.calls.append(("task", task_terms_log2, subtree_bytes))
+    def set_task_options(self, task_terms_log2=16, subtree_bytes=32768, warp_teams=True):
+        self.calls.append(("task", task_terms_log2, subtree_bytes, warp_teams))
         self.opts = (self.sr, task_terms_log2, subtree_bytes)
+        self.warp = warp_teams
 
 
 class FakeBatch:
@@ -75,16 +76,20 @@ def test_signature_separates_dtype_gradient_device_and_structure():
     assert len(keys) == 5
 
 
-def test_shared_memory_batches_keep_the_defaults():
+def test_shared_memory_batches_choose_warp_or_cta_teams():
     eng = FakeEngine()
     res = at.autotune(eng, FakeBatch(graph=False), "c64", True,
-                      timer=lambda: pytest.fail("nothing to time"), device_name="GB300")
-    assert res["graph"] is False
+                      timer=lambda: 1.0 if eng.warp else 2.0, device_name="GB300")
+    assert res["graph"] is False and res["warp_teams"] is True and eng.warp is True
+    eng = FakeEngine()
+    res = at.autotune(eng, FakeBatch(graph=False), "c128", True,
+                      timer=lambda: 3.0 if eng.warp else 2.0, device_name="GB300")
+    assert res["warp_teams"] is False and eng.warp is False
     assert eng.opts == (at.DEFAULTS["small_rank"], at.DEFAULTS["task_terms_log2"],
                         at.DEFAULTS["subtree_bytes"])
 
 
 def test_task_option_ranges_are_checked():
     lib = q.lib
-    assert lib.qtc_engine_set_task_options(None, 16, 32768) != 0
+    assert lib.qtc_engine_set_task_options(None, 16, 32768, 1) != 0
 
