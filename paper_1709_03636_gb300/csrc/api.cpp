@@ -777,11 +777,13 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
     const uint32_t shared_arena = hp->max_arena;
     hp->max_arena = max_arena;
     const uint32_t stage = std::min<uint32_t>(max_steps, 128);
-    // (complex128 measured slower on one warp than on a CTA per network with a
-    // single warp team per CTA)
-    const int min_teams = dtype == QTC_C128 ? 2 : 1;
-    for (int teams = kWarpTeamsPerCta; teams >= min_teams && !ok; teams /= 2)
-      ok = layout(true, stage, teams) || layout(true, 0, teams);
+    // (complex128 programs that need streamed steps or fewer teams per CTA
+    // measured slower on warps than on a CTA per network: they stay staged
+    // with four teams, or run on CTA teams)
+    const bool wide = dtype == QTC_C128;
+    for (int teams = kWarpTeamsPerCta; teams >= (wide ? kWarpTeamsPerCta : 1) && !ok;
+         teams /= 2)
+      ok = layout(true, stage, teams) || (!wide && layout(true, 0, teams));
     if (!ok && reuse) ok = try_layout(true, stage);
     if (ok) {
       // With a fixed stride per task a team starts copying its first task's
