@@ -117,14 +117,14 @@ struct alignas(16) SOp {
 };
 
 // The same ops for networks run one per warp (every tensor of rank <= 11,
-// at most 4 summed bits per op): the bit maps are pre-expanded into offset
+// at most 8 summed bits per op): the bit maps are pre-expanded into offset
 // tables.  Output element c = 32 j + lane of a CONTRACT reads
-// in1[a_lo[lane] | a_hi[j] | ya[y]] and in2[b_lo[lane] | b_hi[j] | yb[y]].
+// in1[a_lo[lane] | a_hi[j] | ya[y & 15] | ya_hi[y >> 4]] and in2 likewise.
 // A CONTRACT flagged WOPF_LEAFGRAD produces dS/dleaf and also adds
 // sum_c out[c] * table[der + c] to the parameter gradient slot `slot` (the
 // leaf-gradient dot fused into the op that produces it).
 constexpr int kWarpMaxRank = 11;
-constexpr int kWarpMaxSummed = 4;
+constexpr int kWarpMaxSummed = 8;
 // With at most this many parameters a warp team keeps one complex gradient
 // accumulator per (parameter, lane) in shared memory, right after its staged
 // steps; each lane adds its own leaf-gradient terms there without shuffles.
@@ -137,10 +137,11 @@ struct alignas(16) WOp {
   uint16_t out, in1, in2, slot;   // element offsets (team relative), gradient slot
   uint16_t der, pad0;             // WOPF_LEAFGRAD: table offset of d(leaf)/dparam
   uint16_t a_lo[32], b_lo[32];    // output bits 0..4
-  uint16_t ya[16], yb[16];        // summed bits
+  uint16_t ya[16], yb[16];        // summed bits 0..3
   uint16_t a_hi[64], b_hi[64];    // output bits 5..10
+  uint16_t ya_hi[16], yb_hi[16];  // summed bits 4..7
 };
-static_assert(sizeof(WOp) == 464, "WOp is staged as 29 16-byte words");
+static_assert(sizeof(WOp) == 528, "WOp is staged as 33 16-byte words");
 
 // Warp programs are sequences of steps.  A bundle step packs mutually
 // independent small ops into aligned lane groups of one warp (the host
@@ -178,7 +179,7 @@ struct alignas(16) WStep {
     WOp op;
   };
 };
-static_assert(sizeof(WStep) == 528, "WStep is staged as 33 16-byte words");
+static_assert(sizeof(WStep) == 544, "WStep is staged as 34 16-byte words");
 
 struct TaskDev {
   uint32_t op_begin, op_count;

@@ -48,7 +48,9 @@ __device__ __forceinline__ void warp_contract(const WOp& op, const uint4 head, T
       acc = cfma(a1, b1, cfma(a0, b0, czero<T>()));
     } else {
       acc = czero<T>();
-      for (uint32_t y = 0; y < ny; ++y) acc = cfma(a[oa | op.ya[y]], b[ob | op.yb[y]], acc);
+      for (uint32_t y = 0; y < ny; ++y)
+        acc = cfma(a[oa | op.ya[y & 15] | op.ya_hi[y >> 4]],
+                   b[ob | op.yb[y & 15] | op.yb_hi[y >> 4]], acc);
     }
     if (c < nout) {
       out[c] = acc;

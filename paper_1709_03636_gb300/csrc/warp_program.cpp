@@ -47,8 +47,10 @@ WOp expand(const SOp& op) {
       w.b_hi[j] = deposit(op.p2, 5, hi, j);
     }
     for (uint32_t y = 0; y < 16; ++y) {
-      w.ya[y] = deposit(op.y1, 0, op.ry, y);
-      w.yb[y] = deposit(op.y2, 0, op.ry, y);
+      w.ya[y] = deposit(op.y1, 0, std::min<int>(op.ry, 4), y);
+      w.yb[y] = deposit(op.y2, 0, std::min<int>(op.ry, 4), y);
+      w.ya_hi[y] = deposit(op.y1, 4, std::max<int>(op.ry - 4, 0), y);
+      w.yb_hi[y] = deposit(op.y2, 4, std::max<int>(op.ry - 4, 0), y);
     }
   }
   return w;
@@ -70,8 +72,8 @@ Access accesses(const WOp& w, uint32_t table_elems) {
       for (uint32_t c = 0; c < nout; ++c) {
         const uint32_t oa = w.a_lo[c & 31] | w.a_hi[c >> 5], ob = w.b_lo[c & 31] | w.b_hi[c >> 5];
         for (uint32_t y = 0; y < (1u << w.ry); ++y) {
-          arena(w.in1, oa | w.ya[y], acc.reads);
-          arena(w.in2, ob | w.yb[y], acc.reads);
+          arena(w.in1, oa | w.ya[y & 15] | w.ya_hi[y >> 4], acc.reads);
+          arena(w.in2, ob | w.yb[y & 15] | w.yb_hi[y >> 4], acc.reads);
         }
         arena(w.out, c, acc.writes);
       }
