@@ -159,6 +159,12 @@ enum WLaneFlag : uint8_t {
 // Lane offsets count elements from the start of the warp's gate-table copy
 // (the table, then the warp's arena).
 // WStep::rounds bit 7: some lane adds a leaf gradient (low bits: rounds).
+// WLane::gw packs three fields: bits 0-2 log2 of the op's lane-group width;
+// for an op summing 2^ry terms (ry = 2..4) spread over 2^(ry-1) lanes per
+// output (each lane two terms), bits 3-5 the log2 distance between those
+// lanes (the op's rc) and bits 6-7 the shuffle rounds that add them (ry - 1);
+// only the lane of the first pair stores and adds leaf-gradient terms.
+// WStep::pad[0]: the most such rounds of any lane of the step.
 constexpr uint8_t kWHasLeafGrad = 0x80;
 
 // Unused fields are zero: every lane's loads stay at valid offsets.

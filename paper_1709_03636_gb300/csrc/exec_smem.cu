@@ -79,14 +79,17 @@ __device__ __forceinline__ void warp_contract(const WOp& op, const uint4 head, T
 // their first operands again (ya1 = yb1 = 0), lanes without a leaf
 // derivative read table element 0, and lanes that add no leaf-gradient term
 // read the accumulator of slot 0.
+// Ops summing four to sixteen terms spread them over lane pairs (two terms
+// a lane) and add the pairs with `prounds` shuffle rounds (the step's most).
 template <typename T>
-__device__ __forceinline__ void warp_bundle(const uint4 L, uint32_t rounds, uint32_t base_s,
-                                            decltype(T::x)* grad, uint32_t lacc_s,
-                                            bool lane_grad, uint32_t n_params, uint32_t res_s,
-                                            uint32_t lane) {
+__device__ __forceinline__ void warp_bundle(const uint4 L, uint32_t rounds, uint32_t prounds,
+                                            uint32_t base_s, decltype(T::x)* grad,
+                                            uint32_t lacc_s, bool lane_grad, uint32_t n_params,
+                                            uint32_t res_s, uint32_t lane) {
   constexpr uint32_t kE = sizeof(T);
   const uint32_t kind = L.x & 0xffu, flags = (L.x >> 8) & 0xffu;
-  const uint32_t gw = (L.x >> 16) & 0xffu, slot = L.x >> 24;
+  const uint32_t gwp = (L.x >> 16) & 0xffu, slot = L.x >> 24;
+  const uint32_t gw = gwp & 7u;
   const uint32_t pa = base_s + (L.y >> 16) * kE, pb = base_s + (L.z & 0xffffu) * kE;
   const uint32_t pl = lacc_s + (slot < n_params ? slot : 0u) * (32u * kE);
   const T a0 = lds_c<T>(pa), b0 = lds_c<T>(pb);
@@ -96,6 +99,17 @@ __device__ __forceinline__ void warp_bundle(const uint4 L, uint32_t rounds, uint
   if (lane_grad) s = lds_c<T>(pl);
   T acc = cfma(a0, b0, czero<T>());
   if (flags & WLF_Y1) acc = cfma(a1, b1, acc);
+  if (prounds) {
+    const uint32_t pd = (gwp >> 3) & 7u, pr = gwp >> 6;
+    for (uint32_t r = 0; r < prounds; ++r) {
+      const decltype(T::x) ox = __shfl_xor_sync(0xffffffffu, acc.x, 1u << (pd + r));
+      const decltype(T::x) oy = __shfl_xor_sync(0xffffffffu, acc.y, 1u << (pd + r));
+      if (r < pr) {
+        acc.x += ox;
+        acc.y += oy;
+      }
+    }
+  }
   if (kind == WL_SEED) acc = from_d2<T>(make_double2(1.0, 0.0));
   if (flags & WLF_STORE) sts_c(base_s + (L.y & 0xffffu) * kE, acc);
   if (kind == WL_RESULT) sts_c(res_s, to_d2(a0));
@@ -301,8 +315,8 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
         }
         if (k + kStreamAhead < n) prefetch_l2(&gs[k + kStreamAhead].lane[team.tid]);
         if (!(h & 0xffu)) {
-          warp_bundle<T>(L, (h >> 8) & 0xffu, table_s, grad, lacc_s, lane_grad, (uint32_t)P,
-                         res_s, team.tid);
+          warp_bundle<T>(L, (h >> 8) & 0xffu, (h >> 16) & 0xffu, table_s, grad, lacc_s,
+                         lane_grad, (uint32_t)P, res_s, team.tid);
         } else {
           // solo step, its op read in place
           const WOp& w = gs[k].op;
@@ -355,8 +369,8 @@ __global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
             l_next = lds_u4(nxt + 16 + 16 * team.tid);
           }
           if (!(h & 0xffu)) {
-            warp_bundle<T>(L, (h >> 8) & 0xffu, table_s, grad, lacc_s, lane_grad, (uint32_t)P,
-                           res_s, team.tid);
+            warp_bundle<T>(L, (h >> 8) & 0xffu, (h >> 16) & 0xffu, table_s, grad, lacc_s,
+                           lane_grad, (uint32_t)P, res_s, team.tid);
           } else {
             // solo step; header word: code, rc, ry, flags | out, in1 | in2, slot | der
             const WOp& w = op.op;

@@ -134,10 +134,15 @@ void build_warp_steps(const std::vector<SOp>& ops, uint32_t table_elems, uint32_
     for (uint32_t e : acc.reads) earliest = std::max(earliest, last_write[e] + 1);
     for (uint32_t e : acc.writes)
       earliest = std::max({earliest, last_read[e] + 1, last_write[e] + 1});
+    // 2^ry summed terms (ry = 2..4): 2^(ry-1) lanes per output, two terms each,
+    // added by shuffles
+    const bool paired = w.code == SOP_CONTRACT && w.ry >= 2 && w.ry <= 4 &&
+                        w.rc + w.ry - 1 <= 5;
     const bool bundled =
-        (w.code == SOP_CONTRACT && w.rc <= 5 && w.ry <= 1) ||
+        (w.code == SOP_CONTRACT && w.rc <= 5 && w.ry <= 1) || paired ||
         (w.code == SOP_LEAFGRAD && w.rc <= 5) || w.code == SOP_RESULT || w.code == SOP_SEED;
-    const uint32_t gw = (w.code == SOP_CONTRACT || w.code == SOP_LEAFGRAD) ? w.rc : 0;
+    const uint32_t gw = paired ? (uint32_t)(w.rc + w.ry - 1)
+                               : (w.code == SOP_CONTRACT || w.code == SOP_LEAFGRAD) ? w.rc : 0;
     const uint32_t width = 1u << gw;
     const uint32_t group = width == 32 ? 0xFFFFFFFFu : ((1u << width) - 1u);
     int at = -1;
@@ -165,6 +170,34 @@ void build_warp_steps(const std::vector<SOp>& ops, uint32_t table_elems, uint32_
       st.mask = 0xFFFFFFFFu;
       st.step.solo = 1;
       st.step.op = w;
+    } else if (paired) {
+      st.mask |= group << pos;
+      auto yoff = [](const uint16_t* lo, const uint16_t* hi, uint32_t y) {
+        return (uint32_t)(lo[y & 15] | hi[y >> 4]);
+      };
+      st.step.pad[0] = (uint8_t)std::max<uint32_t>(st.step.pad[0], w.ry - 1u);
+      for (uint32_t i = 0; i < width; ++i) {
+        WLane& l = st.step.lane[pos + i];
+        const uint32_t c = i & ((1u << w.rc) - 1u), yh = i >> w.rc;  // y = 2 yh + ylo
+        const bool first = yh == 0;
+        const bool leaf = first && (w.flags & WOPF_LEAFGRAD);
+        l.gw = (uint8_t)(gw | (uint32_t)w.rc << 3 | (uint32_t)(w.ry - 1) << 6);
+        l.slot = leaf ? (uint8_t)w.slot : (uint8_t)0;
+        l.kind = WL_CONTRACT;
+        l.flags = (uint8_t)(WLF_Y1 | (first ? WLF_STORE : 0) | (leaf ? WLF_LG_MUL : 0));
+        l.c_off = (uint16_t)(w.out + c);
+        l.a_off = (uint16_t)(lane_operand(w.in1, table_elems) +
+                             (w.a_lo[c] | yoff(w.ya, w.ya_hi, 2 * yh)));
+        l.b_off = (uint16_t)(lane_operand(w.in2, table_elems) +
+                             (w.b_lo[c] | yoff(w.yb, w.yb_hi, 2 * yh)));
+        l.ya1 = (uint16_t)yoff(w.ya, w.ya_hi, 1);
+        l.yb1 = (uint16_t)yoff(w.yb, w.yb_hi, 1);
+        if (leaf) {
+          l.der_off = (uint16_t)(w.der + c);
+          st.step.rounds = (uint8_t)(kWHasLeafGrad |
+                                     std::max<uint32_t>(st.step.rounds & 0x7Fu, gw));
+        }
+      }
     } else {
       st.mask |= group << pos;
       for (uint32_t c = 0; c < width; ++c) {
