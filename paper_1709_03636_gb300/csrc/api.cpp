@@ -179,6 +179,7 @@ extern "C" qtc_status qtc_engine_create(int device, void* arena, size_t arena_by
     int v = 0;
     cuda_check(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device), "SM count");
     e->sm_count = v;
+    e->options.sm_count = v;
     cuda_check(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device),
                "shared memory limit");
     e->smem_optin = (size_t)v;
@@ -738,25 +739,32 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
     }
   };
   bool ok = false;
-  // Schedule each network's ops into warp steps (lane-packed bundles).  First
-  // with an arena buffer per intermediate and adjoint: ops that would reuse
-  // memory no longer wait for its last reader, so independent subtrees share
-  // steps; then with buffers of their own for the small tensors only (<= 32
-  // elements: the lane-packed ops); then the reused arena.  Each is taken
-  // when it fits with the whole step list staged at once, or else with the
-  // steps streamed from global memory (no stage region), with 4, 2 or 1
-  // warp teams per CTA; the reused arena last tries smaller stages.
-  for (int pass = 0; warp_ok && pass < 3 && !ok; ++pass) {
-    const bool reuse = pass == 2;
-    const uint32_t private_below = pass == 0 ? UINT32_MAX : 32u;
-    std::vector<TaskDev> wtasks = hp->tasks;
+  // Schedule each network's ops into warp steps (lane-packed bundles), three
+  // ways: with an arena buffer per intermediate and adjoint (ops that would
+  // reuse memory no longer wait for its last reader, so independent subtrees
+  // share steps); with buffers of their own for the small tensors only (<= 32
+  // elements: the lane-packed ops); and with the reused arena.  Each can run
+  // with its whole step list staged in shared memory or streamed from global
+  // memory (no stage region), with 4, 2 or 1 warp teams per CTA.  The layout
+  // taken is the one with the fewest (rounds of resident teams) x (steps of
+  // the longest network); the reused arena with smaller stages is the last
+  // resort.
+  struct WarpCand {
+    std::vector<TaskDev> tasks;
     std::vector<WStep> wsteps;
     uint32_t max_steps = 1, max_arena = 0;
+  };
+  std::vector<WarpCand> cands;
+  for (int pass = 0; warp_ok && pass < 3; ++pass) {
+    const bool reuse = pass == 2;
+    const uint32_t private_below = pass == 0 ? UINT32_MAX : 32u;
+    WarpCand c;
+    c.tasks = hp->tasks;
     bool fit = true;
-    for (TaskDev& t : wtasks) {
+    for (TaskDev& t : c.tasks) {
       std::vector<SOp> net_ops(hp->ops.begin() + t.op_begin,
                                hp->ops.begin() + t.op_begin + t.op_count);
-      const uint32_t begin = (uint32_t)wsteps.size();
+      const uint32_t begin = (uint32_t)c.wsteps.size();
       if (!reuse) {
         LoweredNet ln = lower_smem(b->plans[t.net], leaf_gate[t.net], val_off, der_off,
                                    table_elems, want_grad != 0, max_elems, private_below);
@@ -767,47 +775,75 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
         t.arena_elems = ln.arena_elems;
         net_ops = std::move(ln.ops);
       }
-      build_warp_steps(net_ops, table_elems, t.arena_elems, wsteps);
-      max_arena = std::max(max_arena, t.arena_elems);
+      build_warp_steps(net_ops, table_elems, t.arena_elems, c.wsteps);
+      c.max_arena = std::max(c.max_arena, t.arena_elems);
       t.op_begin = begin;
-      t.op_count = (uint32_t)wsteps.size() - begin;
-      max_steps = std::max(max_steps, t.op_count);
+      t.op_count = (uint32_t)c.wsteps.size() - begin;
+      c.max_steps = std::max(c.max_steps, t.op_count);
     }
-    if (!fit) continue;
-    const uint32_t shared_arena = hp->max_arena;
-    hp->max_arena = max_arena;
-    const uint32_t stage = std::min<uint32_t>(max_steps, 128);
-    // (complex128 programs that need streamed steps or fewer teams per CTA
-    // measured slower on warps than on a CTA per network: they stay staged
-    // with four teams, or run on CTA teams)
-    const bool wide = dtype == QTC_C128;
-    for (int teams = kWarpTeamsPerCta; teams >= (wide ? kWarpTeamsPerCta : 1) && !ok;
-         teams /= 2)
-      ok = layout(true, stage, teams) || (!wide && layout(true, 0, teams));
-    if (!ok && reuse) ok = try_layout(true, stage);
-    if (ok) {
-      // With a fixed stride per task a team starts copying its first task's
-      // steps without first reading the task record; taken when the padding
-      // costs little.
-      const size_t padded = (size_t)wtasks.size() * max_steps;
-      if (padded <= wsteps.size() + wsteps.size() / 2 || padded * sizeof(WStep) <= (16u << 20)) {
-        std::vector<WStep> fixed(padded);
-        for (size_t i = 0; i < wtasks.size(); ++i) {
-          std::copy(wsteps.begin() + wtasks[i].op_begin,
-                    wsteps.begin() + wtasks[i].op_begin + wtasks[i].op_count,
-                    fixed.begin() + i * max_steps);
-          wtasks[i].op_begin = (uint32_t)(i * max_steps);
+    if (fit) cands.push_back(std::move(c));
+  }
+  // (complex128 programs that need streamed steps or fewer teams per CTA
+  // measured slower on warps than on a CTA per network: they stay staged
+  // with four teams, or run on CTA teams)
+  const bool wide = dtype == QTC_C128;
+  const uint32_t shared_arena = hp->max_arena;
+  const size_t sm_smem = 233472;  // shared memory of one SM
+  int best = -1, best_teams = 0;
+  bool best_stream = false;
+  double best_cost = 0;
+  for (size_t ci = 0; ci < cands.size(); ++ci) {
+    hp->max_arena = cands[ci].max_arena;
+    const uint32_t stage = std::min<uint32_t>(cands[ci].max_steps, 128);
+    for (int teams = kWarpTeamsPerCta; teams >= (wide ? kWarpTeamsPerCta : 1); teams /= 2)
+      for (int stream = 0; stream < (wide ? 1 : 2); ++stream) {
+        if (!layout(true, stream ? 0 : stage, teams)) continue;
+        const size_t per_sm = std::max<size_t>(1, sm_smem / (hp->smem + 12288));
+        const double slots = (double)opts.sm_count * (double)per_sm * teams;
+        const double rounds = std::ceil((double)hp->tasks.size() / slots);
+        const double cost = rounds * cands[ci].max_steps * (stream ? 1.05 : 1.0);
+        if (best < 0 || cost < best_cost) {
+          best = (int)ci;
+          best_teams = teams;
+          best_stream = stream != 0;
+          best_cost = cost;
         }
-        wsteps = std::move(fixed);
-        hp->task_stride = max_steps;
       }
-      hp->tasks = std::move(wtasks);
-      hp->wsteps = std::move(wsteps);
-      hp->coef = coefficient_table(hp->gates, table_elems, dtype);
-      hp->ops.clear();
-    } else {
-      hp->max_arena = shared_arena;
+  }
+  if (best >= 0) {
+    WarpCand& c = cands[best];
+    hp->max_arena = c.max_arena;
+    ok = layout(true, best_stream ? 0 : std::min<uint32_t>(c.max_steps, 128), best_teams);
+  } else if (!cands.empty()) {
+    WarpCand& c = cands.back();  // the reused arena, smaller stages
+    hp->max_arena = c.max_arena;
+    ok = try_layout(true, std::min<uint32_t>(c.max_steps, 128));
+    if (ok) best = (int)cands.size() - 1;
+  }
+  if (ok) {
+    WarpCand& c = cands[best];
+    // With a fixed stride per task a team starts reading its first task's
+    // steps without first reading the task record; taken when the padding
+    // costs little.
+    const size_t padded = c.tasks.size() * c.max_steps;
+    if (padded <= c.wsteps.size() + c.wsteps.size() / 2 ||
+        padded * sizeof(WStep) <= (16u << 20)) {
+      std::vector<WStep> fixed(padded);
+      for (size_t i = 0; i < c.tasks.size(); ++i) {
+        std::copy(c.wsteps.begin() + c.tasks[i].op_begin,
+                  c.wsteps.begin() + c.tasks[i].op_begin + c.tasks[i].op_count,
+                  fixed.begin() + i * c.max_steps);
+        c.tasks[i].op_begin = (uint32_t)(i * c.max_steps);
+      }
+      c.wsteps = std::move(fixed);
+      hp->task_stride = c.max_steps;
     }
+    hp->tasks = std::move(c.tasks);
+    hp->wsteps = std::move(c.wsteps);
+    hp->coef = coefficient_table(hp->gates, table_elems, dtype);
+    hp->ops.clear();
+  } else {
+    hp->max_arena = shared_arena;
   }
   if (!ok) ok = try_layout(false, std::min<uint32_t>(max_ops, 64));
   if (!ok)

@@ -224,10 +224,12 @@ struct ProgramOptions {
   int task_terms_log2 = 16;        // multiply-adds per chunk task of a global step
   int subtree_bytes = 32768;       // values of one shared-memory subtree task
   bool warp_teams = true;          // networks may run one per warp
+  int sm_count = 152;              // SMs of the device the program is laid out for
   bool operator==(const ProgramOptions& o) const {
     return wave_cap_bytes == o.wave_cap_bytes && force_graph == o.force_graph &&
            small_rank == o.small_rank && task_terms_log2 == o.task_terms_log2 &&
-           subtree_bytes == o.subtree_bytes && warp_teams == o.warp_teams;
+           subtree_bytes == o.subtree_bytes && warp_teams == o.warp_teams &&
+           sm_count == o.sm_count;
   }
 };
 
