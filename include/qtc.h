@@ -338,9 +338,11 @@ qtc_status qtc_engine_set_graph_options(qtc_engine* e, int force_graph, int smal
  * task of a global step of the graph executor covers about
  * 2^task_terms_log2 multiply-adds (12..20, default 16); a shared-memory
  * subtree task holds at most subtree_bytes of values (4096..32768, default
- * 32768); warp_teams = 0 keeps the shared-memory executor at one network per
- * CTA (default 1: one per warp where the network's program fits).
- * Invalidates prepared programs.  QTC_ERR_INVALID outside those ranges. */
+ * 32768); warp_teams: 0 keeps the shared-memory executor at one network per
+ * CTA, 1 (default) runs one network per warp where the network's program
+ * fits, 2 does so with the warp steps always read from global memory
+ * (complex64 only).  Invalidates prepared programs.  QTC_ERR_INVALID
+ * outside those ranges. */
 qtc_status qtc_engine_set_task_options(qtc_engine* e, int task_terms_log2, int subtree_bytes,
                                        int warp_teams);
 

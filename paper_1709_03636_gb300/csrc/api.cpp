@@ -237,7 +237,9 @@ extern "C" qtc_status qtc_engine_set_task_options(qtc_engine* e, int task_terms_
       fail(QTC_ERR_INVALID, "subtree of %d bytes (4096..32768)", subtree_bytes);
     e->options.task_terms_log2 = task_terms_log2;
     e->options.subtree_bytes = subtree_bytes;
-    e->options.warp_teams = warp_teams != 0;
+    if (warp_teams < 0 || warp_teams > 2)
+      fail(QTC_ERR_INVALID, "warp_teams %d (0..2)", warp_teams);
+    e->options.warp_teams = warp_teams;
     e->generation += 1;
     e->used = 0;
     e->work = 0;
@@ -708,7 +710,7 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
   auto round16 = [](size_t x) { return (uint32_t)((x + 15) & ~size_t(15)); };
   // warp teams need every op within the pre-expanded tables, and every
   // element of the table copy and arena within a 16-bit lane offset
-  bool warp_ok = opts.warp_teams && max_rank <= kWarpMaxRank &&
+  bool warp_ok = opts.warp_teams != 0 && max_rank <= kWarpMaxRank &&
                  (size_t)table_elems + hp->max_arena <= 0xffffu;
   for (const SOp& op : hp->ops)
     if (op.code == SOP_CONTRACT && (op.rc > kWarpMaxRank || op.ry > kWarpMaxSummed))
@@ -796,7 +798,7 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
     hp->max_arena = cands[ci].max_arena;
     const uint32_t stage = std::min<uint32_t>(cands[ci].max_steps, 128);
     for (int teams = kWarpTeamsPerCta; teams >= (wide ? kWarpTeamsPerCta : 1); teams /= 2)
-      for (int stream = 0; stream < (wide ? 1 : 2); ++stream) {
+      for (int stream = opts.warp_teams == 2 ? 1 : 0; stream < (wide ? 1 : 2); ++stream) {
         if (!layout(true, stream ? 0 : stage, teams)) continue;
         const size_t per_sm = std::max<size_t>(1, sm_smem / (hp->smem + 12288));
         const double slots = (double)opts.sm_count * (double)per_sm * teams;

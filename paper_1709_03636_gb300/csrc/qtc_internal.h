@@ -223,7 +223,8 @@ struct ProgramOptions {
   int small_rank = 0;
   int task_terms_log2 = 16;        // multiply-adds per chunk task of a global step
   int subtree_bytes = 32768;       // values of one shared-memory subtree task
-  bool warp_teams = true;          // networks may run one per warp
+  int warp_teams = 1;              // 0: one network per CTA; 1: per warp where it fits;
+                                   // 2: per warp, steps always streamed
   int sm_count = 152;              // SMs of the device the program is laid out for
   bool operator==(const ProgramOptions& o) const {
     return wave_cap_bytes == o.wave_cap_bytes && force_graph == o.force_graph &&

@@ -21,14 +21,15 @@ import json
 import os
 
 DEFAULTS = {"small_rank": 10, "task_terms_log2": 16, "subtree_bytes": 32768,
-            "warp_teams": True}
+            "warp_teams": 1}
 
 
 def default_candidates(graph: bool = True):
     """Graph programs: small_rank x task size x subtree size around the
-    defaults.  Shared-memory programs: one network per warp or per CTA."""
+    defaults.  Shared-memory programs: one network per warp (layout by cost,
+    or with streamed steps) or one per CTA."""
     if not graph:
-        return [dict(DEFAULTS), dict(DEFAULTS, warp_teams=False)]
+        return [dict(DEFAULTS), dict(DEFAULTS, warp_teams=2), dict(DEFAULTS, warp_teams=0)]
     out = []
     for sr in (9, 10, 11):
         for tt in (15, 16, 17):
@@ -71,7 +72,7 @@ def apply(engine, choice: dict):
     prepared programs)."""
     engine.set_graph_options(False, int(choice["small_rank"]))
     engine.set_task_options(int(choice["task_terms_log2"]), int(choice["subtree_bytes"]),
-                            bool(choice.get("warp_teams", True)))
+                            int(choice.get("warp_teams", 1)))
 
 
 def _device_timer(engine, batch, dtype, want_grad, steps, warmup):

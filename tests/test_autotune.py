@@ -20,7 +20,7 @@ class FakeEngine:
         self.calls.append(("graph", force_graph, small_rank))
         self.sr = small_rank
 
-    def set_task_options(self, task_terms_log2=16, subtree_bytes=32768, warp_teams=True):
+    def set_task_options(self, task_terms_log2=16, subtree_bytes=32768, warp_teams=1):
         self.calls.append(("task", task_terms_log2, subtree_bytes, warp_teams))
         self.opts = (self.sr, task_terms_log2, subtree_bytes)
         self.warp = warp_teams
@@ -79,12 +79,12 @@ def test_signature_separates_dtype_gradient_device_and_structure():
 def test_shared_memory_batches_choose_warp_or_cta_teams():
     eng = FakeEngine()
     res = at.autotune(eng, FakeBatch(graph=False), "c64", True,
-                      timer=lambda: 1.0 if eng.warp else 2.0, device_name="GB300")
-    assert res["graph"] is False and res["warp_teams"] is True and eng.warp is True
+                      timer=lambda: {0: 2.0, 1: 1.5, 2: 1.0}[eng.warp], device_name="GB300")
+    assert res["graph"] is False and res["warp_teams"] == 2 and eng.warp == 2
     eng = FakeEngine()
     res = at.autotune(eng, FakeBatch(graph=False), "c128", True,
                       timer=lambda: 3.0 if eng.warp else 2.0, device_name="GB300")
-    assert res["warp_teams"] is False and eng.warp is False
+    assert res["warp_teams"] == 0 and eng.warp == 0
     assert eng.opts == (at.DEFAULTS["small_rank"], at.DEFAULTS["task_terms_log2"],
                         at.DEFAULTS["subtree_bytes"])
 

@@ -26,7 +26,7 @@ def test_autotune_keeps_values_and_caches(tmp_path):
                      steps=3, warmup=1)
     assert res["cached"] is False
     assert len([t for t in res["trials"] if t["ms"] is not None]) == 3
-    assert engine.task_options == (res["task_terms_log2"], res["subtree_bytes"], True)
+    assert engine.task_options == (res["task_terms_log2"], res["subtree_bytes"], 1)
     for cand in cands:
         q.tuning.apply(engine, cand)
         C1, e1, g1 = q.qaoa_expectation(engine, batch, g, b, "c64", want_grad=True)

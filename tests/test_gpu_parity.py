@@ -245,3 +245,26 @@ def test_cnot_heavy_circuit_sparse_and_dense(engine, diag):
     plan = q.Plan(net, "lg", seed=1)
     assert abs(q.contract(engine, plan, [], "c128") - ref) < 1e-11
     assert abs(q.contract(engine, plan, [], "c64") - ref) < 2e-5
+
+
+@pytest.mark.parametrize("name", ["qaoa_p1_n50_d3", "qaoa_p2_n100_d5"])
+def test_warp_step_modes_agree(name):
+    """The same complex64 batch with warp programs whose steps are staged in
+    shared memory (default layout), streamed from global memory (forced), and
+    on CTA teams: identical math, so results agree to rounding."""
+    w = WORKLOADS[name]
+    edges = w.graph()
+    g, b = w.angles()
+    batch = q.Batch(q.Circuit.qaoa(w.n, edges, w.p), lightcone=True, diag=True, ordering="lg")
+    eng = q.Engine(0, arena_bytes=256 << 20)
+    res = {}
+    for mode in (1, 2, 0):
+        eng.set_task_options(16, 32768, mode)
+        res[mode] = q.qaoa_expectation(eng, batch, g, b, "c64", want_grad=True)
+    info = batch.program_info("c64", True)
+    assert info["warp_teams"] == 1
+    for mode in (2, 0):
+        C, per_edge, grad = res[mode]
+        assert _rel(C, res[1][0]) < 1e-6
+        assert np.max(np.abs(np.array(per_edge) - np.array(res[1][1]))) < 2e-6
+        _grad_close(grad, res[1][2])
