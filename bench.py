@@ -109,6 +109,30 @@ def dist_env():
     return world, rank, local
 
 
+def rank_workload(base, rank):
+    """Rank r contracts the same family's graph with seed (seed + r):
+    independent problems, no data exchanged between ranks (weak scaling)."""
+    from dataclasses import replace
+    return replace(base, graph_seed=base.graph_seed + rank)
+
+
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank timings over all ranks (the job is as
+    slow as its slowest rank); the identity with one rank."""
+    import torch
+    if int(os.environ.get("WORLD_SIZE", "1")) <= 1:
+        return list(values)
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rate(world, networks_per_rank, seconds_per_step):
+    """Whole-job throughput: the networks every rank contracted per step over
+    the slowest rank's step time."""
+    return world * networks_per_rank / seconds_per_step
+
+
 def workload_config(w, networks, want_grad, dtype, noise=None):
     cfg = {
         "workload": w.name,
@@ -311,7 +335,7 @@ def run_ours(args):
     want_grad = True
     # rank r contracts graph seed (seed + r): independent problems
     from dataclasses import replace
-    w = replace(base, graph_seed=base.graph_seed + rank)
+    w = rank_workload(base, rank)
     if args.dense:
         w = replace(w, diag=False)
     edges = w.graph()
@@ -415,11 +439,8 @@ def run_ours(args):
     ms = sum(step_ms) / len(step_ms)
     e2e_s = sum(e2e_times) / len(e2e_times)
     fwd = sum(fwd_ms) / len(fwd_ms)
-    if world > 1:
-        t = torch.tensor([ms, e2e_s, fwd], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e_s, fwd = t.tolist()
-    value = world * n_nets / (ms * 1e-3)
+    ms, e2e_s, fwd = max_over_ranks([ms, e2e_s, fwd], dev)
+    value = job_rate(world, n_nets, ms * 1e-3)
     elem = 16 if dtype == "c128" else 8
     alg_bytes = (stats["bytes_c64"] + stats["grad_bytes_c64"]) * elem / 8
     peak, peak_kind = measured_peaks()
@@ -439,7 +460,7 @@ def run_ours(args):
                      "launches_per_step": engine.last_launches,
                      "peak_kind": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_step": alg_bytes},
-        "e2e": {"value": world * n_nets / e2e_s, "unit": "networks/s",
+        "e2e": {"value": job_rate(world, n_nets, e2e_s), "unit": "networks/s",
                 "h2d_bytes_per_step": 8 * P, "d2h_bytes_per_step": 8 * (2 + P + n_nets)},
         "complex_gflops": {"value": 8.0 * (stats["cmacs"] + (stats["grad_cmacs"] if want_grad
                                                                 else 0.0)) / (ms * 1e-3) / 1e9,
@@ -449,7 +470,7 @@ def run_ours(args):
         "autotuned": tuned,
         "clocks": clocks.summary(),
         "step_ms_min_median_max": [min(step_ms), statistics.median(step_ms), max(step_ms)],
-        "forward_only": {"value": world * n_nets / (fwd * 1e-3), "unit": "networks/s",
+        "forward_only": {"value": job_rate(world, n_nets, fwd * 1e-3), "unit": "networks/s",
                          "ms_per_step": fwd},
         "grad_fwd_ratio": ms / fwd,
         "timed_wall_s": wall,
