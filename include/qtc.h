@@ -341,10 +341,12 @@ qtc_status qtc_engine_set_graph_options(qtc_engine* e, int force_graph, int smal
  * 32768); warp_teams: 0 keeps the shared-memory executor at one network per
  * CTA, 1 (default) runs one network per warp where the network's program
  * fits, 2 does so with the warp steps always read from global memory
- * (complex64 only).  Invalidates prepared programs.  QTC_ERR_INVALID
+ * (complex64 only); graph_hi_occupancy != 0 runs complex64 graph programs
+ * without tensor-core tasks on a kernel build capped for five CTAs per SM
+ * (default 0: four).  Invalidates prepared programs.  QTC_ERR_INVALID
  * outside those ranges. */
 qtc_status qtc_engine_set_task_options(qtc_engine* e, int task_terms_log2, int subtree_bytes,
-                                       int warp_teams);
+                                       int warp_teams, int graph_hi_occupancy);
 
 /* Launches a one-task program whose task waits for a counter nothing ever
  * signals, so that the bounded wait expires after the engine's wait limit and

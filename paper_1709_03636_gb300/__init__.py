@@ -88,7 +88,7 @@ class Engine(_Handle):
         super().__init__(h)
         self.device = device
         self.graph_options = (False, 0)
-        self.task_options = (16, 32768, 1)
+        self.task_options = (16, 32768, 1, False)
 
     def reset(self):
         check(lib.qtc_engine_reset(self.ptr))
@@ -103,14 +103,18 @@ class Engine(_Handle):
         check(lib.qtc_engine_set_graph_options(self.ptr, int(force_graph), int(small_rank)))
         self.graph_options = (bool(force_graph), int(small_rank))
 
-    def set_task_options(self, task_terms_log2=16, subtree_bytes=32768, warp_teams=1):
+    def set_task_options(self, task_terms_log2=16, subtree_bytes=32768, warp_teams=1,
+                         graph_hi_occupancy=False):
         """Task shapes: about 2^task_terms_log2 multiply-adds per graph chunk
-        task, at most subtree_bytes of values per shared-memory subtree, and
-        how small networks run (0: one per CTA; 1: one per warp where it fits;
-        2: one per warp with the steps streamed from global memory)."""
+        task, at most subtree_bytes of values per shared-memory subtree, how
+        small networks run (0: one per CTA; 1: one per warp where it fits;
+        2: one per warp with the steps streamed from global memory), and the
+        graph executor's five-CTAs-per-SM build (complex64)."""
         check(lib.qtc_engine_set_task_options(self.ptr, int(task_terms_log2),
-                                              int(subtree_bytes), int(warp_teams)))
-        self.task_options = (int(task_terms_log2), int(subtree_bytes), int(warp_teams))
+                                              int(subtree_bytes), int(warp_teams),
+                                              int(bool(graph_hi_occupancy))))
+        self.task_options = (int(task_terms_log2), int(subtree_bytes), int(warp_teams),
+                             bool(graph_hi_occupancy))
 
     @property
     def last_launches(self) -> int:

@@ -88,7 +88,7 @@ SIGNATURES = {
     "qtc_engine_set_limits": (c_int, [c_void_p, c_size_t, c_double]),
     "qtc_selftest_wait_timeout": (c_int, [c_void_p, c_void_p]),
     "qtc_engine_set_graph_options": (c_int, [c_void_p, c_int, c_int]),
-    "qtc_engine_set_task_options": (c_int, [c_void_p, c_int, c_int, c_int]),
+    "qtc_engine_set_task_options": (c_int, [c_void_p, c_int, c_int, c_int, c_int]),
     "qtc_batch_launch_info": (c_int, [c_void_p, c_void_p, c_int, c_int, P(c_int32)]),
     "qtc_statevector_qaoa": (c_int, [c_void_p, c_void_p, P(c_double), P(c_double), c_int, c_int,
                                      c_void_p, P(c_double), P(c_double)]),

@@ -590,8 +590,12 @@ __device__ bool run_tc(const GraphProgDev& prog, const GTask& task, unsigned cha
 // memory-bound task kinds alone.  The tensor-core instantiation runs four
 // teams in one 1024-thread CTA per SM and gives each team 128 columns of
 // tensor memory.
-template <typename T, bool kTc>
-__global__ void __launch_bounds__(kGraphBlock*(kTc ? 4 : 1))
+// kHiOcc (complex64, no tensor cores): registers capped for five 256-thread
+// CTAs per SM instead of four (some spilling); helps programs dominated by
+// large memory-bound steps, hurts others (chosen per batch by tuning).
+template <typename T, bool kTc, bool kHiOcc = false>
+__global__ void __launch_bounds__(kGraphBlock*(kTc ? 4 : 1),
+                                  kTc ? 1 : kHiOcc ? 5 : sizeof(T) == 8 ? 4 : 2)
     graph_exec_kernel(const GraphProgDev prog) {
   constexpr int kTeams = kTc ? 4 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -709,17 +713,18 @@ __global__ void __launch_bounds__(kGraphBlock*(kTc ? 4 : 1))
   }
 }
 
-static const void* graph_kernel(int dtype, bool tc) {
+static const void* graph_kernel(int dtype, bool tc, bool hi_occ) {
   if (dtype == 0)
     return tc ? (const void*)graph_exec_kernel<double2, true>
               : (const void*)graph_exec_kernel<double2, false>;
-  return tc ? (const void*)graph_exec_kernel<float2, true>
-            : (const void*)graph_exec_kernel<float2, false>;
+  if (tc) return (const void*)graph_exec_kernel<float2, true>;
+  return hi_occ ? (const void*)graph_exec_kernel<float2, false, true>
+                : (const void*)graph_exec_kernel<float2, false>;
 }
 
-cudaError_t graph_exec_configure(int dtype, bool tc, size_t smem_bytes, size_t max_dynamic,
-                                 int* blocks_per_sm) {
-  const void* fn = graph_kernel(dtype, tc);
+cudaError_t graph_exec_configure(int dtype, bool tc, bool hi_occ, size_t smem_bytes,
+                                 size_t max_dynamic, int* blocks_per_sm) {
+  const void* fn = graph_kernel(dtype, tc, hi_occ);
   if (smem_bytes > max_dynamic) return cudaErrorInvalidValue;
   cudaError_t err =
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dynamic);
@@ -728,8 +733,8 @@ cudaError_t graph_exec_configure(int dtype, bool tc, size_t smem_bytes, size_t m
                                                        kGraphBlock * (tc ? 4 : 1), smem_bytes);
 }
 
-cudaError_t graph_exec_launch(const GraphProgDev& prog, int dtype, int grid, size_t smem_bytes,
-                              cudaStream_t stream) {
+cudaError_t graph_exec_launch(const GraphProgDev& prog, int dtype, bool hi_occ, int grid,
+                              size_t smem_bytes, cudaStream_t stream) {
   const bool tc = prog.tmem_cols > 0;
   if (dtype == 0) {
     if (tc)
@@ -739,6 +744,8 @@ cudaError_t graph_exec_launch(const GraphProgDev& prog, int dtype, int grid, siz
   } else {
     if (tc)
       graph_exec_kernel<float2, true><<<grid, 4 * kGraphBlock, smem_bytes, stream>>>(prog);
+    else if (hi_occ)
+      graph_exec_kernel<float2, false, true><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
     else
       graph_exec_kernel<float2, false><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
   }

@@ -19,9 +19,11 @@ cudaError_t smem_exec_launch(const ProgramDev& prog, int dtype, int mode, int gr
 // Graph executor (networks larger than one CTA's shared memory); one launch
 // per wave.
 // tc: the program has tensor-core GEMM tasks (GraphProgDev.tmem_cols > 0).
-cudaError_t graph_exec_configure(int dtype, bool tc, size_t smem_bytes, size_t max_dynamic,
-                                 int* blocks_per_sm);
-cudaError_t graph_exec_launch(const GraphProgDev& prog, int dtype, int grid, size_t smem_bytes,
-                              cudaStream_t stream);
+// hi_occ (complex64 without tensor cores): the instantiation capped for five
+// CTAs per SM.
+cudaError_t graph_exec_configure(int dtype, bool tc, bool hi_occ, size_t smem_bytes,
+                                 size_t max_dynamic, int* blocks_per_sm);
+cudaError_t graph_exec_launch(const GraphProgDev& prog, int dtype, bool hi_occ, int grid,
+                              size_t smem_bytes, cudaStream_t stream);
 
 }  // namespace qtc

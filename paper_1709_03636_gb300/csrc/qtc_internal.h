@@ -226,11 +226,12 @@ struct ProgramOptions {
   int warp_teams = 1;              // 0: one network per CTA; 1: per warp where it fits;
                                    // 2: per warp, steps always streamed
   int sm_count = 152;              // SMs of the device the program is laid out for
+  bool graph_hi_occupancy = false; // graph executor: the five-CTAs-per-SM instantiation
   bool operator==(const ProgramOptions& o) const {
     return wave_cap_bytes == o.wave_cap_bytes && force_graph == o.force_graph &&
            small_rank == o.small_rank && task_terms_log2 == o.task_terms_log2 &&
            subtree_bytes == o.subtree_bytes && warp_teams == o.warp_teams &&
-           sm_count == o.sm_count;
+           sm_count == o.sm_count && graph_hi_occupancy == o.graph_hi_occupancy;
   }
 };
 

@@ -21,20 +21,23 @@ import json
 import os
 
 DEFAULTS = {"small_rank": 10, "task_terms_log2": 16, "subtree_bytes": 32768,
-            "warp_teams": 1}
+            "warp_teams": 1, "graph_hi_occupancy": False}
 
 
 def default_candidates(graph: bool = True):
     """Graph programs: small_rank x task size x subtree size around the
-    defaults.  Shared-memory programs: one network per warp (layout by cost,
-    or with streamed steps) or one per CTA."""
+    defaults, on the regular and on the five-CTAs-per-SM kernel build.
+    Shared-memory programs: one network per warp (layout by cost, or with
+    streamed steps) or one per CTA."""
     if not graph:
         return [dict(DEFAULTS), dict(DEFAULTS, warp_teams=2), dict(DEFAULTS, warp_teams=0)]
     out = []
-    for sr in (9, 10, 11):
-        for tt in (15, 16, 17):
-            for sb in (16384, 32768):
-                out.append(dict(DEFAULTS, small_rank=sr, task_terms_log2=tt, subtree_bytes=sb))
+    for occ in (False, True):
+        for sr in (9, 10, 11):
+            for tt in (15, 16, 17):
+                for sb in (16384, 32768):
+                    out.append(dict(DEFAULTS, small_rank=sr, task_terms_log2=tt,
+                                    subtree_bytes=sb, graph_hi_occupancy=occ))
     return out
 
 
@@ -72,7 +75,8 @@ def apply(engine, choice: dict):
     prepared programs)."""
     engine.set_graph_options(False, int(choice["small_rank"]))
     engine.set_task_options(int(choice["task_terms_log2"]), int(choice["subtree_bytes"]),
-                            int(choice.get("warp_teams", 1)))
+                            int(choice.get("warp_teams", 1)),
+                            bool(choice.get("graph_hi_occupancy", False)))
 
 
 def _device_timer(engine, batch, dtype, want_grad, steps, warmup):

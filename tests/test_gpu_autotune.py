@@ -20,13 +20,16 @@ def test_autotune_keeps_values_and_caches(tmp_path):
     C0, e0, g0 = q.qaoa_expectation(engine, batch, g, b, "c64", want_grad=True)
     cands = [dict(small_rank=10, task_terms_log2=16, subtree_bytes=32768),
              dict(small_rank=9, task_terms_log2=15, subtree_bytes=16384),
-             dict(small_rank=11, task_terms_log2=17, subtree_bytes=32768)]
+             dict(small_rank=11, task_terms_log2=17, subtree_bytes=32768),
+             dict(small_rank=10, task_terms_log2=16, subtree_bytes=32768,
+                  graph_hi_occupancy=True)]
     path = tmp_path / "tune.json"
     res = q.autotune(engine, batch, "c64", True, cache_path=str(path), candidates=cands,
                      steps=3, warmup=1)
     assert res["cached"] is False
-    assert len([t for t in res["trials"] if t["ms"] is not None]) == 3
-    assert engine.task_options == (res["task_terms_log2"], res["subtree_bytes"], 1)
+    assert len([t for t in res["trials"] if t["ms"] is not None]) == len(cands)
+    assert engine.task_options == (res["task_terms_log2"], res["subtree_bytes"], 1,
+                                   res["graph_hi_occupancy"])
     for cand in cands:
         q.tuning.apply(engine, cand)
         C1, e1, g1 = q.qaoa_expectation(engine, batch, g, b, "c64", want_grad=True)
