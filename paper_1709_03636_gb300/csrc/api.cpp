@@ -704,8 +704,9 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
     b->host_programs.push_back(std::move(hp));
     return *b->host_programs.back();
   }
-  // Networks of rank <= 7 (<= 4 elements per lane) run one per warp;
-  // larger ones use the whole CTA.  Each team stages its op list in chunks.
+  // Networks of rank <= 11 whose ops sum over <= 8 labels may run one per
+  // warp (warp programs); the others use the whole CTA, which stages its op
+  // list in chunks.
   uint32_t max_ops = 1;
   int max_rank = 0;
   for (const TaskDev& t : hp->tasks) max_ops = std::max(max_ops, t.op_count);

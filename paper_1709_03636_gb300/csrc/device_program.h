@@ -147,8 +147,9 @@ static_assert(sizeof(WOp) == 528, "WOp is staged as 33 16-byte words");
 // independent small ops into aligned lane groups of one warp (the host
 // schedules the op graph of the network; hazards are tracked per element):
 // each lane computes at most one output element with at most two summed
-// terms.  A solo step runs one WOp on the whole warp (outputs above 32
-// elements or more than one summed bit).
+// terms, or two of the 4-16 terms of one output whose lanes are then added
+// by shuffles.  A solo step runs one WOp on the whole warp (the other ops:
+// outputs above 32 elements, or more lanes than the warp has).
 enum WLaneKind : uint8_t { WL_IDLE = 0, WL_CONTRACT = 1, WL_RESULT = 2, WL_SEED = 3 };
 enum WLaneFlag : uint8_t {
   WLF_STORE = 1,    // write the lane's output element
