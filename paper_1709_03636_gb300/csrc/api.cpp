@@ -846,6 +846,9 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
     }
     hp->tasks = std::move(c.tasks);
     hp->wsteps = std::move(c.wsteps);
+    for (const TaskDev& t : hp->tasks)
+      validate_warp_steps(hp->wsteps.data() + t.op_begin, t.op_count,
+                          table_elems + t.arena_elems, P);
     hp->coef = coefficient_table(hp->gates, table_elems, dtype);
     hp->ops.clear();
   } else {

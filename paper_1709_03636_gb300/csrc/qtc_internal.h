@@ -164,6 +164,8 @@ struct LoweredNet {
 // independent small ops, solo steps for the rest), appended to `out`.
 void build_warp_steps(const std::vector<SOp>& ops, uint32_t table_elems, uint32_t arena_elems,
                       std::vector<WStep>& out);
+// Host check of a warp program's every access against its team region.
+void validate_warp_steps(const WStep* steps, size_t n, uint32_t team_elems, int n_params);
 
 // Lowers one plan to a shared-memory op program.  table_elems: size of the
 // gate value + derivative region that precedes the arena.  Intermediates and

@@ -255,3 +255,66 @@ void build_warp_steps(const std::vector<SOp>& ops, uint32_t table_elems, uint32_
 }
 
 }  // namespace qtc
+
+namespace qtc {
+
+// Every shared-memory access a warp program can make, checked on the host
+// against the team's region (gate-table copy + arena, `team_elems`
+// elements), and every shuffle and gradient slot against its bounds; throws
+// on the first violation.
+void validate_warp_steps(const WStep* steps, size_t n, uint32_t team_elems, int n_params) {
+  auto need = [&](bool ok, size_t k, int lane, const char* what) {
+    if (!ok) fail(QTC_ERR_INVALID, "internal: warp step %zu lane %d: %s", k, lane, what);
+  };
+  for (size_t k = 0; k < n; ++k) {
+    const WStep& st = steps[k];
+    if (st.solo) {
+      const WOp& w = st.op;
+      const uint32_t nout = 1u << w.rc, ny = 1u << w.ry;
+      need(w.rc <= kWarpMaxRank && w.ry <= kWarpMaxSummed, k, -1, "op shape");
+      if (w.code == SOP_CONTRACT) {
+        uint32_t ma = 0, mb = 0;
+        for (uint32_t c = 0; c < nout; ++c) {
+          ma = std::max<uint32_t>(ma, w.a_lo[c & 31] | w.a_hi[c >> 5]);
+          mb = std::max<uint32_t>(mb, w.b_lo[c & 31] | w.b_hi[c >> 5]);
+        }
+        uint32_t ya = 0, yb = 0;
+        for (uint32_t y = 0; y < ny; ++y) {
+          ya = std::max<uint32_t>(ya, w.ya[y & 15] | w.ya_hi[y >> 4]);
+          yb = std::max<uint32_t>(yb, w.yb[y & 15] | w.yb_hi[y >> 4]);
+        }
+        need((size_t)w.in1 + (ma | ya) < team_elems, k, -1, "first operand");
+        need((size_t)w.in2 + (mb | yb) < team_elems, k, -1, "second operand");
+        need((size_t)w.out + nout <= team_elems, k, -1, "output");
+        if (w.flags & WOPF_LEAFGRAD) {
+          need((size_t)w.der + nout <= team_elems, k, -1, "leaf derivative");
+          need(w.slot < n_params, k, -1, "gradient slot");
+        }
+      } else if (w.code == SOP_LEAFGRAD) {
+        need((size_t)w.in1 + nout <= team_elems && (size_t)w.in2 + nout <= team_elems, k, -1,
+             "leaf-gradient operands");
+        need(w.slot < n_params, k, -1, "gradient slot");
+      } else if (w.code == SOP_RESULT) {
+        need(w.in1 < team_elems, k, -1, "result operand");
+      } else if (w.code == SOP_SEED) {
+        need(w.out < team_elems, k, -1, "seed");
+      }
+      continue;
+    }
+    need((st.rounds & 0x7Fu) <= 5 && st.pad[0] <= 3, k, -1, "step rounds");
+    for (int l = 0; l < 32; ++l) {
+      const WLane& L = st.lane[l];
+      const uint32_t gw = L.gw & 7u, pd = (L.gw >> 3) & 7u, pr = L.gw >> 6;
+      need(gw <= 5 && pd + pr <= 5 && pr <= st.pad[0], k, l, "lane group");
+      need(L.a_off < team_elems && L.b_off < team_elems, k, l, "operands");
+      if (L.flags & WLF_Y1)
+        need((size_t)L.a_off + L.ya1 < team_elems && (size_t)L.b_off + L.yb1 < team_elems, k,
+             l, "second term");
+      if (L.flags & WLF_STORE) need(L.c_off < team_elems, k, l, "output");
+      if (L.flags & WLF_LG_MUL) need(L.der_off < team_elems, k, l, "leaf derivative");
+      if (L.flags & (WLF_LG_MUL | WLF_LG_ADD)) need(L.slot < n_params, k, l, "gradient slot");
+    }
+  }
+}
+
+}  // namespace qtc
