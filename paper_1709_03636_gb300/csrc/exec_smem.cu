@@ -35,26 +35,45 @@ __device__ __forceinline__ void warp_contract(const WOp& op, const uint4 head, T
   const uint32_t nout = 1u << rc, ny = 1u << ry;
   const uint32_t alo = op.a_lo[lane], blo = op.b_lo[lane];
   const uint32_t ay1 = op.ya[1], by1 = op.yb[1];
+  const uint32_t nj = (nout + 31) >> 5;
   T dot = czero<T>();
-  for (uint32_t j = 0; 32 * j < nout; ++j) {
-    const uint32_t c = 32 * j + lane;
-    const uint32_t oa = alo | op.a_hi[j];
-    const uint32_t ob = blo | op.b_hi[j];
-    T acc;
-    if (ry == 0) {  // a product (batch and free labels only)
-      acc = cfma(a[oa], b[ob], czero<T>());
-    } else if (ry == 1) {
-      const T a0 = a[oa], b0 = b[ob], a1 = a[oa | ay1], b1 = b[ob | by1];
-      acc = cfma(a1, b1, cfma(a0, b0, czero<T>()));
-    } else {
-      acc = czero<T>();
+  if (ry <= 1) {
+    // four output chunks at a time: their operand loads issue together
+    for (uint32_t j0 = 0; j0 < nj; j0 += 4) {
+      T a0[4], b0[4], a1[4], b1[4];
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u) {
+        const uint32_t j = j0 + u < nj ? j0 + u : j0;
+        const uint32_t oa = alo | op.a_hi[j], ob = blo | op.b_hi[j];
+        a0[u] = a[oa];
+        b0[u] = b[ob];
+        a1[u] = a[oa | ay1];
+        b1[u] = b[ob | by1];
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u) {
+        const uint32_t c = 32 * (j0 + u) + lane;
+        T acc = cfma(a0[u], b0[u], czero<T>());
+        if (ry == 1) acc = cfma(a1[u], b1[u], acc);
+        if (j0 + u < nj && c < nout) {
+          out[c] = acc;
+          if (leafgrad) dot = cfma(acc, table[(head.w & 0xffffu) + c], dot);
+        }
+      }
+    }
+  } else {
+    for (uint32_t j = 0; j < nj; ++j) {
+      const uint32_t c = 32 * j + lane;
+      const uint32_t oa = alo | op.a_hi[j];
+      const uint32_t ob = blo | op.b_hi[j];
+      T acc = czero<T>();
       for (uint32_t y = 0; y < ny; ++y)
         acc = cfma(a[oa | op.ya[y & 15] | op.ya_hi[y >> 4]],
                    b[ob | op.yb[y & 15] | op.yb_hi[y >> 4]], acc);
-    }
-    if (c < nout) {
-      out[c] = acc;
-      if (leafgrad) dot = cfma(acc, table[(head.w & 0xffffu) + c], dot);
+      if (c < nout) {
+        out[c] = acc;
+        if (leafgrad) dot = cfma(acc, table[(head.w & 0xffffu) + c], dot);
+      }
     }
   }
   if (leafgrad) {
