@@ -19,6 +19,9 @@
 namespace qtc {
 
 constexpr int kMaxTeams = 8;
+// Threads of one CTA of this kernel: 128 (a CTA team, or up to four warp
+// teams); the launch bound lets the compiler plan registers for it.
+constexpr int kExecBlockThreads = 128;
 
 // One CONTRACT op of a warp team from its pre-expanded offset tables: lane
 // handles outputs c = 32 j + lane (j < 2^(rc - 5), up to 64 for rank 11).
@@ -62,14 +65,30 @@ __device__ __forceinline__ void warp_contract(const WOp& op, const uint4 head, T
       }
     }
   } else {
+    // 4..256 summed terms (ny a power of two >= 4): four accumulators, the
+    // loads of four terms issued together
     for (uint32_t j = 0; j < nj; ++j) {
       const uint32_t c = 32 * j + lane;
       const uint32_t oa = alo | op.a_hi[j];
       const uint32_t ob = blo | op.b_hi[j];
-      T acc = czero<T>();
-      for (uint32_t y = 0; y < ny; ++y)
-        acc = cfma(a[oa | op.ya[y & 15] | op.ya_hi[y >> 4]],
-                   b[ob | op.yb[y & 15] | op.yb_hi[y >> 4]], acc);
+      T acc4[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
+      for (uint32_t y = 0; y < ny; y += 4) {
+        T av[4], bv[4];
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) {
+          const uint32_t yy = y + u;
+          av[u] = a[oa | op.ya[yy & 15] | op.ya_hi[yy >> 4]];
+          bv[u] = b[ob | op.yb[yy & 15] | op.yb_hi[yy >> 4]];
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) acc4[u] = cfma(av[u], bv[u], acc4[u]);
+      }
+      T acc = acc4[0];
+#pragma unroll
+      for (uint32_t u = 1; u < 4; ++u) {
+        acc.x += acc4[u].x;
+        acc.y += acc4[u].y;
+      }
       if (c < nout) {
         out[c] = acc;
         if (leafgrad) dot = cfma(acc, table[(head.w & 0xffffu) + c], dot);
@@ -229,7 +248,7 @@ constexpr uint32_t kStreamAhead = 16;
 // queue per lane (header word and the lane's descriptor) instead of being
 // staged; a solo step's op is read where it lies.
 template <typename T, bool kWarp, bool kStream = false>
-__global__ void __launch_bounds__(256) smem_exec_kernel(const ProgramDev prog) {
+__global__ void __launch_bounds__(kExecBlockThreads) smem_exec_kernel(const ProgramDev prog) {
   using R = decltype(T::x);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // one network's partial derivatives per team, in the element precision
