@@ -804,7 +804,8 @@ const HostProgram& qtc::host_program(qtc_batch* b, int dtype, int want_grad,
     for (int teams = kWarpTeamsPerCta; teams >= (wide ? kWarpTeamsPerCta : 1); teams /= 2)
       for (int stream = opts.warp_teams == 2 ? 1 : 0; stream < (wide ? 1 : 2); ++stream) {
         if (!layout(true, stream ? 0 : stage, teams)) continue;
-        const size_t per_sm = std::max<size_t>(1, sm_smem / (hp->smem + 12288));
+        const size_t per_sm = std::max<size_t>(
+            1, std::min<size_t>(kExecCtasPerSmByRegs, sm_smem / (hp->smem + 12288)));
         const double slots = (double)opts.sm_count * (double)per_sm * teams;
         const double rounds = std::ceil((double)hp->tasks.size() / slots);
         const double cost = rounds * cands[ci].max_steps * (stream ? 1.05 : 1.0);

@@ -7,6 +7,12 @@
 
 namespace qtc {
 
+// Register cap of the shared-memory executor (CTAs of 128 threads: a CTA
+// team, or up to four warp teams).  96 keeps the float warp kernels free of
+// spills; it also caps residency at 65536 / (96 * 128) = 5 CTAs per SM.
+constexpr int kExecMaxRegs = 96;
+constexpr int kExecCtasPerSmByRegs = 65536 / (kExecMaxRegs * 128);
+
 // dtype: 0 = complex double, otherwise complex float.
 // mode: 0 = the whole CTA runs one network at a time; 1 = each warp of a CTA
 // runs its own network from steps staged in shared memory; 2 = the same with

@@ -19,9 +19,6 @@
 namespace qtc {
 
 constexpr int kMaxTeams = 8;
-// Threads of one CTA of this kernel: 128 (a CTA team, or up to four warp
-// teams); the launch bound lets the compiler plan registers for it.
-constexpr int kExecBlockThreads = 128;
 
 // One CONTRACT op of a warp team from its pre-expanded offset tables: lane
 // handles outputs c = 32 j + lane (j < 2^(rc - 5), up to 64 for rank 11).
@@ -248,7 +245,7 @@ constexpr uint32_t kStreamAhead = 16;
 // queue per lane (header word and the lane's descriptor) instead of being
 // staged; a solo step's op is read where it lies.
 template <typename T, bool kWarp, bool kStream = false>
-__global__ void __launch_bounds__(kExecBlockThreads) smem_exec_kernel(const ProgramDev prog) {
+__global__ void __maxnreg__(kExecMaxRegs) smem_exec_kernel(const ProgramDev prog) {
   using R = decltype(T::x);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // one network's partial derivatives per team, in the element precision
