@@ -23,8 +23,11 @@
  *    qtc_engine_destroy) through which such calls pass parameters and
  *    results without copies.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
- *    stream).  Calls with host outputs synchronise that stream before they
- *    return; calls with device outputs are asynchronous on it.
+ *    stream).  Calls with host outputs return once their results are in
+ *    host memory (for qtc_qaoa_expectation on the shared-memory executor,
+ *    before the launch has fully retired: later work on any stream that
+ *    needs the launch gone should wait on the stream); calls with device
+ *    outputs are asynchronous on it.
  *  - Handles are not thread-safe; use one engine per host thread.
  */
 #ifndef QTC_H
@@ -290,9 +293,12 @@ qtc_status qtc_batch_prepare(qtc_engine* e, qtc_batch* b, int dtype,
  * gammas, betas: host, p values each.  C_out: host, 1 double.
  * per_edge_out: host, nullable, m doubles <Z_u Z_v>_i.
  * grad_out: host, nullable (needs want_grad), 2p doubles
- * d<C>/d(gamma_1..p, beta_1..p).  One launch per wave and one stream
- * synchronisation: the kernel reads the parameters from and writes the
- * results to the engine's mapped host buffer.  Synchronises `stream`.  <C> and the
+ * d<C>/d(gamma_1..p, beta_1..p).  One launch per wave: the kernel reads the
+ * parameters from and writes the results to the engine's mapped host buffer.
+ * With the shared-memory executor the kernel then stores a per-call sequence
+ * number there after a system-scope fence, and the call returns when it reads
+ * that number (or when `stream` is idle); the graph executor synchronises
+ * `stream`.  A launch or kernel error is returned either way.  <C> and the
  * gradient are FP64 sums over the edge networks; with the shared-memory
  * executor the terms are added in no fixed order (atomics), so repeated
  * calls can differ in the last bits. */

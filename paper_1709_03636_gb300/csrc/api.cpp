@@ -91,14 +91,21 @@ struct qtc_engine {
 
   // Host-pointer calls pass parameters and results through a small pinned,
   // device-mapped host buffer: the kernel reads and writes it in place, so a
-  // call is one launch and one stream synchronisation with no copies.
+  // call is one launch with no copies.  The shared-memory executor also
+  // publishes a sequence number there once its results are visible, and the
+  // call returns on that (its launch may still be retiring): a reallocation
+  // or the engine's end waits for the device first.
   double* staging_host = nullptr;
   double* staging_dev = nullptr;
   size_t staging_elems = 0;
+  uint64_t seq = 0;
 
   double* staging(size_t n) {
     if (n > staging_elems) {
-      if (staging_host) cuda_check(cudaFreeHost(staging_host), "free staging buffer");
+      if (staging_host) {
+        cuda_check(cudaDeviceSynchronize(), "synchronise before freeing the staging buffer");
+        cuda_check(cudaFreeHost(staging_host), "free staging buffer");
+      }
       staging_host = nullptr;
       staging_elems = 0;
       void* h = nullptr;
@@ -114,7 +121,14 @@ struct qtc_engine {
   }
 
   ~qtc_engine() {
-    if (staging_host) cudaFreeHost(staging_host);
+    if (staging_host) {
+      int cur = -1;
+      cudaGetDevice(&cur);
+      cudaSetDevice(device);
+      cudaDeviceSynchronize();
+      cudaFreeHost(staging_host);
+      if (cur >= 0) cudaSetDevice(cur);
+    }
   }
 };
 
@@ -1043,7 +1057,8 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
 }
 
 static void launch(qtc_engine* e, const Prepared& pr, const double* params_dev, double* out_dev,
-                   cudaStream_t stream) {
+                   cudaStream_t stream, unsigned long long* done = nullptr,
+                   uint64_t seq = 0) {
   if (pr.graph) {
     for (const GraphProgDev& w : pr.waves) {
       GraphProgDev d = w;
@@ -1060,6 +1075,8 @@ static void launch(qtc_engine* e, const Prepared& pr, const double* params_dev, 
   ProgramDev d = pr.prog;
   d.params = params_dev;
   d.out = out_dev;
+  d.done = done;
+  d.seq = seq;
   cuda_check(smem_exec_launch(d, pr.dtype == QTC_C128 ? 0 : 1,
                               pr.warp_teams ? (pr.stream ? 2 : 1) : 0, pr.grid, pr.block,
                               pr.smem, stream),
@@ -1149,6 +1166,20 @@ extern "C" qtc_status qtc_qaoa_expectation_device(qtc_engine* e, qtc_batch* b,
   });
 }
 
+// Returns once the kernel has published `seq` at `flag` (an acquire load
+// pairs with its system-scope release), or once the stream is idle (results
+// visible all the same); a launch or kernel error ends the wait with that error.
+static void wait_published(const uint64_t* flag, uint64_t seq, cudaStream_t s) {
+  for (uint32_t i = 1;; ++i) {
+    if (__atomic_load_n(flag, __ATOMIC_ACQUIRE) == seq) return;
+    if ((i & 1023) == 0) {
+      const cudaError_t q = cudaStreamQuery(s);
+      if (q == cudaSuccess) return;
+      if (q != cudaErrorNotReady) cuda_check(q, "executor");
+    }
+  }
+}
+
 extern "C" qtc_status qtc_qaoa_expectation(qtc_engine* e, qtc_batch* b, const double* gammas,
                                            const double* betas, int dtype, int want_grad,
                                            void* stream, double* C_out, double* per_edge_out,
@@ -1163,15 +1194,26 @@ extern "C" qtc_status qtc_qaoa_expectation(qtc_engine* e, qtc_batch* b, const do
     const Prepared& pr = prepare(e, b, dtype, want_grad, s);
     const int P = 2 * p;
     const int N = (int)b->plans.size();
-    // parameters and results in the engine's mapped staging buffer
-    double* params = e->staging((size_t)P + 2 + P + N);
+    // parameters, results and the completion word in the engine's mapped
+    // staging buffer
+    double* params = e->staging((size_t)P + 3 + P + N);
     double* host_out = params + P;
     for (int k = 0; k < p; ++k) {
       params[k] = gammas[k];
       params[p + k] = betas[k];
     }
-    launch(e, pr, e->staging_dev, e->staging_dev + P, s);
-    cuda_check(cudaStreamSynchronize(s), "synchronise stream");
+    if (pr.graph) {
+      launch(e, pr, e->staging_dev, e->staging_dev + P, s);
+      cuda_check(cudaStreamSynchronize(s), "synchronise stream");
+    } else {
+      const size_t at = (size_t)P + 2 + P + N;
+      auto* flag = reinterpret_cast<uint64_t*>(params + at);
+      const uint64_t seq = ++e->seq;
+      __atomic_store_n(flag, (uint64_t)0, __ATOMIC_RELAXED);
+      launch(e, pr, e->staging_dev, e->staging_dev + P, s,
+             reinterpret_cast<unsigned long long*>(e->staging_dev + at), seq);
+      wait_published(flag, seq, s);
+    }
     if (host_out[1 + P + N] != 0.0)
       fail(QTC_ERR_TIMEOUT, "a device-side dependency wait expired (status %g)",
            host_out[1 + P + N]);

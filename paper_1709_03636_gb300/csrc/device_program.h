@@ -227,6 +227,8 @@ struct ProgramDev {
   unsigned int* counters;      // [0] task queue, [1] finished blocks, [2] error
   int want_grad;
   int qaoa_reduce;             // 1: reduce to the Max-Cut objective
+  unsigned long long* done;    // optional (host-mapped): set to seq once out is
+  unsigned long long seq;      // visible to the host (system-scope release)
 };
 
 // ---- graph executor: shared-memory subtrees and global-memory steps ---------

@@ -511,6 +511,17 @@ __global__ void __maxnreg__(kExecMaxRegs) smem_exec_kernel(const ProgramDev prog
     prog.counters[0] = 0;
     prog.counters[1] = 0;
   }
+  // Host-polled completion: every lane's writes are fenced at system scope
+  // (the other teams' per-network entries are covered by cumulativity: the
+  // counter's acquire observed them), then one release store of the sequence
+  // number tells the host the output is complete.
+  if (prog.done) {
+    __threadfence_system();
+    team.sync();
+    if (team.tid == 0)
+      asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(prog.done), "l"(prog.seq)
+                   : "memory");
+  }
 }
 
 template <typename T, bool kWarp, bool kStream>
