@@ -196,20 +196,38 @@ __device__ __forceinline__ void build_warp_gate_table(const ProgramDev& prog, T*
   }
   const Rec* rec = static_cast<const Rec*>(prog.coef);
   const uint32_t ne = prog.table_elems;
+  // One memory round trip before the sines: the first 128 records, the
+  // lane's gate entry and the parameters (lane k holds params[k] and
+  // params[k + 32], shuffled to the gates that use them) load together.
+  Rec r[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t j = 32 * k + lane;
+    r[k] = j < ne ? rec[j] : Rec{};
+  }
+  const int P = prog.n_params;
+  const double p_lo = (int)lane < P ? prog.params[lane] : 0.0;
+  const double p_hi = (int)lane + 32 < P ? prog.params[lane + 32] : 0.0;
+  GateSpec spec{};
+  spec.slot = -1;
+  if ((int)lane < prog.n_gates)
+    spec = ((int)lane < kInlineGates ? prog.gates_inline[lane] : prog.gates[lane]).spec;
+  const int slot = spec.slot < 0 ? 0 : spec.slot;
+  const double v_lo = __shfl_sync(0xffffffffu, p_lo, slot & 31);
+  const double v_hi = __shfl_sync(0xffffffffu, p_hi, slot & 31);
   R c = R(1), s = R(0);
   if ((int)lane < prog.n_gates) {
-    const GateEntryDev g =
-        (int)lane < kInlineGates ? prog.gates_inline[lane] : prog.gates[lane];
     const double theta =
-        g.spec.constant + (g.spec.slot >= 0 ? g.spec.coeff * prog.params[g.spec.slot] : 0.0);
+        spec.constant + (spec.slot >= 0 ? spec.coeff * (slot < 32 ? v_lo : v_hi) : 0.0);
     sincos_r((R)(0.5 * theta), &s, &c);
   }
   for (uint32_t j0 = 0; j0 < ne; j0 += 128) {
-    Rec r[4];
+    if (j0 > 0) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint32_t j = j0 + 32 * k + lane;
-      r[k] = j < ne ? rec[j] : Rec{};
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t j = j0 + 32 * k + lane;
+        r[k] = j < ne ? rec[j] : Rec{};
+      }
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {

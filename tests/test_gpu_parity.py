@@ -310,3 +310,39 @@ def test_host_call_returns_published_results(engine, name):
     other.synchronize()
     C_last, _, _ = q.qaoa_expectation(engine, batch, g, b, "c64", want_grad=True)
     assert abs(C_last - out[0].item()) <= 1e-12 * abs(out[0].item())
+
+
+def test_gate_table_parameters_above_slot_32(engine):
+    """40 parameters, gates on slots 2 and 33-39 only (fewer than 32 gates):
+    the warp gate table takes each gate's angle from the parameter held by
+    lane slot - 32.  Value against a full state-vector reference, gradient
+    against the complex128 run and against central differences."""
+    from test_host_plans import GENERIC, _full_unitary_reference
+    n, P = 4, 40
+    rng = np.random.default_rng(5)
+    params = list(rng.uniform(-2.0, 2.0, P))
+    circ = q.Circuit(n, P)
+    gates = []
+    slots = [33, 2, 39, 35, 36, 37, 34, 38]
+    for i, (gname, qs) in enumerate(GENERIC):
+        if gname in ("rx", "rz", "zz"):
+            k = slots[i % len(slots)]
+            circ.add_gate(gname, qs, k, 0.8, 0.1)
+            gates.append((gname, qs, 0.8 * params[k] + 0.1))
+        else:
+            circ.add_gate(gname, qs)
+            gates.append((gname, qs, 0.0))
+    _, ref = _full_unitary_reference(n, gates, "ZIIZ")
+    plan = q.Plan(q.Network(circ, "pauli", pauli="ZIIZ", lightcone=True, diag=True), "lg")
+    v64, g64 = q.contract(engine, plan, params, "c64", want_grad=True)
+    v128, g128 = q.contract(engine, plan, params, "c128", want_grad=True)
+    assert abs(v128 - ref) < 1e-12
+    assert abs(v64 - ref) < 2e-6
+    _grad_close([z.real for z in g64], [z.real for z in g128], rel=1e-4)
+    h = 1e-5
+    for k in (2, 33, 39, 0):
+        pp, pm = list(params), list(params)
+        pp[k] += h
+        pm[k] -= h
+        fd = (q.contract(engine, plan, pp, "c128") - q.contract(engine, plan, pm, "c128")) / (2 * h)
+        assert abs(g128[k] - fd) < 1e-7, (k, g128[k], fd)
