@@ -1058,7 +1058,7 @@ static Prepared& prepare(qtc_engine* e, qtc_batch* b, int dtype, int want_grad,
 
 static void launch(qtc_engine* e, const Prepared& pr, const double* params_dev, double* out_dev,
                    cudaStream_t stream, unsigned long long* done = nullptr,
-                   uint64_t seq = 0) {
+                   uint64_t seq = 0, const double* host_params = nullptr) {
   if (pr.graph) {
     for (const GraphProgDev& w : pr.waves) {
       GraphProgDev d = w;
@@ -1077,6 +1077,11 @@ static void launch(qtc_engine* e, const Prepared& pr, const double* params_dev, 
   d.out = out_dev;
   d.done = done;
   d.seq = seq;
+  d.n_inline_params = 0;
+  if (host_params && d.n_params > 0 && d.n_params <= kInlineParams) {
+    d.n_inline_params = d.n_params;
+    for (int k = 0; k < d.n_params; ++k) d.params_inline[k] = host_params[k];
+  }
   cuda_check(smem_exec_launch(d, pr.dtype == QTC_C128 ? 0 : 1,
                               pr.warp_teams ? (pr.stream ? 2 : 1) : 0, pr.grid, pr.block,
                               pr.smem, stream),
@@ -1211,7 +1216,7 @@ extern "C" qtc_status qtc_qaoa_expectation(qtc_engine* e, qtc_batch* b, const do
       const uint64_t seq = ++e->seq;
       __atomic_store_n(flag, (uint64_t)0, __ATOMIC_RELAXED);
       launch(e, pr, e->staging_dev, e->staging_dev + P, s,
-             reinterpret_cast<unsigned long long*>(e->staging_dev + at), seq);
+             reinterpret_cast<unsigned long long*>(e->staging_dev + at), seq, params);
       wait_published(flag, seq, s);
     }
     if (host_out[1 + P + N] != 0.0)

@@ -199,6 +199,9 @@ struct TaskDev {
 // read from `gates`): building the gate table then waits only for the
 // parameter values themselves.
 constexpr int kInlineGates = 16;
+// Parameter values a host-pointer call passes in the kernel parameters (the
+// warp gate table then reads no parameter from host memory).
+constexpr int kInlineParams = 8;
 
 struct ProgramDev {
   const GateEntryDev* gates;
@@ -229,6 +232,8 @@ struct ProgramDev {
   int qaoa_reduce;             // 1: reduce to the Max-Cut objective
   unsigned long long* done;    // optional (host-mapped): set to seq once out is
   unsigned long long seq;      // visible to the host (system-scope release)
+  int n_inline_params;         // > 0: params[0 .. n) also in params_inline
+  double params_inline[kInlineParams];
 };
 
 // ---- graph executor: shared-memory subtrees and global-memory steps ---------

@@ -206,8 +206,16 @@ __device__ __forceinline__ void build_warp_gate_table(const ProgramDev& prog, T*
     r[k] = j < ne ? rec[j] : Rec{};
   }
   const int P = prog.n_params;
-  const double p_lo = (int)lane < P ? prog.params[lane] : 0.0;
-  const double p_hi = (int)lane + 32 < P ? prog.params[lane + 32] : 0.0;
+  double p_lo = 0.0, p_hi = 0.0;
+  if (prog.n_inline_params > 0) {
+    // passed by value (host-pointer calls): lane k selects entry k
+#pragma unroll
+    for (int k = 0; k < kInlineParams; ++k)
+      if ((int)lane == k && k < prog.n_inline_params) p_lo = prog.params_inline[k];
+  } else {
+    p_lo = (int)lane < P ? prog.params[lane] : 0.0;
+    p_hi = (int)lane + 32 < P ? prog.params[lane + 32] : 0.0;
+  }
   GateSpec spec{};
   spec.slot = -1;
   if ((int)lane < prog.n_gates)
