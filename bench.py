@@ -50,7 +50,7 @@ KERNEL_SOURCES = {
 NCU_TRAFFIC = {
     # (workload, kernel, dtype, want_grad): (bytes per launch, source hash, profile summary)
     ("qaoa_p1_n50_d3", "smem_exec_kernel", "c64", True):
-        (640256, "869d8755a32bb4db", "profiles/smem_exec_kernel_qaoa_p1_n50_d3.md"),
+        (640640, "9c63c5f0b746d4c1", "profiles/smem_exec_kernel_qaoa_p1_n50_d3.md"),
 }
 
 
