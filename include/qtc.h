@@ -176,6 +176,9 @@ const char* qtc_last_error(void);
  * until qtc_engine_destroy. */
 qtc_status qtc_engine_create(int device, void* arena, size_t arena_bytes,
                              qtc_engine** out);
+/* Frees the engine's host objects and its mapped host buffer, after waiting
+ * for the engine's device to finish (a host-pointer call may return before
+ * its launch has retired).  The arena stays the caller's. */
 void qtc_engine_destroy(qtc_engine* e);
 /* Forget every prepared program, making the whole arena free again. */
 qtc_status qtc_engine_reset(qtc_engine* e);
