@@ -461,7 +461,10 @@ def run_ours(args):
                      "peak_kind": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_step": alg_bytes},
         "e2e": {"value": job_rate(world, n_nets, e2e_s), "unit": "networks/s",
-                "h2d_bytes_per_step": 8 * P, "d2h_bytes_per_step": 8 * (2 + P + n_nets)},
+                "h2d_bytes_per_step": 8 * P,
+                # <C>, gradient, per-edge values, status; the shared-memory
+                # executor also writes its 8-byte completion word
+                "d2h_bytes_per_step": 8 * (2 + P + n_nets + (0 if prog["graph"] else 1))},
         "complex_gflops": {"value": 8.0 * (stats["cmacs"] + (stats["grad_cmacs"] if want_grad
                                                                 else 0.0)) / (ms * 1e-3) / 1e9,
                            "unit": "GFLOP/s", "count": "algorithmic, 8 real flops per complex "
