@@ -305,3 +305,30 @@ def test_pins_catch_unconjugated_bra(monkeypatch):
     edges = TRI7
     val = tn.identity_value(7, edges, [0.7], [0.4], edge=edges[0])
     assert abs(val - 1.0) > 1e-3
+
+
+@pytest.mark.parametrize("n,p", [(8, 2), (10, 3)])
+def test_ring_of_disagrees_optimum(n, p):
+    """Ring of disagrees (the 2-regular cycle): once the ring is longer than
+    an edge's light cone (n > 2p + 1), the best cut fraction level-p QAOA
+    reaches is (2p + 1)/(2p + 2) (Farhi, Goldstone and Gutmann 2014; proved
+    through the fermionic mapping by Wang, Hadfield, Jiang and Rieffel 2018).
+    Every edge network of the ring is the same up to relabelling, so the
+    oracle's value and forward-mode gradient of one edge, maximised over the
+    angles from several starts, must reach the bound and never pass it."""
+    from scipy.optimize import minimize
+    edges = [(i, (i + 1) % n) for i in range(n)]
+
+    def neg(x):
+        s, ds = tn.edge_value_grad(n, edges, list(x[:p]), list(x[p:]), edges[0])
+        return -(1.0 - s.real) / 2.0, 0.5 * np.asarray(ds).real
+
+    bound = (2 * p + 1) / (2 * p + 2)
+    rng = np.random.default_rng(0)
+    best = 0.0
+    for _ in range(8):
+        r = minimize(neg, rng.uniform(-1.5, 1.5, 2 * p), jac=True, method="BFGS",
+                     options={"gtol": 1e-10})
+        assert -r.fun <= bound + 1e-12
+        best = max(best, -r.fun)
+    assert abs(best - bound) < 1e-9
