@@ -461,3 +461,37 @@ def test_leaf_values_rejects_bad_leaf():
     net = q.Network(q.Circuit.qaoa(4, [(0, 1), (1, 2)], 1), edge=(0, 1))
     with pytest.raises(q.QtcError):
         net.leaf_values(10 ** 6, [0.1, 0.2])
+
+
+DEGENERATE = {
+    "ring8": (8, [(i, (i + 1) % 8) for i in range(8)]),
+    "star8": (8, [(0, k) for k in range(1, 8)]),
+    "path7": (7, [(i, i + 1) for i in range(6)]),
+    "isolated6": (6, [(0, 1), (2, 3)]),
+    "single2": (2, [(0, 1)]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(DEGENERATE))
+@pytest.mark.parametrize("p", [1, 2])
+def test_degenerate_graph_shapes(name, p):
+    """Graphs away from the random-regular workloads: a ring (every light cone
+    a path), a star (one vertex of degree 7), a path (degree-1 ends), isolated
+    vertices and a single edge.  Every edge network and its plan match the
+    state vector, with and without the light cone, dense or diagonal; the
+    batch lowers to warp programs that pass the host validator."""
+    n, edges = DEGENERATE[name]
+    gammas = [0.3 + 0.4 * k for k in range(p)]
+    betas = [0.9 - 0.3 * k for k in range(p)]
+    ref = sv.edge_zz(n, edges, gammas, betas)
+    circ = q.Circuit.qaoa(n, edges, p)
+    for lightcone in (True, False):
+        for diag in (True, False):
+            for i, e in enumerate(edges):
+                net = q.Network(circ, "zz", edge=e, lightcone=lightcone, diag=diag)
+                val = run_plan(net, q.Plan(net, "lg", seed=3), gammas + betas)
+                assert abs(val.real - ref[i]) < 1e-12 and abs(val.imag) < 1e-12
+    for diag in (True, False):
+        info = q.Batch(circ, ordering="lg", diag=diag).program_info("c64", True)
+        assert info["graph"] == 0 and info["warp_teams"] == 1
+        assert info["n_tasks"] == len(edges)
