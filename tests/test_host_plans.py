@@ -479,7 +479,9 @@ def test_degenerate_graph_shapes(name, p):
     a path), a star (one vertex of degree 7), a path (degree-1 ends), isolated
     vertices and a single edge.  Every edge network and its plan match the
     state vector, with and without the light cone, dense or diagonal; the
-    batch lowers to warp programs that pass the host validator."""
+    batch lowers to warp programs that pass the host validator, and, forced
+    into the graph form (small subtree ranks push steps to global memory), to
+    waves that pass the wave validator."""
     n, edges = DEGENERATE[name]
     gammas = [0.3 + 0.4 * k for k in range(p)]
     betas = [0.9 - 0.3 * k for k in range(p)]
@@ -492,6 +494,12 @@ def test_degenerate_graph_shapes(name, p):
                 val = run_plan(net, q.Plan(net, "lg", seed=3), gammas + betas)
                 assert abs(val.real - ref[i]) < 1e-12 and abs(val.imag) < 1e-12
     for diag in (True, False):
-        info = q.Batch(circ, ordering="lg", diag=diag).program_info("c64", True)
+        batch = q.Batch(circ, ordering="lg", diag=diag)
+        info = batch.program_info("c64", True)
         assert info["graph"] == 0 and info["warp_teams"] == 1
         assert info["n_tasks"] == len(edges)
+        for small_rank in (0, 4):
+            for dtype in ("c64", "c128"):
+                info = batch.program_info(dtype, True, force_graph=True, small_rank=small_rank,
+                                          max_wave_bytes=1 << 22)
+                assert info["graph"] == 1 and info["n_tasks"] >= len(edges)
