@@ -4,19 +4,22 @@
 One step = one evaluation of <C>(gamma, beta) and its gradient for one
 graph: every per-edge <Z_u Z_v> light-cone network is contracted (forward
 pass) and swept backwards (adjoint), and the per-edge scalars are reduced to
-<C> and d<C>/d(gamma, beta) in FP64 - all in one launch of the executor.
-The planner (host) runs once before timing, as the paper excludes ordering
-time.  `value` is edge networks per second with inputs resident in device
-memory; `e2e` is the same through the host-pointer C call (every step, the
-parameters go in and the results come out through the engine's pinned,
-device-mapped host buffer).
+<C> and d<C>/d(gamma, beta) in FP64.  The headline workload is the largest
+single-GPU one: p = 3 on a 4-regular 60-vertex graph, value and gradient
+(120 networks, intermediates of rank up to 24).  The planner (host) runs once
+before timing, as the paper excludes ordering time.  `value` is edge
+networks per second with inputs resident in device memory; `e2e` is the same
+through the host-pointer C call (every step, the parameters go in and the
+results come out through the engine's pinned, device-mapped host buffer).
+The other workloads are reported on the same line under "configs".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference   # the FP64 CPU oracle on the same metric
 
-With N > 1 (torchrun) every rank contracts its own seeded graph of the
-same family (independent problems, weak scaling) and no collective touches
-the data path.
+With N > 1 (torchrun) the graph's edge networks are sharded over the ranks
+(longest processing time first on their algorithmic bytes, the same
+partition on every rank) and each step ends with one FP64 all-reduce of the
+1 + 2p partial sums: the total work is fixed (strong scaling).
 """
 
 from __future__ import annotations
@@ -35,7 +38,7 @@ sys.path.insert(0, ROOT)
 
 from synth import WORKLOADS  # noqa: E402
 
-DEFAULT_WORKLOAD = "qaoa_p1_n50_d3"
+DEFAULT_WORKLOAD = "qaoa_p3_n60_d4"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, per launch) of
 # the dominant kernel from one ncu capture of the same workload, reported only
@@ -75,20 +78,20 @@ METRIC = "edge-<ZZ> networks/s (value + gradient)"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--dtype", default=None, help="override the workload's element type")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads reported under \"configs\"")
     ap.add_argument("--edges", type=int, default=0,
                     help="contract only the first K edge networks (small profiling cases)")
     ap.add_argument("--dense", action="store_true",
                     help="rank-4 ZZ tensors instead of diagonal (hyperedge) ZZ")
     ap.add_argument("--per-network", action="store_true",
                     help="also time the plain form: one launch per edge network")
-    ap.add_argument("--statevector", action="store_true",
-                    help="also time the full 2^n state vector on the GPU for the same graph")
     ap.add_argument("--crossover", action="store_true",
                     help="tensor network vs state vector over regularities 3..7 (table)")
     ap.add_argument("--width-sweep", action="store_true",
@@ -109,13 +112,6 @@ def dist_env():
     return world, rank, local
 
 
-def rank_workload(base, rank):
-    """Rank r contracts the same family's graph with seed (seed + r):
-    independent problems, no data exchanged between ranks (weak scaling)."""
-    from dataclasses import replace
-    return replace(base, graph_seed=base.graph_seed + rank)
-
-
 def max_over_ranks(values, device):
     """Element-wise maximum of per-rank timings over all ranks (the job is as
     slow as its slowest rank); the identity with one rank."""
@@ -127,13 +123,13 @@ def max_over_ranks(values, device):
     return t.tolist()
 
 
-def job_rate(world, networks_per_rank, seconds_per_step):
-    """Whole-job throughput: the networks every rank contracted per step over
-    the slowest rank's step time."""
-    return world * networks_per_rank / seconds_per_step
+def job_rate(networks_total, seconds_per_step):
+    """Whole-job throughput: every network of the graph (over all ranks)
+    per step, over the slowest rank's step time."""
+    return networks_total / seconds_per_step
 
 
-def workload_config(w, networks, want_grad, dtype, noise=None):
+def workload_config(w, networks, want_grad, dtype, noise=None, world=1):
     cfg = {
         "workload": w.name,
         "graph": f"{w.d}-regular, n={w.n}, configuration model seed {w.graph_seed}",
@@ -144,15 +140,22 @@ def workload_config(w, networks, want_grad, dtype, noise=None):
                 (", light cone" if w.lightcone else ", full network"),
         "want_grad": want_grad,
         "dtype": dtype,
-        "l2": "flushed between timed steps (256 MiB write outside the events)",
+        "l2": "flushed between timed steps (256 MiB write outside the events); the "
+              "largest intermediates (2^20-2^24 complex64) exceed L2 as well",
     }
+    if world > 1:
+        cfg["parallelism"] = (f"edge networks sharded over {world} ranks (longest processing "
+                              "time first on algorithmic bytes), one FP64 all-reduce of the "
+                              "1 + 2p sums per step")
     if noise:
         cfg["noise"] = f"{noise[0]} channel, strength {noise[1]}, every qubit after each mixer"
     return cfg
 
 
 class ClockSampler:
-    """nvidia-smi samples during the timed region."""
+    """nvidia-smi samples (every 20 ms) over the headline workload's
+    warm-up and timed phases; the summary covers that whole window and says
+    how many samples fell inside the timed steps themselves."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -163,14 +166,15 @@ class ClockSampler:
         self.proc = None
         self.lines = []          # (host time, csv line)
         self.window = (0.0, 0.0)
+        self.timed = (0.0, 0.0)
 
     def start(self):
         """Start sampling and wait for the first sample, so that nvidia-smi's
-        own start-up never overlaps the timed region."""
+        own start-up never overlaps the measured phases."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -186,8 +190,10 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append((time.perf_counter(), line.strip()))
 
-    def mark(self, t_begin, t_end):
+    def mark(self, t_begin, t_end, timed=None):
         self.window = (t_begin, t_end)
+        if timed:
+            self.timed = timed
 
     def stop(self):
         if self.proc:
@@ -197,12 +203,11 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
+    @staticmethod
+    def _parse(lines):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        t0, t1 = self.window
-        inside = [ln for t, ln in self.lines if t0 <= t <= t1]
-        for line in inside:
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -214,10 +219,22 @@ class ClockSampler:
             for name, val in zip(names, f[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(name)
+        return sm, mx, reasons
+
+    def summary(self):
+        t0, t1 = self.window
+        sm, mx, reasons = self._parse([ln for t, ln in self.lines if t0 <= t <= t1])
+        tt0, tt1 = self.timed
+        sm_t, _, _ = self._parse([ln for t, ln in self.lines if tt0 <= t <= tt1])
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "samples_in_timed_steps": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "samples_in_timed_steps": len(sm_t),
+                "sm_mhz_timed_steps": statistics.median(sm_t) if sm_t else None,
+                "window": "warm-up, value+gradient, forward and end-to-end phases of the "
+                          "headline workload"}
 
 
 def measured_peaks():
@@ -281,8 +298,19 @@ def oracle_all_cores(w, want_grad, seconds):
     return sum(d / el for d, el in res), n, sum(d for d, _ in res)
 
 
+def cpu_baseline_line(w, want_grad, seconds):
+    edges = w.graph()
+    g, b = w.angles()
+    rate, done, el = oracle_networks_per_s(w, edges, g, b, want_grad, seconds)
+    return {"value": rate, "unit": "networks/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} edge networks of {w.name}" + (" with gradient" if want_grad else "")
+                      + f" in {el:.1f} s (FP64 tensor-network oracle, numpy einsum, one thread)"}
+
+
 def run_reference(args):
-    """The oracle as the reference arm: same metric, rank 0 only."""
+    """The oracle as the reference arm: same workload and metric, rank 0
+    only; each step is a bounded sample (one edge network, value and
+    gradient, rotating over the graph's edges)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
@@ -290,37 +318,222 @@ def run_reference(args):
     edges = w.graph()
     g, b = w.angles()
     want_grad = True
-    sample = edges[:min(len(edges), 25)]
-    for _ in range(args.warmup):
-        oracle_networks_per_s(w, edges, g, b, want_grad, 0.0)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        from oracle import tensornet as tn
-        for e in sample:
+    from oracle import tensornet as tn
+    per_step = 1 if w.p >= 3 else min(len(edges), 25)
+
+    def step(k):
+        for j in range(per_step):
+            e = edges[(k * per_step + j) % len(edges)]
             tn.edge_value_grad(w.n, edges, g, b, e, lightcone=w.lightcone, dense=not w.diag)
+
+    for k in range(args.warmup):
+        step(k)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        step(args.warmup + k)
         times.append(time.perf_counter() - t0)
-    per_step = sum(times) / len(times)
-    value = len(sample) / per_step
+    sec = sum(times) / len(times)
+    value = per_step / sec
     line = {
         "impl": "reference",
         "metric": METRIC, "value": value, "unit": "networks/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-        "data": "synthetic", "config": workload_config(w, len(sample), want_grad, "c128"),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+        "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "config": workload_config(w, per_step, want_grad, "c128"),
         "cpu_baseline": {"value": value, "unit": "networks/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{len(sample)} of {len(edges)} edge networks per step, "
-                                   "FP64 tensor-network oracle with forward-mode gradient"},
+                         "sample": f"{per_step} of {len(edges)} edge networks per step (rotating "
+                                   "over the edges), FP64 tensor-network oracle with "
+                                   "forward-mode gradient, one thread"},
         "e2e": {"value": value, "unit": "networks/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+class Bench:
+    """Device state shared by every workload measured in one run."""
+
+    def __init__(self, q, dev, stream, world, rank):
+        import torch
+        self.q, self.dev, self.stream, self.world, self.rank = q, dev, stream, world, rank
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(self, fn, steps):
+        """Per-step device times (ms) of `steps` calls of fn, CUDA events on
+        the launching stream, L2 flushed between steps outside the events.
+        A short device-side sleep first, so that the steps are all queued
+        before the GPU reaches them: the events then time the GPU alone."""
+        import torch
+        torch.cuda._sleep(int(4e6))
+        evs = []
+        for _ in range(steps):
+            self.flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(self.stream)
+            fn()
+            e.record(self.stream)
+            evs.append((s, e))
+        torch.cuda.synchronize()
+        return [s.elapsed_time(e) for s, e in evs]
+
+    def barrier(self):
+        import torch
+        torch.cuda.synchronize()
+        if self.world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def setup(self, w, dtype, grads, noise=None, obs_edges=None, autotune=None):
+        """Circuit, whole batch, this rank's shard, an engine sized for its
+        programs, prepared for every gradient flag in `grads`."""
+        import torch
+        q = self.q
+        edges = w.graph()
+        g, b = w.angles()
+        circ = q.Circuit.qaoa(w.n, edges, w.p, noise=noise)
+        full = q.Batch(circ, obs_edges, lightcone=w.lightcone, diag=w.diag, ordering=w.ordering)
+        batch, mine = q.shard(full, self.rank, self.world, want_grad=max(grads))
+        if batch is None:
+            raise SystemExit(f"rank {self.rank} has no edge network of {w.name}")
+        need = 0
+        for grad in grads:
+            info = batch.program_info(dtype, grad)
+            need += info["work_bytes"] + 2 * info["table_bytes"]
+        engine = q.Engine(self.dev.index, arena_bytes=int(need) + (256 << 20))
+        tuned = None
+        if autotune:
+            tuned = q.autotune(engine, batch, dtype, max(grads), cache_path=autotune)
+            tuned = {k: tuned[k] for k in ("small_rank", "task_terms_log2", "subtree_bytes",
+                                           "cached")}
+        for grad in grads:
+            batch.prepare(engine, dtype, want_grad=grad)
+        P = 2 * w.p
+        params = torch.tensor(g + b, dtype=torch.float64, device=self.dev)
+        out = torch.zeros(2 + P + len(mine), dtype=torch.float64, device=self.dev)
+        return dict(w=w, edges=edges, g=g, b=b, circ=circ, full=full, batch=batch, mine=mine,
+                    engine=engine, params=params, out=out, P=P, dtype=dtype, tuned=tuned,
+                    n_total=len(full.edges))
+
+    def step_fn(self, st, grad):
+        """One evaluation: the rank's launches, then (N > 1) the one FP64
+        all-reduce of the 1 + 2p sums."""
+        q = self.q
+        sums = st["out"][:1 + st["P"]]
+
+        def fn():
+            q.qaoa_expectation_device(st["engine"], st["batch"], st["params"], st["out"],
+                                      st["dtype"], want_grad=grad, stream=self.stream)
+            if self.world > 1:
+                q.allreduce_sum(sums)
+        return fn
+
+    def roofline(self, st, ms, want_grad, peak, peak_kind, traffic=None, traffic_src=None):
+        stats = st["batch"].stats()
+        prog = st["batch"].program_info(st["dtype"], want_grad)
+        elem = 16 if st["dtype"] == "c128" else 8
+        alg = (stats["bytes_c64"] + (stats["grad_bytes_c64"] if want_grad else 0.0)) * elem / 8
+        launches = prog["n_waves"] if prog["graph"] else 1
+        achieved = alg / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+                "kernel": "graph_exec_kernel" if prog["graph"] else "smem_exec_kernel",
+                "launches_per_step": launches, "peak_kind": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_step": alg,
+                "algorithmic_bytes_per_launch": alg / launches}
+
+    def e2e(self, st, steps, warmup):
+        """The host-pointer C call per step: pinned parameters in, <C>, the
+        gradient and the per-edge values out (plus, N > 1, the all-reduce)."""
+        import torch
+        q = self.q
+        from paper_1709_03636_gb300 import _lib
+        P, n = st["P"], len(st["mine"])
+        h_gam = torch.tensor(st["g"], dtype=torch.float64).pin_memory()
+        h_bet = torch.tensor(st["b"], dtype=torch.float64).pin_memory()
+        h_C = torch.zeros(1, dtype=torch.float64).pin_memory()
+        h_edge = torch.zeros(n, dtype=torch.float64).pin_memory()
+        h_grad = torch.zeros(P, dtype=torch.float64).pin_memory()
+        dptr = lambda t: q.ctypes.cast(q.ctypes.c_void_p(t.data_ptr()),  # noqa: E731
+                                       q.ctypes.POINTER(q.ctypes.c_double))
+        args = (st["engine"].ptr, st["batch"].ptr, dptr(h_gam), dptr(h_bet), q.DTYPES[st["dtype"]],
+                1, q.ctypes.c_void_p(self.stream.cuda_stream), dptr(h_C), dptr(h_edge),
+                dptr(h_grad))
+        call = _lib.lib.qtc_qaoa_expectation
+
+        def step():
+            _lib.check(call(*args))
+            if self.world > 1:
+                q.allreduce_sum(torch.cat([h_C, h_grad]).to(self.dev))
+
+        for _ in range(warmup):
+            step()
+        self.barrier()
+        times = []
+        for _ in range(steps):
+            self.flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step()
+            times.append(time.perf_counter() - t0)
+        self.barrier()
+        prog = st["batch"].program_info(st["dtype"], True)
+        d2h = 8 * (2 + P + n + (0 if prog["graph"] else 1))
+        return sum(times) / len(times), 8 * P, d2h
+
+
+def measure_extra(bench, name, dtype, want_grad, steps, warmup, peak, peak_kind, dense=False,
+                  cpu_seconds=5.0, statevector=False):
+    """One more workload on the same line: device-timed rate, roofline
+    fraction and a one-thread oracle sample (rank 0, N = 1)."""
+    from dataclasses import replace
+    import torch
+    w = WORKLOADS[name]
+    if dense:
+        w = replace(w, diag=False)
+    st = bench.setup(w, dtype, [want_grad])
+    fn = bench.step_fn(st, want_grad)
+    for _ in range(warmup):
+        fn()
+    bench.barrier()
+    ms_list = bench.timed(fn, steps)
+    ms = max_over_ranks([sum(ms_list) / len(ms_list)], bench.dev)[0]
+    rec = {"dtype": dtype, "want_grad": want_grad,
+           "form": ("diagonal ZZ" if w.diag else "rank-4 ZZ") +
+                   (", light cone" if w.lightcone else ", full network"),
+           "networks_per_step": st["n_total"], "ms_per_step": ms,
+           "value": job_rate(st["n_total"], ms * 1e-3), "unit": "networks/s",
+           "launches_per_step": st["engine"].last_launches,
+           "roofline": bench.roofline(st, ms, want_grad, peak, peak_kind),
+           "C": st["out"][0].item()}
+    prog = st["batch"].program_info(dtype, want_grad)
+    rec["gemm_steps"] = prog["n_gemm_steps"]
+    if statevector:
+        out_sv = torch.zeros(1 + len(st["edges"]), dtype=torch.float64, device=bench.dev)
+        sv_dtype = "c128" if dtype == "c128" else "c64"
+
+        def sv_step():
+            bench.q.statevector_expectation_device(st["engine"], st["circ"], st["params"],
+                                                   out_sv, sv_dtype, stream=bench.stream)
+
+        for _ in range(warmup):
+            sv_step()
+        sv = bench.timed(sv_step, steps)
+        svt = sum(sv) / len(sv)
+        rec["statevector"] = {"ms_per_eval": svt, "tn_over_sv_time": ms / svt,
+                              "C": out_sv[0].item(), "bytes_per_eval_hint":
+                              "about 3 passes over 2^n complex64"}
+    if bench.rank == 0 and bench.world == 1 and cpu_seconds > 0:
+        rec["cpu_baseline"] = cpu_baseline_line(w, want_grad, cpu_seconds)
+    del st
+    torch.cuda.empty_cache()
+    return rec
+
+
 def run_ours(args):
     import torch
     import paper_1709_03636_gb300 as q
-    from paper_1709_03636_gb300 import _lib
 
     world, rank, local = dist_env()
     if world > 1:
@@ -329,199 +542,107 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    bench = Bench(q, dev, stream, world, rank)
+    peak, peak_kind = measured_peaks()
 
-    base = WORKLOADS[args.workload]
-    dtype = args.dtype or base.dtype
-    want_grad = True
-    # rank r contracts graph seed (seed + r): independent problems
     from dataclasses import replace
-    w = rank_workload(base, rank)
+    w = WORKLOADS[args.workload]
     if args.dense:
         w = replace(w, diag=False)
-    edges = w.graph()
-    g, b = w.angles()
+    dtype = args.dtype or w.dtype
+    want_grad = True
     noise = None
     if args.noise:
         kind, strength = args.noise.split(":")
         noise = (kind, float(strength))
-    circ = q.Circuit.qaoa(w.n, edges, w.p, noise=noise)
-    obs = edges[:args.edges] if args.edges else None
-    batch = q.Batch(circ, obs, lightcone=w.lightcone, diag=w.diag, ordering=w.ordering)
-    stats = batch.stats()
-    n_nets = stats["n_networks"]
-    need = 0
-    for grad in (True, False):
-        info = batch.program_info(dtype, grad)
-        need += info["work_bytes"] + 2 * info["table_bytes"]
-    engine = q.Engine(local, arena_bytes=int(need) + (256 << 20))
-    tuned = None
-    if args.autotune:
-        tuned = q.autotune(engine, batch, dtype, want_grad, cache_path=args.autotune)
-        tuned = {k: tuned[k] for k in ("small_rank", "task_terms_log2", "subtree_bytes",
-                                       "cached")}
-    batch.prepare(engine, dtype, want_grad=want_grad)
-    batch.prepare(engine, dtype, want_grad=False)
-    P = 2 * w.p
-    params = torch.tensor(g + b, dtype=torch.float64, device=dev)
-    out = torch.zeros(2 + P + n_nets, dtype=torch.float64, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
+    obs = w.graph()[:args.edges] if args.edges else None
+    st = bench.setup(w, dtype, [True, False], noise=noise, obs_edges=obs,
+                     autotune=args.autotune)
+    n_total = st["n_total"]
+    grad_step, fwd_step = bench.step_fn(st, True), bench.step_fn(st, False)
 
-    def device_step(grad):
-        q.qaoa_expectation_device(engine, batch, params, out, dtype, want_grad=grad,
-                                  stream=stream)
-
-    def timed(fn, steps):
-        # a short device-side sleep first, so that the following steps are all
-        # queued before the GPU reaches them: the events then time the GPU
-        # alone, not the host's enqueue latency
-        torch.cuda._sleep(int(4e6))
-        evs = []
-        for _ in range(steps):
-            flush.zero_()
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record(stream)
-            fn()
-            e.record(stream)
-            evs.append((s, e))
-        torch.cuda.synchronize()
-        return [s.elapsed_time(e) for s, e in evs]
-
-    def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-
-    for _ in range(args.warmup):
-        device_step(True)
-        device_step(False)
     clocks = ClockSampler(local).start()
-    barrier()
-    wall0 = time.perf_counter()
-    step_ms = timed(lambda: device_step(True), args.steps)
-    wall = time.perf_counter() - wall0
-    clocks.mark(wall0, wall0 + wall)
-    launches = args.steps * engine.last_launches
-    prog = batch.program_info(dtype, True)
-    barrier()
-    fwd_ms = timed(lambda: device_step(False), args.steps)
-    barrier()
-
-    # end to end through the host-pointer call: pinned params in, results out
-    h_gam = torch.tensor(g, dtype=torch.float64).pin_memory()
-    h_bet = torch.tensor(b, dtype=torch.float64).pin_memory()
-    h_C = torch.zeros(1, dtype=torch.float64).pin_memory()
-    h_edge = torch.zeros(n_nets, dtype=torch.float64).pin_memory()
-    h_grad = torch.zeros(P, dtype=torch.float64).pin_memory()
-    vp = lambda t: q.ctypes.c_void_p(t.data_ptr())  # noqa: E731
-
-    dptr = lambda t: q.ctypes.cast(vp(t), q.ctypes.POINTER(q.ctypes.c_double))  # noqa: E731
-    e2e_args = (engine.ptr, batch.ptr, dptr(h_gam), dptr(h_bet), q.DTYPES[dtype], 1,
-                q.ctypes.c_void_p(stream.cuda_stream), dptr(h_C), dptr(h_edge), dptr(h_grad))
-    e2e_call = _lib.lib.qtc_qaoa_expectation
-
-    def e2e_step():
-        _lib.check(e2e_call(*e2e_args))
-
+    t_begin = time.perf_counter()
     for _ in range(args.warmup):
-        e2e_step()
-    barrier()
-    e2e_times = []
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e2e_step()
-        e2e_times.append(time.perf_counter() - t0)
-    barrier()
+        grad_step()
+        fwd_step()
+    bench.barrier()
+    t0 = time.perf_counter()
+    step_ms = bench.timed(grad_step, args.steps)
+    t1 = time.perf_counter()
+    launches = args.steps * st["engine"].last_launches
+    bench.barrier()
+    fwd_ms = bench.timed(fwd_step, args.steps)
+    bench.barrier()
+    e2e_s, h2d, d2h = bench.e2e(st, args.steps, args.warmup)
+    t_end = time.perf_counter()
+    clocks.mark(t_begin, t_end, timed=(t0, t1))
 
     ms = sum(step_ms) / len(step_ms)
-    e2e_s = sum(e2e_times) / len(e2e_times)
     fwd = sum(fwd_ms) / len(fwd_ms)
     ms, e2e_s, fwd = max_over_ranks([ms, e2e_s, fwd], dev)
-    value = job_rate(world, n_nets, ms * 1e-3)
-    elem = 16 if dtype == "c128" else 8
-    alg_bytes = (stats["bytes_c64"] + stats["grad_bytes_c64"]) * elem / 8
-    peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / (ms * 1e-3) / 1e9
-    kernel = "graph_exec_kernel" if prog["graph"] else "smem_exec_kernel"
-    traffic, traffic_src = ncu_traffic(w.name, kernel, dtype, want_grad) if not noise \
-        else (None, None)
+    stats = st["batch"].stats()
+    kernel = "graph_exec_kernel" if st["batch"].program_info(dtype, True)["graph"] \
+        else "smem_exec_kernel"
+    traffic, traffic_src = ncu_traffic(w.name, kernel, dtype, want_grad) \
+        if not noise and not args.edges and world == 1 else (None, None)
+    roof = bench.roofline(st, ms, want_grad, peak, peak_kind, traffic, traffic_src)
+    clk = clocks.summary()
+    clocks.stop()
     line = {
-        "metric": METRIC, "value": value, "unit": "networks/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
-        "data": "synthetic", "config": workload_config(w, n_nets, want_grad, dtype, noise),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "traffic_source": traffic_src,
-                     "kernel": kernel,
-                     "launches_per_step": engine.last_launches,
-                     "peak_kind": f"{peak_kind} hbm_gbs",
-                     "algorithmic_bytes_per_step": alg_bytes},
-        "e2e": {"value": job_rate(world, n_nets, e2e_s), "unit": "networks/s",
-                "h2d_bytes_per_step": 8 * P,
+        "metric": METRIC, "value": job_rate(n_total, ms * 1e-3), "unit": "networks/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": workload_config(w, n_total, want_grad, dtype, noise, world),
+        "roofline": roof,
+        "e2e": {"value": job_rate(n_total, e2e_s), "unit": "networks/s",
+                "h2d_bytes_per_step": h2d,
                 # <C>, gradient, per-edge values, status; the shared-memory
                 # executor also writes its 8-byte completion word
-                "d2h_bytes_per_step": 8 * (2 + P + n_nets + (0 if prog["graph"] else 1))},
-        "complex_gflops": {"value": 8.0 * (stats["cmacs"] + (stats["grad_cmacs"] if want_grad
-                                                                else 0.0)) / (ms * 1e-3) / 1e9,
-                           "unit": "GFLOP/s", "count": "algorithmic, 8 real flops per complex "
-                           "multiply-add (forward and adjoint contractions)"},
+                "d2h_bytes_per_step": d2h},
+        "complex_gflops": {"value": 8.0 * (stats["cmacs"] + stats["grad_cmacs"]) / (ms * 1e-3)
+                           / 1e9, "unit": "GFLOP/s",
+                           "count": "algorithmic, 8 real flops per complex multiply-add "
+                                    "(forward and adjoint contractions), this rank"},
         "gpu_launches": launches,
-        "autotuned": tuned,
-        "clocks": clocks.summary(),
+        "autotuned": st["tuned"],
+        "clocks": clk,
         "step_ms_min_median_max": [min(step_ms), statistics.median(step_ms), max(step_ms)],
-        "forward_only": {"value": job_rate(world, n_nets, fwd * 1e-3), "unit": "networks/s",
-                         "ms_per_step": fwd},
+        "forward_only": {"value": job_rate(n_total, fwd * 1e-3), "unit": "networks/s",
+                         "ms_per_step": fwd,
+                         "roofline": bench.roofline(st, fwd, False, peak, peak_kind)},
         "grad_fwd_ratio": ms / fwd,
-        "timed_wall_s": wall,
+        "C": st["out"][0].item(),
+        "timed_wall_s": t1 - t0,
     }
-    clocks.stop()
+    if clk.get("sm_mhz"):
+        line["clocks"]["ms_x_median_sm_mhz"] = ms * clk["sm_mhz"]
     if args.per_network:
-        # the plain form: every edge network is its own batch and launch, c64
-        singles = [q.Batch(circ, [e], lightcone=w.lightcone, diag=w.diag, ordering=w.ordering)
-                   for e in (obs or edges)]
-        outs = [torch.zeros(2 + P + 1, dtype=torch.float64, device=dev) for _ in singles]
-        for sb in singles:
-            sb.prepare(engine, "c64", want_grad=False)
-
-        def per_network_step():
-            for sb, o in zip(singles, outs):
-                q.qaoa_expectation_device(engine, sb, params, o, "c64", want_grad=False,
-                                          stream=stream)
-
-        for _ in range(args.warmup):
-            per_network_step()
-        pn_ms = timed(per_network_step, args.steps)
-        pn = sum(pn_ms) / len(pn_ms)
-        line["per_network_c64_forward"] = {
-            "value": n_nets / (pn * 1e-3), "unit": "networks/s", "ms_per_step": pn,
-            "launches_per_step": len(singles),
-            "batched_forward_speedup": pn / fwd}
-    if args.statevector:
-        out_sv = torch.zeros(1 + len(edges), dtype=torch.float64, device=dev)
-        sv_dtype = "c128" if dtype == "c128" else "c64"
-
-        def sv_step():
-            q.statevector_expectation_device(engine, circ, params, out_sv, sv_dtype,
-                                             stream=stream)
-
-        for _ in range(args.warmup):
-            sv_step()
-        sv_ms = timed(sv_step, args.steps)
-        svt = sum(sv_ms) / len(sv_ms)
-        line["statevector_forward"] = {
-            "ms_per_eval": svt, "launches": engine.last_launches,
-            "tensor_network_forward_ms": fwd, "tn_over_sv_time": fwd / svt,
-            "C_statevector": out_sv[0].item(), "C_tensor_network": out[0].item()}
+        line["per_network_c64_forward"] = per_network(bench, st, args, fwd)
+    del st
+    torch.cuda.empty_cache()
+    if not args.no_extras and not args.edges and not noise:
+        k, wu = min(args.steps, 20), min(args.warmup, 3)
+        cpu_s = 0.0 if args.no_cpu_baseline else 5.0
+        extras = {}
+        extras["qaoa_p1_n50_d3"] = measure_extra(
+            bench, "qaoa_p1_n50_d3", "c64", True, k, wu, peak, peak_kind, cpu_seconds=cpu_s)
+        extras["qaoa_p2_n100_d5"] = measure_extra(
+            bench, "qaoa_p2_n100_d5", "c64", True, k, wu, peak, peak_kind, cpu_seconds=cpu_s)
+        extras["qaoa_p2_n100_d5_dense_split_bf16"] = measure_extra(
+            bench, "qaoa_p2_n100_d5", "split_bf16", False, k, wu, peak, peak_kind, dense=True,
+            cpu_seconds=cpu_s)
+        extras["qaoa_p2_n100_d5_dense_c64"] = measure_extra(
+            bench, "qaoa_p2_n100_d5", "c64", False, k, wu, peak, peak_kind, dense=True,
+            cpu_seconds=0.0)
+        extras["qaoa_p1_n26_d7_full"] = measure_extra(
+            bench, "qaoa_p1_n26_d7", "c64", False, k, wu, peak, peak_kind, cpu_seconds=cpu_s,
+            statevector=True)
+        line["configs"] = extras
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not noise:
-        rate, done, el = oracle_networks_per_s(w, edges, g, b, want_grad, 10.0)
-        line["cpu_baseline"] = {
-            "value": rate, "unit": "networks/s", "cores": 1, "kind": "oracle",
-            "sample": f"{done} edge networks of {w.name} with gradient in {el:.1f} s "
-                      "(FP64 tensor-network oracle, numpy einsum, one thread)"}
+        line["cpu_baseline"] = cpu_baseline_line(w, want_grad, 10.0)
         rate_all, cores, done_all = oracle_all_cores(w, want_grad, 10.0)
         line["cpu_baseline_all_cores"] = {
             "value": rate_all, "unit": "networks/s", "cores": cores, "kind": "oracle",
@@ -531,6 +652,31 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def per_network(bench, st, args, fwd):
+    """The plain form: every edge network its own batch and launch, c64."""
+    import torch
+    q = bench.q
+    w = st["w"]
+    singles = [q.Batch(st["circ"], [e], lightcone=w.lightcone, diag=w.diag, ordering=w.ordering)
+               for e in st["batch"].edges]
+    outs = [torch.zeros(2 + st["P"] + 1, dtype=torch.float64, device=bench.dev)
+            for _ in singles]
+    for sb in singles:
+        sb.prepare(st["engine"], "c64", want_grad=False)
+
+    def step():
+        for sb, o in zip(singles, outs):
+            q.qaoa_expectation_device(st["engine"], sb, st["params"], o, "c64", want_grad=False,
+                                      stream=bench.stream)
+
+    for _ in range(args.warmup):
+        step()
+    pn = bench.timed(step, args.steps)
+    pn = sum(pn) / len(pn)
+    return {"value": len(singles) / (pn * 1e-3), "unit": "networks/s", "ms_per_step": pn,
+            "launches_per_step": len(singles), "batched_forward_speedup": pn / fwd}
 
 
 def run_width_sweep(args):

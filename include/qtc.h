@@ -251,6 +251,13 @@ qtc_status qtc_plan_stats(const qtc_plan* p, qtc_plan_info* info);
  * tensor ids (0..n_tensors-1 leaves, n_tensors+t the result of step t).
  * Arrays hold n_steps entries (host). */
 qtc_status qtc_plan_steps(const qtc_plan* p, int32_t* lhs, int32_t* rhs);
+/* Every step as Eq. 1's index classes (the step lowering of Section 3.1's
+ * pairwise contractions): shapes[4s .. 4s+3] = (b, x, y, z), the numbers of
+ * batch labels (held by both operands and kept), free labels of the first
+ * operand, summed labels, and free labels of the second operand, so that
+ * rank A = b + x + y, rank B = b + y + z, rank C = b + x + z and the step
+ * costs 2^(b+x+y+z) complex multiply-adds.  shapes: host, 4 * n_steps ints. */
+qtc_status qtc_plan_step_shapes(const qtc_plan* p, int32_t* shapes);
 void qtc_plan_destroy(qtc_plan* p);
 
 /* Contract one network on the GPU (Eq. 1 applied step by step).
@@ -269,6 +276,24 @@ qtc_status qtc_batch_create(const qtc_circuit* c, const int32_t* obs_edges,
                             const qtc_plan_opts* opts, qtc_batch** out);
 qtc_status qtc_batch_stats(const qtc_batch* b, qtc_batch_info* info);
 void qtc_batch_destroy(qtc_batch* b);
+
+/* Edge networks are independent (the objective of Section 4.1 is a sum over
+ * edges), so one graph shards over devices or processes with a single sum of
+ * the 1 + 2p results at the end.  qtc_batch_partition assigns each network of
+ * b to one of n_parts parts by longest processing time first on its
+ * algorithmic bytes (forward, plus the adjoint sweep when want_grad): the
+ * costliest remaining network goes to the part with the least work so far.
+ * part_of_net: host, n_networks ints (0..n_parts-1) out; part_cost: host,
+ * nullable, n_parts doubles out (bytes per part).  Host only, deterministic:
+ * every process computes the same partition without communication. */
+qtc_status qtc_batch_partition(const qtc_batch* b, int n_parts, int want_grad,
+                               int32_t* part_of_net, double* part_cost);
+/* A new batch holding networks nets[0..k-1] of b (host, k ints), with their
+ * observables, weights and plans as they are in b (no new ordering search), so
+ * that a part's results are those of the same networks in the whole batch.
+ * Its expectation calls return the part's share: <C> and the gradient summed
+ * over its networks only. */
+qtc_status qtc_batch_subset(const qtc_batch* b, const int32_t* nets, int k, qtc_batch** out);
 
 /* Builds, validates and describes the batch's device program on the host
  * only (no GPU call): every access range, counter and dependency order of a
@@ -363,6 +388,22 @@ qtc_status qtc_engine_set_task_options(qtc_engine* e, int task_terms_log2, int s
  * (anything else is a failure).  Used by the failure-detection tests. */
 qtc_status qtc_selftest_wait_timeout(qtc_engine* e, void* stream);
 
+/* ---- answer strings (Section 3.3) ----------------------------------------
+ * The sequential estimate of a likely output string: for q = 0..n-1,
+ * contract <psi| prod P |psi> with qubits 0..q-1 projected on the values
+ * already chosen, qubit q on |0> and the others traced out (n contractions of
+ * networks that share one structure, so the first plan's contraction tree,
+ * ordered by `opts`, is reused for all), compare P(prefix, x_q = 0) with
+ * P(prefix) - P(prefix, x_q = 0) and keep the likelier value; an exact tie
+ * is broken by a SplitMix64 stream seeded with tie_seed.  params: host,
+ * n_params values (nullable when the circuit has none); opts: host, nullable
+ * (LG defaults).  bits_out: host, n bytes (0 or 1); probs_out: host, n
+ * doubles, the probability of each chosen prefix.  Synchronous; the circuit
+ * may hold noise channels (density-matrix marginals). */
+qtc_status qtc_answer_string(qtc_engine* e, const qtc_circuit* c, const double* params,
+                             int dtype, const qtc_plan_opts* opts, uint64_t tie_seed,
+                             void* stream, uint8_t* bits_out, double* probs_out);
+
 /* ---- full-Hilbert-space reference (Section 5's comparison method) ---------
  * <C> of a QAOA circuit (qtc_circuit_qaoa) from the 2^n state vector on the
  * GPU: |+>^n, per layer the diagonal phase and the RX mixer, moved through
@@ -395,9 +436,14 @@ qtc_status qtc_statevector_qaoa_device(qtc_engine* e, const qtc_circuit* c,
  * that loads the library keeps until the process exits.  The call allocates
  * no device memory and calls no allocating CUDA or library routine; a batch
  * whose program does not fit returns QTC_ERR_ARENA with the size it needs.
- * The first call on a device resolves the array's device address on that
- * device (cudaGetSymbolAddress); make that first call before any stream
- * capture.  The host-side program is built once per batch and cached.
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, no allocation); the first call on a device also
+ * loads the library's device code there, so make it before any stream
+ * capture.  The host-side program is built once per batch and cached; when a
+ * call brings a batch other than the previous call's, it first copies that
+ * batch's program tables into the array from pageable host memory on
+ * `stream`, so run every batch through this call once before any stream
+ * capture that contains it.
  * Every call shares the one array and leaves its contents behind (the call
  * clears the counters it needs zeroed), so calls whose executions overlap on
  * the GPU — from two streams or two host threads — race and must not be

@@ -326,6 +326,21 @@ def edge_value_grad(n, edges, gammas, betas, edge, **kw):
     return contract(fs, n_params=P)
 
 
+def edge_grad_fd(n, edges, gammas, betas, edge, h=1e-4, **kw):
+    """d Re s / d(gamma, beta) of one edge network by central differences
+    with step h: (s(theta + h e_i) - s(theta - h e_i)) / 2h per parameter."""
+    x = np.array(list(gammas) + list(betas), dtype=np.float64)
+    p = len(gammas)
+    out = np.zeros(len(x))
+    for i in range(len(x)):
+        xp, xm = x.copy(), x.copy()
+        xp[i] += h
+        xm[i] -= h
+        out[i] = (edge_value(n, edges, xp[:p], xp[p:], edge, **kw).real
+                  - edge_value(n, edges, xm[:p], xm[p:], edge, **kw).real) / (2 * h)
+    return out
+
+
 def maxcut(n, edges, gammas, betas, **kw):
     """<C> = sum_e (1 - Re s_e) / 2 over every edge network."""
     return float(sum((1.0 - edge_value(n, edges, gammas, betas, e, **kw).real) / 2.0

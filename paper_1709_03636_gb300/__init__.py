@@ -17,7 +17,7 @@ __all__ = [
     "QtcError", "Engine", "Circuit", "Network", "Plan", "Batch", "DTYPES", "ORDERINGS",
     "contract", "qaoa_expectation", "qaoa_expectation_device", "QAOAExpectation",
     "statevector_expectation", "statevector_expectation_device", "optimize_angles",
-    "answer_string", "autotune",
+    "answer_string", "autotune", "shard", "allreduce_sum",
     "GATES",
 ]
 
@@ -249,6 +249,14 @@ class Plan(_Handle):
         check(lib.qtc_plan_steps(self.ptr, a, b))
         return list(zip(a, b))
 
+    def step_shapes(self):
+        """(b, x, y, z) of every step: batch, free-in-A, summed, free-in-B
+        label counts (Eq. 1 with batch indices kept)."""
+        n = self.stats()["n_steps"]
+        s = (ctypes.c_int32 * (4 * n))()
+        check(lib.qtc_plan_step_shapes(self.ptr, s))
+        return [tuple(s[4 * i:4 * i + 4]) for i in range(n)]
+
 
 class Batch(_Handle):
     """All per-edge <Z_u Z_v> networks of a QAOA circuit, each with its plan."""
@@ -292,6 +300,29 @@ class Batch(_Handle):
         out = (ctypes.c_int32 * 6)()
         check(lib.qtc_batch_launch_info(engine.ptr, self.ptr, _dtype(dtype), int(want_grad), out))
         return dict(zip(["grid", "block", "smem", "per_sm", "launches", "tmem_cols"], out))
+
+    def partition(self, n_parts: int, want_grad: bool = True):
+        """Part (0..n_parts-1) of every network, by longest processing time
+        first on algorithmic bytes (qtc_batch_partition), and each part's
+        bytes."""
+        n = len(self.edges)
+        parts = (ctypes.c_int32 * n)()
+        cost = (ctypes.c_double * n_parts)()
+        check(lib.qtc_batch_partition(self.ptr, int(n_parts), int(want_grad), parts, cost))
+        return list(parts), list(cost)
+
+    def subset(self, nets) -> "Batch":
+        """The networks `nets` of this batch as a batch of their own, with the
+        same plans (qtc_batch_subset)."""
+        nets = [int(i) for i in nets]
+        h = ctypes.c_void_p()
+        check(lib.qtc_batch_subset(self.ptr, _i32(nets), len(nets), ctypes.byref(h)))
+        sub = Batch.__new__(Batch)
+        _Handle.__init__(sub, h)
+        sub.edges = [self.edges[i] for i in nets]
+        sub.p = self.p
+        sub.n_params = self.n_params
+        return sub
 
     def prepare(self, engine: Engine, dtype="c64", want_grad=False, stream=None):
         check(lib.qtc_batch_prepare(engine.ptr, self.ptr, _dtype(dtype), int(want_grad),
@@ -383,35 +414,21 @@ def _autograd():
 
 
 def answer_string(engine: Engine, circuit: Circuit, params, dtype="c128", ordering="lg",
-                  seed=0, rng=None):
-    """Section 3.3's estimate of a likely output bit string: qubit by qubit,
-    contract <psi| P |psi> with the earlier qubits projected on their chosen
-    values and the current one on |0>; keep the more probable value (a tie
-    is broken at random with `rng`, default numpy's seeded generator).  All
-    n contractions share one contraction tree (the networks differ only in
-    projector values).  Returns (bits, probabilities of each chosen prefix).
-    The circuit may hold noise channels (density-matrix marginals)."""
-    import numpy as np
-    rng = rng or np.random.default_rng(seed)
+                  seed=0, stream=None):
+    """Section 3.3's estimate of a likely output bit string (the library's
+    qtc_answer_string): qubit by qubit, the prefix probability with the
+    current qubit projected on |0> against the rest, keeping the likelier
+    value (an exact tie is broken by a generator seeded with `seed`).  All n
+    contractions share one contraction tree.  Returns (bits, probabilities of
+    each chosen prefix).  The circuit may hold noise channels."""
     n = circuit.n
-    bits = [2] * n
-    probs = []
-    prev = 1.0
-    first = None
-    for q in range(n):
-        bits[q] = 0
-        net = Network(circuit, "projector", bits=bits, lightcone=False)
-        plan = Plan(net, like=first) if first is not None else Plan(net, ordering, seed)
-        if first is None:
-            first = plan
-        p0 = contract(engine, plan, params, dtype).real
-        p1 = prev - p0
-        if p0 > p1 or (p0 == p1 and rng.integers(2) == 0):
-            bits[q], prev = 0, p0
-        else:
-            bits[q], prev = 1, p1
-        probs.append(prev)
-    return bits, probs
+    bits = (ctypes.c_uint8 * n)()
+    probs = (ctypes.c_double * n)()
+    opts = plan_opts(ordering, seed)
+    check(lib.qtc_answer_string(engine.ptr, circuit.ptr, _f64(params) if len(params) else None,
+                                _dtype(dtype), ctypes.byref(opts), int(seed), _stream(stream),
+                                bits, probs))
+    return list(bits), list(probs)
 
 
 def optimize_angles(engine: Engine, batch: Batch, gammas, betas, *, steps: int = 200,
@@ -453,4 +470,5 @@ class _LazyAutograd:
 QAOAExpectation = _LazyAutograd()
 
 
+from .shard import allreduce_sum, shard  # noqa: E402  (edge sharding over ranks)
 from .tuning import autotune  # noqa: E402  (graph-executor task shapes)

@@ -71,6 +71,7 @@ SIGNATURES = {
     "qtc_plan_create": (c_int, [c_void_p, P(qtc_plan_opts), P(c_void_p)]),
     "qtc_plan_stats": (c_int, [c_void_p, P(qtc_plan_info)]),
     "qtc_plan_steps": (c_int, [c_void_p, P(c_int32), P(c_int32)]),
+    "qtc_plan_step_shapes": (c_int, [c_void_p, P(c_int32)]),
     "qtc_plan_destroy": (None, [c_void_p]),
     "qtc_contract": (c_int, [c_void_p, c_void_p, P(c_double), c_int, c_void_p, P(c_double),
                              P(c_double)]),
@@ -78,6 +79,8 @@ SIGNATURES = {
                                  P(c_void_p)]),
     "qtc_batch_stats": (c_int, [c_void_p, P(qtc_batch_info)]),
     "qtc_batch_destroy": (None, [c_void_p]),
+    "qtc_batch_partition": (c_int, [c_void_p, c_int, c_int, P(c_int32), P(c_double)]),
+    "qtc_batch_subset": (c_int, [c_void_p, P(c_int32), c_int, P(c_void_p)]),
     "qtc_batch_prepare": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "qtc_qaoa_expectation": (c_int, [c_void_p, c_void_p, P(c_double), P(c_double), c_int, c_int,
                                      c_void_p, P(c_double), P(c_double), P(c_double)]),
@@ -94,6 +97,8 @@ SIGNATURES = {
                                      c_void_p, P(c_double), P(c_double)]),
     "qtc_statevector_qaoa_device": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p,
                                             c_void_p]),
+    "qtc_answer_string": (c_int, [c_void_p, c_void_p, P(c_double), c_int, P(qtc_plan_opts),
+                                  c_uint64, c_void_p, P(ctypes.c_uint8), P(c_double)]),
     "qtc_batch_program_info": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_size_t, c_size_t,
                                        P(qtc_program_info)]),
 }

@@ -545,6 +545,33 @@ extern "C" qtc_status qtc_plan_steps(const qtc_plan* p, int32_t* lhs, int32_t* r
   });
 }
 
+extern "C" qtc_status qtc_plan_step_shapes(const qtc_plan* p, int32_t* shapes) {
+  return guarded([&] {
+    if (!p || !shapes) fail(QTC_ERR_INVALID, "null argument");
+    const Plan& pl = p->plan;
+    const int L = (int)pl.net.leaves.size();
+    auto has = [](const std::vector<int>& v, int x) {
+      return std::find(v.begin(), v.end(), x) != v.end();
+    };
+    for (size_t s = 0; s < pl.steps.size(); ++s) {
+      const auto& la = pl.labels[pl.steps[s].a];
+      const auto& lb = pl.labels[pl.steps[s].b];
+      const auto& lc = pl.labels[L + s];
+      int nb = 0, nx = 0, ny = 0, nz = 0;
+      for (int x : la) {
+        if (has(lc, x)) (has(lb, x) ? nb : nx) += 1;
+        else ny += 1;
+      }
+      for (int x : lb)
+        if (!has(la, x)) (has(lc, x) ? nz : ny) += 1;
+      shapes[4 * s] = nb;
+      shapes[4 * s + 1] = nx;
+      shapes[4 * s + 2] = ny;
+      shapes[4 * s + 3] = nz;
+    }
+  });
+}
+
 extern "C" void qtc_plan_destroy(qtc_plan* p) { delete p; }
 
 // ---- batches --------------------------------------------------------------------
@@ -629,6 +656,73 @@ extern "C" qtc_status qtc_batch_stats(const qtc_batch* b, qtc_batch_info* info) 
       if (p.max_rank <= kMaxSmemRank) info->n_smem_networks += 1;
       else info->n_global_networks += 1;
     }
+  });
+}
+
+// Algorithmic bytes of one network's evaluation (forward; with want_grad
+// also the adjoint sweep's two contractions per step that needs them).
+static double network_cost(const Plan& p, bool want_grad) {
+  double cost = p.bytes_c64;
+  if (!want_grad) return cost;
+  const int L = (int)p.net.leaves.size(), S = (int)p.steps.size();
+  std::vector<char> need(L + S, 0);
+  for (int i = 0; i < L; ++i) need[i] = p.net.leaves[i].spec.slot >= 0;
+  for (int s = 0; s < S; ++s) need[L + s] = need[p.steps[s].a] || need[p.steps[s].b];
+  for (int s = 0; s < S; ++s) {
+    const double ec = std::ldexp(1.0, (int)p.labels[L + s].size());
+    for (int side = 0; side < 2; ++side) {
+      const int x = side ? p.steps[s].b : p.steps[s].a;
+      const int y = side ? p.steps[s].a : p.steps[s].b;
+      if (!need[x]) continue;
+      cost += 8.0 * (ec + std::ldexp(1.0, (int)p.labels[x].size()) +
+                     std::ldexp(1.0, (int)p.labels[y].size()));
+    }
+  }
+  return cost;
+}
+
+extern "C" qtc_status qtc_batch_partition(const qtc_batch* b, int n_parts, int want_grad,
+                                          int32_t* part_of_net, double* part_cost) {
+  return guarded([&] {
+    if (!b || !part_of_net) fail(QTC_ERR_INVALID, "null argument");
+    if (n_parts < 1) fail(QTC_ERR_INVALID, "%d parts", n_parts);
+    const int N = (int)b->plans.size();
+    std::vector<double> cost(N);
+    for (int i = 0; i < N; ++i) cost[i] = network_cost(b->plans[i], want_grad != 0);
+    // longest processing time first: the costliest network goes to the part
+    // with the least work so far (ties: the lower network, the lower part)
+    std::vector<int> order(N);
+    for (int i = 0; i < N; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<double> load(n_parts, 0.0);
+    for (int i : order) {
+      int best = 0;
+      for (int k = 1; k < n_parts; ++k)
+        if (load[k] < load[best]) best = k;
+      part_of_net[i] = best;
+      load[best] += cost[i];
+    }
+    if (part_cost)
+      for (int k = 0; k < n_parts; ++k) part_cost[k] = load[k];
+  });
+}
+
+extern "C" qtc_status qtc_batch_subset(const qtc_batch* b, const int32_t* nets, int k,
+                                       qtc_batch** out) {
+  return guarded([&] {
+    if (!b || !out || (k > 0 && !nets)) fail(QTC_ERR_INVALID, "null argument");
+    if (k < 1) fail(QTC_ERR_INVALID, "a subset of %d networks", k);
+    auto s = std::make_unique<qtc_batch>();
+    s->circuit = b->circuit;
+    s->qaoa_reduce = b->qaoa_reduce;
+    for (int j = 0; j < k; ++j) {
+      const int i = nets[j];
+      if (i < 0 || i >= (int)b->plans.size()) fail(QTC_ERR_INVALID, "network %d out of range", i);
+      s->plans.push_back(b->plans[i]);
+      s->obs_edges.push_back(b->obs_edges[i]);
+      s->weights.push_back(b->weights[i]);
+    }
+    *out = s.release();
   });
 }
 
@@ -1268,6 +1362,57 @@ extern "C" qtc_status qtc_contract(qtc_engine* e, const qtc_plan* p, const doubl
     out_re_im[1] = res[1];
     if (grad_re_im)
       for (int k = 0; k < 2 * P; ++k) grad_re_im[k] = res[2 + k];
+  });
+}
+
+// ---- answer strings (Section 3.3) ---------------------------------------------------
+
+extern "C" qtc_status qtc_answer_string(qtc_engine* e, const qtc_circuit* c,
+                                        const double* params, int dtype,
+                                        const qtc_plan_opts* opts, uint64_t tie_seed,
+                                        void* stream, uint8_t* bits_out, double* probs_out) {
+  return guarded([&] {
+    if (!e || !c || !bits_out || !probs_out) fail(QTC_ERR_INVALID, "null argument");
+    const int n = c->c.n;
+    if (n <= 0) fail(QTC_ERR_INVALID, "circuit without qubits");
+    if (c->c.n_params > 0 && !params) fail(QTC_ERR_INVALID, "null parameters");
+    SplitMix64 rng(tie_seed);
+    std::vector<uint8_t> bits(n, 2);
+    qtc_observable obs{};
+    obs.kind = QTC_OBS_PROJECTOR;
+    std::unique_ptr<qtc_plan> first;
+    double prev = 1.0;
+    for (int q = 0; q < n; ++q) {
+      // P(prefix, x_q = 0): qubits 0..q-1 projected on their chosen values,
+      // qubit q on |0>, the rest traced out; every network has one closing
+      // tensor per qubit, so all share the first one's contraction tree
+      bits[q] = 0;
+      obs.bits = bits.data();
+      auto plan = std::make_unique<qtc_plan>();
+      Network net = build_network(c->c, obs, false, true);
+      if (first) {
+        const Network& like = first->plan.net;
+        bool same = like.leaves.size() == net.leaves.size();
+        for (size_t i = 0; same && i < net.leaves.size(); ++i)
+          same = like.leaves[i].labels == net.leaves[i].labels;
+        if (!same) fail(QTC_ERR_INVALID, "internal: projector networks differ in structure");
+        plan->plan = first->plan;
+        plan->plan.net = std::move(net);
+      } else {
+        plan->plan = make_plan(net, opts ? *opts : default_opts());
+      }
+      double v[2] = {0.0, 0.0};
+      const qtc_status st = qtc_contract(e, plan.get(), params, dtype, stream, v, nullptr);
+      if (st != QTC_OK) fail(st, "%s", qtc_last_error());
+      const double p0 = v[0], p1 = prev - p0;
+      // the likelier value; a tie is broken by the seeded generator
+      const bool zero = p0 > p1 || (p0 == p1 && rng.below(2) == 0);
+      bits[q] = zero ? 0 : 1;
+      prev = zero ? p0 : p1;
+      bits_out[q] = bits[q];
+      probs_out[q] = prev;
+      if (!first) first = std::move(plan);
+    }
   });
 }
 

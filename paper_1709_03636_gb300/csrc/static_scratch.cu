@@ -28,22 +28,29 @@ struct DeviceSetup {
 std::mutex g_mutex;
 DeviceSetup g_setup[kMaxDevices];
 
-// Once per device, with that device current: the host-side name of the array
-// is only a stand-in, so resolve its device address and keep it.
+// With the device current: the host-side name of the array is only a
+// stand-in, so its device address is resolved here.  The lookup allocates
+// nothing and is repeated on every call, so that a module reloaded after a
+// device reset (the array may then sit elsewhere, with its contents lost)
+// is noticed: a new address forgets which program's tables were resident.
+// The device attributes are read once per device.
 DeviceSetup& setup_device(int dev) {
   if (dev < 0 || dev >= kMaxDevices) qtc::fail(QTC_ERR_INVALID, "device %d out of range", dev);
   DeviceSetup& s = g_setup[dev];
-  if (!s.scratch) {
-    void* p = nullptr;
-    qtc::cuda_check(cudaGetSymbolAddress(&p, g_static_scratch),
-                    "cudaGetSymbolAddress(static scratch)");
+  void* p = nullptr;
+  qtc::cuda_check(cudaGetSymbolAddress(&p, g_static_scratch),
+                  "cudaGetSymbolAddress(static scratch)");
+  if (s.sm_count == 0) {
     int v = 0;
     qtc::cuda_check(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev),
                     "shared memory limit");
     s.smem_optin = (size_t)v;
     qtc::cuda_check(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev), "SM count");
     s.sm_count = v;
+  }
+  if (p != s.scratch) {
     s.scratch = p;
+    s.resident = 0;
   }
   return s;
 }

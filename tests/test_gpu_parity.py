@@ -346,3 +346,30 @@ def test_gate_table_parameters_above_slot_32(engine):
         pm[k] -= h
         fd = (q.contract(engine, plan, pp, "c128") - q.contract(engine, plan, pm, "c128")) / (2 * h)
         assert abs(g128[k] - fd) < 1e-7, (k, g128[k], fd)
+
+
+@pytest.mark.parametrize("name", ["qaoa_p1_n12_d3", "qaoa_p1_n50_d3"])
+def test_sharded_parts_sum_to_the_whole_graph(engine, name):
+    """The multi-GPU split run part by part on one GPU: the library's
+    partition into 2 and 3 parts, each part's sub-batch evaluated on its own,
+    and the parts' <C> and gradient added in FP64 equal the whole batch's
+    (complex128, to rounding); the per-edge values are the same networks'."""
+    w = WORKLOADS[name]
+    edges = w.graph()
+    g, b = w.angles()
+    circ = q.Circuit.qaoa(w.n, edges, w.p)
+    full = q.Batch(circ, lightcone=w.lightcone, diag=w.diag, ordering=w.ordering)
+    C, per_edge, grad = q.qaoa_expectation(engine, full, g, b, "c128", want_grad=True)
+    for world in (2, 3):
+        tot_C, tot_g = 0.0, np.zeros(2 * w.p)
+        seen = []
+        for rank in range(world):
+            sub, mine = q.shard(full, rank, world)
+            c, pe, gr = q.qaoa_expectation(engine, sub, g, b, "c128", want_grad=True)
+            tot_C += c
+            tot_g += np.array(gr)
+            assert np.max(np.abs(np.array(pe) - np.array(per_edge)[mine])) < 1e-13
+            seen += mine
+        assert sorted(seen) == list(range(len(edges)))
+        assert abs(tot_C - C) < 1e-12
+        assert np.max(np.abs(tot_g - np.array(grad))) < 1e-12

@@ -138,3 +138,24 @@ def test_lightcone_density_matches_full(kind):
         for i in (0, 4, 9):
             got = dm.edge_zz_lightcone(n, edges, G[:p], B[:p], edges[i], kind, 0.15)
             assert abs(got - full[i]) < 1e-12
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_lightcone_fd_gradient_matches_adjoint_at_zero_noise(p):
+    """The light-cone central-difference gradient (the density oracle's only
+    gradient per edge) against the state-vector adjoint on the same ball
+    with no noise, and at p = 1 against the closed form's derivatives.  A
+    wrong divisor (h instead of 2h), a swapped sign or a parameter slot
+    mix-up would each miss these by far more than the O(h^2) truncation."""
+    from oracle import closed_form as cf
+    from oracle import lightcone as lc
+    n = 10
+    edges = random_regular_graph(n, 3, 8)
+    for i in (0, 5, 13):
+        e = edges[i]
+        got = dm.edge_grad_lightcone(n, edges, G[:p], B[:p], e, "dephase", 0.0)
+        _, ref = lc.edge_gradient(n, edges, G[:p], B[:p], e)
+        assert np.max(np.abs(got - np.asarray(ref))) < 1e-7 * max(np.max(np.abs(ref)), 1.0)
+        if p == 1:
+            dg, db = cf.zz_p1_grad(G[0], B[0], *cf.edge_params(n, edges, e))
+            assert abs(got[0] - dg) < 1e-7 and abs(got[1] - db) < 1e-7
