@@ -152,6 +152,16 @@ typedef struct qtc_program_info {
   int max_warp_steps;     /* warp steps of the longest network               */
   int n_solo_steps;       /* of the warp steps, those one op runs alone      */
   int stage_ops;          /* ops or warp steps a team stages at a time       */
+  /* graph executor: global intermediates and adjoints summed over networks,
+   * as placed (tensors whose live ranges do not meet share memory) and with
+   * a region of their own per tensor (what reuse saves) */
+  double net_global_bytes;
+  double net_global_bytes_unshared;
+  /* graph executor with the gradient: the most checkpoint segments of any
+   * network (1: every forward value stored for the adjoint sweep; k > 1: the
+   * network's stored values alone exceed the wave limit, so values used only
+   * inside one of k segments are dropped and recomputed by the sweep) */
+  int checkpoint_segments;
 } qtc_program_info;
 
 typedef struct qtc_engine qtc_engine;

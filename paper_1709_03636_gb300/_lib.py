@@ -46,7 +46,9 @@ class qtc_program_info(ctypes.Structure):
                 ("n_global_steps", c_int), ("n_smem_tasks", c_int), ("smem_bytes", c_int),
                 ("work_bytes", c_double), ("table_bytes", c_double), ("n_gemm_steps", c_int),
                 ("warp_teams", c_int), ("n_ops", c_int), ("n_warp_steps", c_int),
-                ("max_warp_steps", c_int), ("n_solo_steps", c_int), ("stage_ops", c_int)]
+                ("max_warp_steps", c_int), ("n_solo_steps", c_int), ("stage_ops", c_int),
+                ("net_global_bytes", c_double), ("net_global_bytes_unshared", c_double),
+                ("checkpoint_segments", c_int)]
 
 
 # name -> (restype, argtypes)

@@ -1212,6 +1212,9 @@ extern "C" qtc_status qtc_batch_program_info(qtc_batch* b, int dtype, int want_g
                   sizeof(WaitDev) * w.waits.size();
       }
       info->work_bytes = (double)hp.max_global_elems * elem_bytes(dtype);
+      info->net_global_bytes = (double)hp.sum_global_elems * elem_bytes(dtype);
+      info->net_global_bytes_unshared = (double)hp.sum_unshared_elems * elem_bytes(dtype);
+      info->checkpoint_segments = hp.max_checkpoint_segments;
     } else {
       info->n_waves = 1;
       info->n_tasks = info->n_smem_tasks = (int)hp.tasks.size();

@@ -275,6 +275,26 @@ void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
     if (!graphs[i].fits)
       fail(QTC_ERR_UNSUPPORTED, "network %d (max rank %d): %s", i, plans[i].max_rank,
            graphs[i].why.c_str());
+    // a network whose stored values exceed the wave limit on their own:
+    // checkpoint segments, recomputed by the adjoint sweep (fewest that fit)
+    const uint64_t cap_elems = wave_cap_bytes / elem;
+    if (hp.want_grad && ((graphs[i].global_elems + 63) & ~uint64_t(63)) > cap_elems) {
+      for (int k : {2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64}) {
+        GraphLimits lk = li;
+        lk.checkpoint_segments = k;
+        NetGraph g = lower_graph(plans[i], leaf_gate[i], val_off, der_off, hp.table_elems,
+                                 true, lk);
+        if (!g.fits) break;
+        const bool ok = ((g.global_elems + 63) & ~uint64_t(63)) <= cap_elems;
+        if (ok || g.global_elems < graphs[i].global_elems) graphs[i] = std::move(g);
+        if (ok) break;
+      }
+    }
+    check_global_placement(graphs[i]);
+    hp.max_checkpoint_segments = std::max(hp.max_checkpoint_segments,
+                                          graphs[i].checkpoint_segments);
+    hp.sum_global_elems += graphs[i].global_elems;
+    hp.sum_unshared_elems += graphs[i].unshared_elems;
   }
   // waves: largest networks first, first fit under the cap
   const uint64_t cap = wave_cap_bytes / elem;

@@ -370,6 +370,154 @@ bool encode_tstep(TStep& t, const std::vector<int>& lc, const std::vector<int>& 
   return true;
 }
 
+// ---- global work-buffer placement by live range ------------------------------
+
+namespace {
+
+struct GRef {
+  uint32_t* off;   // element offset in the work buffer (a buffer's start)
+  bool write;
+};
+
+// Every work-buffer reference of a unit, with whether the unit writes it.
+std::vector<GRef> unit_refs(GUnit& u) {
+  std::vector<GRef> r;
+  if (u.kind == GT_SMEM) {
+    for (SOp& op : u.ops) {
+      if (op.flags & SOPF_OUT_GLOBAL) r.push_back({&op.out, true});
+      if (op.flags & SOPF_IN1_GLOBAL) r.push_back({&op.in1, false});
+      if (op.flags & SOPF_IN2_GLOBAL) r.push_back({&op.in2, false});
+    }
+  } else if (u.kind == GT_CHUNK) {
+    GStep& st = u.step;
+    if (!(st.flags & GSF_A_TABLE)) r.push_back({&st.a_off, false});
+    if (!(st.flags & GSF_B_TABLE)) r.push_back({&st.b_off, false});
+    if (!(st.flags & GSF_LEAFGRAD)) r.push_back({&st.c_off, true});
+    if (st.flags & GSF_SPLIT) r.push_back({&st.partial_off, true});
+  } else {
+    r.push_back({&u.tstep.a_off, false});
+    r.push_back({&u.tstep.b_off, false});
+    r.push_back({&u.tstep.c_off, true});
+  }
+  return r;
+}
+
+}  // namespace
+
+void place_global_buffers(NetGraph& ng, const std::vector<uint64_t>& vbase,
+                          const std::vector<uint64_t>& vsize) {
+  const int B = (int)vbase.size();
+  const int U = (int)ng.units.size();
+  if (B == 0) return;
+  auto buffer_of = [&](uint32_t off) {
+    const int b = (int)(std::upper_bound(vbase.begin(), vbase.end(), (uint64_t)off) -
+                        vbase.begin()) - 1;
+    if (b < 0 || off >= vbase[b] + vsize[b]) fail(QTC_ERR_INVALID, "internal: global offset %u", off);
+    return b;
+  };
+  // live range of each buffer in unit (creation) order, its writers and all
+  // units that touch it
+  std::vector<int> first(B, -1), last(B, -1);
+  std::vector<std::vector<int>> writers(B), users(B);
+  for (int i = 0; i < U; ++i)
+    for (const GRef& r : unit_refs(ng.units[i])) {
+      const int b = buffer_of(*r.off);
+      if (first[b] < 0) first[b] = i;
+      last[b] = i;
+      if (users[b].empty() || users[b].back() != i) users[b].push_back(i);
+      if (r.write && (writers[b].empty() || writers[b].back() != i)) writers[b].push_back(i);
+    }
+  // first fit, largest buffers first; two buffers share memory only when
+  // their live ranges are disjoint
+  std::vector<int> order;
+  for (int b = 0; b < B; ++b)
+    if (first[b] >= 0) order.push_back(b);
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    if (vsize[a] != vsize[b]) return vsize[a] > vsize[b];
+    return a < b;
+  });
+  std::vector<uint64_t> at(B, 0);
+  std::vector<int> placed;
+  uint64_t peak = 0;
+  for (int b : order) {
+    std::vector<std::pair<uint64_t, uint64_t>> busy;
+    for (int q : placed)
+      if (!(last[q] < first[b] || last[b] < first[q])) busy.push_back({at[q], at[q] + vsize[q]});
+    std::sort(busy.begin(), busy.end());
+    uint64_t pos = 0;
+    for (auto& iv : busy) {
+      if (pos + vsize[b] <= iv.first) break;
+      pos = std::max(pos, iv.second);
+    }
+    at[b] = pos;
+    placed.push_back(b);
+    peak = std::max(peak, pos + vsize[b]);
+  }
+  // write after read: a buffer's writers start only after every unit that
+  // touched earlier buffers in the same memory has finished
+  for (int b : placed)
+    for (int q : placed) {
+      if (q == b || !(last[q] < first[b])) continue;
+      if (at[q] >= at[b] + vsize[b] || at[b] >= at[q] + vsize[q]) continue;
+      for (int w : writers[b])
+        for (int u : users[q]) ng.units[w].deps.push_back(u);
+    }
+  // depths again (dependencies still point to earlier units)
+  for (int i = 0; i < U; ++i) {
+    GUnit& u = ng.units[i];
+    std::sort(u.deps.begin(), u.deps.end());
+    u.deps.erase(std::unique(u.deps.begin(), u.deps.end()), u.deps.end());
+    int depth = 0;
+    for (int d : u.deps) {
+      if (d >= i) fail(QTC_ERR_INVALID, "internal: a dependency on a later unit");
+      depth = std::max(depth, ng.units[d].depth + 1);
+    }
+    u.depth = depth;
+  }
+  for (int i = 0; i < U; ++i)
+    for (const GRef& r : unit_refs(ng.units[i])) {
+      const int b = buffer_of(*r.off);
+      *r.off = (uint32_t)(at[b] + (*r.off - vbase[b]));
+    }
+  ng.global_elems = peak;
+  ng.buffers.clear();
+  for (int b : placed) ng.buffers.push_back({at[b], vsize[b], first[b], last[b], writers[b], users[b]});
+}
+
+// Host check of a placement: every pair of buffers that share memory is
+// ordered (all units touching the earlier one are ancestors of every writer
+// of the later one) and no two live buffers overlap.
+void check_global_placement(const NetGraph& ng) {
+  const int U = (int)ng.units.size();
+  const int W = (U + 63) / 64;
+  std::vector<uint64_t> anc((size_t)U * W, 0);
+  for (int i = 0; i < U; ++i)
+    for (int d : ng.units[i].deps) {
+      uint64_t* a = &anc[(size_t)i * W];
+      const uint64_t* ad = &anc[(size_t)d * W];
+      for (int k = 0; k < W; ++k) a[k] |= ad[k];
+      a[d / 64] |= 1ull << (d % 64);
+    }
+  auto is_anc = [&](int a, int of) { return (anc[(size_t)of * W + a / 64] >> (a % 64)) & 1; };
+  const auto& bs = ng.buffers;
+  for (size_t x = 0; x < bs.size(); ++x)
+    for (size_t y = 0; y < bs.size(); ++y) {
+      if (x == y) continue;
+      const auto& p = bs[x];
+      const auto& q = bs[y];
+      if (p.at >= q.at + q.size || q.at >= p.at + p.size) continue;
+      if (!(p.last < q.first))
+        if (!(q.last < p.first))
+          fail(QTC_ERR_INVALID, "internal: live global buffers share memory");
+      if (p.last < q.first)
+        for (int w : q.writers)
+          for (int u : p.users)
+            if (u != w && !is_anc(u, w))
+              fail(QTC_ERR_INVALID, "internal: a write to reused memory is not ordered after "
+                                    "the earlier reads");
+    }
+}
+
 NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
                      const std::vector<uint32_t>& gate_val_off,
                      const std::vector<uint32_t>& gate_der_off, uint32_t table_elems,
@@ -417,10 +565,16 @@ NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
   for (int s = 0; s < S; ++s)
     if (bigstep[s] || (sub_root[sub[s]] == s && L + s != root)) in_global[L + s] = 1;
   std::vector<int64_t> val_g(T, -1), grad_g(T, -1);
+  // Every global tensor first gets a region of its own in a virtual layout
+  // (vbase, vsize); place_global_buffers then overlaps regions whose live
+  // ranges do not meet and rewrites the offsets.
   uint64_t gsize = 0;
+  std::vector<uint64_t> vbase, vsize;
   auto galloc = [&](uint64_t elems) {
     const uint64_t at = gsize;
-    gsize += (elems + 63) & ~uint64_t(63);
+    vbase.push_back(at);
+    vsize.push_back((elems + 63) & ~uint64_t(63));
+    gsize += vsize.back();
     return (int64_t)at;
   };
   for (int t = L; t < T; ++t)
@@ -659,9 +813,75 @@ NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
     producer_grad[root] = id;
   }
 
+  // ---- checkpoint segments (gradient runs whose stored values exceed the cap)
+  // The steps that write global tensors are cut, in step order, into
+  // segments of about equal output size.  A global value used by a later
+  // segment is a checkpoint and stays stored; one whose forward consumer is in
+  // its own segment (the last segment excepted) is dropped after that use and
+  // computed again when the adjoint sweep reaches its segment, so only the
+  // checkpoints and one segment's values are held at a time.
+  const int n_seg = want_grad ? std::max(1, lim.checkpoint_segments) : 1;
+  ng.checkpoint_segments = n_seg;
+  std::vector<int> seg(S, 0);
+  std::vector<char> dropped(T, 0);
+  if (n_seg > 1) {
+    auto produces = [&](int s) { return bigstep[s] || (sub_root[sub[s]] == s && in_global[L + s]); };
+    double total = 0;
+    for (int s = 0; s < S; ++s)
+      if (produces(s)) total += (double)size(L + s);
+    double run = 0;
+    int j = 0;
+    for (int s = 0; s < S; ++s) {
+      if (!bigstep[s] && sub_root[sub[s]] != s) continue;
+      seg[s] = j;
+      if (produces(s)) {
+        run += (double)size(L + s);
+        if (run >= (j + 1) * total / n_seg && j < n_seg - 1) ++j;
+      }
+    }
+    auto seg_of = [&](int s) { return bigstep[s] ? seg[s] : seg[sub_root[sub[s]]]; };
+    for (int s = 0; s < S; ++s) {
+      const int t = L + s;
+      if (!in_global[t] || t == root || !produces(s)) continue;
+      const int c = consumer[t];
+      if (seg[s] < n_seg - 1 && c >= 0 && seg_of(c) == seg[s]) dropped[t] = 1;
+    }
+  }
+  // the segment's dropped values again, in step order, into fresh buffers
+  auto recompute_segment = [&](int j) -> bool {
+    for (int s = 0; s < S; ++s) {
+      if (seg[s] != j || !dropped[L + s]) continue;
+      if (bigstep[s]) {
+        const Step& st = plan.steps[s];
+        std::vector<int> deps;
+        Ref ra = value_ref_global(st.a, deps);
+        Ref rb = value_ref_global(st.b, deps);
+        val_g[L + s] = galloc(size(L + s));
+        const int id = gstep_unit(L + s, plan.labels[L + s], st.a, plan.labels[st.a], ra, st.b,
+                                  plan.labels[st.b], rb, val_g[L + s], deps, -1);
+        if (id < 0) return false;
+        producer_val[L + s] = id;
+      } else if (sub_root[sub[s]] == s) {
+        val_g[L + s] = galloc(size(L + s));
+        if (!subtree_unit(sub[s], false)) {
+          ng.fits = false;
+          ng.why = "a subtree does not fit in shared memory";
+          return false;
+        }
+      }
+    }
+    ng.recomputed_segments += 1;
+    return true;
+  };
+
   // ---- adjoint sweep, in reverse step order ----
   if (want_grad && need_grad[root]) {
+    int entered = n_seg - 1;
     for (int s = S - 1; s >= 0; --s) {
+      if (n_seg > 1 && (bigstep[s] || sub_root[sub[s]] == s) && seg[s] < entered) {
+        entered = seg[s];
+        if (!recompute_segment(entered)) return ng;
+      }
       if (bigstep[s]) {
         const int c = L + s;
         const Step& st = plan.steps[s];
@@ -687,7 +907,10 @@ NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
   for (const GUnit& u : ng.units)
     for (int d : u.deps)
       if (d < 0) return fail_net("internal: a dependency without a producer");
+  if (gsize >> 32) return fail_net("a network's global intermediates exceed 2^32 elements");
   ng.global_elems = gsize;
+  ng.unshared_elems = gsize;
+  if (lim.reuse_global) place_global_buffers(ng, vbase, vsize);
   (void)sub_done;
   return ng;
 }

@@ -187,6 +187,8 @@ struct GraphLimits {
   uint64_t subtree_elems = 4096;     // elements of all values of one subtree
   uint32_t arena_elems = 8192;       // shared-memory arena of one subtree task
   bool tensor_cores = false;         // split-BF16 GEMM tasks for GEMM-shaped steps
+  bool reuse_global = true;          // place global tensors by live range (memory reuse)
+  int checkpoint_segments = 1;       // > 1: adjoint recomputes dropped values per segment
 };
 
 // A unit is one shared-memory subtree task or one global step (its chunks);
@@ -202,12 +204,33 @@ struct GUnit {
   uint32_t target = 1;
 };
 
+// A global tensor's placement: element offset and size in the network's
+// work-buffer region, its live range over the units (creation order), the
+// units that write it and every unit that touches it.
+struct GBuffer {
+  uint64_t at, size;
+  int first, last;
+  std::vector<int> writers, users;
+};
+
 struct NetGraph {
   std::vector<GUnit> units;
   uint64_t global_elems = 0;         // global buffers of this network (elements)
+  uint64_t unshared_elems = 0;       // the same with a region per tensor (no reuse)
+  std::vector<GBuffer> buffers;      // placement by live range (empty without reuse)
+  int checkpoint_segments = 1;       // segments the adjoint sweep recomputes by
+  int recomputed_segments = 0;       // of which recomputed (all but the last)
   bool fits = true;
   std::string why;
 };
+
+// Overlaps the network's global tensors whose live ranges (in unit order) are
+// disjoint, adds the write-after-read dependencies that reuse needs and
+// rewrites every work-buffer offset; global_elems becomes the peak.
+void place_global_buffers(NetGraph& ng, const std::vector<uint64_t>& vbase,
+                          const std::vector<uint64_t>& vsize);
+// Host check of that placement (ordering of every reuse; no live overlap).
+void check_global_placement(const NetGraph& ng);
 
 // Lowers one plan to units: maximal subtrees of small steps run in shared
 // memory (and are recomputed for the adjoint sweep), the other steps are
@@ -280,6 +303,9 @@ struct HostProgram {
   std::vector<WaveHost> waves;
   uint32_t work_bytes = 0;         // graph form: shared memory after the table
   uint64_t max_global_elems = 0;
+  uint64_t sum_global_elems = 0;   // over networks: each network's placed peak
+  uint64_t sum_unshared_elems = 0; // over networks: a region per global tensor
+  int max_checkpoint_segments = 1; // most checkpoint segments of any network
   uint32_t max_counters = 0;
   bool tensor_cores = false;       // some wave has tensor-core GEMM tasks
 };

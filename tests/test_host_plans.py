@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 from oracle import statevector as sv
-from synth import random_regular_graph
+from synth import WORKLOADS, random_regular_graph
 
 q = pytest.importorskip("paper_1709_03636_gb300")
 
@@ -503,3 +503,51 @@ def test_degenerate_graph_shapes(name, p):
                 info = batch.program_info(dtype, True, force_graph=True, small_rank=small_rank,
                                           max_wave_bytes=1 << 22)
                 assert info["graph"] == 1 and info["n_tasks"] >= len(edges)
+
+
+def test_global_buffers_reuse_memory_by_live_range():
+    """Graph-executor intermediates and adjoints are placed by live range:
+    for p=3 n=60 with the gradient the networks' placed peaks sum to well
+    under their tensors' total (the placement and every write-after-read
+    ordering it needs are checked on the host when the program is built),
+    and the whole graph fits one launch under the default 8 GiB limit."""
+    w = WORKLOADS["qaoa_p3_n60_d4"]
+    edges = w.graph()
+    batch = q.Batch(q.Circuit.qaoa(w.n, edges, w.p), ordering="lg")
+    fwd = batch.program_info("c64", False)
+    grad = batch.program_info("c64", True)
+    for info in (fwd, grad):
+        assert info["graph"] == 1
+        assert 0 < info["net_global_bytes"] < 0.75 * info["net_global_bytes_unshared"]
+        assert info["work_bytes"] <= info["net_global_bytes"]
+    assert grad["n_waves"] == 1 and grad["work_bytes"] <= 8 << 30
+    # forward only, a tensor is dead after the step that consumes it
+    assert fwd["net_global_bytes"] < 0.6 * fwd["net_global_bytes_unshared"]
+
+
+def test_checkpoint_segments_when_one_network_exceeds_the_limit():
+    """With the gradient, a network whose stored values alone exceed the wave
+    limit is lowered with checkpoint segments: values used only inside one
+    segment are dropped after their forward use and recomputed by the
+    adjoint sweep.  The peak then fits the limit, every reuse of memory is
+    ordered (checked when the program is built), and a limit below what any
+    segmentation reaches is refused with QTC_ERR_ARENA."""
+    w = WORKLOADS["qaoa_p3_n60_d4"]
+    edges = w.graph()
+    full = q.Batch(q.Circuit.qaoa(w.n, edges, w.p), ordering="lg")
+    for i in (9, 42, 60):
+        one = full.subset([i])
+        base = one.program_info("c64", True)
+        assert base["checkpoint_segments"] == 1
+        cap = int(0.9 * base["net_global_bytes"])
+        info = one.program_info("c64", True, max_wave_bytes=cap)
+        assert info["checkpoint_segments"] > 1
+        assert info["net_global_bytes"] <= cap
+        # the recomputed forward steps are extra tasks
+        assert info["n_tasks"] > base["n_tasks"]
+        # forward only: nothing to recompute, the limit applies as before
+        fwd = one.program_info("c64", False)
+        assert fwd["checkpoint_segments"] == 0 or fwd["checkpoint_segments"] == 1
+        with pytest.raises(q.QtcError, match="ARENA"):
+            one.program_info("c64", True, max_wave_bytes=max(1 << 20, int(0.3 * fwd[
+                "net_global_bytes"])))
