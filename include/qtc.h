@@ -392,6 +392,25 @@ qtc_status qtc_engine_set_graph_options(qtc_engine* e, int force_graph, int smal
 qtc_status qtc_engine_set_task_options(qtc_engine* e, int task_terms_log2, int subtree_bytes,
                                        int warp_teams, int graph_hi_occupancy);
 
+/* Tile form of the graph executor's global steps (tuning and tests): 0 keeps
+ * every step on the row and split chunk paths; 1 (default) stages the steps
+ * with both operands in global memory, and the long reductions, through
+ * shared memory in tiles (16-byte copies of each operand's tile, contraction
+ * in shared memory and registers); 2 does so for every step that tiles.
+ * Invalidates prepared programs.  QTC_ERR_INVALID outside 0..2. */
+qtc_status qtc_engine_set_tile_mode(qtc_engine* e, int mode);
+
+/* Host-only check of the tile lowering (no GPU call): builds the batch's
+ * graph program with force_graph, small_rank and tile_mode as above and, for
+ * every tile step with at most 2^max_bits multiply-adds, emulates its tile
+ * copies, thread decomposition and reductions on seeded random operands and
+ * compares the result with the plain contraction over the step's bit maps.
+ * max_err: host, 1 double (largest absolute difference); n_checked: host,
+ * 1 int (steps compared). */
+qtc_status qtc_selftest_tile_steps(qtc_batch* b, int dtype, int want_grad, int force_graph,
+                                   int small_rank, int tile_mode, int max_bits,
+                                   double* max_err, int32_t* n_checked);
+
 /* Launches a one-task program whose task waits for a counter nothing ever
  * signals, so that the bounded wait expires after the engine's wait limit and
  * the kernel returns normally.  Returns QTC_ERR_TIMEOUT when the bound works

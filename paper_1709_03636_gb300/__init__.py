@@ -116,6 +116,12 @@ class Engine(_Handle):
         self.task_options = (int(task_terms_log2), int(subtree_bytes), int(warp_teams),
                              bool(graph_hi_occupancy))
 
+    def set_tile_mode(self, mode=1):
+        """Graph executor: 0 row/split chunk paths only, 1 tiles for steps
+        with both operands in global memory and long reductions, 2 tiles for
+        every step that tiles (footprints staged through shared memory)."""
+        check(lib.qtc_engine_set_tile_mode(self.ptr, int(mode)))
+
     @property
     def last_launches(self) -> int:
         return lib.qtc_engine_last_launches(self.ptr)

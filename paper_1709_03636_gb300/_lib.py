@@ -92,6 +92,9 @@ SIGNATURES = {
                                             c_void_p]),
     "qtc_engine_set_limits": (c_int, [c_void_p, c_size_t, c_double]),
     "qtc_selftest_wait_timeout": (c_int, [c_void_p, c_void_p]),
+    "qtc_engine_set_tile_mode": (c_int, [c_void_p, c_int]),
+    "qtc_selftest_tile_steps": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int,
+                                        P(c_double), P(c_int32)]),
     "qtc_engine_set_graph_options": (c_int, [c_void_p, c_int, c_int]),
     "qtc_engine_set_task_options": (c_int, [c_void_p, c_int, c_int, c_int, c_int]),
     "qtc_batch_launch_info": (c_int, [c_void_p, c_void_p, c_int, c_int, P(c_int32)]),

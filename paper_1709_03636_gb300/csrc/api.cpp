@@ -263,6 +263,41 @@ extern "C" qtc_status qtc_engine_set_task_options(qtc_engine* e, int task_terms_
   });
 }
 
+extern "C" qtc_status qtc_engine_set_tile_mode(qtc_engine* e, int mode) {
+  return guarded([&] {
+    if (!e) fail(QTC_ERR_INVALID, "null engine");
+    if (mode < 0 || mode > 2) fail(QTC_ERR_INVALID, "tile mode %d (0..2)", mode);
+    e->options.tile_mode = mode;
+    e->generation += 1;
+    e->used = 0;
+    e->work = 0;
+  });
+}
+
+extern "C" qtc_status qtc_selftest_tile_steps(qtc_batch* b, int dtype, int want_grad,
+                                              int force_graph, int small_rank, int tile_mode,
+                                              int max_bits, double* max_err, int32_t* n_checked) {
+  return guarded([&] {
+    if (!b || !max_err || !n_checked) fail(QTC_ERR_INVALID, "null argument");
+    ProgramOptions opts;
+    opts.force_graph = force_graph != 0;
+    opts.small_rank = small_rank;
+    opts.tile_mode = tile_mode;
+    const HostProgram& hp = host_program(b, dtype, want_grad, max_dynamic_smem(232448), opts);
+    double err = 0;
+    int n = 0;
+    uint64_t seed = 1;
+    for (const WaveHost& w : hp.waves)
+      for (const GStep& st : w.steps)
+        if ((st.flags & GSF_TILE) && st.rc + st.ry <= max_bits) {
+          err = std::max(err, emulate_tile_step(st, seed++));
+          ++n;
+        }
+    *max_err = err;
+    *n_checked = n;
+  });
+}
+
 extern "C" qtc_status qtc_selftest_wait_timeout(qtc_engine* e, void* stream) {
   qtc_status result = QTC_OK;
   qtc_status st = guarded([&] {

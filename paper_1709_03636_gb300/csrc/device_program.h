@@ -257,7 +257,40 @@ enum GStepFlag : uint16_t {
   GSF_A_TABLE = 1,     // operand A is a gate table entry (shared memory)
   GSF_B_TABLE = 2,
   GSF_SPLIT = 4,       // chunks split the summed index; the last chunk reduces
-  GSF_LEAFGRAD = 8     // output is dS/dleaf: reduce it against d(leaf)/dparam
+  GSF_LEAFGRAD = 8,    // output is dS/dleaf: reduce it against d(leaf)/dparam
+  GSF_TILE = 16        // staged through shared memory in tiles (the tile fields)
+};
+
+// Tile form of a global step.  The step's labels split into tile labels
+// (varying inside one task) and outer labels: outer output labels (one task
+// per value o) and outer summed labels (values q, looped over inside a task,
+// or cut into chunks whose partial sums the last chunk adds when the whole
+// output lies in the tile).  For every q a task copies the A and B elements
+// of its tile (an operand's footprint: the tile labels it holds, in its own
+// bit order, so that its lowest bits come first and the copies are
+// contiguous 16-byte transfers) into shared memory, contracts there, and
+// finally copies its C tile (footprint likewise) out.  Tile index bits:
+// [0, 5) lanes, [5, 8) warps, [8, 8 + kout) output labels held in registers,
+// the rest summed labels looped over in registers.  Lane and warp bits that
+// are summed labels are reduced by shuffles and through shared memory.
+constexpr int kTileMaxOut = 2;        // output bits held in registers
+constexpr int kTileMaxRegSum = 8;     // summed bits looped over in registers
+constexpr uint32_t kTileBudgetBytes = 40960;   // footprints per team
+
+struct GTileMap {
+  uint8_t nv, nfa, nfb, nfc;  // tile bits; footprint bits of A, B, C
+  uint8_t no, nq;             // outer output bits, outer summed bits
+  uint8_t kout, ns;           // register output bits, register summed bits
+  uint32_t q_per_chunk;       // outer summed values per chunk (split)
+  uint32_t o_per_chunk;       // outer output values per chunk (not split)
+  uint8_t sum_lane_mask;      // lane bits that are summed labels
+  uint8_t sum_warp_mask;      // warp bits that are summed labels
+  uint8_t pad[6];
+  GRuns tfa, tfb, tfc;        // tile index -> footprint index (table operand:
+                              //   -> its element index)
+  GRuns ffa, ffb, ffc;        // footprint index -> operand element index
+  GRuns oa, ob, oc;           // outer output index -> operand element index
+  GRuns qa, qb;               // outer summed index -> operand element index
 };
 
 // One contraction C = sum_y A * B in global memory (Eq. 1), cut into chunks.
@@ -279,6 +312,7 @@ struct alignas(16) GStep {
   uint8_t rc, ry, pad0, pad1;
   GRuns ca, cb;             // output bits -> A bits, B bits
   GRuns ya, yb;             // summed bits -> A bits, B bits
+  GTileMap tile;            // GSF_TILE
 };
 
 // One complex GEMM C[b][m][n] = sum_k A[b][m][k] B[b][k][n] (Eq. 1 with the

@@ -223,6 +223,226 @@ __device__ __forceinline__ void rows_unrolled(const T* A, const T* B, T* C, cons
   }
 }
 
+// ---- tile tasks: footprints staged through shared memory -------------------
+
+// Copies the footprint (2^nf elements) of an operand at element offset
+// `base`: footprint index j -> operand element base | ff(j).  Index bit 0 is
+// the operand's bit 0, so element pairs (complex64) are contiguous.
+template <typename T>
+__device__ __forceinline__ void stage_footprint(T* dst, const T* src, uint32_t base,
+                                                const GRuns& ff, uint32_t nf, uint32_t tid,
+                                                uint32_t nthreads) {
+  constexpr uint32_t per = 16 / sizeof(T);   // elements per 16-byte copy
+  const uint32_t n = 1u << nf;
+  if (per == 2 && nf == 0) {
+    if (tid == 0) dst[0] = src[base];
+    return;
+  }
+  for (uint32_t j = tid * per; j < n; j += nthreads * per)
+    cp_async16(dst + j, src + (base | runs_offset(ff, j)));
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_xor_c(T v, int m);
+template <>
+__device__ __forceinline__ float2 shfl_xor_c<float2>(float2 v, int m) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+template <>
+__device__ __forceinline__ double2 shfl_xor_c<double2>(double2 v, int m) {
+  return make_double2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+// The contraction of one outer output value o over outer summed values
+// [q0, q1): 2^kOut register accumulators per thread, summed over the tile's
+// register-summed bits, then over summed lane and warp bits; the owners
+// write the C tile into shared memory (Cs, footprint order).
+template <typename T, int kTeams, int kOut>
+__device__ void tile_contract(const GStep& st, const T* Ag, const T* Bg, T* As, T* Bs, T* Cs,
+                              T* red, const uint2* soff, uint32_t o, uint32_t q0, uint32_t q1,
+                              const GTeam<kTeams>& team) {
+  const GTileMap& tm = st.tile;
+  const bool sa = !(st.flags & GSF_A_TABLE), sb = !(st.flags & GSF_B_TABLE);
+  const uint32_t tid = team.tid, lane = tid & 31u, warp = tid >> 5;
+  const uint32_t a_lw = runs_offset(tm.tfa, tid), b_lw = runs_offset(tm.tfb, tid);
+  uint32_t ak[1 << kOut], bk[1 << kOut];
+#pragma unroll
+  for (int k = 0; k < (1 << kOut); ++k) {
+    ak[k] = a_lw | runs_offset(tm.tfa, (uint32_t)k << 8);
+    bk[k] = b_lw | runs_offset(tm.tfb, (uint32_t)k << 8);
+  }
+  T acc[1 << kOut];
+#pragma unroll
+  for (int k = 0; k < (1 << kOut); ++k) acc[k] = czero<T>();
+  const uint32_t abase = runs_offset(tm.oa, o), bbase = runs_offset(tm.ob, o);
+  const uint32_t ns = 1u << tm.ns;
+  for (uint32_t q = q0; q < q1; ++q) {
+    const uint32_t aq = abase | runs_offset(tm.qa, q), bq = bbase | runs_offset(tm.qb, q);
+    if (sa) stage_footprint(As, Ag, aq, tm.ffa, tm.nfa, tid, team.size);
+    if (sb) stage_footprint(Bs, Bg, bq, tm.ffb, tm.nfb, tid, team.size);
+    cp_async_wait_all();
+    team.sync();
+    const T* Ab = sa ? As : Ag + aq;
+    const T* Bb = sb ? Bs : Bg + bq;
+    uint32_t s = 0;
+    for (; s + 1 < ns; s += 2) {
+      const uint2 o0 = soff[s], o1 = soff[s + 1];
+#pragma unroll
+      for (int k = 0; k < (1 << kOut); ++k) {
+        const T a0 = Ab[ak[k] | o0.x], b0 = Bb[bk[k] | o0.y];
+        const T a1 = Ab[ak[k] | o1.x], b1 = Bb[bk[k] | o1.y];
+        acc[k] = cfma(a1, b1, cfma(a0, b0, acc[k]));
+      }
+    }
+    for (; s < ns; ++s) {
+      const uint2 o0 = soff[s];
+#pragma unroll
+      for (int k = 0; k < (1 << kOut); ++k) acc[k] = cfma(Ab[ak[k] | o0.x], Bb[bk[k] | o0.y], acc[k]);
+    }
+    team.sync();   // the footprints are refilled (or reused) next
+  }
+  // summed lane bits: butterfly over those bits, every lane gets the sum
+#pragma unroll
+  for (int m = 0; m < 5; ++m)
+    if ((tm.sum_lane_mask >> m) & 1u) {
+#pragma unroll
+      for (int k = 0; k < (1 << kOut); ++k) acc[k] = cadd(acc[k], shfl_xor_c(acc[k], 1 << m));
+    }
+  const bool lane_owner = (lane & tm.sum_lane_mask) == 0;
+  if (tm.sum_warp_mask) {
+#pragma unroll
+    for (int k = 0; k < (1 << kOut); ++k) red[((uint32_t)k << 8) | tid] = acc[k];
+    team.sync();
+    if ((warp & tm.sum_warp_mask) == 0 && lane_owner) {
+#pragma unroll
+      for (int k = 0; k < (1 << kOut); ++k) {
+        T sum = czero<T>();
+        for (uint32_t w2 = 0; w2 < 8; ++w2)
+          if ((w2 & ~(uint32_t)tm.sum_warp_mask) == warp) sum = cadd(sum, red[((uint32_t)k << 8) | (w2 << 5) | lane]);
+        acc[k] = sum;
+      }
+    }
+  }
+  if ((warp & tm.sum_warp_mask) == 0 && lane_owner) {
+    const uint32_t c_lw = runs_offset(tm.tfc, tid);
+#pragma unroll
+    for (int k = 0; k < (1 << kOut); ++k) Cs[c_lw | runs_offset(tm.tfc, (uint32_t)k << 8)] = acc[k];
+  }
+  team.sync();
+}
+
+// A tile task: for each outer output value of the chunk (or, split, the
+// chunk's outer summed values) contract the tile, then copy the C tile out
+// (or into the chunk's partial slot; the last chunk of a split step adds the
+// partials in chunk order).
+template <typename T, int kTeams>
+__device__ void run_tile(const GraphProgDev& prog, const GTask& task, T* table,
+                         unsigned char* work, const GStep& st, int& s_last,
+                         const GTeam<kTeams>& team) {
+  const GTileMap& tm = st.tile;
+  const bool sa = !(st.flags & GSF_A_TABLE), sb = !(st.flags & GSF_B_TABLE);
+  const bool split = (st.flags & GSF_SPLIT) != 0;
+  T* gb = reinterpret_cast<T*>(prog.gbase);
+  const T* Ag = sa ? gb + st.a_off : table + st.a_off;
+  const T* Bg = sb ? gb + st.b_off : table + st.b_off;
+  constexpr uint32_t min_fp = sizeof(T) == 8 ? 2 : 1;
+  const uint32_t fa = sa ? max(min_fp, 1u << tm.nfa) : 0, fb = sb ? max(min_fp, 1u << tm.nfb) : 0;
+  uint32_t ab = fa + fb;
+  if (tm.sum_warp_mask) ab = max(ab, 256u << tm.kout);
+  const uint32_t fc = max(min_fp, 1u << tm.nfc);
+  T* As = reinterpret_cast<T*>(work);
+  T* Bs = As + fa;
+  T* Cs = As + ab;
+  uint2* soff = reinterpret_cast<uint2*>(work + (((size_t)(ab + fc) * sizeof(T) + 15) & ~size_t(15)));
+  const uint32_t tid = team.tid;
+  const uint32_t shift = 8u + tm.kout;
+  for (uint32_t s = tid; s < (1u << tm.ns); s += team.size)
+    soff[s] = make_uint2(runs_offset(tm.tfa, s << shift), runs_offset(tm.tfb, s << shift));
+  team.sync();
+  const uint32_t nq = 1u << tm.nq, no = 1u << tm.no;
+  uint32_t o0, o1, q0, q1;
+  if (split) {
+    o0 = 0;
+    o1 = 1;
+    q0 = task.b * tm.q_per_chunk;
+    q1 = min(q0 + tm.q_per_chunk, nq);
+  } else {
+    o0 = task.b * tm.o_per_chunk;
+    o1 = min(o0 + tm.o_per_chunk, no);
+    q0 = 0;
+    q1 = nq;
+  }
+  constexpr uint32_t per = 16 / sizeof(T);
+  T* C = gb + st.c_off;
+  T* partial = gb + st.partial_off;
+  for (uint32_t o = o0; o < o1; ++o) {
+    switch (tm.kout) {
+      case 0: tile_contract<T, kTeams, 0>(st, Ag, Bg, As, Bs, Cs, As, soff, o, q0, q1, team); break;
+      case 1: tile_contract<T, kTeams, 1>(st, Ag, Bg, As, Bs, Cs, As, soff, o, q0, q1, team); break;
+      default: tile_contract<T, kTeams, 2>(st, Ag, Bg, As, Bs, Cs, As, soff, o, q0, q1, team); break;
+    }
+    // C tile out: 16-byte stores (footprint bit 0 is C's bit 0)
+    const uint32_t n = 1u << tm.nfc;
+    if (split) {
+      T* dst = partial + (size_t)task.b * n;
+      for (uint32_t j = tid; j < n; j += team.size) dst[j] = Cs[j];
+    } else if (per == 2 && tm.nfc >= 1) {
+      const uint32_t cbase = runs_offset(tm.oc, o);
+      for (uint32_t j = tid * 2; j < n; j += team.size * 2)
+        *reinterpret_cast<float4*>(C + (cbase | runs_offset(tm.ffc, j))) =
+            *reinterpret_cast<const float4*>(Cs + j);
+    } else {
+      const uint32_t cbase = runs_offset(tm.oc, o);
+      for (uint32_t j = tid; j < n; j += team.size) C[cbase | runs_offset(tm.ffc, j)] = Cs[j];
+    }
+    team.sync();
+  }
+  if (!split) {
+    signal_done(prog, st.done_ctr, team);
+    return;
+  }
+  __threadfence();
+  team.sync();
+  if (tid == 0)
+    s_last = atomicAdd(prog.counters + ctr_index(st.arrive_ctr), 1u) == st.n_chunks - 1;
+  team.sync();
+  if (!s_last) return;
+  __threadfence();
+  const uint32_t n = 1u << tm.nfc;
+  if (st.flags & GSF_LEAFGRAD) {
+    // dS/dparam += sum_c dS/dleaf[c] * dleaf[c]/dparam  (leaf has <= 16 entries)
+    if (tid < 32) {
+      double2 prod = make_double2(0.0, 0.0);
+      if (tid < n) {
+        T total = czero<T>();
+        for (uint32_t k = 0; k < st.n_chunks; ++k)
+          total = cadd(total, load_l2(partial + (size_t)k * n + tid));
+        const double2 t = to_d2(total);
+        const double2 d = to_d2(table[st.der_off + runs_offset(tm.ffc, tid)]);
+        prod.x = t.x * d.x - t.y * d.y;
+        prod.y = t.x * d.y + t.y * d.x;
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        prod.x += __shfl_down_sync(0xffffffffu, prod.x, off);
+        prod.y += __shfl_down_sync(0xffffffffu, prod.y, off);
+      }
+      if (tid == 0) {
+        const size_t row = (size_t)st.net * (2 + 2 * prog.n_params);
+        atomicAdd(&prog.results[row + 2 + 2 * st.slot], prod.x);
+        atomicAdd(&prog.results[row + 3 + 2 * st.slot], prod.y);
+      }
+    }
+  } else {
+    for (uint32_t j = tid; j < n; j += team.size) {
+      T total = czero<T>();
+      for (uint32_t k = 0; k < st.n_chunks; ++k)
+        total = cadd(total, load_l2(partial + (size_t)k * n + j));
+      C[runs_offset(tm.ffc, j)] = total;
+    }
+  }
+  signal_done(prog, st.done_ctr, team);
+}
+
 template <typename T, int kTeams>
 __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
                           unsigned char* work, GStep& s_step, int& s_last,
@@ -234,6 +454,10 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
   }
   team.sync();
   const GStep& st = s_step;
+  if (st.flags & GSF_TILE) {
+    run_tile<T, kTeams>(prog, task, table, work, st, s_last, team);
+    return;
+  }
   T* gb = reinterpret_cast<T*>(prog.gbase);
   const T* A = (st.flags & GSF_A_TABLE) ? table + st.a_off : gb + st.a_off;
   const T* B = (st.flags & GSF_B_TABLE) ? table + st.b_off : gb + st.b_off;

@@ -132,7 +132,8 @@ uint64_t positions_max(const uint8_t* pos, int n) {
 // Checks every access of a wave against its buffers and the task order
 // against the dependencies, so that a lowering mistake is an error on the
 // host instead of a bad address or a wait that never ends on the device.
-void validate_wave(const WaveHost& w, uint32_t table_elems, uint32_t arena_elems) {
+void validate_wave(const WaveHost& w, uint32_t table_elems, uint32_t arena_elems,
+                   size_t elem_of_wave, size_t work_bytes) {
   auto check_ref = [&](uint32_t off, bool global, uint64_t max_index, const char* what) {
     const uint64_t end = (uint64_t)off + max_index + 1;
     if (global) {
@@ -189,6 +190,44 @@ void validate_wave(const WaveHost& w, uint32_t table_elems, uint32_t arena_elems
     if (ts.nb < 6 || ((1ull << ts.nb) % kTcCols)) fail(QTC_ERR_INVALID, "internal: GEMM N");
   }
   for (const GStep& st : w.steps) {
+    if (st.flags & GSF_TILE) {
+      const GTileMap& t = st.tile;
+      const bool sa = !(st.flags & GSF_A_TABLE), sb = !(st.flags & GSF_B_TABLE);
+      if (t.nv != 8 + t.kout + t.ns || t.kout > kTileMaxOut || t.ns > kTileMaxRegSum)
+        fail(QTC_ERR_INVALID, "internal: tile bit split");
+      const uint64_t ta = runs_max(t.tfa, t.nv), tb = runs_max(t.tfb, t.nv);
+      const uint64_t tc = runs_max(t.tfc, t.nv);
+      if (sa && ta >= (1ull << t.nfa)) fail(QTC_ERR_INVALID, "internal: tile beyond footprint A");
+      if (sb && tb >= (1ull << t.nfb)) fail(QTC_ERR_INVALID, "internal: tile beyond footprint B");
+      if (tc >= (1ull << t.nfc)) fail(QTC_ERR_INVALID, "internal: tile beyond footprint C");
+      const uint64_t ea = runs_max(t.oa, t.no) | runs_max(t.qa, t.nq) |
+                          (sa ? runs_max(t.ffa, t.nfa) : ta);
+      const uint64_t eb = runs_max(t.ob, t.no) | runs_max(t.qb, t.nq) |
+                          (sb ? runs_max(t.ffb, t.nfb) : tb);
+      check_ref(st.a_off, sa, ea, "tile operand A");
+      check_ref(st.b_off, sb, eb, "tile operand B");
+      if (!(st.flags & GSF_LEAFGRAD))
+        check_ref(st.c_off, true, runs_max(t.oc, t.no) | runs_max(t.ffc, t.nfc), "tile output");
+      else
+        check_ref(st.der_off, false, runs_max(t.ffc, t.nfc), "leaf derivative");
+      if (!(st.flags & GSF_SPLIT)) {
+        const uint64_t no = 1ull << t.no;
+        if (t.o_per_chunk == 0 || (uint64_t)st.n_chunks * t.o_per_chunk < no ||
+            (uint64_t)(st.n_chunks - 1) * t.o_per_chunk >= no || t.q_per_chunk != (1ull << t.nq))
+          fail(QTC_ERR_INVALID, "internal: tile chunks do not cover the outputs");
+      }
+      if (st.flags & GSF_SPLIT) {
+        if (t.no != 0) fail(QTC_ERR_INVALID, "internal: split tile with outer outputs");
+        if (t.q_per_chunk == 0 || (uint64_t)st.n_chunks * t.q_per_chunk < (1ull << t.nq))
+          fail(QTC_ERR_INVALID, "internal: tile chunks do not cover the summed values");
+        check_ref(st.partial_off, true, ((uint64_t)st.n_chunks << t.nfc) - 1, "tile partials");
+        if (st.arrive_ctr >= w.n_counters) fail(QTC_ERR_INVALID, "internal: arrive counter");
+      }
+      if (tile_region_bytes(st, elem_of_wave) > work_bytes)
+        fail(QTC_ERR_INVALID, "internal: tile footprints beyond the team's shared memory");
+      if (st.done_ctr >= w.n_counters) fail(QTC_ERR_INVALID, "internal: done counter");
+      continue;
+    }
     const uint64_t ma = runs_max(st.ca, st.rc) | runs_max(st.ya, st.ry);
     const uint64_t mb = runs_max(st.cb, st.rc) | runs_max(st.yb, st.ry);
     check_ref(st.a_off, !(st.flags & GSF_A_TABLE), ma, "step operand A");
@@ -247,6 +286,8 @@ void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
   lim.arena_elems = (uint32_t)(49152 / elem);
   lim.subtree_elems = (uint64_t)opts.subtree_bytes / elem;
   lim.task_terms_log2 = opts.task_terms_log2;
+  lim.tile_mode = opts.tile_mode;
+  lim.elem = elem;
   if (opts.small_rank > 0) lim.small_rank = opts.small_rank;
   lim.tensor_cores = hp.dtype == QTC_SPLIT_BF16;
   // with tensor cores four teams share one CTA's shared memory
@@ -330,7 +371,7 @@ void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
   for (auto& wnets : waves) {
     std::sort(wnets.begin(), wnets.end());
     hp.waves.push_back(assemble_wave(wnets, graphs));
-    validate_wave(hp.waves.back(), hp.table_elems, max_arena);
+
     if (!hp.waves.back().tsteps.empty()) hp.tensor_cores = true;
     hp.max_global_elems = std::max(hp.max_global_elems, hp.waves.back().global_elems);
     hp.max_counters = std::max(hp.max_counters, hp.waves.back().n_counters);
@@ -341,9 +382,14 @@ void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
   const size_t smem_task = (size_t)hp.stage_ops * sizeof(SOp) + (size_t)max_arena * elem;
   const size_t chunk_task = 2 * (size_t)kYTab * sizeof(uint32_t) + 256 * elem +
                             2 * (size_t)kMaxChunkRows * sizeof(uint32_t);
-  hp.work_bytes = round16(std::max(smem_task, chunk_task));
+  size_t tile_task = 0;
+  for (const WaveHost& w : hp.waves)
+    for (const GStep& st : w.steps)
+      if (st.flags & GSF_TILE) tile_task = std::max(tile_task, tile_region_bytes(st, elem));
+  hp.work_bytes = round16(std::max({smem_task, chunk_task, tile_task}));
   hp.table_bytes = round16((size_t)hp.table_elems * elem);
   hp.smem = hp.table_bytes + (size_t)(hp.tensor_cores ? 4 : 1) * hp.work_bytes;
+  for (const WaveHost& w : hp.waves) validate_wave(w, hp.table_elems, max_arena, elem, hp.work_bytes);
   if (hp.smem > max_dynamic)
     fail(QTC_ERR_UNSUPPORTED, "graph program needs %zu bytes of shared memory (limit %zu)",
          hp.smem, max_dynamic);

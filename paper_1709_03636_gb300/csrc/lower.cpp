@@ -427,8 +427,29 @@ void place_global_buffers(NetGraph& ng, const std::vector<uint64_t>& vbase,
       if (users[b].empty() || users[b].back() != i) users[b].push_back(i);
       if (r.write && (writers[b].empty() || writers[b].back() != i)) writers[b].push_back(i);
     }
+  // ancestors of every unit (dependencies point to earlier units)
+  const int W = (U + 63) / 64;
+  std::vector<uint64_t> anc((size_t)U * W, 0);
+  for (int i = 0; i < U; ++i)
+    for (int d : ng.units[i].deps) {
+      if (d < 0 || d >= i) continue;
+      uint64_t* a = &anc[(size_t)i * W];
+      const uint64_t* ad = &anc[(size_t)d * W];
+      for (int k = 0; k < W; ++k) a[k] |= ad[k];
+      a[d / 64] |= 1ull << (d % 64);
+    }
+  auto is_anc = [&](int a, int of) { return (anc[(size_t)of * W + a / 64] >> (a % 64)) & 1; };
+  // q's memory may be taken by b without a new dependency when every unit
+  // that touches q already precedes every writer of b
+  auto ordered_before = [&](int q, int b) {
+    if (!(last[q] < first[b])) return false;
+    for (int w : writers[b])
+      for (int u : users[q])
+        if (u != w && !is_anc(u, w)) return false;
+    return true;
+  };
   // first fit, largest buffers first; two buffers share memory only when
-  // their live ranges are disjoint
+  // one's every use is ordered before the other's writes
   std::vector<int> order;
   for (int b = 0; b < B; ++b)
     if (first[b] >= 0) order.push_back(b);
@@ -442,7 +463,7 @@ void place_global_buffers(NetGraph& ng, const std::vector<uint64_t>& vbase,
   for (int b : order) {
     std::vector<std::pair<uint64_t, uint64_t>> busy;
     for (int q : placed)
-      if (!(last[q] < first[b] || last[b] < first[q])) busy.push_back({at[q], at[q] + vsize[q]});
+      if (!ordered_before(q, b) && !ordered_before(b, q)) busy.push_back({at[q], at[q] + vsize[q]});
     std::sort(busy.begin(), busy.end());
     uint64_t pos = 0;
     for (auto& iv : busy) {
@@ -452,27 +473,6 @@ void place_global_buffers(NetGraph& ng, const std::vector<uint64_t>& vbase,
     at[b] = pos;
     placed.push_back(b);
     peak = std::max(peak, pos + vsize[b]);
-  }
-  // write after read: a buffer's writers start only after every unit that
-  // touched earlier buffers in the same memory has finished
-  for (int b : placed)
-    for (int q : placed) {
-      if (q == b || !(last[q] < first[b])) continue;
-      if (at[q] >= at[b] + vsize[b] || at[b] >= at[q] + vsize[q]) continue;
-      for (int w : writers[b])
-        for (int u : users[q]) ng.units[w].deps.push_back(u);
-    }
-  // depths again (dependencies still point to earlier units)
-  for (int i = 0; i < U; ++i) {
-    GUnit& u = ng.units[i];
-    std::sort(u.deps.begin(), u.deps.end());
-    u.deps.erase(std::unique(u.deps.begin(), u.deps.end()), u.deps.end());
-    int depth = 0;
-    for (int d : u.deps) {
-      if (d >= i) fail(QTC_ERR_INVALID, "internal: a dependency on a later unit");
-      depth = std::max(depth, ng.units[d].depth + 1);
-    }
-    u.depth = depth;
   }
   for (int i = 0; i < U; ++i)
     for (const GRef& r : unit_refs(ng.units[i])) {
@@ -737,6 +737,14 @@ NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
     (void)lc_t;
     (void)a;
     (void)b;
+    if (leaf_for_grad >= 0) u.step.flags |= GSF_LEAFGRAD;
+    const bool two_global = ra.global && rb.global;
+    if (lim.tile_mode == 2 || (lim.tile_mode == 1 && (two_global || (u.step.flags & GSF_SPLIT)))) {
+      GStep tiled = u.step;
+      tiled.flags &= (uint16_t)~GSF_SPLIT;
+      if (encode_tile(tiled, lc, la, lb, !ra.global, !rb.global, lim.elem, lim.task_terms_log2))
+        u.step = tiled;
+    }
     u.step.c_off = (uint32_t)std::max<int64_t>(c_off, 0);
     if (ra.global) u.step.a_off = ra.abs;
     else { u.step.a_off = ra.abs; u.step.flags |= GSF_A_TABLE; }
@@ -749,12 +757,12 @@ NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
         ng.why = "internal: a leaf adjoint that is not a split reduction";
         return -1;
       }
-      u.step.flags |= GSF_LEAFGRAD;
       u.step.der_off = gate_der_off[leaf_gate[leaf_for_grad]];
       u.step.slot = plan.net.leaves[leaf_for_grad].spec.slot;
     }
     if (u.step.flags & GSF_SPLIT) {
-      u.step.partial_off = (uint32_t)galloc((uint64_t)u.step.n_chunks << u.step.rc);
+      const uint32_t pbits = (u.step.flags & GSF_TILE) ? u.step.tile.nfc : u.step.rc;
+      u.step.partial_off = (uint32_t)galloc((uint64_t)u.step.n_chunks << pbits);
       u.target = 1;
     } else {
       u.target = u.step.n_chunks;

@@ -189,7 +189,22 @@ struct GraphLimits {
   bool tensor_cores = false;         // split-BF16 GEMM tasks for GEMM-shaped steps
   bool reuse_global = true;          // place global tensors by live range (memory reuse)
   int checkpoint_segments = 1;       // > 1: adjoint recomputes dropped values per segment
+  int tile_mode = 1;                 // global steps in tile form: 0 never, 1 steps with two
+                                     // operands in global memory, 2 every step that tiles
+  size_t elem = 8;                   // bytes per element
 };
+
+// Tile form of a global step (tile_plan.cpp): fills g.tile, g.n_chunks and
+// the GSF_TILE / GSF_SPLIT flags when the step tiles (g's rc, ry and bit maps
+// already set); false leaves g as it was.
+bool encode_tile(GStep& g, const std::vector<int>& lc, const std::vector<int>& la,
+                 const std::vector<int>& lb, bool a_table, bool b_table, size_t elem,
+                 int task_terms_log2);
+// Shared memory of a team's work region a tile task needs.
+size_t tile_region_bytes(const GStep& g, size_t elem);
+// Host emulation of one tile step on seeded random operands against the
+// plain contraction over its bit maps: the largest absolute difference.
+double emulate_tile_step(const GStep& g, uint64_t seed);
 
 // A unit is one shared-memory subtree task or one global step (its chunks);
 // its counter reaches `target` when it is complete.
@@ -246,6 +261,7 @@ struct ProgramOptions {
   size_t wave_cap_bytes = (size_t)8 << 30;
   bool force_graph = false;
   int small_rank = 0;
+  int tile_mode = 1;               // see GraphLimits::tile_mode
   int task_terms_log2 = 16;        // multiply-adds per chunk task of a global step
   int subtree_bytes = 32768;       // values of one shared-memory subtree task
   int warp_teams = 1;              // 0: one network per CTA; 1: per warp where it fits;
@@ -255,6 +271,7 @@ struct ProgramOptions {
   bool operator==(const ProgramOptions& o) const {
     return wave_cap_bytes == o.wave_cap_bytes && force_graph == o.force_graph &&
            small_rank == o.small_rank && task_terms_log2 == o.task_terms_log2 &&
+           tile_mode == o.tile_mode &&
            subtree_bytes == o.subtree_bytes && warp_teams == o.warp_teams &&
            sm_count == o.sm_count && graph_hi_occupancy == o.graph_hi_occupancy;
   }

@@ -551,3 +551,27 @@ def test_checkpoint_segments_when_one_network_exceeds_the_limit():
         with pytest.raises(q.QtcError, match="ARENA"):
             one.program_info("c64", True, max_wave_bytes=max(1 << 20, int(0.3 * fwd[
                 "net_global_bytes"])))
+
+
+@pytest.mark.parametrize("tile_mode", [1, 2])
+def test_tile_steps_emulated_against_the_plain_contraction(tile_mode):
+    """The tile form of global steps (footprints copied through shared memory,
+    lanes/warps/registers over the tile, reductions over summed lane and warp
+    bits, split chunks) emulated on the host on random operands equals the
+    plain contraction over each step's bit maps, for forward and adjoint
+    programs of dense, diagonal and full networks."""
+    import ctypes
+    from paper_1709_03636_gb300 import _lib
+    checked = 0
+    edges = random_regular_graph(12, 3, 6)
+    circ = q.Circuit.qaoa(12, edges, 2)
+    for kw in (dict(), dict(lightcone=False), dict(diag=False)):
+        batch = q.Batch(circ, ordering="lg", **kw)
+        for small, grad, dtype in ((2, 1, "c64"), (4, 0, "c128"), (6, 1, "c64")):
+            err, cnt = ctypes.c_double(), ctypes.c_int32()
+            _lib.check(_lib.lib.qtc_selftest_tile_steps(
+                batch.ptr, q.DTYPES[dtype], grad, 1, small, tile_mode, 16,
+                ctypes.byref(err), ctypes.byref(cnt)))
+            assert err.value < 1e-11, (kw, small, grad, dtype)
+            checked += cnt.value
+    assert checked > 500
