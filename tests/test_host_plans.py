@@ -506,11 +506,13 @@ def test_degenerate_graph_shapes(name, p):
 
 
 def test_global_buffers_reuse_memory_by_live_range():
-    """Graph-executor intermediates and adjoints are placed by live range:
-    for p=3 n=60 with the gradient the networks' placed peaks sum to well
-    under their tensors' total (the placement and every write-after-read
-    ordering it needs are checked on the host when the program is built),
-    and the whole graph fits one launch under the default 8 GiB limit."""
+    """Graph-executor intermediates and adjoints are placed by live range,
+    sharing memory only where every use of one tensor already precedes the
+    writes of the other in the dependency order: for p=3 n=60 the networks'
+    placed peaks sum to well under their tensors' total (the placement and
+    that ordering are checked on the host when the program is built), and
+    the whole graph with its gradient fits one launch under the default
+    8 GiB limit."""
     w = WORKLOADS["qaoa_p3_n60_d4"]
     edges = w.graph()
     batch = q.Batch(q.Circuit.qaoa(w.n, edges, w.p), ordering="lg")
@@ -518,7 +520,8 @@ def test_global_buffers_reuse_memory_by_live_range():
     grad = batch.program_info("c64", True)
     for info in (fwd, grad):
         assert info["graph"] == 1
-        assert 0 < info["net_global_bytes"] < 0.75 * info["net_global_bytes_unshared"]
+        # with the gradient most forward values stay live until the sweep
+        assert 0 < info["net_global_bytes"] < 0.85 * info["net_global_bytes_unshared"]
         assert info["work_bytes"] <= info["net_global_bytes"]
     assert grad["n_waves"] == 1 and grad["work_bytes"] <= 8 << 30
     # forward only, a tensor is dead after the step that consumes it
