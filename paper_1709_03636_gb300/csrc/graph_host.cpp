@@ -319,9 +319,24 @@ void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
     // a network whose stored values exceed the wave limit on their own:
     // checkpoint segments, recomputed by the adjoint sweep (fewest that fit)
     const uint64_t cap_elems = wave_cap_bytes / elem;
-    if (hp.want_grad && ((graphs[i].global_elems + 63) & ~uint64_t(63)) > cap_elems) {
+    auto over = [&](const NetGraph& g) {
+      return ((g.global_elems + 63) & ~uint64_t(63)) > cap_elems;
+    };
+    if (over(graphs[i])) {
+      // reuse memory also where that adds write-after-read dependencies
+      GraphLimits ld = li;
+      ld.reuse_with_deps = true;
+      NetGraph g = lower_graph(plans[i], leaf_gate[i], val_off, der_off, hp.table_elems,
+                               hp.want_grad != 0, ld);
+      if (g.fits && g.global_elems < graphs[i].global_elems) {
+        graphs[i] = std::move(g);
+        li = ld;
+      }
+    }
+    if (hp.want_grad && over(graphs[i])) {
       for (int k : {2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64}) {
         GraphLimits lk = li;
+        lk.reuse_with_deps = true;
         lk.checkpoint_segments = k;
         NetGraph g = lower_graph(plans[i], leaf_gate[i], val_off, der_off, hp.table_elems,
                                  true, lk);

@@ -405,7 +405,7 @@ std::vector<GRef> unit_refs(GUnit& u) {
 }  // namespace
 
 void place_global_buffers(NetGraph& ng, const std::vector<uint64_t>& vbase,
-                          const std::vector<uint64_t>& vsize) {
+                          const std::vector<uint64_t>& vsize, bool add_deps) {
   const int B = (int)vbase.size();
   const int U = (int)ng.units.size();
   if (B == 0) return;
@@ -443,6 +443,7 @@ void place_global_buffers(NetGraph& ng, const std::vector<uint64_t>& vbase,
   // that touches q already precedes every writer of b
   auto ordered_before = [&](int q, int b) {
     if (!(last[q] < first[b])) return false;
+    if (add_deps) return true;   // the dependencies are added below
     for (int w : writers[b])
       for (int u : users[q])
         if (u != w && !is_anc(u, w)) return false;
@@ -473,6 +474,30 @@ void place_global_buffers(NetGraph& ng, const std::vector<uint64_t>& vbase,
     at[b] = pos;
     placed.push_back(b);
     peak = std::max(peak, pos + vsize[b]);
+  }
+  if (add_deps) {
+    // write after read: a buffer's writers start only after every unit that
+    // touched an earlier buffer in the same memory has finished
+    for (int b : placed)
+      for (int q : placed) {
+        if (q == b || !(last[q] < first[b])) continue;
+        if (at[q] >= at[b] + vsize[b] || at[b] >= at[q] + vsize[q]) continue;
+        for (int w : writers[b])
+          for (int u : users[q])
+            if (u != w) ng.units[w].deps.push_back(u);
+      }
+    // depths again (dependencies still point to earlier units)
+    for (int i = 0; i < U; ++i) {
+      GUnit& u = ng.units[i];
+      std::sort(u.deps.begin(), u.deps.end());
+      u.deps.erase(std::unique(u.deps.begin(), u.deps.end()), u.deps.end());
+      int depth = 0;
+      for (int d : u.deps) {
+        if (d >= i) fail(QTC_ERR_INVALID, "internal: a dependency on a later unit");
+        depth = std::max(depth, ng.units[d].depth + 1);
+      }
+      u.depth = depth;
+    }
   }
   for (int i = 0; i < U; ++i)
     for (const GRef& r : unit_refs(ng.units[i])) {
@@ -584,6 +609,9 @@ NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
       if (in_global[t] && need_grad[t]) grad_g[t] = galloc(size(t));
 
   std::vector<int> producer_val(T, -1), producer_grad(T, -1);
+  // recomputed segments start after the adjoint sweep reaches them (>= 0:
+  // the unit every forward unit emitted now also waits for)
+  int recompute_after = -1;
   auto add_unit = [&](GUnit&& u) {
     int depth = 0;
     std::sort(u.deps.begin(), u.deps.end());
@@ -609,6 +637,7 @@ NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
     std::vector<uint32_t> buf_size;
     GUnit u;
     u.kind = GT_SMEM;
+    if (!reverse && recompute_after >= 0) u.deps.push_back(recompute_after);
     auto value_ref = [&](int t) {
       Ref r;
       if (t < L) {
@@ -857,11 +886,14 @@ NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
   }
   // the segment's dropped values again, in step order, into fresh buffers
   auto recompute_segment = [&](int j) -> bool {
+    // after the sweep so far: its memory can then be reused for the values
+    recompute_after = ng.units.empty() ? -1 : (int)ng.units.size() - 1;
     for (int s = 0; s < S; ++s) {
       if (seg[s] != j || !dropped[L + s]) continue;
       if (bigstep[s]) {
         const Step& st = plan.steps[s];
         std::vector<int> deps;
+        if (recompute_after >= 0) deps.push_back(recompute_after);
         Ref ra = value_ref_global(st.a, deps);
         Ref rb = value_ref_global(st.b, deps);
         val_g[L + s] = galloc(size(L + s));
@@ -879,6 +911,7 @@ NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
       }
     }
     ng.recomputed_segments += 1;
+    recompute_after = -1;
     return true;
   };
 
@@ -918,7 +951,7 @@ NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
   if (gsize >> 32) return fail_net("a network's global intermediates exceed 2^32 elements");
   ng.global_elems = gsize;
   ng.unshared_elems = gsize;
-  if (lim.reuse_global) place_global_buffers(ng, vbase, vsize);
+  if (lim.reuse_global) place_global_buffers(ng, vbase, vsize, lim.reuse_with_deps);
   (void)sub_done;
   return ng;
 }

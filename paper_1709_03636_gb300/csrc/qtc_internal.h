@@ -188,6 +188,7 @@ struct GraphLimits {
   uint32_t arena_elems = 8192;       // shared-memory arena of one subtree task
   bool tensor_cores = false;         // split-BF16 GEMM tasks for GEMM-shaped steps
   bool reuse_global = true;          // place global tensors by live range (memory reuse)
+  bool reuse_with_deps = false;      // also where it takes new write-after-read dependencies
   int checkpoint_segments = 1;       // > 1: adjoint recomputes dropped values per segment
   int tile_mode = 1;                 // global steps in tile form: 0 never, 1 steps with two
                                      // operands in global memory, 2 every step that tiles
@@ -239,11 +240,13 @@ struct NetGraph {
   std::string why;
 };
 
-// Overlaps the network's global tensors whose live ranges (in unit order) are
-// disjoint, adds the write-after-read dependencies that reuse needs and
-// rewrites every work-buffer offset; global_elems becomes the peak.
+// Overlaps the network's global tensors whose uses are ordered: where every
+// unit touching one already precedes (through the dependencies) every unit
+// writing the other, or, with add_deps, wherever their live ranges in unit
+// order are disjoint, adding the write-after-read dependencies that takes.
+// Rewrites every work-buffer offset; global_elems becomes the peak.
 void place_global_buffers(NetGraph& ng, const std::vector<uint64_t>& vbase,
-                          const std::vector<uint64_t>& vsize);
+                          const std::vector<uint64_t>& vsize, bool add_deps);
 // Host check of that placement (ordering of every reuse; no live overlap).
 void check_global_placement(const NetGraph& ng);
 

@@ -159,7 +159,7 @@ def test_bounded_wait_expires_and_reports_timeout():
     assert abs(C - sv.maxcut_expectation(8, edges, [0.4], [0.3])) < 1e-11
 
 
-@pytest.mark.parametrize("i", [42, 9])
+@pytest.mark.parametrize("i", [42, 60])
 def test_checkpointed_gradient_under_a_small_limit(engine, i):
     """A p=3 n=60 edge network whose stored values exceed a lowered wave
     limit: the adjoint sweep recomputes the dropped segments and the value
@@ -169,9 +169,17 @@ def test_checkpointed_gradient_under_a_small_limit(engine, i):
     g, b = w.angles()
     circ = q.Circuit.qaoa(w.n, edges, w.p)
     one = q.Batch(circ, ordering="lg").subset([i])
-    base = one.program_info("c64", True)
-    cap = int(0.9 * base["net_global_bytes"])
-    assert one.program_info("c64", True, max_wave_bytes=cap)["checkpoint_segments"] > 1
+    cap = None
+    base = one.program_info("c64", True)["net_global_bytes"]
+    for frac in (0.7, 0.6, 0.55, 0.5, 0.45, 0.4):
+        try:
+            info = one.program_info("c64", True, max_wave_bytes=max(1 << 20, int(frac * base)))
+        except q.QtcError:
+            continue
+        if info["checkpoint_segments"] > 1:
+            cap = max(1 << 20, int(frac * base))
+            break
+    assert cap is not None
     C0, pe0, g0 = q.qaoa_expectation(engine, one, g, b, "c64", want_grad=True)
     engine.set_limits(max_wave_bytes=cap)
     try:
