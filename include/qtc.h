@@ -392,11 +392,12 @@ qtc_status qtc_engine_set_graph_options(qtc_engine* e, int force_graph, int smal
 qtc_status qtc_engine_set_task_options(qtc_engine* e, int task_terms_log2, int subtree_bytes,
                                        int warp_teams, int graph_hi_occupancy);
 
-/* Tile form of the graph executor's global steps (tuning and tests): 0 keeps
- * every step on the row and split chunk paths; 1 (default) stages the steps
- * with both operands in global memory, and the long reductions, through
- * shared memory in tiles (16-byte copies of each operand's tile, contraction
- * in shared memory and registers); 2 does so for every step that tiles.
+/* Tile form of the graph executor's global steps (tuning and tests): 0
+ * (default) keeps every step on the row and split chunk paths; 1 stages the
+ * steps with both operands in global memory, and the long reductions,
+ * through shared memory in tiles (16-byte copies of each operand's tile,
+ * contraction in shared memory and registers); 2 does so for every step that
+ * tiles.
  * Invalidates prepared programs.  QTC_ERR_INVALID outside 0..2. */
 qtc_status qtc_engine_set_tile_mode(qtc_engine* e, int mode);
 

@@ -190,7 +190,7 @@ struct GraphLimits {
   bool reuse_global = true;          // place global tensors by live range (memory reuse)
   bool reuse_with_deps = false;      // also where it takes new write-after-read dependencies
   int checkpoint_segments = 1;       // > 1: adjoint recomputes dropped values per segment
-  int tile_mode = 1;                 // global steps in tile form: 0 never, 1 steps with two
+  int tile_mode = 0;                 // global steps in tile form: 0 never, 1 steps with two
                                      // operands in global memory, 2 every step that tiles
   size_t elem = 8;                   // bytes per element
 };
@@ -264,7 +264,7 @@ struct ProgramOptions {
   size_t wave_cap_bytes = (size_t)8 << 30;
   bool force_graph = false;
   int small_rank = 0;
-  int tile_mode = 1;               // see GraphLimits::tile_mode
+  int tile_mode = 0;               // see GraphLimits::tile_mode
   int task_terms_log2 = 16;        // multiply-adds per chunk task of a global step
   int subtree_bytes = 32768;       // values of one shared-memory subtree task
   int warp_teams = 1;              // 0: one network per CTA; 1: per warp where it fits;
