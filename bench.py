@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--dtype", default=None, help="override the workload's element type")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile-mode", type=int, default=None, choices=[0, 1, 2],
+                    help="graph executor's tile form of global steps (default: the library's)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads reported under \"configs\"")
     ap.add_argument("--edges", type=int, default=0,
@@ -359,6 +361,7 @@ class Bench:
         import torch
         self.q, self.dev, self.stream, self.world, self.rank = q, dev, stream, world, rank
         self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        self.tile_mode = None
 
     def timed(self, fn, steps):
         """Per-step device times (ms) of `steps` calls of fn, CUDA events on
@@ -402,6 +405,8 @@ class Bench:
             info = batch.program_info(dtype, grad)
             need += info["work_bytes"] + 2 * info["table_bytes"]
         engine = q.Engine(self.dev.index, arena_bytes=int(need) + (256 << 20))
+        if self.tile_mode is not None:
+            engine.set_tile_mode(self.tile_mode)
         tuned = None
         if autotune:
             tuned = q.autotune(engine, batch, dtype, max(grads), cache_path=autotune)
@@ -544,6 +549,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     bench = Bench(q, dev, stream, world, rank)
+    bench.tile_mode = args.tile_mode
     peak, peak_kind = measured_peaks()
 
     from dataclasses import replace

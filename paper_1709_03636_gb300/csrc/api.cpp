@@ -266,7 +266,7 @@ extern "C" qtc_status qtc_engine_set_task_options(qtc_engine* e, int task_terms_
 extern "C" qtc_status qtc_engine_set_tile_mode(qtc_engine* e, int mode) {
   return guarded([&] {
     if (!e) fail(QTC_ERR_INVALID, "null engine");
-    if (mode < 0 || mode > 2) fail(QTC_ERR_INVALID, "tile mode %d (0..2)", mode);
+    if (mode < 0 || mode > 4) fail(QTC_ERR_INVALID, "tile mode %d (0..4)", mode);
     e->options.tile_mode = mode;
     e->generation += 1;
     e->used = 0;

@@ -258,7 +258,11 @@ enum GStepFlag : uint16_t {
   GSF_B_TABLE = 2,
   GSF_SPLIT = 4,       // chunks split the summed index; the last chunk reduces
   GSF_LEAFGRAD = 8,    // output is dS/dleaf: reduce it against d(leaf)/dparam
-  GSF_TILE = 16        // staged through shared memory in tiles (the tile fields)
+  GSF_TILE = 16,       // staged through shared memory in tiles (the tile fields)
+  GSF_YPAIR = 32,      // summed bit 0 is bit 0 of A and of B (both in global memory):
+                       //   complex64 terms are read as 16-byte element pairs
+  GSF_LANES_Y = 64     // split: the summed index's low bits are A's (or B's) lowest
+                       //   bits, so a warp's lanes run over it (one warp per output)
 };
 
 // Tile form of a global step.  The step's labels split into tile labels
@@ -285,7 +289,9 @@ struct GTileMap {
   uint32_t o_per_chunk;       // outer output values per chunk (not split)
   uint8_t sum_lane_mask;      // lane bits that are summed labels
   uint8_t sum_warp_mask;      // warp bits that are summed labels
-  uint8_t pad[6];
+  uint8_t staged;             // bit 0: A's footprint is copied to shared memory, bit 1: B's
+                              //   (otherwise the tile reads the operand where it is)
+  uint8_t pad[5];
   GRuns tfa, tfb, tfc;        // tile index -> footprint index (table operand:
                               //   -> its element index)
   GRuns ffa, ffb, ffc;        // footprint index -> operand element index

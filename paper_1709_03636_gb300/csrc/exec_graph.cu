@@ -262,7 +262,7 @@ __device__ void tile_contract(const GStep& st, const T* Ag, const T* Bg, T* As, 
                               T* red, const uint2* soff, uint32_t o, uint32_t q0, uint32_t q1,
                               const GTeam<kTeams>& team) {
   const GTileMap& tm = st.tile;
-  const bool sa = !(st.flags & GSF_A_TABLE), sb = !(st.flags & GSF_B_TABLE);
+  const bool sa = (tm.staged & 1) != 0, sb = (tm.staged & 2) != 0;
   const uint32_t tid = team.tid, lane = tid & 31u, warp = tid >> 5;
   const uint32_t a_lw = runs_offset(tm.tfa, tid), b_lw = runs_offset(tm.tfb, tid);
   uint32_t ak[1 << kOut], bk[1 << kOut];
@@ -280,8 +280,10 @@ __device__ void tile_contract(const GStep& st, const T* Ag, const T* Bg, T* As, 
     const uint32_t aq = abase | runs_offset(tm.qa, q), bq = bbase | runs_offset(tm.qb, q);
     if (sa) stage_footprint(As, Ag, aq, tm.ffa, tm.nfa, tid, team.size);
     if (sb) stage_footprint(Bs, Bg, bq, tm.ffb, tm.nfb, tid, team.size);
-    cp_async_wait_all();
-    team.sync();
+    if (sa || sb) {
+      cp_async_wait_all();
+      team.sync();
+    }
     const T* Ab = sa ? As : Ag + aq;
     const T* Bb = sb ? Bs : Bg + bq;
     uint32_t s = 0;
@@ -299,7 +301,7 @@ __device__ void tile_contract(const GStep& st, const T* Ag, const T* Bg, T* As, 
 #pragma unroll
       for (int k = 0; k < (1 << kOut); ++k) acc[k] = cfma(Ab[ak[k] | o0.x], Bb[bk[k] | o0.y], acc[k]);
     }
-    team.sync();   // the footprints are refilled (or reused) next
+    if (sa || sb) team.sync();   // the footprints are refilled (or reused) next
   }
   // summed lane bits: butterfly over those bits, every lane gets the sum
 #pragma unroll
@@ -340,11 +342,11 @@ __device__ void run_tile(const GraphProgDev& prog, const GTask& task, T* table,
                          unsigned char* work, const GStep& st, int& s_last,
                          const GTeam<kTeams>& team) {
   const GTileMap& tm = st.tile;
-  const bool sa = !(st.flags & GSF_A_TABLE), sb = !(st.flags & GSF_B_TABLE);
+  const bool sa = (tm.staged & 1) != 0, sb = (tm.staged & 2) != 0;
   const bool split = (st.flags & GSF_SPLIT) != 0;
   T* gb = reinterpret_cast<T*>(prog.gbase);
-  const T* Ag = sa ? gb + st.a_off : table + st.a_off;
-  const T* Bg = sb ? gb + st.b_off : table + st.b_off;
+  const T* Ag = (st.flags & GSF_A_TABLE) ? table + st.a_off : gb + st.a_off;
+  const T* Bg = (st.flags & GSF_B_TABLE) ? table + st.b_off : gb + st.b_off;
   constexpr uint32_t min_fp = sizeof(T) == 8 ? 2 : 1;
   const uint32_t fa = sa ? max(min_fp, 1u << tm.nfa) : 0, fb = sb ? max(min_fp, 1u << tm.nfb) : 0;
   uint32_t ab = fa + fb;
@@ -443,6 +445,128 @@ __device__ void run_tile(const GraphProgDev& prog, const GTask& task, T* table,
   signal_done(prog, st.done_ctr, team);
 }
 
+// ---- paired loads: summed bit 0 is bit 0 of both operands ------------------
+
+__device__ __forceinline__ float4 ld_pair(const float2* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+
+__device__ __forceinline__ float2 cfma2(float4 a, float4 b, float2 acc) {
+  return cfma(make_float2(a.z, a.w), make_float2(b.z, b.w),
+              cfma(make_float2(a.x, a.y), make_float2(b.x, b.y), acc));
+}
+
+// sum over y of A[oa | ya[y]] B[ob | yb[y]] for n_y >= 8 summed values, two
+// at a time (y, y + 1 adjacent in both operands): eight 16-byte loads in
+// flight per thread, four accumulators.
+__device__ __forceinline__ float2 ysum_pair(const float2* A, const float2* B, uint32_t oa,
+                                            uint32_t ob, const uint32_t* ya, const uint32_t* yb,
+                                            uint32_t n_y) {
+  float2 acc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
+  for (uint32_t y = 0; y < n_y; y += 8) {
+    float4 a[4], b[4];
+#pragma unroll
+    for (uint32_t u = 0; u < 4; ++u) {
+      a[u] = ld_pair(A + (oa | ya[y + 2 * u]));
+      b[u] = ld_pair(B + (ob | yb[y + 2 * u]));
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = cfma2(a[u], b[u], acc[u]);
+  }
+  return cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+}
+
+// R rows at a time, n_y = 2 * NP summed values as NP pairs per row.
+template <uint32_t R, uint32_t NP>
+__device__ __forceinline__ void rows_pair(const float2* A, const float2* B, float2* C,
+                                          const uint32_t* rowa, const uint32_t* rowb,
+                                          uint32_t a_lo, uint32_t b_lo, const uint32_t* ya,
+                                          const uint32_t* yb, uint32_t r0, uint32_t r1,
+                                          uint32_t rowlen, uint32_t tid) {
+  uint32_t yav[NP], ybv[NP];
+#pragma unroll
+  for (uint32_t k = 0; k < NP; ++k) {
+    yav[k] = ya[2 * k];
+    ybv[k] = yb[2 * k];
+  }
+  for (uint32_t row = r0; row < r1; row += R) {
+    float4 av[R][NP], bv[R][NP];
+#pragma unroll
+    for (uint32_t r = 0; r < R; ++r) {
+      const uint32_t rr = min(row + r, r1 - 1) - r0;
+      const uint32_t oa = rowa[rr] | a_lo, ob = rowb[rr] | b_lo;
+#pragma unroll
+      for (uint32_t k = 0; k < NP; ++k) {
+        av[r][k] = ld_pair(A + (oa | yav[k]));
+        bv[r][k] = ld_pair(B + (ob | ybv[k]));
+      }
+    }
+#pragma unroll
+    for (uint32_t r = 0; r < R; ++r) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (uint32_t k = 0; k < NP; ++k) acc = cfma2(av[r][k], bv[r][k], acc);
+      if (row + r < r1) C[(row + r) * rowlen + tid] = acc;
+    }
+  }
+}
+
+// Rows of a complex64 step with paired loads; false for other element types.
+template <typename T>
+__device__ __forceinline__ bool rows_paired(const T* A, const T* B, T* C, const uint32_t* rowa,
+                                            const uint32_t* rowb, uint32_t a_lo, uint32_t b_lo,
+                                            const uint32_t* ya, const uint32_t* yb, uint32_t r0,
+                                            uint32_t r1, uint32_t rowlen, uint32_t tid,
+                                            uint32_t n_y) {
+  if constexpr (sizeof(T) != 8) {
+    return false;
+  } else {
+    const float2* a = reinterpret_cast<const float2*>(A);
+    const float2* b = reinterpret_cast<const float2*>(B);
+    float2* c = reinterpret_cast<float2*>(C);
+    if (n_y == 2)
+      rows_pair<8, 1>(a, b, c, rowa, rowb, a_lo, b_lo, ya, yb, r0, r1, rowlen, tid);
+    else if (n_y == 4)
+      rows_pair<4, 2>(a, b, c, rowa, rowb, a_lo, b_lo, ya, yb, r0, r1, rowlen, tid);
+    else if (n_y == 8)
+      rows_pair<2, 4>(a, b, c, rowa, rowb, a_lo, b_lo, ya, yb, r0, r1, rowlen, tid);
+    else
+      for (uint32_t row = r0; row < r1; ++row)
+        c[row * rowlen + tid] =
+            ysum_pair(a, b, rowa[row - r0] | a_lo, rowb[row - r0] | b_lo, ya, yb, n_y);
+    return true;
+  }
+}
+
+// Split chunk with lanes over the summed index (its low bits are the
+// operands' lowest): warp w sums outputs c = w, w + 8, ... over the chunk's
+// cnt values, lanes 32 apart, four accumulators, then a shuffle reduction.
+template <typename T>
+__device__ __forceinline__ T warp_ysum(const T* A, const T* B, uint32_t oa, uint32_t ob,
+                                       const uint32_t* ya, const uint32_t* yb, uint32_t cnt,
+                                       uint32_t lane) {
+  T acc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) acc[u] = czero<T>();
+  uint32_t y = lane;
+  for (; y + 96 < cnt; y += 128) {
+    T av[4], bv[4];
+#pragma unroll
+    for (uint32_t u = 0; u < 4; ++u) {
+      av[u] = A[oa | ya[y + 32 * u]];
+      bv[u] = B[ob | yb[y + 32 * u]];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = cfma(av[u], bv[u], acc[u]);
+  }
+  for (; y < cnt; y += 32) acc[0] = cfma(A[oa | ya[y]], B[ob | yb[y]], acc[0]);
+  T sum = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+  for (int off = 16; off > 0; off >>= 1) sum = cadd(sum, shfl_xor_c(sum, off));
+  return sum;
+}
+
 template <typename T, int kTeams>
 __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
                           unsigned char* work, GStep& s_step, int& s_last,
@@ -491,7 +615,10 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
       team.sync();
       constexpr uint32_t R = 4;
       const uint32_t n_y = (uint32_t)ny;
-      if (active && r1 - r0 < R) {
+      if (active && (st.flags & GSF_YPAIR) &&
+          rows_paired(A, B, C, rowa, rowb, a_lo, b_lo, ya, yb, r0, r1, rowlen, tid, n_y)) {
+        // complex64 element pairs along summed bit 0
+      } else if (active && r1 - r0 < R) {
         // few rows with long sums: the summed index unrolled instead
         for (uint32_t row = r0; row < r1; ++row)
           C[row * rowlen + tid] = ysum(A, B, rowa[row - r0] | a_lo, rowb[row - r0] | b_lo, ya,
@@ -561,16 +688,25 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
     yb[y] = runs_offset(st.yb, (uint32_t)(y0 + y));
   }
   team.sync();
-  const uint32_t oa = runs_offset(st.ca, c), ob = runs_offset(st.cb, c);
-  T acc = czero<T>();
-  if (g < groups) acc = ysum(A, B, oa, ob, ya, yb, g, cnt, groups);
-  red[tid] = acc;
-  team.sync();
   T* partial = gb + st.partial_off;
-  if (tid < nout) {
-    T sum = czero<T>();
-    for (uint32_t k = 0; k < groups; ++k) sum = cadd(sum, red[k * nout + tid]);
-    partial[(size_t)task.b * nout + tid] = sum;
+  if (st.flags & GSF_LANES_Y) {
+    const uint32_t lane = tid & 31u, warp = tid >> 5, n_warps = team.size >> 5;
+    for (uint32_t cc = warp; cc < nout; cc += n_warps) {
+      const T sum = warp_ysum(A, B, runs_offset(st.ca, cc), runs_offset(st.cb, cc), ya, yb, cnt,
+                              lane);
+      if (lane == 0) partial[(size_t)task.b * nout + cc] = sum;
+    }
+  } else {
+    const uint32_t oa = runs_offset(st.ca, c), ob = runs_offset(st.cb, c);
+    T acc = czero<T>();
+    if (g < groups) acc = ysum(A, B, oa, ob, ya, yb, g, cnt, groups);
+    red[tid] = acc;
+    team.sync();
+    if (tid < nout) {
+      T sum = czero<T>();
+      for (uint32_t k = 0; k < groups; ++k) sum = cadd(sum, red[k * nout + tid]);
+      partial[(size_t)task.b * nout + tid] = sum;
+    }
   }
   __threadfence();
   team.sync();

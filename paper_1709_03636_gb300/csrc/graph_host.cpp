@@ -192,7 +192,9 @@ void validate_wave(const WaveHost& w, uint32_t table_elems, uint32_t arena_elems
   for (const GStep& st : w.steps) {
     if (st.flags & GSF_TILE) {
       const GTileMap& t = st.tile;
-      const bool sa = !(st.flags & GSF_A_TABLE), sb = !(st.flags & GSF_B_TABLE);
+      const bool sa = (t.staged & 1) != 0, sb = (t.staged & 2) != 0;
+      const bool ga = !(st.flags & GSF_A_TABLE), gbl = !(st.flags & GSF_B_TABLE);
+      if ((sa && !ga) || (sb && !gbl)) fail(QTC_ERR_INVALID, "internal: a table operand staged");
       if (t.nv != 8 + t.kout + t.ns || t.kout > kTileMaxOut || t.ns > kTileMaxRegSum)
         fail(QTC_ERR_INVALID, "internal: tile bit split");
       const uint64_t ta = runs_max(t.tfa, t.nv), tb = runs_max(t.tfb, t.nv);
@@ -204,8 +206,8 @@ void validate_wave(const WaveHost& w, uint32_t table_elems, uint32_t arena_elems
                           (sa ? runs_max(t.ffa, t.nfa) : ta);
       const uint64_t eb = runs_max(t.ob, t.no) | runs_max(t.qb, t.nq) |
                           (sb ? runs_max(t.ffb, t.nfb) : tb);
-      check_ref(st.a_off, sa, ea, "tile operand A");
-      check_ref(st.b_off, sb, eb, "tile operand B");
+      check_ref(st.a_off, ga, ea, "tile operand A");
+      check_ref(st.b_off, gbl, eb, "tile operand B");
       if (!(st.flags & GSF_LEAFGRAD))
         check_ref(st.c_off, true, runs_max(t.oc, t.no) | runs_max(t.ffc, t.nfc), "tile output");
       else
@@ -227,6 +229,19 @@ void validate_wave(const WaveHost& w, uint32_t table_elems, uint32_t arena_elems
         fail(QTC_ERR_INVALID, "internal: tile footprints beyond the team's shared memory");
       if (st.done_ctr >= w.n_counters) fail(QTC_ERR_INVALID, "internal: done counter");
       continue;
+    }
+    if (st.flags & (GSF_YPAIR | GSF_LANES_Y)) {
+      auto low_run = [](const GRuns& r) {
+        return (r.n > 0 && r.src[0] == 0 && r.dst[0] == 0) ? (int)r.len[0] : 0;
+      };
+      if (st.flags & (GSF_A_TABLE | GSF_B_TABLE))
+        fail(QTC_ERR_INVALID, "internal: paired or lane-summed step on a table operand");
+      if ((st.flags & GSF_YPAIR) &&
+          (low_run(st.ya) < 1 || low_run(st.yb) < 1 || (st.a_off & 1u) || (st.b_off & 1u) ||
+           (st.flags & GSF_SPLIT)))
+        fail(QTC_ERR_INVALID, "internal: paired loads without adjacent summed pairs");
+      if ((st.flags & GSF_LANES_Y) && !(st.flags & GSF_SPLIT))
+        fail(QTC_ERR_INVALID, "internal: lanes over the summed index outside a split step");
     }
     const uint64_t ma = runs_max(st.ca, st.rc) | runs_max(st.ya, st.ry);
     const uint64_t mb = runs_max(st.cb, st.rc) | runs_max(st.yb, st.ry);

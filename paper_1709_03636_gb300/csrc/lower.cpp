@@ -276,7 +276,7 @@ uint32_t log2_floor(uint64_t x) {
 // A chunk task covers about 2^task_terms_log2 multiply-adds.
 bool encode_gstep(GStep& g, const std::vector<int>& lc, const std::vector<int>& la,
                   const std::vector<int>& lb, bool force_split, int task_terms_log2,
-                  std::string* why) {
+                  bool a_global, bool b_global, std::string* why) {
   std::vector<int> pa, pb, ya, yb;
   for (int x : lc) {
     pa.push_back(pos_in(la, x));
@@ -323,6 +323,15 @@ bool encode_gstep(GStep& g, const std::vector<int>& lc, const std::vector<int>& 
     g.chunk = (uint32_t)per;
     g.n_chunks = (uint32_t)((rows + per - 1) / per);
   }
+  // access forms: the summed index's lowest bits against the operands' own
+  auto low_run = [](const GRuns& r) {
+    return (r.n > 0 && r.src[0] == 0 && r.dst[0] == 0) ? (int)r.len[0] : 0;
+  };
+  const int la0 = low_run(g.ya), lb0 = low_run(g.yb);
+  if (a_global && b_global && g.ry >= 1 && la0 >= 1 && lb0 >= 1 && !(g.flags & GSF_SPLIT))
+    g.flags |= GSF_YPAIR;
+  if (a_global && b_global && (g.flags & GSF_SPLIT) && std::max(la0, lb0) >= 3)
+    g.flags |= GSF_LANES_Y;
   (void)log2_floor;
   return true;
 }
@@ -758,7 +767,8 @@ NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
     u.kind = GT_CHUNK;
     std::memset(&u.step, 0, sizeof u.step);
     std::string why;
-    if (!encode_gstep(u.step, lc, la, lb, leaf_for_grad >= 0, lim.task_terms_log2, &why)) {
+    if (!encode_gstep(u.step, lc, la, lb, leaf_for_grad >= 0, lim.task_terms_log2, ra.global,
+                      rb.global, &why)) {
       ng.fits = false;
       ng.why = why;
       return -1;
@@ -768,10 +778,13 @@ NetGraph lower_graph(const Plan& plan, const std::vector<int>& leaf_gate,
     (void)b;
     if (leaf_for_grad >= 0) u.step.flags |= GSF_LEAFGRAD;
     const bool two_global = ra.global && rb.global;
-    if (lim.tile_mode == 2 || (lim.tile_mode == 1 && (two_global || (u.step.flags & GSF_SPLIT)))) {
+    const int tm = lim.tile_mode;
+    if (tm == 2 || tm == 4 || (tm == 1 && (two_global || (u.step.flags & GSF_SPLIT))) ||
+        (tm == 3 && u.step.ry >= 3)) {
       GStep tiled = u.step;
-      tiled.flags &= (uint16_t)~GSF_SPLIT;
-      if (encode_tile(tiled, lc, la, lb, !ra.global, !rb.global, lim.elem, lim.task_terms_log2))
+      tiled.flags &= (uint16_t)~(GSF_SPLIT | GSF_YPAIR | GSF_LANES_Y);
+      if (encode_tile(tiled, lc, la, lb, !ra.global, !rb.global, lim.elem, lim.task_terms_log2,
+                      tm >= 3))
         u.step = tiled;
     }
     u.step.c_off = (uint32_t)std::max<int64_t>(c_off, 0);

@@ -190,8 +190,10 @@ struct GraphLimits {
   bool reuse_global = true;          // place global tensors by live range (memory reuse)
   bool reuse_with_deps = false;      // also where it takes new write-after-read dependencies
   int checkpoint_segments = 1;       // > 1: adjoint recomputes dropped values per segment
-  int tile_mode = 0;                 // global steps in tile form: 0 never, 1 steps with two
-                                     // operands in global memory, 2 every step that tiles
+  int tile_mode = 0;                 // global steps in tile form: 0 never; staged through
+                                     // shared memory: 1 steps with two operands in global
+                                     // memory, 2 every step that tiles; read in place:
+                                     // 3 steps summing >= 3 labels, 4 every step that tiles
   size_t elem = 8;                   // bytes per element
 };
 
@@ -200,7 +202,7 @@ struct GraphLimits {
 // already set); false leaves g as it was.
 bool encode_tile(GStep& g, const std::vector<int>& lc, const std::vector<int>& la,
                  const std::vector<int>& lb, bool a_table, bool b_table, size_t elem,
-                 int task_terms_log2);
+                 int task_terms_log2, bool direct);
 // Shared memory of a team's work region a tile task needs.
 size_t tile_region_bytes(const GStep& g, size_t elem);
 // Host emulation of one tile step on seeded random operands against the

@@ -50,7 +50,7 @@ uint64_t apply(const GRuns& r, uint64_t idx) {
 
 bool encode_tile(GStep& g, const std::vector<int>& lc, const std::vector<int>& la,
                  const std::vector<int>& lb, bool a_table, bool b_table, size_t elem,
-                 int task_terms_log2) {
+                 int task_terms_log2, bool direct) {
   GTileMap& t = g.tile;
   std::memset(&t, 0, sizeof t);
   std::vector<int> all(lc);
@@ -61,7 +61,10 @@ bool encode_tile(GStep& g, const std::vector<int>& lc, const std::vector<int>& l
   auto in_a = [&](int l) { return pos_of(la, l) >= 0; };
   auto in_b = [&](int l) { return pos_of(lb, l) >= 0; };
   auto in_c = [&](int l) { return pos_of(lc, l) >= 0; };
-  const bool stage_a = !a_table, stage_b = !b_table;
+  // operands in global memory are copied through shared memory, unless the
+  // tile reads them where they are (direct)
+  const bool glob_a = !a_table, glob_b = !b_table;
+  const bool stage_a = glob_a && !direct, stage_b = glob_b && !direct;
   const uint32_t budget = kTileBudgetBytes / (uint32_t)elem;
 
   std::vector<int> V;
@@ -73,7 +76,8 @@ bool encode_tile(GStep& g, const std::vector<int>& lc, const std::vector<int>& l
       fb += in_b(l);
       fc += in_c(l);
     }
-    uint64_t need = (1ull << fc);
+    // (read in place, the cross-warp reduction needs its own room)
+    uint64_t need = (1ull << fc) + (direct ? (256ull << kTileMaxOut) : 0);
     if (stage_a) need += 1ull << fa;
     if (stage_b) need += 1ull << fb;
     return need;
@@ -87,10 +91,11 @@ bool encode_tile(GStep& g, const std::vector<int>& lc, const std::vector<int>& l
     }
     return true;
   };
-  // the lowest bits of every copied tensor, for contiguous copies
+  // the lowest bits of every tensor in global memory, for contiguous copies
+  // (or coalesced reads)
   for (int i = 0; i < 5; ++i) {
-    if (stage_a && i < (int)la.size()) V.push_back(la[i]);
-    if (stage_b && i < (int)lb.size() && !has(lb[i])) V.push_back(lb[i]);
+    if (glob_a && i < (int)la.size()) V.push_back(la[i]);
+    if (glob_b && i < (int)lb.size() && !has(lb[i])) V.push_back(lb[i]);
     if (i < (int)lc.size() && !has(lc[i])) V.push_back(lc[i]);
   }
   {
@@ -114,10 +119,11 @@ bool encode_tile(GStep& g, const std::vector<int>& lc, const std::vector<int>& l
   int n_reg_sum = 0;
   for (int l : summed)
     if (!has(l) && n_reg_sum < kTileMaxRegSum) n_reg_sum += try_add(l);
+  const size_t max_v = direct ? 8 + kTileMaxOut + kTileMaxRegSum : 24;
   // reuse: output labels an operand lacks make it be copied once per value
   // outside the tile; take them into the tile, the larger operand's first
-  const double bytes_a = stage_a ? std::ldexp(1.0, (int)la.size()) : 0.0;
-  const double bytes_b = stage_b ? std::ldexp(1.0, (int)lb.size()) : 0.0;
+  const double bytes_a = glob_a ? std::ldexp(1.0, (int)la.size()) : 0.0;
+  const double bytes_b = glob_b ? std::ldexp(1.0, (int)lb.size()) : 0.0;
   std::vector<int> z_lab, x_lab;   // output labels not in A / not in B
   for (int l : lc) {
     if (!in_a(l)) z_lab.push_back(l);
@@ -131,7 +137,7 @@ bool encode_tile(GStep& g, const std::vector<int>& lc, const std::vector<int>& l
   const int max_out = 8 + kTileMaxOut;
   auto add_reuse = [&](const std::vector<int>& lab) {
     for (int l : lab)
-      if (!has(l) && output_bits() < max_out) try_add(l);
+      if (!has(l) && output_bits() < max_out && V.size() < max_v) try_add(l);
   };
   if (bytes_a >= bytes_b) {
     add_reuse(z_lab);
@@ -142,16 +148,16 @@ bool encode_tile(GStep& g, const std::vector<int>& lc, const std::vector<int>& l
   }
   // larger tiles of output labels, lowest first, while the task stays small
   for (int l : lc) {
-    if ((int)V.size() >= 13 || output_bits() >= max_out) break;
+    if ((int)V.size() >= 13 || output_bits() >= max_out || V.size() >= max_v) break;
     if (!has(l)) try_add(l);
   }
-  if (V.size() < 8 || V.size() > 24) return false;
+  if (V.size() < 8 || V.size() > max_v) return false;
 
   // tile index order: lanes follow the larger copied operand's footprint
   // (consecutive lanes read consecutive shared-memory words), warps prefer
   // output labels, then register output labels, then register summed labels
-  const std::vector<int>& lead = (stage_a && (bytes_a >= bytes_b || !stage_b)) ? la
-                                 : stage_b ? lb : lc;
+  const std::vector<int>& lead = (glob_a && (bytes_a >= bytes_b || !glob_b)) ? la
+                                 : glob_b ? lb : lc;
   std::vector<int> foot;   // V's labels in the lead tensor's bit order
   for (int l : lead)
     if (has(l)) foot.push_back(l);
@@ -179,6 +185,7 @@ bool encode_tile(GStep& g, const std::vector<int>& lc, const std::vector<int>& l
   if (order.size() != V.size()) return false;
 
   t.nv = (uint8_t)order.size();
+  t.staged = (uint8_t)((stage_a ? 1 : 0) | (stage_b ? 2 : 0));
   t.kout = (uint8_t)reg_out.size();
   t.ns = (uint8_t)reg_sum.size();
   for (int i = 0; i < 5; ++i)
@@ -275,8 +282,8 @@ size_t tile_region_bytes(const GStep& g, size_t elem) {
   // footprint of complex64 is at least one 16-byte pair
   const size_t min_fp = elem == 8 ? 2 : 1;
   size_t ab = 0;
-  if (!(g.flags & GSF_A_TABLE)) ab += std::max(min_fp, (size_t)1 << t.nfa);
-  if (!(g.flags & GSF_B_TABLE)) ab += std::max(min_fp, (size_t)1 << t.nfb);
+  if (t.staged & 1) ab += std::max(min_fp, (size_t)1 << t.nfa);
+  if (t.staged & 2) ab += std::max(min_fp, (size_t)1 << t.nfb);
   if (t.sum_warp_mask) ab = std::max(ab, (size_t)256 << t.kout);
   const size_t c = std::max(min_fp, (size_t)1 << t.nfc);
   return (((ab + c) * elem + 15) & ~size_t(15)) + ((size_t)8 << t.ns);
@@ -300,7 +307,7 @@ double emulate_tile_step(const GStep& g, uint64_t seed) {
     for (uint64_t y = 0; y < (1ull << g.ry); ++y)
       R[c] += A[apply(g.ca, c) | apply(g.ya, y)] * B[apply(g.cb, c) | apply(g.yb, y)];
   // tile form, chunk by chunk
-  const bool sa = !(g.flags & GSF_A_TABLE), sb = !(g.flags & GSF_B_TABLE);
+  const bool sa = (t.staged & 1) != 0, sb = (t.staged & 2) != 0;
   const uint64_t nq = 1ull << t.nq;
   std::vector<std::complex<double>> partial;
   const bool split = (g.flags & GSF_SPLIT) != 0;

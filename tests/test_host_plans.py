@@ -571,7 +571,7 @@ def test_checkpoint_segments_when_one_network_exceeds_the_limit():
                 "net_global_bytes"])))
 
 
-@pytest.mark.parametrize("tile_mode", [1, 2])
+@pytest.mark.parametrize("tile_mode", [1, 2, 3, 4])
 def test_tile_steps_emulated_against_the_plain_contraction(tile_mode):
     """The tile form of global steps (footprints copied through shared memory,
     lanes/warps/registers over the tile, reductions over summed lane and warp
@@ -592,4 +592,4 @@ def test_tile_steps_emulated_against_the_plain_contraction(tile_mode):
                 ctypes.byref(err), ctypes.byref(cnt)))
             assert err.value < 1e-11, (kw, small, grad, dtype)
             checked += cnt.value
-    assert checked > 500
+    assert checked > (500 if tile_mode != 3 else 20)
