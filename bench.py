@@ -137,7 +137,8 @@ def workload_config(w, networks, want_grad, dtype, noise=None, world=1):
         "graph": f"{w.d}-regular, n={w.n}, configuration model seed {w.graph_seed}",
         "p": w.p,
         "networks_per_step": networks,
-        "ordering": w.ordering,
+        "ordering": w.ordering + (f" ({w.restarts} randomised min-fill runs)"
+                                  if w.ordering == "lg" else ""),
         "form": ("diagonal ZZ (hyperedges)" if w.diag else "rank-4 ZZ") +
                 (", light cone" if w.lightcone else ", full network"),
         "want_grad": want_grad,
@@ -396,7 +397,8 @@ class Bench:
         edges = w.graph()
         g, b = w.angles()
         circ = q.Circuit.qaoa(w.n, edges, w.p, noise=noise)
-        full = q.Batch(circ, obs_edges, lightcone=w.lightcone, diag=w.diag, ordering=w.ordering)
+        full = q.Batch(circ, obs_edges, lightcone=w.lightcone, diag=w.diag, ordering=w.ordering,
+                       restarts=w.restarts)
         batch, mine = q.shard(full, self.rank, self.world, want_grad=max(grads))
         if batch is None:
             raise SystemExit(f"rank {self.rank} has no edge network of {w.name}")
@@ -665,7 +667,8 @@ def per_network(bench, st, args, fwd):
     import torch
     q = bench.q
     w = st["w"]
-    singles = [q.Batch(st["circ"], [e], lightcone=w.lightcone, diag=w.diag, ordering=w.ordering)
+    singles = [q.Batch(st["circ"], [e], lightcone=w.lightcone, diag=w.diag, ordering=w.ordering,
+                       restarts=w.restarts)
                for e in st["batch"].edges]
     outs = [torch.zeros(2 + st["P"] + 1, dtype=torch.float64, device=bench.dev)
             for _ in singles]

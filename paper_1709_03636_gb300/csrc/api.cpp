@@ -43,6 +43,7 @@ struct Prepared {
   bool stream = false;               // warp teams: steps streamed from global memory
   bool graph = false;
   bool hi_occ = false;               // graph form: the five-CTAs-per-SM instantiation
+  bool tiles = false;                // graph form: the instantiation with tile steps
   int per_sm = 0;                    // resident CTAs per SM reported by the runtime
   std::vector<GraphProgDev> waves;   // graph form: one launch each
   double* raw = nullptr;             // graph form: copy of the result rows
@@ -335,8 +336,8 @@ extern "C" qtc_status qtc_selftest_wait_timeout(qtc_engine* e, void* stream) {
     int per_sm = 0;
     const size_t max_dyn = max_dynamic_smem(e->smem_optin);
     const size_t smem = 2 * (size_t)kYTab * sizeof(uint32_t) + 256 * 16;
-    cuda_check(graph_exec_configure(1, false, false, smem, max_dyn, &per_sm), "configure");
-    cuda_check(graph_exec_launch(d, 1, false, 1, smem, s), "launch");
+    cuda_check(graph_exec_configure(1, false, false, false, smem, max_dyn, &per_sm), "configure");
+    cuda_check(graph_exec_launch(d, 1, false, false, 1, smem, s), "launch");
     double host_out[2] = {0, 0};
     cuda_check(cudaMemcpyAsync(host_out, out, sizeof host_out, cudaMemcpyDeviceToHost, s), "read");
     cuda_check(cudaStreamSynchronize(s), "synchronise");
@@ -1045,9 +1046,11 @@ static Prepared& prepare_graph(qtc_engine* e, qtc_batch* b, const HostProgram& h
   cuda_check(cudaMemsetAsync(dres, 0, sizeof(double) * N * stride, stream), "clear results");
   cuda_check(cudaStreamSynchronize(stream), "prepare sync");
   int per_sm = 0;
-  pr.hi_occ = hp.options.graph_hi_occupancy && hp.dtype == QTC_C64 && !hp.tensor_cores;
+  pr.tiles = hp.tiles && !hp.tensor_cores;
+  pr.hi_occ = hp.options.graph_hi_occupancy && hp.dtype == QTC_C64 && !hp.tensor_cores &&
+              !pr.tiles;
   cuda_check(graph_exec_configure(hp.dtype == QTC_C128 ? 0 : 1, hp.tensor_cores, pr.hi_occ,
-                                  hp.smem, max_dyn, &per_sm),
+                                  pr.tiles, hp.smem, max_dyn, &per_sm),
              "configure graph executor");
   if (per_sm < 1) fail(QTC_ERR_UNSUPPORTED, "graph executor does not fit on an SM");
   // tensor memory: 512 columns per SM shared by the resident CTAs; a GEMM
@@ -1194,8 +1197,8 @@ static void launch(qtc_engine* e, const Prepared& pr, const double* params_dev, 
       d.params = params_dev;
       d.out = out_dev;
       d.gbase = e->work_base();
-      cuda_check(graph_exec_launch(d, pr.dtype == QTC_C128 ? 0 : 1, pr.hi_occ, pr.grid,
-                                   pr.smem, stream),
+      cuda_check(graph_exec_launch(d, pr.dtype == QTC_C128 ? 0 : 1, pr.hi_occ, pr.tiles,
+                                   pr.grid, pr.smem, stream),
                  "launch graph executor");
     }
     e->last_launches = (int)pr.waves.size();

@@ -333,6 +333,105 @@ __device__ void tile_contract(const GStep& st, const T* Ag, const T* Bg, T* As, 
   team.sync();
 }
 
+// A tile whose operands are read where they are (nothing staged): per
+// thread the tile offsets are formed once, every outer output value o is
+// contracted in registers (global or table loads, lanes over the lead
+// operand's lowest bits), reduced over summed lane bits by shuffles and over
+// summed warp bits through shared memory, and the owners store their outputs
+// to C (or, split, to the chunk's partial slot in C-footprint order)
+// directly.  Returns the split arrival like run_tile's staged form.
+template <typename T, int kTeams, int kOut>
+__device__ void tile_direct(const GStep& st, const GTask& task, const T* Ag, const T* Bg, T* C,
+                            T* partial, T* red, const uint2* soff, const GTeam<kTeams>& team) {
+  const GTileMap& tm = st.tile;
+  const bool split = (st.flags & GSF_SPLIT) != 0;
+  const uint32_t tid = team.tid, lane = tid & 31u, warp = tid >> 5;
+  const uint32_t a_lw = runs_offset(tm.tfa, tid), b_lw = runs_offset(tm.tfb, tid);
+  uint32_t ak[1 << kOut], bk[1 << kOut], ck[1 << kOut];
+#pragma unroll
+  for (int k = 0; k < (1 << kOut); ++k) {
+    const uint32_t t = tid | ((uint32_t)k << 8);
+    ak[k] = a_lw | runs_offset(tm.tfa, (uint32_t)k << 8);
+    bk[k] = b_lw | runs_offset(tm.tfb, (uint32_t)k << 8);
+    const uint32_t fc = runs_offset(tm.tfc, t);   // C-footprint index
+    ck[k] = split ? fc : runs_offset(tm.ffc, fc);
+  }
+  const bool owner = (lane & tm.sum_lane_mask) == 0 && (warp & tm.sum_warp_mask) == 0;
+  const uint32_t nq = 1u << tm.nq, no = 1u << tm.no, ns = 1u << tm.ns;
+  uint32_t o0, o1, q0, q1;
+  if (split) {
+    o0 = 0;
+    o1 = 1;
+    q0 = task.b * tm.q_per_chunk;
+    q1 = min(q0 + tm.q_per_chunk, nq);
+  } else {
+    o0 = task.b * tm.o_per_chunk;
+    o1 = min(o0 + tm.o_per_chunk, no);
+    q0 = 0;
+    q1 = nq;
+  }
+  for (uint32_t o = o0; o < o1; ++o) {
+    T acc[1 << kOut];
+#pragma unroll
+    for (int k = 0; k < (1 << kOut); ++k) acc[k] = czero<T>();
+    const uint32_t abase = runs_offset(tm.oa, o), bbase = runs_offset(tm.ob, o);
+    for (uint32_t q = q0; q < q1; ++q) {
+      const T* Ab = Ag + (abase | runs_offset(tm.qa, q));
+      const T* Bb = Bg + (bbase | runs_offset(tm.qb, q));
+      uint32_t sidx = 0;
+      for (; sidx + 3 < ns; sidx += 4) {
+        const uint2 o0_ = soff[sidx], o1_ = soff[sidx + 1], o2_ = soff[sidx + 2], o3_ = soff[sidx + 3];
+#pragma unroll
+        for (int k = 0; k < (1 << kOut); ++k) {
+          const T a0 = Ab[ak[k] | o0_.x], b0 = Bb[bk[k] | o0_.y];
+          const T a1 = Ab[ak[k] | o1_.x], b1 = Bb[bk[k] | o1_.y];
+          const T a2 = Ab[ak[k] | o2_.x], b2 = Bb[bk[k] | o2_.y];
+          const T a3 = Ab[ak[k] | o3_.x], b3 = Bb[bk[k] | o3_.y];
+          acc[k] = cfma(a3, b3, cfma(a2, b2, cfma(a1, b1, cfma(a0, b0, acc[k]))));
+        }
+      }
+      for (; sidx < ns; ++sidx) {
+        const uint2 oo = soff[sidx];
+#pragma unroll
+        for (int k = 0; k < (1 << kOut); ++k) acc[k] = cfma(Ab[ak[k] | oo.x], Bb[bk[k] | oo.y], acc[k]);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 5; ++m)
+      if ((tm.sum_lane_mask >> m) & 1u) {
+#pragma unroll
+        for (int k = 0; k < (1 << kOut); ++k) acc[k] = cadd(acc[k], shfl_xor_c(acc[k], 1 << m));
+      }
+    if (tm.sum_warp_mask) {
+#pragma unroll
+      for (int k = 0; k < (1 << kOut); ++k) red[((uint32_t)k << 8) | tid] = acc[k];
+      team.sync();
+      if (owner) {
+#pragma unroll
+        for (int k = 0; k < (1 << kOut); ++k) {
+          T sum = czero<T>();
+          for (uint32_t w2 = 0; w2 < 8; ++w2)
+            if ((w2 & ~(uint32_t)tm.sum_warp_mask) == warp)
+              sum = cadd(sum, red[((uint32_t)k << 8) | (w2 << 5) | lane]);
+          acc[k] = sum;
+        }
+      }
+      team.sync();
+    }
+    if (owner) {
+      if (split) {
+        T* dst = partial + ((size_t)task.b << tm.nfc);
+#pragma unroll
+        for (int k = 0; k < (1 << kOut); ++k) dst[ck[k]] = acc[k];
+      } else {
+        const uint32_t cbase = runs_offset(tm.oc, o);
+#pragma unroll
+        for (int k = 0; k < (1 << kOut); ++k) C[cbase | ck[k]] = acc[k];
+      }
+    }
+  }
+}
+
 // A tile task: for each outer output value of the chunk (or, split, the
 // chunk's outer summed values) contract the tile, then copy the C tile out
 // (or into the chunk's partial slot; the last chunk of a split step adds the
@@ -377,6 +476,15 @@ __device__ void run_tile(const GraphProgDev& prog, const GTask& task, T* table,
   constexpr uint32_t per = 16 / sizeof(T);
   T* C = gb + st.c_off;
   T* partial = gb + st.partial_off;
+  if (tm.staged == 0) {
+    // read in place: no footprints, outputs stored by their owners
+    switch (tm.kout) {
+      case 0: tile_direct<T, kTeams, 0>(st, task, Ag, Bg, C, partial, As, soff, team); break;
+      case 1: tile_direct<T, kTeams, 1>(st, task, Ag, Bg, C, partial, As, soff, team); break;
+      default: tile_direct<T, kTeams, 2>(st, task, Ag, Bg, C, partial, As, soff, team); break;
+    }
+    o1 = o0;   // done
+  }
   for (uint32_t o = o0; o < o1; ++o) {
     switch (tm.kout) {
       case 0: tile_contract<T, kTeams, 0>(st, Ag, Bg, As, Bs, Cs, As, soff, o, q0, q1, team); break;
@@ -567,7 +675,7 @@ __device__ __forceinline__ T warp_ysum(const T* A, const T* B, uint32_t oa, uint
   return sum;
 }
 
-template <typename T, int kTeams>
+template <typename T, int kTeams, bool kTile>
 __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
                           unsigned char* work, GStep& s_step, int& s_last,
                           const GTeam<kTeams>& team) {
@@ -578,9 +686,11 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
   }
   team.sync();
   const GStep& st = s_step;
-  if (st.flags & GSF_TILE) {
-    run_tile<T, kTeams>(prog, task, table, work, st, s_last, team);
-    return;
+  if constexpr (kTile) {
+    if (st.flags & GSF_TILE) {
+      run_tile<T, kTeams>(prog, task, table, work, st, s_last, team);
+      return;
+    }
   }
   T* gb = reinterpret_cast<T*>(prog.gbase);
   const T* A = (st.flags & GSF_A_TABLE) ? table + st.a_off : gb + st.a_off;
@@ -953,7 +1063,9 @@ __device__ bool run_tc(const GraphProgDev& prog, const GTask& task, unsigned cha
 // kHiOcc (complex64, no tensor cores): registers capped for five 256-thread
 // CTAs per SM instead of four (some spilling); helps programs dominated by
 // large memory-bound steps, hurts others (chosen per batch by tuning).
-template <typename T, bool kTc, bool kHiOcc = false>
+// kTile: the program has steps in tile form (a separate instantiation keeps
+// the tile code's registers out of the row and split paths).
+template <typename T, bool kTc, bool kHiOcc = false, bool kTile = false>
 __global__ void __launch_bounds__(kGraphBlock*(kTc ? 4 : 1),
                                   kTc ? 1 : kHiOcc ? 5 : sizeof(T) == 8 ? 4 : 2)
     graph_exec_kernel(const GraphProgDev prog) {
@@ -1013,7 +1125,7 @@ __global__ void __launch_bounds__(kGraphBlock*(kTc ? 4 : 1),
     if (task.kind == GT_SMEM) {
       run_smem_task<T, kTeams>(prog, task, table, work, s_grad[team.id], team);
     } else if (task.kind == GT_CHUNK) {
-      run_chunk<T, kTeams>(prog, task, table, work, s_step[team.id], s_last[team.id], team);
+      run_chunk<T, kTeams, kTile>(prog, task, table, work, s_step[team.id], s_last[team.id], team);
     } else if (kTc && prog.tmem_cols > 0) {
       if (!run_tc<T, kTeams>(prog, task, work, s_tstep[kTc ? team.id : 0], tmem,
                              smem_addr(&s_mbar[team.id]), phase, team)) {
@@ -1073,18 +1185,21 @@ __global__ void __launch_bounds__(kGraphBlock*(kTc ? 4 : 1),
   }
 }
 
-static const void* graph_kernel(int dtype, bool tc, bool hi_occ) {
-  if (dtype == 0)
-    return tc ? (const void*)graph_exec_kernel<double2, true>
-              : (const void*)graph_exec_kernel<double2, false>;
+static const void* graph_kernel(int dtype, bool tc, bool hi_occ, bool tiles) {
+  if (dtype == 0) {
+    if (tc) return (const void*)graph_exec_kernel<double2, true>;
+    return tiles ? (const void*)graph_exec_kernel<double2, false, false, true>
+                 : (const void*)graph_exec_kernel<double2, false>;
+  }
   if (tc) return (const void*)graph_exec_kernel<float2, true>;
+  if (tiles) return (const void*)graph_exec_kernel<float2, false, false, true>;
   return hi_occ ? (const void*)graph_exec_kernel<float2, false, true>
                 : (const void*)graph_exec_kernel<float2, false>;
 }
 
-cudaError_t graph_exec_configure(int dtype, bool tc, bool hi_occ, size_t smem_bytes,
+cudaError_t graph_exec_configure(int dtype, bool tc, bool hi_occ, bool tiles, size_t smem_bytes,
                                  size_t max_dynamic, int* blocks_per_sm) {
-  const void* fn = graph_kernel(dtype, tc, hi_occ);
+  const void* fn = graph_kernel(dtype, tc, hi_occ, tiles);
   if (smem_bytes > max_dynamic) return cudaErrorInvalidValue;
   cudaError_t err =
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dynamic);
@@ -1093,17 +1208,23 @@ cudaError_t graph_exec_configure(int dtype, bool tc, bool hi_occ, size_t smem_by
                                                        kGraphBlock * (tc ? 4 : 1), smem_bytes);
 }
 
-cudaError_t graph_exec_launch(const GraphProgDev& prog, int dtype, bool hi_occ, int grid,
-                              size_t smem_bytes, cudaStream_t stream) {
+cudaError_t graph_exec_launch(const GraphProgDev& prog, int dtype, bool hi_occ, bool tiles,
+                              int grid, size_t smem_bytes, cudaStream_t stream) {
   const bool tc = prog.tmem_cols > 0;
   if (dtype == 0) {
     if (tc)
       graph_exec_kernel<double2, true><<<grid, 4 * kGraphBlock, smem_bytes, stream>>>(prog);
+    else if (tiles)
+      graph_exec_kernel<double2, false, false, true>
+          <<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
     else
       graph_exec_kernel<double2, false><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
   } else {
     if (tc)
       graph_exec_kernel<float2, true><<<grid, 4 * kGraphBlock, smem_bytes, stream>>>(prog);
+    else if (tiles)
+      graph_exec_kernel<float2, false, false, true>
+          <<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
     else if (hi_occ)
       graph_exec_kernel<float2, false, true><<<grid, kGraphBlock, smem_bytes, stream>>>(prog);
     else

@@ -27,9 +27,10 @@ cudaError_t smem_exec_launch(const ProgramDev& prog, int dtype, int mode, int gr
 // tc: the program has tensor-core GEMM tasks (GraphProgDev.tmem_cols > 0).
 // hi_occ (complex64 without tensor cores): the instantiation capped for five
 // CTAs per SM.
-cudaError_t graph_exec_configure(int dtype, bool tc, bool hi_occ, size_t smem_bytes,
+// tiles: the program has steps in tile form (the instantiation with tile code)
+cudaError_t graph_exec_configure(int dtype, bool tc, bool hi_occ, bool tiles, size_t smem_bytes,
                                  size_t max_dynamic, int* blocks_per_sm);
-cudaError_t graph_exec_launch(const GraphProgDev& prog, int dtype, bool hi_occ, int grid,
-                              size_t smem_bytes, cudaStream_t stream);
+cudaError_t graph_exec_launch(const GraphProgDev& prog, int dtype, bool hi_occ, bool tiles,
+                              int grid, size_t smem_bytes, cudaStream_t stream);
 
 }  // namespace qtc

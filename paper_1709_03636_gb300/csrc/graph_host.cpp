@@ -305,6 +305,7 @@ void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
   lim.elem = elem;
   if (opts.small_rank > 0) lim.small_rank = opts.small_rank;
   lim.tensor_cores = hp.dtype == QTC_SPLIT_BF16;
+  if (lim.tensor_cores) lim.tile_mode = 0;   // the tensor-core build has no tile tasks
   // with tensor cores four teams share one CTA's shared memory
   if (lim.tensor_cores) lim.arena_elems = (uint32_t)(32768 / elem);
   std::vector<NetGraph> graphs(N);
@@ -413,9 +414,13 @@ void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
   const size_t chunk_task = 2 * (size_t)kYTab * sizeof(uint32_t) + 256 * elem +
                             2 * (size_t)kMaxChunkRows * sizeof(uint32_t);
   size_t tile_task = 0;
+  hp.tiles = false;
   for (const WaveHost& w : hp.waves)
     for (const GStep& st : w.steps)
-      if (st.flags & GSF_TILE) tile_task = std::max(tile_task, tile_region_bytes(st, elem));
+      if (st.flags & GSF_TILE) {
+        tile_task = std::max(tile_task, tile_region_bytes(st, elem));
+        hp.tiles = true;
+      }
   hp.work_bytes = round16(std::max({smem_task, chunk_task, tile_task}));
   hp.table_bytes = round16((size_t)hp.table_elems * elem);
   hp.smem = hp.table_bytes + (size_t)(hp.tensor_cores ? 4 : 1) * hp.work_bytes;

@@ -330,6 +330,7 @@ struct HostProgram {
   int max_checkpoint_segments = 1; // most checkpoint segments of any network
   uint32_t max_counters = 0;
   bool tensor_cores = false;       // some wave has tensor-core GEMM tasks
+  bool tiles = false;              // some wave has steps in tile form
 };
 
 // Built once per (batch, dtype, want_grad, budget, options) and cached in the

@@ -114,7 +114,7 @@ def test_p3_n60_d4_all_edges_waves_agree(engine):
     edges = w.graph()
     g, b = w.angles()
     circ = q.Circuit.qaoa(w.n, edges, w.p)
-    batch = q.Batch(circ, ordering="lg")
+    batch = q.Batch(circ, ordering="lg", restarts=w.restarts)
     C, per_edge, grad = q.qaoa_expectation(engine, batch, g, b, "c64", want_grad=True)
     assert engine.last_launches == 1
     C1, per_edge1, _ = q.qaoa_expectation(engine, batch, g, b, "c64", want_grad=False)

@@ -107,7 +107,7 @@ def test_p3_n60_every_edge_value_and_sampled_gradients(engine):
     edges = w.graph()
     g, b = w.angles()
     circ = q.Circuit.qaoa(w.n, edges, w.p)
-    batch = q.Batch(circ, ordering="lg")
+    batch = q.Batch(circ, ordering="lg", restarts=w.restarts)   # as the bench plans it
     C, per_edge, grad = q.qaoa_expectation(engine, batch, g, b, "c64", want_grad=True)
     ref = np.array([v.real for v in _oracle_map(
         functools.partial(tn.edge_value, w.n, edges, g, b), edges)])
