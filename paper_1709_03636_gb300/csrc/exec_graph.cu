@@ -751,16 +751,20 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
             ob[r] = rowb[rr] | b_lo;
             acc[r] = czero<T>();
           }
-          for (uint32_t y = 0; y < n_y; ++y) {
-            const uint32_t ay = ya[y], by = yb[y];
-            T av[R], bv[R];
+          // two summed values per pass (n_y >= 8 here): sixteen loads in flight
+          for (uint32_t y = 0; y < n_y; y += 2) {
+            const uint32_t ay0 = ya[y], by0 = yb[y], ay1 = ya[y + 1], by1 = yb[y + 1];
+            T av[R][2], bv[R][2];
 #pragma unroll
             for (uint32_t r = 0; r < R; ++r) {
-              av[r] = A[oa[r] | ay];
-              bv[r] = B[ob[r] | by];
+              av[r][0] = A[oa[r] | ay0];
+              bv[r][0] = B[ob[r] | by0];
+              av[r][1] = A[oa[r] | ay1];
+              bv[r][1] = B[ob[r] | by1];
             }
 #pragma unroll
-            for (uint32_t r = 0; r < R; ++r) acc[r] = cfma(av[r], bv[r], acc[r]);
+            for (uint32_t r = 0; r < R; ++r)
+              acc[r] = cfma(av[r][1], bv[r][1], cfma(av[r][0], bv[r][0], acc[r]));
           }
 #pragma unroll
           for (uint32_t r = 0; r < R; ++r)
@@ -978,11 +982,37 @@ __device__ bool run_tc(const GraphProgDev& prog, const GTask& task, unsigned cha
   const uint32_t n_g = nt * kTcCols + b_c;
   const uint32_t b_col = runs_offset(ts.bn, n_g) | runs_offset(ts.bbt, bi);
   const uint32_t nk = (K + kTcK - 1) / kTcK;
-  for (uint32_t kc = 0; kc < nk; ++kc) {
+  // the operands of K slice kc + 1 are loaded into registers while the MMAs
+  // of slice kc run (the shared-memory stage is single, so they are stored
+  // after the MMAs complete)
+  T av[8], bv[4];
+  // the K maps are bit permutations: offset(kc * 16 + kl) = offset(kc * 16) |
+  // offset(kl), so each thread keeps the offsets of its own k within a slice
+  uint32_t akl[8], bkl[4];
+#pragma unroll
+  for (uint32_t j = 0; j < 8; ++j) akl[j] = runs_offset(ts.ak, a_k0 + j);
+#pragma unroll
+  for (uint32_t j = 0; j < 4; ++j) bkl[j] = runs_offset(ts.bk, b_k0 + j);
+  auto load_slice = [&](uint32_t kc) {
+    const uint32_t ka = a_row | runs_offset(ts.ak, kc * kTcK);
+    const uint32_t kb = b_col | runs_offset(ts.bk, kc * kTcK);
+#pragma unroll
     for (uint32_t j = 0; j < 8; ++j) {
-      const uint32_t kl = a_k0 + j, k = kc * kTcK + kl;
-      double2 v = make_double2(0.0, 0.0);
-      if (m_ok && k < K) v = to_d2(A[a_row | runs_offset(ts.ak, k)]);
+      const uint32_t k = kc * kTcK + a_k0 + j;
+      av[j] = (m_ok && k < K) ? A[ka | akl[j]] : czero<T>();
+    }
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j) {
+      const uint32_t k = kc * kTcK + b_k0 + j;
+      bv[j] = k < K ? B[kb | bkl[j]] : czero<T>();
+    }
+  };
+  load_slice(0);
+  for (uint32_t kc = 0; kc < nk; ++kc) {
+#pragma unroll
+    for (uint32_t j = 0; j < 8; ++j) {
+      const uint32_t kl = a_k0 + j;
+      const double2 v = to_d2(av[j]);
       __nv_bfloat16 rh, rl, ih, il;
       split_bf16((float)v.x, rh, rl);
       split_bf16((float)v.y, ih, il);
@@ -990,10 +1020,10 @@ __device__ bool run_tc(const GraphProgDev& prog, const GTask& task, unsigned cha
       *reinterpret_cast<uint32_t*>(a_hi + off) = pack_bf16(rh, ih);
       *reinterpret_cast<uint32_t*>(a_lo + off) = pack_bf16(rl, il);
     }
+#pragma unroll
     for (uint32_t j = 0; j < 4; ++j) {
-      const uint32_t kl = b_k0 + j, k = kc * kTcK + kl;
-      double2 v = make_double2(0.0, 0.0);
-      if (k < K) v = to_d2(B[b_col | runs_offset(ts.bk, k)]);
+      const uint32_t kl = b_k0 + j;
+      const double2 v = to_d2(bv[j]);
       __nv_bfloat16 rh, rl, ih, il;
       split_bf16((float)v.x, rh, rl);
       split_bf16((float)v.y, ih, il);
@@ -1018,6 +1048,7 @@ __device__ bool run_tc(const GraphProgDev& prog, const GTask& task, unsigned cha
       }
       tc_commit(mbar);
     }
+    if (kc + 1 < nk) load_slice(kc + 1);
     const bool ok = mbar_wait_bounded(mbar, phase, prog.wait_limit_ns);
     phase ^= 1u;
     if (!ok) {
