@@ -48,7 +48,7 @@ KERNEL_SOURCES = {
     "smem_exec_kernel": ["exec_smem.cu", "exec_common.cuh", "device_program.h",
                          "warp_program.cpp", "api.cpp", "gate_coef.cpp", "lower.cpp"],
     "graph_exec_kernel": ["exec_graph.cu", "exec_common.cuh", "device_program.h", "lower.cpp",
-                          "graph_host.cpp"],
+                          "graph_host.cpp", "tile_plan.cpp"],
 }
 NCU_TRAFFIC = {
     # (workload, kernel, dtype, want_grad): (bytes per launch, source hash, profile summary)

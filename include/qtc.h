@@ -397,8 +397,10 @@ qtc_status qtc_engine_set_task_options(qtc_engine* e, int task_terms_log2, int s
  * steps with both operands in global memory, and the long reductions,
  * through shared memory in tiles (16-byte copies of each operand's tile,
  * contraction in shared memory and registers); 2 does so for every step that
- * tiles.
- * Invalidates prepared programs.  QTC_ERR_INVALID outside 0..2. */
+ * tiles; 3 reads the operands of steps summing at least three labels in
+ * place (tile decomposition without staging copies) and 4 does so for every
+ * step that tiles.
+ * Invalidates prepared programs.  QTC_ERR_INVALID outside 0..4. */
 qtc_status qtc_engine_set_tile_mode(qtc_engine* e, int mode);
 
 /* Host-only check of the tile lowering (no GPU call): builds the batch's
@@ -406,6 +408,8 @@ qtc_status qtc_engine_set_tile_mode(qtc_engine* e, int mode);
  * every tile step with at most 2^max_bits multiply-adds, emulates its tile
  * copies, thread decomposition and reductions on seeded random operands and
  * compares the result with the plain contraction over the step's bit maps.
+ * Steps whose rows go four at a time sharing operand elements are emulated
+ * the same way (row order, the group's distinct elements).
  * max_err: host, 1 double (largest absolute difference); n_checked: host,
  * 1 int (steps compared). */
 qtc_status qtc_selftest_tile_steps(qtc_batch* b, int dtype, int want_grad, int force_graph,

@@ -293,6 +293,9 @@ extern "C" qtc_status qtc_selftest_tile_steps(qtc_batch* b, int dtype, int want_
         if ((st.flags & GSF_TILE) && st.rc + st.ry <= max_bits) {
           err = std::max(err, emulate_tile_step(st, seed++));
           ++n;
+        } else if ((st.flags & GSF_ROWS) && st.rc + st.ry <= max_bits) {
+          err = std::max(err, emulate_rows_step(st, seed++));
+          ++n;
         }
     *max_err = err;
     *n_checked = n;
@@ -1480,7 +1483,7 @@ static SvPrepared& sv_prepare(qtc_engine* e, qtc_circuit* c, cudaStream_t s) {
   p.edges = upload(e, edges, s, "upload edges");
   p.params = (double*)e->alloc(sizeof(double) * 2 * cc.p);
   p.acc = (double*)e->alloc(sizeof(double) * (1 + cc.edges.size()));
-  void* scratch = e->alloc((size_t)16 * (cc.p * (cc.edges.size() + 1) + cc.p));
+  void* scratch = e->alloc((size_t)16 * (cc.p * (cc.edges.size() + 1) + cc.p + 2));
   for (int d = 0; d < 2; ++d) {
     int lo[16], len[16], rl[16];
     const int passes = sv_passes(cc.n, sv_tile_bits(d), lo, len, rl);

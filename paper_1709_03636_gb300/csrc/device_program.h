@@ -261,8 +261,19 @@ enum GStepFlag : uint16_t {
   GSF_TILE = 16,       // staged through shared memory in tiles (the tile fields)
   GSF_YPAIR = 32,      // summed bit 0 is bit 0 of A and of B (both in global memory):
                        //   complex64 terms are read as 16-byte element pairs
-  GSF_LANES_Y = 64     // split: the summed index's low bits are A's (or B's) lowest
+  GSF_LANES_Y = 64,    // split: the summed index's low bits are A's (or B's) lowest
                        //   bits, so a warp's lanes run over it (one warp per output)
+  GSF_ROWS = 128       // rows taken four at a time in the order of `rows`, so that the
+                       //   four share operand elements (`share`): fewer loads per term
+};
+
+// How the four rows of a GSF_ROWS group share operands: row-counter bit 0 and
+// bit 1 map to output labels missing from A (A's element is the same for both
+// values) or from B.
+enum GRowShare : uint8_t {
+  GRS_ZX = 1,   // bit 0 not in A, bit 1 not in B: two A and two B elements per term
+  GRS_ZZ = 2,   // neither bit in A: one A and four B elements per term
+  GRS_XX = 3    // neither bit in B: four A and one B element per term
 };
 
 // Tile form of a global step.  The step's labels split into tile labels
@@ -315,9 +326,10 @@ struct alignas(16) GStep {
   uint32_t net;
   uint16_t flags;
   int16_t slot;             // leafgrad: parameter slot
-  uint8_t rc, ry, pad0, pad1;
+  uint8_t rc, ry, share, pad1;  // share: GRowShare of a GSF_ROWS step
   GRuns ca, cb;             // output bits -> A bits, B bits
   GRuns ya, yb;             // summed bits -> A bits, B bits
+  GRuns rows;               // GSF_ROWS: row counter bits -> output row bits
   GTileMap tile;            // GSF_TILE
 };
 

@@ -223,6 +223,53 @@ __device__ __forceinline__ void rows_unrolled(const T* A, const T* B, T* C, cons
   }
 }
 
+// Rows of a GSF_ROWS step, four at a time: row k of a group reads A element
+// ia(k) and B element ib(k) of the group's distinct ones (GRS_ZX: A varies
+// with row bit 1, B with bit 0; GRS_ZZ: one A, four B; GRS_XX: four A, one
+// B), two summed values per pass, so a pass issues 8 (ZX) or 10 loads for 8
+// terms instead of 16.  nr is a multiple of four; rowc holds each row's
+// output offset.
+template <typename T, int kShare>
+__device__ __forceinline__ void rows_shared(const T* A, const T* B, T* C, const uint32_t* rowa,
+                                            const uint32_t* rowb, const uint32_t* rowc,
+                                            uint32_t a_lo, uint32_t b_lo, const uint32_t* ya,
+                                            const uint32_t* yb, uint32_t nr, uint32_t n_y,
+                                            uint32_t tid) {
+  constexpr int NA = kShare == GRS_ZZ ? 1 : (kShare == GRS_ZX ? 2 : 4);
+  constexpr int NB = kShare == GRS_XX ? 1 : (kShare == GRS_ZX ? 2 : 4);
+  auto ia = [](int k) { return kShare == GRS_ZZ ? 0 : (kShare == GRS_ZX ? k >> 1 : k); };
+  auto ib = [](int k) { return kShare == GRS_XX ? 0 : (kShare == GRS_ZX ? k & 1 : k); };
+  for (uint32_t r = 0; r < nr; r += 4) {
+    uint32_t oa[NA], ob[NB];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) oa[i] = rowa[r + (kShare == GRS_ZX ? 2 * i : i)] | a_lo;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) ob[i] = rowb[r + i] | b_lo;
+    T acc[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = czero<T>();
+    for (uint32_t y = 0; y < n_y; y += 2) {
+      const uint32_t ay0 = ya[y], by0 = yb[y], ay1 = ya[y + 1], by1 = yb[y + 1];
+      T av[NA][2], bv[NB][2];
+#pragma unroll
+      for (int i = 0; i < NA; ++i) {
+        av[i][0] = A[oa[i] | ay0];
+        av[i][1] = A[oa[i] | ay1];
+      }
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        bv[i][0] = B[ob[i] | by0];
+        bv[i][1] = B[ob[i] | by1];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        acc[k] = cfma(av[ia(k)][1], bv[ib(k)][1], cfma(av[ia(k)][0], bv[ib(k)][0], acc[k]));
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) C[rowc[r + k] + tid] = acc[k];
+  }
+}
+
 // ---- tile tasks: footprints staged through shared memory -------------------
 
 // Copies the footprint (2^nf elements) of an operand at element offset
@@ -714,18 +761,29 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
       // offsets of the summed index and of this chunk's rows, tabulated once
       uint32_t* rowa = reinterpret_cast<uint32_t*>(red + kGraphBlock);
       uint32_t* rowb = rowa + kMaxChunkRows;
+      uint32_t* rowc = rowb + kMaxChunkRows;
+      const bool shared_rows = (st.flags & GSF_ROWS) != 0;
       for (uint32_t y = tid; y < ny; y += team.size) {
         ya[y] = runs_offset(st.ya, y);
         yb[y] = runs_offset(st.yb, y);
       }
       for (uint32_t r = tid; r < r1 - r0; r += team.size) {
-        rowa[r] = runs_offset(st.ca, (r0 + r) * rowlen);
-        rowb[r] = runs_offset(st.cb, (r0 + r) * rowlen);
+        const uint32_t o = shared_rows ? runs_offset(st.rows, r0 + r) : r0 + r;
+        rowa[r] = runs_offset(st.ca, o * rowlen);
+        rowb[r] = runs_offset(st.cb, o * rowlen);
+        rowc[r] = o * rowlen;
       }
       team.sync();
       constexpr uint32_t R = 4;
       const uint32_t n_y = (uint32_t)ny;
-      if (active && (st.flags & GSF_YPAIR) &&
+      if (active && shared_rows) {
+        if (st.share == GRS_ZX)
+          rows_shared<T, GRS_ZX>(A, B, C, rowa, rowb, rowc, a_lo, b_lo, ya, yb, r1 - r0, n_y, tid);
+        else if (st.share == GRS_ZZ)
+          rows_shared<T, GRS_ZZ>(A, B, C, rowa, rowb, rowc, a_lo, b_lo, ya, yb, r1 - r0, n_y, tid);
+        else
+          rows_shared<T, GRS_XX>(A, B, C, rowa, rowb, rowc, a_lo, b_lo, ya, yb, r1 - r0, n_y, tid);
+      } else if (active && (st.flags & GSF_YPAIR) &&
           rows_paired(A, B, C, rowa, rowb, a_lo, b_lo, ya, yb, r0, r1, rowlen, tid, n_y)) {
         // complex64 element pairs along summed bit 0
       } else if (active && r1 - r0 < R) {

@@ -1,5 +1,7 @@
 // Host side of the graph executor: per-network units -> waves of tasks.
 #include <algorithm>
+#include <cmath>
+#include <queue>
 #include <tuple>
 
 #include "qtc_internal.h"
@@ -14,16 +16,42 @@ uint32_t rebase32(uint64_t base, uint32_t local) {
   return (uint32_t)v;
 }
 
-WaveHost assemble_wave(const std::vector<int>& nets, const std::vector<NetGraph>& graphs) {
+uint64_t runs_max(const GRuns& r, uint32_t bits);
+
+// Expected time of one task of a unit on one team (ns): a chunk task moves
+// its share of the step's operand and output bytes at the rate measured for
+// its class of step (by summed bits; split reductions apart) divided over
+// the resident teams, plus a fixed cost per task.
+double task_time_estimate(const GUnit& u, size_t elem, int teams) {
+  if (u.kind == GT_SMEM) return 30000.0;
+  if (u.kind == GT_TC) return 5000.0;
+  const GStep& st = u.step;
+  const double a = (st.flags & GSF_A_TABLE)
+                       ? 0.0
+                       : (double)((runs_max(st.ca, st.rc) | runs_max(st.ya, st.ry)) + 1);
+  const double b = (st.flags & GSF_B_TABLE)
+                       ? 0.0
+                       : (double)((runs_max(st.cb, st.rc) | runs_max(st.yb, st.ry)) + 1);
+  const double c = (st.flags & GSF_LEAFGRAD) ? 0.0 : std::ldexp(1.0, st.rc);
+  static const double kRate[6] = {7500, 4900, 3300, 2500, 1800, 2200};   // bytes per ns
+  const double rate = (st.flags & GSF_SPLIT) ? 3900.0 : kRate[std::min<int>(st.ry, 5)];
+  const double bytes = (double)elem * (a + b + c) / std::max<uint32_t>(st.n_chunks, 1);
+  return 1000.0 + bytes * teams / rate;
+}
+
+WaveHost assemble_wave(const std::vector<int>& nets, const std::vector<NetGraph>& graphs,
+                       size_t elem, int teams) {
   WaveHost w;
   std::vector<std::vector<uint32_t>> ctr(nets.size()), arrive(nets.size());
   std::vector<uint64_t> base(nets.size());
+  std::vector<size_t> uoff(nets.size() + 1, 0);
   uint32_t next_ctr = 0;
   uint64_t gsize = 0;
   for (size_t k = 0; k < nets.size(); ++k) {
     const NetGraph& g = graphs[nets[k]];
     base[k] = gsize;
     gsize += (g.global_elems + 63) & ~uint64_t(63);
+    uoff[k + 1] = uoff[k] + g.units.size();
     ctr[k].resize(g.units.size());
     arrive[k].assign(g.units.size(), 0xFFFFFFFFu);
     for (size_t u = 0; u < g.units.size(); ++u) {
@@ -34,8 +62,13 @@ WaveHost assemble_wave(const std::vector<int>& nets, const std::vector<NetGraph>
   }
   w.global_elems = gsize;
   w.n_counters = next_ctr;
-  // every unit after its producers: sort by depth (producers are shallower),
-  // interleaving the networks of the wave
+  // Each unit's records (ops, step, waits) and the template of its tasks, in
+  // dependency-depth order.
+  const size_t U = uoff.back();
+  std::vector<GTask> tmpl(U);
+  std::vector<uint32_t> n_tasks(U, 1);
+  std::vector<double> dur(U), rank(U, 0.0);
+  std::vector<int> depth(U);
   std::vector<std::tuple<int, int, int>> order;
   for (size_t k = 0; k < nets.size(); ++k)
     for (size_t u = 0; u < graphs[nets[k]].units.size(); ++u)
@@ -43,19 +76,22 @@ WaveHost assemble_wave(const std::vector<int>& nets, const std::vector<NetGraph>
   std::sort(order.begin(), order.end());
   for (const auto& item : order) {
     const int k = std::get<1>(item), ui = std::get<2>(item);
+    const size_t gid = uoff[k] + ui;
     const NetGraph& g = graphs[nets[k]];
     const GUnit& u = g.units[ui];
+    depth[gid] = u.depth;
+    dur[gid] = task_time_estimate(u, elem, teams);
     const uint32_t wait_begin = (uint32_t)w.waits.size();
     for (int d : u.deps) w.waits.push_back({ctr[k][d], g.units[d].target});
-    const uint32_t wait_count = (uint32_t)u.deps.size();
+    GTask t{};
+    t.net = (uint32_t)nets[k];
+    t.wait_begin = wait_begin;
+    t.wait_count = (uint32_t)u.deps.size();
+    t.signal = 0xFFFFFFFFu;
     if (u.kind == GT_SMEM) {
-      GTask t{};
       t.kind = GT_SMEM;
       t.a = (uint32_t)w.ops.size();
       t.b = (uint32_t)u.ops.size();
-      t.net = (uint32_t)nets[k];
-      t.wait_begin = wait_begin;
-      t.wait_count = wait_count;
       t.signal = ctr[k][ui];
       for (SOp op : u.ops) {
         if (op.flags & SOPF_OUT_GLOBAL) op.out = rebase32(base[k], op.out);
@@ -63,7 +99,6 @@ WaveHost assemble_wave(const std::vector<int>& nets, const std::vector<NetGraph>
         if (op.flags & SOPF_IN2_GLOBAL) op.in2 = rebase32(base[k], op.in2);
         w.ops.push_back(op);
       }
-      w.tasks.push_back(t);
     } else if (u.kind == GT_TC) {
       TStep ts = u.tstep;
       ts.net = (uint32_t)nets[k];
@@ -71,19 +106,10 @@ WaveHost assemble_wave(const std::vector<int>& nets, const std::vector<NetGraph>
       ts.c_off = rebase32(base[k], ts.c_off);
       ts.a_off = rebase32(base[k], ts.a_off);
       ts.b_off = rebase32(base[k], ts.b_off);
-      const uint32_t idx = (uint32_t)w.tsteps.size();
+      t.kind = GT_TC;
+      t.a = (uint32_t)w.tsteps.size();
+      n_tasks[gid] = u.target;
       w.tsteps.push_back(ts);
-      for (uint32_t tile = 0; tile < u.target; ++tile) {
-        GTask t{};
-        t.kind = GT_TC;
-        t.a = idx;
-        t.b = tile;
-        t.net = (uint32_t)nets[k];
-        t.wait_begin = wait_begin;
-        t.wait_count = wait_count;
-        t.signal = 0xFFFFFFFFu;
-        w.tasks.push_back(t);
-      }
     } else {
       GStep st = u.step;
       st.net = (uint32_t)nets[k];
@@ -93,20 +119,73 @@ WaveHost assemble_wave(const std::vector<int>& nets, const std::vector<NetGraph>
       if (!(st.flags & GSF_A_TABLE)) st.a_off = rebase32(base[k], st.a_off);
       if (!(st.flags & GSF_B_TABLE)) st.b_off = rebase32(base[k], st.b_off);
       if (st.flags & GSF_SPLIT) st.partial_off = rebase32(base[k], st.partial_off);
-      const uint32_t idx = (uint32_t)w.steps.size();
+      t.kind = GT_CHUNK;
+      t.a = (uint32_t)w.steps.size();
+      n_tasks[gid] = st.n_chunks;
       w.steps.push_back(st);
-      for (uint32_t c = 0; c < st.n_chunks; ++c) {
-        GTask t{};
-        t.kind = GT_CHUNK;
-        t.a = idx;
-        t.b = c;
-        t.net = (uint32_t)nets[k];
-        t.wait_begin = wait_begin;
-        t.wait_count = wait_count;
-        t.signal = 0xFFFFFFFFu;
-        w.tasks.push_back(t);
-      }
     }
+    tmpl[gid] = t;
+  }
+  // Queue order from a list-scheduling run on the host: `teams` teams take
+  // tasks as they become free, each the next task of the ready unit (all its
+  // producers complete) with the longest chain of expected task times to the
+  // end of its network; tasks enter the queue in the order they start.
+  // Every task then comes after the tasks it waits for (no team can wait on
+  // a task behind it in the queue), and teams that take tasks in this order
+  // seldom wait when the estimates hold.
+  std::vector<std::vector<int>> succ(U);
+  std::vector<int> n_deps(U, 0);
+  for (size_t k = 0; k < nets.size(); ++k) {
+    const NetGraph& g = graphs[nets[k]];
+    for (size_t u = 0; u < g.units.size(); ++u) {
+      n_deps[uoff[k] + u] = (int)g.units[u].deps.size();
+      for (int d : g.units[u].deps) succ[uoff[k] + d].push_back((int)(uoff[k] + u));
+    }
+  }
+  std::vector<int> by_depth(U);
+  for (size_t i = 0; i < U; ++i) by_depth[i] = (int)i;
+  std::stable_sort(by_depth.begin(), by_depth.end(),
+                   [&](int a, int b) { return depth[a] > depth[b]; });
+  for (int gid : by_depth) {
+    double tail = 0.0;
+    for (int s : succ[gid]) tail = std::max(tail, rank[s]);
+    rank[gid] = dur[gid] + tail;
+  }
+  auto lower = [&](int a, int b) { return rank[a] < rank[b] || (rank[a] == rank[b] && a > b); };
+  std::priority_queue<int, std::vector<int>, decltype(lower)> ready(lower);
+  using Event = std::pair<double, int>;
+  std::priority_queue<Event, std::vector<Event>, std::greater<Event>> done;
+  std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+  for (int i = 0; i < std::max(teams, 1); ++i) free_at.push(0.0);
+  std::vector<uint32_t> next(U, 0), left(n_tasks);
+  size_t total = 0;
+  for (size_t i = 0; i < U; ++i) {
+    total += n_tasks[i];
+    if (n_deps[i] == 0) ready.push((int)i);
+  }
+  w.tasks.reserve(total);
+  while (w.tasks.size() < total) {
+    const double now = free_at.top();
+    free_at.pop();
+    while (!done.empty() && done.top().first <= now) {
+      const int gid = done.top().second;
+      done.pop();
+      if (--left[gid] == 0)
+        for (int s : succ[gid])
+          if (--n_deps[s] == 0) ready.push(s);
+    }
+    if (ready.empty()) {
+      if (done.empty()) fail(QTC_ERR_INVALID, "internal: units with unmet dependencies");
+      free_at.push(done.top().first);   // idle until the next task ends
+      continue;
+    }
+    const int gid = ready.top();
+    GTask t = tmpl[gid];
+    if (t.kind != GT_SMEM) t.b = next[gid];
+    w.tasks.push_back(t);
+    if (++next[gid] == n_tasks[gid]) ready.pop();
+    done.push({now + dur[gid], gid});
+    free_at.push(now + dur[gid]);
   }
   return w;
 }
@@ -119,6 +198,13 @@ uint64_t runs_max(const GRuns& r, uint32_t bits) {
       const uint32_t len = std::min<uint32_t>(r.len[k], bits - r.src[k]);
       off |= (((uint64_t)1 << len) - 1) << r.dst[k];
     }
+  return off;
+}
+
+uint64_t runs_offset_host(const GRuns& r, uint64_t idx) {
+  uint64_t off = 0;
+  for (int k = 0; k < r.n; ++k)
+    off |= ((idx >> r.src[k]) & ((1ull << r.len[k]) - 1)) << r.dst[k];
   return off;
 }
 
@@ -242,6 +328,35 @@ void validate_wave(const WaveHost& w, uint32_t table_elems, uint32_t arena_elems
         fail(QTC_ERR_INVALID, "internal: paired loads without adjacent summed pairs");
       if ((st.flags & GSF_LANES_Y) && !(st.flags & GSF_SPLIT))
         fail(QTC_ERR_INVALID, "internal: lanes over the summed index outside a split step");
+    }
+    if (st.flags & GSF_ROWS) {
+      // rows in groups of four along output bits that one operand lacks; the
+      // row order a bijection of the row bits
+      const int row0 = 8, nrb = (int)st.rc - row0;
+      const uint64_t ny = 1ull << st.ry;
+      bool ok = nrb >= 2 && !(st.flags & (GSF_SPLIT | GSF_YPAIR | GSF_TILE | GSF_A_TABLE |
+                                          GSF_B_TABLE | GSF_LEAFGRAD)) &&
+                ny >= 8 && ny <= kYTab && st.chunk >= 4 && st.chunk % 4 == 0 &&
+                (uint64_t)st.n_chunks * st.chunk == (1ull << nrb) &&
+                st.share >= GRS_ZX && st.share <= GRS_XX && kGRow == (1u << row0);
+      uint64_t seen = 0;
+      for (int i = 0; ok && i < nrb; ++i) {
+        const uint64_t o = runs_offset_host(st.rows, 1ull << i);
+        ok = o != 0 && (o & (o - 1)) == 0 && o < (1ull << nrb) && !(seen & o);
+        seen |= o;
+      }
+      if (ok) {
+        const uint64_t r0 = runs_offset_host(st.rows, 1) << row0;
+        const uint64_t r1 = runs_offset_host(st.rows, 2) << row0;
+        const bool r0_not_a = runs_offset_host(st.ca, r0) == 0;
+        const bool r0_not_b = runs_offset_host(st.cb, r0) == 0;
+        const bool r1_not_a = runs_offset_host(st.ca, r1) == 0;
+        const bool r1_not_b = runs_offset_host(st.cb, r1) == 0;
+        ok = st.share == GRS_ZX   ? (r0_not_a && r1_not_b)
+             : st.share == GRS_ZZ ? (r0_not_a && r1_not_a)
+                                  : (r0_not_b && r1_not_b);
+      }
+      if (!ok) fail(QTC_ERR_INVALID, "internal: shared rows on an unfit step");
     }
     const uint64_t ma = runs_max(st.ca, st.rc) | runs_max(st.ya, st.ry);
     const uint64_t mb = runs_max(st.cb, st.rc) | runs_max(st.yb, st.ry);
@@ -401,7 +516,7 @@ void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
   hp.tensor_cores = false;
   for (auto& wnets : waves) {
     std::sort(wnets.begin(), wnets.end());
-    hp.waves.push_back(assemble_wave(wnets, graphs));
+    hp.waves.push_back(assemble_wave(wnets, graphs, elem, opts.sm_count * 4));
 
     if (!hp.waves.back().tsteps.empty()) hp.tensor_cores = true;
     hp.max_global_elems = std::max(hp.max_global_elems, hp.waves.back().global_elems);
@@ -412,7 +527,7 @@ void build_graph_program(HostProgram& hp, const std::vector<Plan>& plans,
   auto round16 = [](size_t x) { return (uint32_t)((x + 15) & ~size_t(15)); };
   const size_t smem_task = (size_t)hp.stage_ops * sizeof(SOp) + (size_t)max_arena * elem;
   const size_t chunk_task = 2 * (size_t)kYTab * sizeof(uint32_t) + 256 * elem +
-                            2 * (size_t)kMaxChunkRows * sizeof(uint32_t);
+                            3 * (size_t)kMaxChunkRows * sizeof(uint32_t);
   size_t tile_task = 0;
   hp.tiles = false;
   for (const WaveHost& w : hp.waves)

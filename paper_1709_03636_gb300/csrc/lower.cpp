@@ -332,7 +332,41 @@ bool encode_gstep(GStep& g, const std::vector<int>& lc, const std::vector<int>& 
     g.flags |= GSF_YPAIR;
   if (a_global && b_global && (g.flags & GSF_SPLIT) && std::max(la0, lb0) >= 3)
     g.flags |= GSF_LANES_Y;
-  (void)log2_floor;
+  // long sums over rows: take rows four at a time along output labels missing
+  // from one operand, so the four rows read fewer distinct elements per term
+  if (a_global && b_global && !(g.flags & (GSF_SPLIT | GSF_YPAIR)) && ny >= 8 && ny <= kYTab &&
+      nout >= 4 * kGRow) {
+    const int row0 = log2_floor(kGRow), nrow_bits = g.rc - row0;
+    std::vector<int> zs, xs;   // row bits (relative) missing from A, from B
+    for (int i = 0; i < nrow_bits; ++i) {
+      if (pa[row0 + i] < 0) zs.push_back(i);
+      else if (pb[row0 + i] < 0) xs.push_back(i);
+    }
+    int b0 = -1, b1 = -1;
+    uint8_t share = 0;
+    if (!zs.empty() && !xs.empty()) {
+      b0 = zs[0], b1 = xs[0], share = GRS_ZX;
+    } else if (zs.size() >= 2) {
+      b0 = zs[0], b1 = zs[1], share = GRS_ZZ;
+    } else if (xs.size() >= 2) {
+      b0 = xs[0], b1 = xs[1], share = GRS_XX;
+    }
+    if (share) {
+      std::vector<int> order = {b0, b1};
+      for (int i = 0; i < nrow_bits; ++i)
+        if (i != b0 && i != b1) order.push_back(i);
+      GRuns rows;
+      if (make_runs(order, rows)) {
+        const uint64_t nrows = nout / kGRow;
+        const uint64_t per = std::min<uint64_t>(std::max<uint64_t>(g.chunk, 4), nrows);
+        g.rows = rows;
+        g.share = share;
+        g.chunk = (uint32_t)per;
+        g.n_chunks = (uint32_t)(nrows / per);
+        g.flags |= GSF_ROWS;
+      }
+    }
+  }
   return true;
 }
 

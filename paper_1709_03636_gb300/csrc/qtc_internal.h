@@ -208,6 +208,7 @@ size_t tile_region_bytes(const GStep& g, size_t elem);
 // Host emulation of one tile step on seeded random operands against the
 // plain contraction over its bit maps: the largest absolute difference.
 double emulate_tile_step(const GStep& g, uint64_t seed);
+double emulate_rows_step(const GStep& g, uint64_t seed);
 
 // A unit is one shared-memory subtree task or one global step (its chunks);
 // its counter reaches `target` when it is complete.

@@ -373,4 +373,52 @@ double emulate_tile_step(const GStep& g, uint64_t seed) {
   return err;
 }
 
+// Host emulation of a GSF_ROWS step: per chunk the kernel's row tables, and
+// per group of four rows only the group's distinct operand elements (A by
+// ia(k), B by ib(k)), against the plain sum over every output's own bit maps.
+double emulate_rows_step(const GStep& g, uint64_t seed) {
+  const uint64_t ra = (apply(g.ca, (1ull << g.rc) - 1) | apply(g.ya, (1ull << g.ry) - 1)) + 1;
+  const uint64_t rb = (apply(g.cb, (1ull << g.rc) - 1) | apply(g.yb, (1ull << g.ry) - 1)) + 1;
+  SplitMix64 rng(seed);
+  auto draw = [&]() { return std::complex<double>((double)(rng.next() >> 11) * 0x1p-53 - 0.5,
+                                                  (double)(rng.next() >> 11) * 0x1p-53 - 0.5); };
+  std::vector<std::complex<double>> A(ra), B(rb), C(1ull << g.rc, 0.0), R(1ull << g.rc, 0.0);
+  std::vector<char> written(1ull << g.rc, 0);
+  for (auto& x : A) x = draw();
+  for (auto& x : B) x = draw();
+  const uint64_t ny = 1ull << g.ry;
+  for (uint64_t c = 0; c < (1ull << g.rc); ++c)
+    for (uint64_t y = 0; y < ny; ++y)
+      R[c] += A[apply(g.ca, c) | apply(g.ya, y)] * B[apply(g.cb, c) | apply(g.yb, y)];
+  const uint64_t rowlen = kGRow;
+  for (uint32_t chunk = 0; chunk < g.n_chunks; ++chunk) {
+    const uint64_t r0 = (uint64_t)chunk * g.chunk;
+    std::vector<uint64_t> rowa(g.chunk), rowb(g.chunk), rowc(g.chunk);
+    for (uint32_t r = 0; r < g.chunk; ++r) {
+      const uint64_t o = apply(g.rows, r0 + r);
+      rowa[r] = apply(g.ca, o * rowlen);
+      rowb[r] = apply(g.cb, o * rowlen);
+      rowc[r] = o * rowlen;
+    }
+    for (uint32_t r = 0; r < g.chunk; r += 4)
+      for (uint64_t tid = 0; tid < rowlen; ++tid) {
+        const uint64_t a_lo = apply(g.ca, tid), b_lo = apply(g.cb, tid);
+        for (int k = 0; k < 4; ++k) {
+          const int ia = g.share == GRS_ZZ ? 0 : (g.share == GRS_ZX ? k >> 1 : k);
+          const int ib = g.share == GRS_XX ? 0 : (g.share == GRS_ZX ? k & 1 : k);
+          const uint64_t oa = rowa[r + (g.share == GRS_ZX ? 2 * ia : ia)] | a_lo;
+          const uint64_t ob = rowb[r + ib] | b_lo;
+          std::complex<double> acc = 0.0;
+          for (uint64_t y = 0; y < ny; ++y) acc += A[oa | apply(g.ya, y)] * B[ob | apply(g.yb, y)];
+          C[rowc[r + k] + tid] = acc;
+          written[rowc[r + k] + tid] = 1;
+        }
+      }
+  }
+  double err = 0;
+  for (uint64_t c = 0; c < C.size(); ++c)
+    err = std::max(err, written[c] ? std::abs(C[c] - R[c]) : 1e30);
+  return err;
+}
+
 }  // namespace qtc
