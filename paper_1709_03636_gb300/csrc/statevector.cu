@@ -11,9 +11,18 @@
 // mixes its own group of qubits and carries as many low qubits along
 // (unmixed) as fill the tile, so tiles stay full and rows contiguous.  The
 // qubits above pass 0 are split evenly over the fewest passes.  The mixer's
-// 2x2 rotation is applied to the pass's own qubits three at a time on eight
-// elements held in registers.
+// 2x2 rotation is applied to the pass's own qubits on elements held in
+// registers (and lane bits by shuffles).
 // The last pass of the last layer accumulates |psi|^2 cut(x).
+//
+// The rotation [[c, -i s], [-i s, c]] (c = cos beta, s = sin beta) is applied
+// without its larger factor f (c when |c| >= |s|, else s): x0' = x0 - i t x1
+// with t = s / c, or x0' = u x0 - i x1 with u = c / s, two fused multiply-adds
+// per element and qubit instead of four.  A layer therefore leaves the state
+// divided by F = f^n; the next layer's phase table carries F (applied with the
+// phase), and the last layer's F scales the stored state and F^2 the sum for
+// <C>.  |f| >= 1/sqrt(2), so the stored amplitudes stay within
+// 2^(-n/2) .. 1 of the unit-norm state's scale.
 //
 // cut(x) without a loop over vertices: with the tile's vertices T and the
 // block's fixed bits f on the other vertices F,
@@ -95,93 +104,41 @@ struct SvArgs {
   int lo, len, rl;           // pass: tile bits 0..len-1 (lo = 0) or 0..rl-1 and lo..lo+len-1
   int first;                 // 1: the state is |+>, do not read it
   int last;                  // 1: accumulate <C> after this pass
+  int store;                 // 0: the pass's result is not needed in memory (last pass, no
+                             // per-edge values): it is only reduced into <C>
+  const double2* scale;      // (F, F^2) of the last layer (see the rotation above)
   double* acc;               // [<C>, <ZZ> per edge]
 };
 
-// Sets up the per-launch tables: phase[layer][c] and rot[layer].
+// Per-block tables for cut(x) = c0(f) + sum_{a in T} t_a coef_a(f) + W[t]
+// (tile vertices T, the block's fixed bits f) and the layer's phase values.
+struct SvBlock {
+  int lo[128], hi[64], coef[16];
+  int c0;
+};
+
 template <typename T>
-__global__ void sv_setup_kernel(const double* params, int p, int m, T* phase, T* rot) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p * (m + 1) + p;
-       i += gridDim.x * blockDim.x) {
-    double sn, cs;
-    if (i < p * (m + 1)) {
-      const int layer = i / (m + 1), c = i % (m + 1);
-      sincos(-0.5 * params[layer] * (double)(m - 2 * c), &sn, &cs);
-      phase[i] = from_d2<T>(make_double2(cs, sn));
-    } else {
-      const int layer = i - p * (m + 1);
-      sincos(params[p + layer], &sn, &cs);
-      rot[layer] = from_d2<T>(make_double2(cs, sn));
-    }
-  }
-}
-
-// exp(-i beta X) on the pair (x0, x1) = amplitudes with the qubit at 0 and 1:
-// [[c, -i s], [-i s, c]].
-template <typename T, typename R>
-__device__ __forceinline__ void rx_pair(T& x0, T& x1, R c, R s) {
-  const T a = x0, b = x1;
-  x0.x = c * a.x + s * b.y;
-  x0.y = c * a.y - s * b.x;
-  x1.x = c * b.x + s * a.y;
-  x1.y = c * b.y - s * a.x;
-}
-
-// The rotation on k = 1..3 consecutive qubit bits of 2^k amplitudes in registers.
-template <int K, typename T, typename R>
-__device__ __forceinline__ void rx_bits(T (&v)[8], R c, R s) {
-#pragma unroll
-  for (int q = 0; q < K; ++q)
-#pragma unroll
-    for (int i = 0; i < (1 << K); ++i)
-      if (!((i >> q) & 1)) rx_pair(v[i], v[i | (1 << q)], c, s);
-}
-
-// One mixer round on tile bits b..b+K-1: groups of 2^K amplitudes.
-template <int K, typename T, typename R>
-__device__ __forceinline__ void rx_round(T* tile, uint32_t tsize, int b, R c, R s) {
-  const uint32_t ngroups = tsize >> K;
-  const uint32_t lowm = (1u << b) - 1u;
-  for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
-    const uint32_t base = (g & lowm) | ((g & ~lowm) << K);
-    T v[8];
-#pragma unroll
-    for (int i = 0; i < (1 << K); ++i) v[i] = tile[base | ((uint32_t)i << b)];
-    rx_bits<K>(v, c, s);
-#pragma unroll
-    for (int i = 0; i < (1 << K); ++i) tile[base | ((uint32_t)i << b)] = v[i];
-  }
+__device__ __forceinline__ uint64_t sv_gidx(const SvArgs& a, uint64_t blk, uint32_t t) {
+  if (a.lo == 0) return (blk << a.len) | t;
+  const int rl = a.rl;
+  const uint64_t low = t & ((1u << rl) - 1u), mid = t >> rl;
+  const uint64_t below = blk & ((1ull << (a.lo - rl)) - 1);  // bits rl..lo-1
+  const uint64_t above = blk >> (a.lo - rl);                   // bits lo+len..
+  return low | (below << rl) | (mid << a.lo) | (above << (a.lo + a.len));
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSvThreads) sv_pass_kernel(const SvArgs a) {
-  using R = typename RealOf<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* tile = reinterpret_cast<T*>(smem_raw);
-  __shared__ T s_phase[kSvMaxEdges + 1];
-  __shared__ int s_lo[128], s_hi[64], s_coef[16];
-  __shared__ int s_c0;
-  __shared__ double s_red[kSvThreads / 32];
+__device__ void sv_block_setup(const SvArgs& a, uint64_t blk, int tb, SvBlock& sb, T* s_phase) {
   const int n = a.n;
   const bool pass0 = a.lo == 0;
   const int rl = a.rl;
-  const int tb = pass0 ? a.len : rl + a.len;
-  const uint32_t tsize = 1u << tb;
-  const uint64_t blk = blockIdx.x;
-  auto gidx = [&](uint32_t t) -> uint64_t {
-    if (pass0) return (blk << a.len) | t;
-    const uint64_t low = t & ((1u << rl) - 1u), mid = t >> rl;
-    const uint64_t below = blk & ((1ull << (a.lo - rl)) - 1);  // bits rl..lo-1
-    const uint64_t above = blk >> (a.lo - rl);                   // bits lo+len..
-    return low | (below << rl) | (mid << a.lo) | (above << (a.lo + a.len));
-  };
-  const bool need_cut = a.wcut != nullptr;
-  if (need_cut) {
+  if (a.wcut != nullptr) {
+    const uint32_t tsize = 1u << tb;
     const uint32_t full = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
     const uint32_t tmask =
         pass0 ? (uint32_t)(tsize - 1u) : (((1u << rl) - 1u) | (((1u << a.len) - 1u) << a.lo));
     const uint32_t fm = full & ~tmask;
-    const uint32_t f = (uint32_t)gidx(0);  // this block's fixed bits (tile bits zero)
+    const uint32_t f = (uint32_t)sv_gidx<T>(a, blk, 0);  // fixed bits (tile bits zero)
     if (threadIdx.x < 32) {
       int part = 0;
       const int v = threadIdx.x;
@@ -193,33 +150,151 @@ __global__ void __launch_bounds__(kSvThreads) sv_pass_kernel(const SvArgs a) {
           part = __popc(adj_f & ~f);         // fixed-fixed cut edges, counted from the 1 end
       }
       for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-      if (v == 0) s_c0 = part;
+      if (v == 0) sb.c0 = part;
     }
     if (threadIdx.x < (unsigned)tb) {
       const int j = threadIdx.x;
       const int v = pass0 || j < rl ? j : a.lo + j - rl;
       const uint32_t adj_f = a.adj[v] & fm;
-      s_coef[j] = __popc(adj_f) - 2 * __popc(adj_f & f);
+      sb.coef[j] = __popc(adj_f) - 2 * __popc(adj_f & f);
     }
     __syncthreads();
     if (threadIdx.x < 128) {
       const int u = threadIdx.x;
       int sl = 0, sh = 0;
-      for (int j = 0; j < 7 && j < tb; ++j) sl += ((u >> j) & 1) * s_coef[j];
-      for (int j = 7; j < tb && u < 64; ++j) sh += ((u >> (j - 7)) & 1) * s_coef[j];
-      s_lo[u] = sl;
-      if (u < 64) s_hi[u] = sh;
+      for (int j = 0; j < 7 && j < tb; ++j) sl += ((u >> j) & 1) * sb.coef[j];
+      for (int j = 7; j < tb && u < 64; ++j) sh += ((u >> (j - 7)) & 1) * sb.coef[j];
+      sb.lo[u] = sl;
+      if (u < 64) sb.hi[u] = sh;
     }
   }
   if (pass0) {
     const T* ph = reinterpret_cast<const T*>(a.phase) + (size_t)a.layer * (a.m + 1);
     for (int c = threadIdx.x; c <= a.m; c += blockDim.x) s_phase[c] = ph[c];
   }
-  const T rot = reinterpret_cast<const T*>(a.rot)[a.layer];
-  const R cb = rot.x, sb = rot.y;
   __syncthreads();
+}
+
+// Sets up the per-launch tables: phase[layer][c] (times the previous layer's
+// F), rot[layer] = (t or u, 1 when the cos form) and scale = (F, F^2) of the
+// last layer.
+template <typename T>
+__global__ void sv_setup_kernel(const double* params, int n, int p, int m, T* phase, T* rot,
+                                double2* scale) {
+  auto form = [&](int layer, double* r, double* f) {
+    double sn, cs;
+    sincos(params[p + layer], &sn, &cs);
+    const bool kc = fabs(cs) >= fabs(sn);
+    *r = kc ? sn / cs : cs / sn;
+    *f = kc ? cs : sn;
+    return kc;
+  };
+  auto layer_scale = [&](int layer) {
+    double r, f, F = 1.0;
+    form(layer, &r, &f);
+    for (int i = 0; i < n; ++i) F *= f;
+    return F;
+  };
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p * (m + 1) + p + 1;
+       i += gridDim.x * blockDim.x) {
+    double sn, cs;
+    if (i < p * (m + 1)) {
+      const int layer = i / (m + 1), c = i % (m + 1);
+      sincos(-0.5 * params[layer] * (double)(m - 2 * c), &sn, &cs);
+      const double F = layer > 0 ? layer_scale(layer - 1) : 1.0;
+      phase[i] = from_d2<T>(make_double2(F * cs, F * sn));
+    } else if (i < p * (m + 1) + p) {
+      const int layer = i - p * (m + 1);
+      double r, f;
+      const bool kc = form(layer, &r, &f);
+      rot[layer] = from_d2<T>(make_double2(r, kc ? 1.0 : 0.0));
+    } else {
+      const double F = layer_scale(p - 1);
+      *scale = make_double2(F, F * F);
+    }
+  }
+}
+
+// exp(-i beta X) on the pair (x0, x1) = amplitudes with the qubit at 0 and 1,
+// without the factor f: KC: x0' = x0 - i t x1; else x0' = u x0 - i x1 (r = t
+// or u; the same on both sides of the pair).
+template <bool KC, typename T, typename R>
+__device__ __forceinline__ void rxs_pair(T& x0, T& x1, R r) {
+  const T a = x0, b = x1;
+  if (KC) {
+    x0.x = a.x + r * b.y;
+    x0.y = a.y - r * b.x;
+    x1.x = b.x + r * a.y;
+    x1.y = b.y - r * a.x;
+  } else {
+    x0.x = r * a.x + b.y;
+    x0.y = r * a.y - b.x;
+    x1.x = r * b.x + a.y;
+    x1.y = r * b.y - a.x;
+  }
+}
+
+// The same with the partner amplitude in another lane (bit q of the lane).
+template <bool KC, typename T, typename R>
+__device__ __forceinline__ void rxs_shfl(T& v, R r, int q) {
+  const R px = __shfl_xor_sync(0xffffffffu, v.x, 1u << q);
+  const R py = __shfl_xor_sync(0xffffffffu, v.y, 1u << q);
+  if (KC) {
+    v.x = v.x + r * py;
+    v.y = v.y - r * px;
+  } else {
+    v.x = r * v.x + py;
+    v.y = r * v.y - px;
+  }
+}
+
+// The rotation on k = 1..3 consecutive qubit bits of 2^k amplitudes in registers.
+template <int K, bool KC, typename T, typename R>
+__device__ __forceinline__ void rx_bits(T (&v)[8], R r) {
+#pragma unroll
+  for (int q = 0; q < K; ++q)
+#pragma unroll
+    for (int i = 0; i < (1 << K); ++i)
+      if (!((i >> q) & 1)) rxs_pair<KC>(v[i], v[i | (1 << q)], r);
+}
+
+// One mixer round on tile bits b..b+K-1: groups of 2^K amplitudes.
+template <int K, bool KC, typename T, typename R>
+__device__ __forceinline__ void rx_round(T* tile, uint32_t tsize, int b, R r) {
+  const uint32_t ngroups = tsize >> K;
+  const uint32_t lowm = (1u << b) - 1u;
+  for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
+    const uint32_t base = (g & lowm) | ((g & ~lowm) << K);
+    T v[8];
+#pragma unroll
+    for (int i = 0; i < (1 << K); ++i) v[i] = tile[base | ((uint32_t)i << b)];
+    rx_bits<K, KC>(v, r);
+#pragma unroll
+    for (int i = 0; i < (1 << K); ++i) tile[base | ((uint32_t)i << b)] = v[i];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSvThreads) sv_pass_kernel(const SvArgs a) {
+  using R = typename RealOf<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  __shared__ T s_phase[kSvMaxEdges + 1];
+  __shared__ SvBlock s_sb;
+  __shared__ double s_red[kSvThreads / 32];
+  const int n = a.n;
+  const bool pass0 = a.lo == 0;
+  const int rl = a.rl;
+  const int tb = pass0 ? a.len : rl + a.len;
+  const uint32_t tsize = 1u << tb;
+  const uint64_t blk = blockIdx.x;
+  auto gidx = [&](uint32_t t) -> uint64_t { return sv_gidx<T>(a, blk, t); };
+  sv_block_setup<T>(a, blk, tb, s_sb, s_phase);
+  const T rot = reinterpret_cast<const T*>(a.rot)[a.layer];
+  const R rr = rot.x;
+  const bool kc = rot.y != (R)0;
   auto cut = [&](uint32_t t) -> int {
-    return s_c0 + s_lo[t & 127u] + s_hi[t >> 7] + (int)__ldg(a.wcut + t);
+    return s_sb.c0 + s_sb.lo[t & 127u] + s_sb.hi[t >> 7] + (int)__ldg(a.wcut + t);
   };
   T* psi = reinterpret_cast<T*>(a.psi);
   const R amp0 = (R)exp2(-0.5 * n);
@@ -256,11 +331,8 @@ __global__ void __launch_bounds__(kSvThreads) sv_pass_kernel(const SvArgs a) {
       }
       if (t0 + k * blockDim.x < tsize)  // uniform: whole warps
         for (int q = 0; q < shuffled; ++q) {
-          const R px = __shfl_xor_sync(0xffffffffu, v[k].x, 1u << q);
-          const R py = __shfl_xor_sync(0xffffffffu, v[k].y, 1u << q);
-          const R x = v[k].x, y = v[k].y;
-          v[k].x = cb * x + sb * py;
-          v[k].y = cb * y - sb * px;
+          if (kc) rxs_shfl<true>(v[k], rr, q);
+          else rxs_shfl<false>(v[k], rr, q);
         }
       if (t < tsize) tile[t] = v[k];
     }
@@ -269,16 +341,27 @@ __global__ void __launch_bounds__(kSvThreads) sv_pass_kernel(const SvArgs a) {
   for (int b = pass0 ? shuffled : rl; b < tb; b += 3) {
     __syncthreads();
     const int k = tb - b < 3 ? tb - b : 3;
-    if (k == 3) rx_round<3>(tile, tsize, b, cb, sb);
-    else if (k == 2) rx_round<2>(tile, tsize, b, cb, sb);
-    else rx_round<1>(tile, tsize, b, cb, sb);
+    if (kc) {
+      if (k == 3) rx_round<3, true>(tile, tsize, b, rr);
+      else if (k == 2) rx_round<2, true>(tile, tsize, b, rr);
+      else rx_round<1, true>(tile, tsize, b, rr);
+    } else {
+      if (k == 3) rx_round<3, false>(tile, tsize, b, rr);
+      else if (k == 2) rx_round<2, false>(tile, tsize, b, rr);
+      else rx_round<1, false>(tile, tsize, b, rr);
+    }
   }
   __syncthreads();
   R part = 0;
+  const R fin = a.last ? (R)a.scale->x : (R)1;
   for (uint32_t t = threadIdx.x; t < tsize; t += blockDim.x) {
-    const T v = tile[t];
-    psi[gidx(t)] = v;
-    if (a.last) part += (v.x * v.x + v.y * v.y) * (R)cut(t);
+    T v = tile[t];
+    if (a.last) {
+      part += (v.x * v.x + v.y * v.y) * (R)cut(t);
+      v.x *= fin;
+      v.y *= fin;
+    }
+    if (a.store) psi[gidx(t)] = v;
   }
   if (!a.last) return;
   for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
@@ -287,7 +370,151 @@ __global__ void __launch_bounds__(kSvThreads) sv_pass_kernel(const SvArgs a) {
   if (threadIdx.x == 0) {
     double sum = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += s_red[w];
-    atomicAdd(&a.acc[0], sum);
+    atomicAdd(&a.acc[0], sum * a.scale->y);
+  }
+}
+
+// A full tile (2^tb elements, tb = sv_tile_bits) with 2^K elements per
+// thread held in registers.  In every layout lanes are tile bits 0..4
+// (consecutive elements: coalesced global access, conflict-free shared
+// memory) and the registers are K consecutive tile bits r0..r0+K-1; the warp
+// index fills the other bits.  The load layout has the registers on the top
+// K bits, which are mixed right after the load (pass 0: after the phase);
+// mixed lane bits use shuffles; the bits in between are mixed in rounds
+// through shared memory, K at a time (one store and one load per element);
+// the pass stores from its last layout.  Bits below the pass's carried range
+// (rl, passes after the first) are not mixed.  Per layout a thread computes
+// its base tile index, global offset and linear cut term once; register r
+// adds r << r0 to the tile index, its deposit to the global offset and its
+// bits' cut coefficients.
+template <int K, bool KC, typename T, typename R>
+__device__ __forceinline__ void rx_reg_bits(T (&v)[1 << K], int r0, int lo, int hi, R r) {
+#pragma unroll
+  for (int q = 0; q < K; ++q)
+    if (r0 + q >= lo && r0 + q < hi)
+#pragma unroll
+      for (int i = 0; i < (1 << K); ++i)
+        if (!((i >> q) & 1)) rxs_pair<KC>(v[i], v[i | (1 << q)], r);
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kSvThreads, 2) sv_tile_kernel(const SvArgs a) {
+  using R = typename RealOf<T>::type;
+  constexpr int NR = 1 << K;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  __shared__ T s_phase[kSvMaxEdges + 1];
+  __shared__ SvBlock s_sb;
+  __shared__ double s_red[kSvThreads / 32];
+  const bool pass0 = a.lo == 0;
+  const int tb = pass0 ? a.len : a.rl + a.len;   // K + 9 (512 threads)
+  const int mix_lo = pass0 ? 0 : a.rl;           // lowest mixed tile bit
+  const uint64_t blk = blockIdx.x;
+  sv_block_setup<T>(a, blk, tb, s_sb, s_phase);
+  const T rot = reinterpret_cast<const T*>(a.rot)[a.layer];
+  const R rr = rot.x;
+  const bool kc = rot.y != (R)0;   // the form of the layer's rotation (uniform)
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  const bool need_cut = pass0 || a.last;
+  // register bits r0..r0+K-1 of a layout: tile index, global offset, linear
+  // cut term and the registers' cut coefficients
+  uint32_t tbase = 0;
+  uint64_t gbase = 0;
+  int lin = 0, cr[K];
+  const uint32_t low_mask = pass0 ? 0xFFFFFFFFu : ((1u << a.rl) - 1u);
+  auto gbits = [&](uint32_t tbits) -> uint64_t {   // tile bits -> global bits
+    return pass0 ? (uint64_t)tbits
+                 : ((uint64_t)(tbits & low_mask) | ((uint64_t)(tbits >> a.rl) << a.lo));
+  };
+  auto set_layout = [&](int r0) {
+    const uint32_t wl = w & ((1u << (r0 - 5)) - 1u), wh = w >> (r0 - 5);
+    tbase = lane | (wl << 5) | (wh << (r0 + K));
+    gbase = sv_gidx<T>(a, blk, tbase);
+    if (need_cut) {
+      lin = s_sb.c0 + s_sb.lo[tbase & 127u] + s_sb.hi[tbase >> 7];
+#pragma unroll
+      for (int k = 0; k < K; ++k) cr[k] = s_sb.coef[r0 + k];
+    }
+  };
+  auto cut_of = [&](int r0, int r) -> int {
+    int c = lin;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if ((r >> k) & 1) c += cr[k];
+    return c + (int)__ldg(a.wcut + (tbase | ((uint32_t)r << r0)));
+  };
+  T* psi = reinterpret_cast<T*>(a.psi);
+  T v[NR];
+  int r0 = tb - K;
+  set_layout(r0);
+  if (pass0 && a.first) {
+    const R amp0 = (R)exp2(-0.5 * a.n);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      v[r].x = amp0;
+      v[r].y = 0;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) v[r] = psi[gbase | gbits((uint32_t)r << r0)];
+  }
+  if (pass0) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const T ph = s_phase[cut_of(r0, r)];
+      const T x = v[r];
+      v[r].x = x.x * ph.x - x.y * ph.y;
+      v[r].y = x.x * ph.y + x.y * ph.x;
+    }
+  }
+  if (kc) rx_reg_bits<K, true>(v, r0, mix_lo, tb, rr);
+  else rx_reg_bits<K, false>(v, r0, mix_lo, tb, rr);
+  // lane bits (tile bits 0..4) that the pass mixes: shuffles
+  for (int q = mix_lo; q < 5; ++q)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (kc) rxs_shfl<true>(v[r], rr, q);
+      else rxs_shfl<false>(v[r], rr, q);
+    }
+  // bits 5..tb-K-1 in rounds of K through shared memory
+  for (int b = 5; b < tb - K; b += K) {
+    const int hi = min(b + K, tb - K);
+    if (hi <= mix_lo) continue;   // carried bits only
+    __syncthreads();   // earlier readers of the tile are done
+#pragma unroll
+    for (int r = 0; r < NR; ++r) tile[tbase | ((uint32_t)r << r0)] = v[r];
+    __syncthreads();
+    r0 = min(b, tb - 2 * K);
+    set_layout(r0);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) v[r] = tile[tbase | ((uint32_t)r << r0)];
+    if (kc) rx_reg_bits<K, true>(v, r0, max(b, mix_lo), hi, rr);
+    else rx_reg_bits<K, false>(v, r0, max(b, mix_lo), hi, rr);
+  }
+  if (!a.last) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) psi[gbase | gbits((uint32_t)r << r0)] = v[r];
+    return;
+  }
+  const R fin = (R)a.scale->x;
+  R part = 0;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    part += (v[r].x * v[r].x + v[r].y * v[r].y) * (R)cut_of(r0, r);
+    if (a.store) {
+      T o = v[r];
+      o.x *= fin;
+      o.y *= fin;
+      psi[gbase | gbits((uint32_t)r << r0)] = o;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+  if (lane == 0) s_red[w] = (double)part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sum += s_red[i];
+    atomicAdd(&a.acc[0], sum * a.scale->y);
   }
 }
 
@@ -336,13 +563,16 @@ static cudaError_t sv_launch_t(void* psi, int n, int m, const uint32_t* adj_dev,
                                const SvTables& tabs, double* acc_dev, int per_edge,
                                cudaStream_t stream, int* launches) {
   int lo[16], len[16], rl[16];
-  const int passes = sv_passes(n, sv_tile_bits(sizeof(T) == 16 ? 0 : 1), lo, len, rl);
+  const int tmax = sv_tile_bits(sizeof(T) == 16 ? 0 : 1);
+  const int passes = sv_passes(n, tmax, lo, len, rl);
   *launches = 0;
   cudaError_t err = cudaMemsetAsync(acc_dev, 0, sizeof(double) * (1 + m), stream);
   if (err != cudaSuccess) return err;
   T* phase = reinterpret_cast<T*>(tabs.scratch);
   T* rot = phase + (size_t)p * (m + 1);
-  sv_setup_kernel<T><<<4, 256, 0, stream>>>(params_dev, p, m, phase, rot);
+  double2* scale = reinterpret_cast<double2*>(
+      (reinterpret_cast<uintptr_t>(rot + p) + 15) & ~static_cast<uintptr_t>(15));
+  sv_setup_kernel<T><<<4, 256, 0, stream>>>(params_dev, n, p, m, phase, rot, scale);
   ++*launches;
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
@@ -362,13 +592,23 @@ static cudaError_t sv_launch_t(void* psi, int n, int m, const uint32_t* adj_dev,
       a.first = layer == 0 && k == 0;
       a.last = layer == p - 1 && k == passes - 1;
       a.wcut = k == 0 ? tabs.wcut_first : (a.last ? tabs.wcut_last : nullptr);
+      a.store = !(a.last && !per_edge);
+      a.scale = scale;
       a.acc = acc_dev;
       const int tb = k == 0 ? len[k] : rl[k] + len[k];
       const size_t smem = sizeof(T) << tb;
       const unsigned blocks = (unsigned)(1ull << (n - tb));
-      cudaFuncSetAttribute(sv_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-      sv_pass_kernel<T><<<blocks, kSvThreads, smem, stream>>>(a);
+      if (tb == tmax) {
+        // full tiles: registers hold 2^K elements per thread (K + 9 = tb)
+        constexpr int K = sizeof(T) == 16 ? 3 : 4;
+        cudaFuncSetAttribute(sv_tile_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        sv_tile_kernel<T, K><<<blocks, kSvThreads, smem, stream>>>(a);
+      } else {
+        cudaFuncSetAttribute(sv_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        sv_pass_kernel<T><<<blocks, kSvThreads, smem, stream>>>(a);
+      }
       ++*launches;
       err = cudaGetLastError();
       if (err != cudaSuccess) return err;

@@ -26,7 +26,8 @@ std::vector<uint16_t> sv_cut_table(const std::vector<uint32_t>& adj, int n, int 
 struct SvTables {
   const uint16_t* wcut_first;   // sv_cut_table of pass 0
   const uint16_t* wcut_last;    // sv_cut_table of the last pass (when there are several)
-  void* scratch;                // p (m + 1) + p elements of 16 bytes: phase and rotation tables
+  void* scratch;                // p (m + 1) + p + 2 elements of 16 bytes: phase and rotation
+                                // tables, the last layer's scale
 };
 
 // Evolves |+>^n through p QAOA layers in psi (2^n elements; dtype 0 = complex

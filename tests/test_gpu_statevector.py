@@ -31,6 +31,31 @@ def test_statevector_matches_oracle(engine, n, d, p, dtype, tol):
     assert np.max(np.abs(np.array(per_edge) - sv.edge_zz(n, edges, g, b))) < tol
 
 
+@pytest.mark.parametrize("n,d,p", [(12, 3, 2), (13, 4, 2), (17, 4, 3), (19, 4, 2), (22, 3, 2)])
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-11), ("c64", 2e-6)])
+def test_statevector_value_only_matches_oracle(engine, n, d, p, dtype, tol):
+    """<C> alone (the last pass reduces the state without storing it), over
+    one, two and three passes per layer, against the FP64 oracle."""
+    edges = [tuple(sorted(e)) for e in random_regular_graph(n, d, 3 * n + p)]
+    g = [0.45 + 0.4 * k for k in range(p)]
+    b = [0.9 - 0.25 * k for k in range(p)]
+    circ = q.Circuit.qaoa(n, edges, p)
+    C, per_edge = q.statevector_expectation(engine, circ, g, b, dtype, per_edge=False)
+    assert abs(C - sv.maxcut_expectation(n, edges, g, b)) < tol * len(edges)
+
+
+@pytest.mark.parametrize("n,d", [(23, 6), (26, 7)])
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-9), ("c64", 1e-5)])
+def test_statevector_value_only_p1_closed_form(n, d, dtype, tol):
+    """Two and three passes of full tiles (the bench's crossover sizes),
+    <C> alone, against the p=1 closed form."""
+    edges = random_regular_graph(n, d, 0)
+    g, b = [0.61], [0.37]
+    eng = q.Engine(0, arena_bytes=(16 << n) + (256 << 20))
+    C, _ = q.statevector_expectation(eng, q.Circuit.qaoa(n, edges, 1), g, b, dtype)
+    assert abs(C - cf.maxcut_p1(n, edges, g[0], b[0])) < tol * abs(C)
+
+
 def test_statevector_d7_n20_closed_form(engine):
     w = WORKLOADS["qaoa_p1_n20_d7"]
     edges = w.graph()
