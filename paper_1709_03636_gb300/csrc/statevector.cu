@@ -33,6 +33,7 @@
 // The phase and rotation values are computed once per launch (FP64 angles).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "exec_common.cuh"
@@ -404,110 +405,151 @@ __global__ void __launch_bounds__(kSvThreads, 2) sv_tile_kernel(const SvArgs a) 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);
   __shared__ T s_phase[kSvMaxEdges + 1];
-  __shared__ SvBlock s_sb;
+  __shared__ uint32_t s_adj[32];
+  __shared__ int s_coef[16];
+  __shared__ int s_c0;
   __shared__ double s_red[kSvThreads / 32];
+  const int n = a.n;
   const bool pass0 = a.lo == 0;
   const int tb = pass0 ? a.len : a.rl + a.len;   // K + 9 (512 threads)
   const int mix_lo = pass0 ? 0 : a.rl;           // lowest mixed tile bit
-  const uint64_t blk = blockIdx.x;
-  sv_block_setup<T>(a, blk, tb, s_sb, s_phase);
+  const uint64_t n_tiles = 1ull << (n - tb);
+  const bool need_cut = a.wcut != nullptr;       // pass 0 and the last pass
+  // once per CTA: adjacency masks, the layer's phase table, the rotation
+  if (threadIdx.x < 32) s_adj[threadIdx.x] = (int)threadIdx.x < n ? a.adj[threadIdx.x] : 0u;
+  if (pass0) {
+    const T* ph = reinterpret_cast<const T*>(a.phase) + (size_t)a.layer * (a.m + 1);
+    for (int c = threadIdx.x; c <= a.m; c += blockDim.x) s_phase[c] = ph[c];
+  }
   const T rot = reinterpret_cast<const T*>(a.rot)[a.layer];
   const R rr = rot.x;
   const bool kc = rot.y != (R)0;   // the form of the layer's rotation (uniform)
   const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-  const bool need_cut = pass0 || a.last;
-  // register bits r0..r0+K-1 of a layout: tile index, global offset, linear
-  // cut term and the registers' cut coefficients
-  uint32_t tbase = 0;
-  uint64_t gbase = 0;
-  int lin = 0, cr[K];
+  const uint32_t full = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+  const uint32_t tmask = pass0 ? (uint32_t)((1u << tb) - 1u)
+                               : (((1u << a.rl) - 1u) | (((1u << a.len) - 1u) << a.lo));
   const uint32_t low_mask = pass0 ? 0xFFFFFFFFu : ((1u << a.rl) - 1u);
   auto gbits = [&](uint32_t tbits) -> uint64_t {   // tile bits -> global bits
     return pass0 ? (uint64_t)tbits
                  : ((uint64_t)(tbits & low_mask) | ((uint64_t)(tbits >> a.rl) << a.lo));
   };
-  auto set_layout = [&](int r0) {
-    const uint32_t wl = w & ((1u << (r0 - 5)) - 1u), wh = w >> (r0 - 5);
-    tbase = lane | (wl << 5) | (wh << (r0 + K));
-    gbase = sv_gidx<T>(a, blk, tbase);
-    if (need_cut) {
-      lin = s_sb.c0 + s_sb.lo[tbase & 127u] + s_sb.hi[tbase >> 7];
-#pragma unroll
-      for (int k = 0; k < K; ++k) cr[k] = s_sb.coef[r0 + k];
-    }
-  };
-  auto cut_of = [&](int r0, int r) -> int {
-    int c = lin;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if ((r >> k) & 1) c += cr[k];
-    return c + (int)__ldg(a.wcut + (tbase | ((uint32_t)r << r0)));
-  };
   T* psi = reinterpret_cast<T*>(a.psi);
-  T v[NR];
-  int r0 = tb - K;
-  set_layout(r0);
-  if (pass0 && a.first) {
-    const R amp0 = (R)exp2(-0.5 * a.n);
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      v[r].x = amp0;
-      v[r].y = 0;
-    }
-  } else {
-#pragma unroll
-    for (int r = 0; r < NR; ++r) v[r] = psi[gbase | gbits((uint32_t)r << r0)];
-  }
-  if (pass0) {
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      const T ph = s_phase[cut_of(r0, r)];
-      const T x = v[r];
-      v[r].x = x.x * ph.x - x.y * ph.y;
-      v[r].y = x.x * ph.y + x.y * ph.x;
-    }
-  }
-  if (kc) rx_reg_bits<K, true>(v, r0, mix_lo, tb, rr);
-  else rx_reg_bits<K, false>(v, r0, mix_lo, tb, rr);
-  // lane bits (tile bits 0..4) that the pass mixes: shuffles
-  for (int q = mix_lo; q < 5; ++q)
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      if (kc) rxs_shfl<true>(v[r], rr, q);
-      else rxs_shfl<false>(v[r], rr, q);
-    }
-  // bits 5..tb-K-1 in rounds of K through shared memory
-  for (int b = 5; b < tb - K; b += K) {
-    const int hi = min(b + K, tb - K);
-    if (hi <= mix_lo) continue;   // carried bits only
-    __syncthreads();   // earlier readers of the tile are done
-#pragma unroll
-    for (int r = 0; r < NR; ++r) tile[tbase | ((uint32_t)r << r0)] = v[r];
-    __syncthreads();
-    r0 = min(b, tb - 2 * K);
-    set_layout(r0);
-#pragma unroll
-    for (int r = 0; r < NR; ++r) v[r] = tile[tbase | ((uint32_t)r << r0)];
-    if (kc) rx_reg_bits<K, true>(v, r0, max(b, mix_lo), hi, rr);
-    else rx_reg_bits<K, false>(v, r0, max(b, mix_lo), hi, rr);
-  }
-  if (!a.last) {
-#pragma unroll
-    for (int r = 0; r < NR; ++r) psi[gbase | gbits((uint32_t)r << r0)] = v[r];
-    return;
-  }
-  const R fin = (R)a.scale->x;
   R part = 0;
+  __syncthreads();
+  for (uint64_t blk = blockIdx.x; blk < n_tiles; blk += gridDim.x) {
+    if (need_cut) {
+      // this tile's cut terms from its fixed bits f (see the file comment)
+      const uint32_t fm = full & ~tmask;
+      const uint32_t f = (uint32_t)sv_gidx<T>(a, blk, 0);
+      __syncthreads();   // the previous tile's readers of s_c0 / s_coef are done
+      if (threadIdx.x < 32) {
+        int c = 0;
+        const int v = threadIdx.x;
+        if (v < n) {
+          const uint32_t adj_f = s_adj[v] & fm;
+          if ((tmask >> v) & 1u) c = __popc(adj_f & f);
+          else if ((f >> v) & 1u) c = __popc(adj_f & ~f);
+        }
+        for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+        if (v == 0) s_c0 = c;
+      }
+      if (threadIdx.x < (unsigned)tb) {
+        const int j = threadIdx.x;
+        const int v = pass0 || j < a.rl ? j : a.lo + j - a.rl;
+        const uint32_t adj_f = s_adj[v] & fm;
+        s_coef[j] = __popc(adj_f) - 2 * __popc(adj_f & f);
+      }
+      __syncthreads();
+    }
+    // register bits r0..r0+K-1 of a layout: tile index, global offset, linear
+    // cut term and the registers' cut coefficients
+    uint32_t tbase = 0;
+    uint64_t gbase = 0;
+    int lin = 0, cr[K];
+    auto set_layout = [&](int r0) {
+      const uint32_t wl = w & ((1u << (r0 - 5)) - 1u), wh = w >> (r0 - 5);
+      tbase = lane | (wl << 5) | (wh << (r0 + K));
+      gbase = sv_gidx<T>(a, blk, tbase);
+      if (need_cut) {
+        lin = s_c0;
+        for (int j = 0; j < tb; ++j)
+          if ((tbase >> j) & 1u) lin += s_coef[j];
 #pragma unroll
-  for (int r = 0; r < NR; ++r) {
-    part += (v[r].x * v[r].x + v[r].y * v[r].y) * (R)cut_of(r0, r);
-    if (a.store) {
-      T o = v[r];
-      o.x *= fin;
-      o.y *= fin;
-      psi[gbase | gbits((uint32_t)r << r0)] = o;
+        for (int k = 0; k < K; ++k) cr[k] = s_coef[r0 + k];
+      }
+    };
+    auto cut_of = [&](int r0, int r) -> int {
+      int c = lin;
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if ((r >> k) & 1) c += cr[k];
+      return c + (int)__ldg(a.wcut + (tbase | ((uint32_t)r << r0)));
+    };
+    T v[NR];
+    int r0 = tb - K;
+    set_layout(r0);
+    if (pass0 && a.first) {
+      const R amp0 = (R)exp2(-0.5 * n);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        v[r].x = amp0;
+        v[r].y = 0;
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) v[r] = psi[gbase | gbits((uint32_t)r << r0)];
+    }
+    if (pass0) {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const T ph = s_phase[cut_of(r0, r)];
+        const T x = v[r];
+        v[r].x = x.x * ph.x - x.y * ph.y;
+        v[r].y = x.x * ph.y + x.y * ph.x;
+      }
+    }
+    if (kc) rx_reg_bits<K, true>(v, r0, mix_lo, tb, rr);
+    else rx_reg_bits<K, false>(v, r0, mix_lo, tb, rr);
+    // lane bits (tile bits 0..4) that the pass mixes: shuffles
+    for (int q = mix_lo; q < 5; ++q)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (kc) rxs_shfl<true>(v[r], rr, q);
+        else rxs_shfl<false>(v[r], rr, q);
+      }
+    // bits 5..tb-K-1 in rounds of K through shared memory
+    for (int b = 5; b < tb - K; b += K) {
+      const int hi = min(b + K, tb - K);
+      if (hi <= mix_lo) continue;   // carried bits only
+      __syncthreads();   // earlier readers of the tile are done
+#pragma unroll
+      for (int r = 0; r < NR; ++r) tile[tbase | ((uint32_t)r << r0)] = v[r];
+      __syncthreads();
+      r0 = min(b, tb - 2 * K);
+      set_layout(r0);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) v[r] = tile[tbase | ((uint32_t)r << r0)];
+      if (kc) rx_reg_bits<K, true>(v, r0, max(b, mix_lo), hi, rr);
+      else rx_reg_bits<K, false>(v, r0, max(b, mix_lo), hi, rr);
+    }
+    if (!a.last) {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) psi[gbase | gbits((uint32_t)r << r0)] = v[r];
+      continue;
+    }
+    const R fin = (R)a.scale->x;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      part += (v[r].x * v[r].x + v[r].y * v[r].y) * (R)cut_of(r0, r);
+      if (a.store) {
+        T o = v[r];
+        o.x *= fin;
+        o.y *= fin;
+        psi[gbase | gbits((uint32_t)r << r0)] = o;
+      }
     }
   }
+  if (!a.last) return;
   for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
   if (lane == 0) s_red[w] = (double)part;
   __syncthreads();
@@ -564,6 +606,11 @@ static cudaError_t sv_launch_t(void* psi, int n, int m, const uint32_t* adj_dev,
                                cudaStream_t stream, int* launches) {
   int lo[16], len[16], rl[16];
   const int tmax = sv_tile_bits(sizeof(T) == 16 ? 0 : 1);
+  int dev = 0, sms = 0;
+  cudaError_t aerr = cudaGetDevice(&dev);
+  if (aerr == cudaSuccess) aerr = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (aerr != cudaSuccess) return aerr;
+  if (sms < 1) sms = 1;
   const int passes = sv_passes(n, tmax, lo, len, rl);
   *launches = 0;
   cudaError_t err = cudaMemsetAsync(acc_dev, 0, sizeof(double) * (1 + m), stream);
@@ -600,10 +647,12 @@ static cudaError_t sv_launch_t(void* psi, int n, int m, const uint32_t* adj_dev,
       const unsigned blocks = (unsigned)(1ull << (n - tb));
       if (tb == tmax) {
         // full tiles: registers hold 2^K elements per thread (K + 9 = tb)
+        // one CTA per resident slot (two per SM), each walking tiles
         constexpr int K = sizeof(T) == 16 ? 3 : 4;
         cudaFuncSetAttribute(sv_tile_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-        sv_tile_kernel<T, K><<<blocks, kSvThreads, smem, stream>>>(a);
+        const unsigned grid = std::min<unsigned>(blocks, 2u * (unsigned)sms);
+        sv_tile_kernel<T, K><<<grid, kSvThreads, smem, stream>>>(a);
       } else {
         cudaFuncSetAttribute(sv_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
