@@ -69,7 +69,7 @@ WORKLOADS = {
                     "light-cone networks"),
     "qaoa_p3_n60_d4": Workload(
         "qaoa_p3_n60_d4", n=60, d=4, p=3, graph_seed=0, ordering="lg",
-        dtype="c64", diag=True, lightcone=True, angle_seed=0, want_grad=True, restarts=64,
+        dtype="c64", diag=True, lightcone=True, angle_seed=0, want_grad=True, restarts=1024,
         description="p=3, 4-regular, 60 vertices / 120 edges, value and "
                     "gradient"),
     "qaoa_p1_n20_d7": Workload(
