@@ -55,7 +55,7 @@ NCU_TRAFFIC = {
     ("qaoa_p1_n50_d3", "smem_exec_kernel", "c64", True):
         (640640, "9c63c5f0b746d4c1", "profiles/smem_exec_kernel_qaoa_p1_n50_d3.md"),
     ("qaoa_p3_n60_d4", "graph_exec_kernel", "c64", True):
-        (22594988288, "836eec967231e53b", "profiles/graph_exec_kernel_qaoa_p3_n60_d4.md"),
+        (23060459648, "af0aa91f218a49c5", "profiles/graph_exec_kernel_qaoa_p3_n60_d4.md"),
 }
 
 
