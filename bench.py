@@ -53,7 +53,7 @@ KERNEL_SOURCES = {
 NCU_TRAFFIC = {
     # (workload, kernel, dtype, want_grad): (bytes per launch, source hash, profile summary)
     ("qaoa_p1_n50_d3", "smem_exec_kernel", "c64", True):
-        (640640, "9c63c5f0b746d4c1", "profiles/smem_exec_kernel_qaoa_p1_n50_d3.md"),
+        (640512, "933297db19fe3c82", "profiles/smem_exec_kernel_qaoa_p1_n50_d3.md"),
     ("qaoa_p3_n60_d4", "graph_exec_kernel", "c64", True):
         (23060459648, "af0aa91f218a49c5", "profiles/graph_exec_kernel_qaoa_p3_n60_d4.md"),
 }
