@@ -273,8 +273,17 @@ enum GStepFlag : uint16_t {
 enum GRowShare : uint8_t {
   GRS_ZX = 1,   // bit 0 not in A, bit 1 not in B: two A and two B elements per term
   GRS_ZZ = 2,   // neither bit in A: one A and four B elements per term
-  GRS_XX = 3    // neither bit in B: four A and one B element per term
+  GRS_XX = 3,   // neither bit in B: four A and one B element per term
+  // short sums (1, 2 or 4 summed values): groups of 2^grs_fix_bits(ny) rows whose
+  // counter bits all miss one operand, read once per group for all its rows
+  GRS_FIXA = 4, // A's elements are the same for the whole group
+  GRS_FIXB = 5  // B's elements are the same for the whole group
 };
+
+// Row-counter bits of a GRS_FIXA / GRS_FIXB group for ny summed values: 16
+// rows for one value, 8 for two, 4 for four (16 loads of the other operand
+// in flight per thread).
+constexpr int grs_fix_bits(uint32_t ny) { return ny == 1 ? 4 : (ny == 2 ? 3 : 2); }
 
 // Tile form of a global step.  The step's labels split into tile labels
 // (varying inside one task) and outer labels: outer output labels (one task

@@ -270,6 +270,62 @@ __device__ __forceinline__ void rows_shared(const T* A, const T* B, T* C, const 
   }
 }
 
+// Rows of a GRS_FIXA / GRS_FIXB step (1, 2 or 4 summed values): groups of 2^G
+// rows read the fixed operand S once per summed value and the other operand
+// O per row, 2^G x NY loads of O in flight per thread.  Kept out of line so
+// its registers do not weigh on the rest of the chunk code.
+template <typename T, uint32_t NY, uint32_t G>
+__device__ __noinline__ void rows_fixed(const T* S, const T* O, T* C, const uint32_t* rows_s,
+                                        const uint32_t* rows_o, const uint32_t* rowc,
+                                        uint32_t s_lo, uint32_t o_lo, const uint32_t* ys,
+                                        const uint32_t* yo, uint32_t nr, uint32_t tid) {
+  constexpr uint32_t NG = 1u << G;
+  uint32_t ysv[NY], yov[NY];
+#pragma unroll
+  for (uint32_t y = 0; y < NY; ++y) {
+    ysv[y] = ys[y];
+    yov[y] = yo[y];
+  }
+  for (uint32_t r = 0; r < nr; r += NG) {
+    const uint32_t os = rows_s[r] | s_lo;
+    T sv[NY], ov[NG][NY];
+#pragma unroll
+    for (uint32_t y = 0; y < NY; ++y) sv[y] = S[os | ysv[y]];
+#pragma unroll
+    for (uint32_t k = 0; k < NG; ++k) {
+      const uint32_t oo = rows_o[r + k] | o_lo;
+#pragma unroll
+      for (uint32_t y = 0; y < NY; ++y) ov[k][y] = O[oo | yov[y]];
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < NG; ++k) {
+      T acc = czero<T>();
+#pragma unroll
+      for (uint32_t y = 0; y < NY; ++y) acc = cfma(ov[k][y], sv[y], acc);
+      C[rowc[r + k] + tid] = acc;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void rows_fixed_dispatch(const T* A, const T* B, T* C,
+                                                    const uint32_t* rowa, const uint32_t* rowb,
+                                                    const uint32_t* rowc, uint32_t a_lo,
+                                                    uint32_t b_lo, const uint32_t* ya,
+                                                    const uint32_t* yb, uint32_t nr, uint32_t n_y,
+                                                    bool fix_b, uint32_t tid) {
+  const T* S = fix_b ? B : A;
+  const T* O = fix_b ? A : B;
+  const uint32_t* rs = fix_b ? rowb : rowa;
+  const uint32_t* ro = fix_b ? rowa : rowb;
+  const uint32_t sl = fix_b ? b_lo : a_lo, ol = fix_b ? a_lo : b_lo;
+  const uint32_t* ys = fix_b ? yb : ya;
+  const uint32_t* yo = fix_b ? ya : yb;
+  if (n_y == 1) rows_fixed<T, 1, grs_fix_bits(1)>(S, O, C, rs, ro, rowc, sl, ol, ys, yo, nr, tid);
+  else if (n_y == 2) rows_fixed<T, 2, grs_fix_bits(2)>(S, O, C, rs, ro, rowc, sl, ol, ys, yo, nr, tid);
+  else rows_fixed<T, 4, grs_fix_bits(4)>(S, O, C, rs, ro, rowc, sl, ol, ys, yo, nr, tid);
+}
+
 // ---- tile tasks: footprints staged through shared memory -------------------
 
 // Copies the footprint (2^nf elements) of an operand at element offset
@@ -776,7 +832,10 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
       team.sync();
       constexpr uint32_t R = 4;
       const uint32_t n_y = (uint32_t)ny;
-      if (active && shared_rows) {
+      if (active && shared_rows && st.share >= GRS_FIXA) {
+        rows_fixed_dispatch(A, B, C, rowa, rowb, rowc, a_lo, b_lo, ya, yb, r1 - r0, n_y,
+                            st.share == GRS_FIXB, tid);
+      } else if (active && shared_rows) {
         if (st.share == GRS_ZX)
           rows_shared<T, GRS_ZX>(A, B, C, rowa, rowb, rowc, a_lo, b_lo, ya, yb, r1 - r0, n_y, tid);
         else if (st.share == GRS_ZZ)

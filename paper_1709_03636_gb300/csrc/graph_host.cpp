@@ -330,31 +330,35 @@ void validate_wave(const WaveHost& w, uint32_t table_elems, uint32_t arena_elems
         fail(QTC_ERR_INVALID, "internal: lanes over the summed index outside a split step");
     }
     if (st.flags & GSF_ROWS) {
-      // rows in groups of four along output bits that one operand lacks; the
-      // row order a bijection of the row bits
+      // rows in groups along output bits that one operand lacks; the row
+      // order a bijection of the row bits
       const int row0 = 8, nrb = (int)st.rc - row0;
       const uint64_t ny = 1ull << st.ry;
-      bool ok = nrb >= 2 && !(st.flags & (GSF_SPLIT | GSF_YPAIR | GSF_TILE | GSF_A_TABLE |
-                                          GSF_B_TABLE | GSF_LEAFGRAD)) &&
-                ny >= 8 && ny <= kYTab && st.chunk >= 4 && st.chunk % 4 == 0 &&
-                (uint64_t)st.n_chunks * st.chunk == (1ull << nrb) &&
-                st.share >= GRS_ZX && st.share <= GRS_XX && kGRow == (1u << row0);
+      const bool fixed = st.share == GRS_FIXA || st.share == GRS_FIXB;
+      const int g = fixed ? grs_fix_bits((uint32_t)ny) : 2;
+      const uint32_t grp = 1u << g;
+      bool ok = nrb >= g && kGRow == (1u << row0) &&
+                !(st.flags & (GSF_SPLIT | GSF_YPAIR | GSF_TILE | GSF_LEAFGRAD)) &&
+                (fixed ? ny <= 4 : (ny >= 8 && ny <= kYTab && st.share >= GRS_ZX &&
+                                    st.share <= GRS_XX &&
+                                    !(st.flags & (GSF_A_TABLE | GSF_B_TABLE)))) &&
+                st.chunk >= grp && st.chunk % grp == 0 &&
+                (uint64_t)st.n_chunks * st.chunk == (1ull << nrb);
       uint64_t seen = 0;
       for (int i = 0; ok && i < nrb; ++i) {
         const uint64_t o = runs_offset_host(st.rows, 1ull << i);
         ok = o != 0 && (o & (o - 1)) == 0 && o < (1ull << nrb) && !(seen & o);
         seen |= o;
       }
-      if (ok) {
-        const uint64_t r0 = runs_offset_host(st.rows, 1) << row0;
-        const uint64_t r1 = runs_offset_host(st.rows, 2) << row0;
-        const bool r0_not_a = runs_offset_host(st.ca, r0) == 0;
-        const bool r0_not_b = runs_offset_host(st.cb, r0) == 0;
-        const bool r1_not_a = runs_offset_host(st.ca, r1) == 0;
-        const bool r1_not_b = runs_offset_host(st.cb, r1) == 0;
-        ok = st.share == GRS_ZX   ? (r0_not_a && r1_not_b)
-             : st.share == GRS_ZZ ? (r0_not_a && r1_not_a)
-                                  : (r0_not_b && r1_not_b);
+      // counter bit i of a group: missing from A (zm) or from B (xm)
+      const int zm = st.share == GRS_ZX ? 1 : st.share == GRS_ZZ ? 3
+                     : st.share == GRS_FIXA ? (int)grp - 1 : 0;
+      const int xm = st.share == GRS_ZX ? 2 : st.share == GRS_XX ? 3
+                     : st.share == GRS_FIXB ? (int)grp - 1 : 0;
+      for (int i = 0; ok && i < g; ++i) {
+        const uint64_t bit = runs_offset_host(st.rows, 1ull << i) << row0;
+        if ((zm >> i) & 1) ok = runs_offset_host(st.ca, bit) == 0;
+        if (ok && ((xm >> i) & 1)) ok = runs_offset_host(st.cb, bit) == 0;
       }
       if (!ok) fail(QTC_ERR_INVALID, "internal: shared rows on an unfit step");
     }

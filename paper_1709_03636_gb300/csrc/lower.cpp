@@ -332,6 +332,37 @@ bool encode_gstep(GStep& g, const std::vector<int>& lc, const std::vector<int>& 
     g.flags |= GSF_YPAIR;
   if (a_global && b_global && (g.flags & GSF_SPLIT) && std::max(la0, lb0) >= 3)
     g.flags |= GSF_LANES_Y;
+  // short sums over rows: groups of rows along output labels one operand
+  // lacks, that operand read once per group (the other's loads all in flight)
+  if (!(g.flags & (GSF_SPLIT | GSF_YPAIR)) && ny <= 4) {
+    const int G = grs_fix_bits((uint32_t)ny);
+    const int row0 = log2_floor(kGRow), nrow_bits = g.rc - row0;
+    if (nout >= ((uint64_t)kGRow << G)) {
+      std::vector<int> zs, xs;   // row bits (relative) missing from A, from B
+      for (int i = 0; i < nrow_bits; ++i) {
+        if (pa[row0 + i] < 0) zs.push_back(i);
+        if (pb[row0 + i] < 0) xs.push_back(i);
+      }
+      const bool fix_b = (int)xs.size() >= G && xs.size() >= zs.size();
+      const bool fix_a = !fix_b && (int)zs.size() >= G;
+      if (fix_a || fix_b) {
+        const std::vector<int>& sel = fix_b ? xs : zs;
+        std::vector<int> order(sel.begin(), sel.begin() + G);
+        for (int i = 0; i < nrow_bits; ++i)
+          if (std::find(order.begin(), order.end(), i) == order.end()) order.push_back(i);
+        GRuns rows;
+        if (make_runs(order, rows)) {
+          const uint64_t nrows = nout / kGRow, grp = 1ull << G;
+          const uint64_t per = std::min<uint64_t>(std::max<uint64_t>(g.chunk, grp), nrows);
+          g.rows = rows;
+          g.share = fix_b ? GRS_FIXB : GRS_FIXA;
+          g.chunk = (uint32_t)per;
+          g.n_chunks = (uint32_t)(nrows / per);
+          g.flags |= GSF_ROWS;
+        }
+      }
+    }
+  }
   // long sums over rows: take rows four at a time along output labels missing
   // from one operand, so the four rows read fewer distinct elements per term
   if (a_global && b_global && !(g.flags & (GSF_SPLIT | GSF_YPAIR)) && ny >= 8 && ny <= kYTab &&

@@ -400,14 +400,20 @@ double emulate_rows_step(const GStep& g, uint64_t seed) {
       rowb[r] = apply(g.cb, o * rowlen);
       rowc[r] = o * rowlen;
     }
-    for (uint32_t r = 0; r < g.chunk; r += 4)
+    // a group's distinct elements: A by the counter bits it holds (the row
+    // with the others clear), B likewise
+    const bool fixed = g.share == GRS_FIXA || g.share == GRS_FIXB;
+    const int ng = 1 << (fixed ? grs_fix_bits((uint32_t)ny) : 2);
+    const int ma = g.share == GRS_ZX ? 2 : g.share == GRS_ZZ ? 0
+                   : g.share == GRS_FIXA ? 0 : ng - 1;   // counter bits A varies with
+    const int mb = g.share == GRS_ZX ? 1 : g.share == GRS_XX ? 0
+                   : g.share == GRS_FIXB ? 0 : ng - 1;
+    for (uint32_t r = 0; r < g.chunk; r += ng)
       for (uint64_t tid = 0; tid < rowlen; ++tid) {
         const uint64_t a_lo = apply(g.ca, tid), b_lo = apply(g.cb, tid);
-        for (int k = 0; k < 4; ++k) {
-          const int ia = g.share == GRS_ZZ ? 0 : (g.share == GRS_ZX ? k >> 1 : k);
-          const int ib = g.share == GRS_XX ? 0 : (g.share == GRS_ZX ? k & 1 : k);
-          const uint64_t oa = rowa[r + (g.share == GRS_ZX ? 2 * ia : ia)] | a_lo;
-          const uint64_t ob = rowb[r + ib] | b_lo;
+        for (int k = 0; k < ng; ++k) {
+          const uint64_t oa = rowa[r + (k & ma)] | a_lo;
+          const uint64_t ob = rowb[r + (k & mb)] | b_lo;
           std::complex<double> acc = 0.0;
           for (uint64_t y = 0; y < ny; ++y) acc += A[oa | apply(g.ya, y)] * B[ob | apply(g.yb, y)];
           C[rowc[r + k] + tid] = acc;
