@@ -724,6 +724,51 @@ __device__ __forceinline__ void rows_pair(const float2* A, const float2* B, floa
   }
 }
 
+// rows_shared for complex64 steps with paired loads (summed bit 0 is bit 0
+// of both operands): two 16-byte pairs per distinct element and pass, so a
+// ZX group of four rows issues 8 loads for 16 terms.  Out of line, like
+// rows_fixed.
+template <int kShare>
+__device__ __noinline__ void rows_shared_pair(const float2* A, const float2* B, float2* C,
+                                              const uint32_t* rowa, const uint32_t* rowb,
+                                              const uint32_t* rowc, uint32_t a_lo, uint32_t b_lo,
+                                              const uint32_t* ya, const uint32_t* yb,
+                                              uint32_t nr, uint32_t n_y, uint32_t tid) {
+  constexpr int NA = kShare == GRS_ZZ ? 1 : (kShare == GRS_ZX ? 2 : 4);
+  constexpr int NB = kShare == GRS_XX ? 1 : (kShare == GRS_ZX ? 2 : 4);
+  auto ia = [](int k) { return kShare == GRS_ZZ ? 0 : (kShare == GRS_ZX ? k >> 1 : k); };
+  auto ib = [](int k) { return kShare == GRS_XX ? 0 : (kShare == GRS_ZX ? k & 1 : k); };
+  for (uint32_t r = 0; r < nr; r += 4) {
+    uint32_t oa[NA], ob[NB];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) oa[i] = rowa[r + (kShare == GRS_ZX ? 2 * i : i)] | a_lo;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) ob[i] = rowb[r + i] | b_lo;
+    float2 acc[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = make_float2(0.f, 0.f);
+    for (uint32_t y = 0; y < n_y; y += 4) {
+      const uint32_t ay0 = ya[y], by0 = yb[y], ay1 = ya[y + 2], by1 = yb[y + 2];
+      float4 av[NA][2], bv[NB][2];
+#pragma unroll
+      for (int i = 0; i < NA; ++i) {
+        av[i][0] = ld_pair(A + (oa[i] | ay0));
+        av[i][1] = ld_pair(A + (oa[i] | ay1));
+      }
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        bv[i][0] = ld_pair(B + (ob[i] | by0));
+        bv[i][1] = ld_pair(B + (ob[i] | by1));
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        acc[k] = cfma2(av[ia(k)][1], bv[ib(k)][1], cfma2(av[ia(k)][0], bv[ib(k)][0], acc[k]));
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) C[rowc[r + k] + tid] = acc[k];
+  }
+}
+
 // Rows of a complex64 step with paired loads; false for other element types.
 template <typename T>
 __device__ __forceinline__ bool rows_paired(const T* A, const T* B, T* C, const uint32_t* rowa,
@@ -835,6 +880,16 @@ __device__ void run_chunk(const GraphProgDev& prog, const GTask& task, T* table,
       if (active && shared_rows && st.share >= GRS_FIXA) {
         rows_fixed_dispatch(A, B, C, rowa, rowb, rowc, a_lo, b_lo, ya, yb, r1 - r0, n_y,
                             st.share == GRS_FIXB, tid);
+      } else if (active && shared_rows && (st.flags & GSF_YPAIR) && sizeof(T) == 8) {
+        const float2* a2 = reinterpret_cast<const float2*>(A);
+        const float2* b2 = reinterpret_cast<const float2*>(B);
+        float2* c2 = reinterpret_cast<float2*>(C);
+        if (st.share == GRS_ZX)
+          rows_shared_pair<GRS_ZX>(a2, b2, c2, rowa, rowb, rowc, a_lo, b_lo, ya, yb, r1 - r0, n_y, tid);
+        else if (st.share == GRS_ZZ)
+          rows_shared_pair<GRS_ZZ>(a2, b2, c2, rowa, rowb, rowc, a_lo, b_lo, ya, yb, r1 - r0, n_y, tid);
+        else
+          rows_shared_pair<GRS_XX>(a2, b2, c2, rowa, rowb, rowc, a_lo, b_lo, ya, yb, r1 - r0, n_y, tid);
       } else if (active && shared_rows) {
         if (st.share == GRS_ZX)
           rows_shared<T, GRS_ZX>(A, B, C, rowa, rowb, rowc, a_lo, b_lo, ya, yb, r1 - r0, n_y, tid);

@@ -338,7 +338,8 @@ void validate_wave(const WaveHost& w, uint32_t table_elems, uint32_t arena_elems
       const int g = fixed ? grs_fix_bits((uint32_t)ny) : 2;
       const uint32_t grp = 1u << g;
       bool ok = nrb >= g && kGRow == (1u << row0) &&
-                !(st.flags & (GSF_SPLIT | GSF_YPAIR | GSF_TILE | GSF_LEAFGRAD)) &&
+                !(st.flags & (GSF_SPLIT | GSF_TILE | GSF_LEAFGRAD)) &&
+                !(fixed && (st.flags & GSF_YPAIR)) &&
                 (fixed ? ny <= 4 : (ny >= 8 && ny <= kYTab && st.share >= GRS_ZX &&
                                     st.share <= GRS_XX &&
                                     !(st.flags & (GSF_A_TABLE | GSF_B_TABLE)))) &&

@@ -365,7 +365,8 @@ bool encode_gstep(GStep& g, const std::vector<int>& lc, const std::vector<int>& 
   }
   // long sums over rows: take rows four at a time along output labels missing
   // from one operand, so the four rows read fewer distinct elements per term
-  if (a_global && b_global && !(g.flags & (GSF_SPLIT | GSF_YPAIR)) && ny >= 8 && ny <= kYTab &&
+  // (with paired loads too)
+  if (a_global && b_global && !(g.flags & GSF_SPLIT) && ny >= 8 && ny <= kYTab &&
       nout >= 4 * kGRow) {
     const int row0 = log2_floor(kGRow), nrow_bits = g.rc - row0;
     std::vector<int> zs, xs;   // row bits (relative) missing from A, from B
