@@ -33,8 +33,16 @@ double task_time_estimate(const GUnit& u, size_t elem, int teams) {
                        ? 0.0
                        : (double)((runs_max(st.cb, st.rc) | runs_max(st.yb, st.ry)) + 1);
   const double c = (st.flags & GSF_LEAFGRAD) ? 0.0 : std::ldexp(1.0, st.rc);
-  static const double kRate[6] = {7500, 4900, 3300, 2500, 1800, 2200};   // bytes per ns
-  const double rate = (st.flags & GSF_SPLIT) ? 3900.0 : kRate[std::min<int>(st.ry, 5)];
+  // measured per class (p=3 n=60, instrumented copy), bytes per ns over all teams
+  static const double kRate[6] = {7500, 4700, 3000, 2300, 2000, 2300};
+  static const double kRateFixed[3] = {8700, 7900, 4700};   // short sums, shared rows
+  static const double kRateShared[6] = {0, 0, 0, 2700, 2100, 2700};   // long sums, shared rows
+  const int ry = std::min<int>(st.ry, 5);
+  double rate = kRate[ry];
+  if (st.flags & GSF_SPLIT) rate = 3900.0;
+  else if ((st.flags & GSF_ROWS) && (st.share == GRS_FIXA || st.share == GRS_FIXB) && ry <= 2)
+    rate = kRateFixed[ry];
+  else if ((st.flags & GSF_ROWS) && ry >= 3) rate = kRateShared[ry];
   const double bytes = (double)elem * (a + b + c) / std::max<uint32_t>(st.n_chunks, 1);
   return 1000.0 + bytes * teams / rate;
 }
@@ -324,7 +332,7 @@ void validate_wave(const WaveHost& w, uint32_t table_elems, uint32_t arena_elems
         fail(QTC_ERR_INVALID, "internal: paired or lane-summed step on a table operand");
       if ((st.flags & GSF_YPAIR) &&
           (low_run(st.ya) < 1 || low_run(st.yb) < 1 || (st.a_off & 1u) || (st.b_off & 1u) ||
-           (st.flags & GSF_SPLIT)))
+           ((st.flags & GSF_SPLIT) && (!(st.flags & GSF_LANES_Y) || (st.chunk & 1u)))))
         fail(QTC_ERR_INVALID, "internal: paired loads without adjacent summed pairs");
       if ((st.flags & GSF_LANES_Y) && !(st.flags & GSF_SPLIT))
         fail(QTC_ERR_INVALID, "internal: lanes over the summed index outside a split step");
