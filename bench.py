@@ -103,6 +103,10 @@ def parse():
     ap.add_argument("--autotune", default=None, metavar="CACHE.json",
                     help="tune the graph executor's task shapes on this workload first "
                          "(cache file, created if missing; no effect on shared-memory batches)")
+    ap.add_argument("--tune", default="quick", choices=["quick", "off"],
+                    help="without --autotune: time six task shapes of the graph executor on "
+                         "the headline workload before the timed steps and keep the fastest "
+                         "(quick, the default), or run the library defaults (off)")
     ap.add_argument("--noise", default=None, metavar="CHANNEL:STRENGTH",
                     help="noisy QAOA: depolarize|dephase|ampdamp channel of that strength on "
                          "every qubit after each mixer (density-matrix networks)")
@@ -391,7 +395,7 @@ class Bench:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def setup(self, w, dtype, grads, noise=None, obs_edges=None, autotune=None):
+    def setup(self, w, dtype, grads, noise=None, obs_edges=None, autotune=None, tune=False):
         """Circuit, whole batch, this rank's shard, an engine sized for its
         programs, prepared for every gradient flag in `grads`."""
         import torch
@@ -406,8 +410,9 @@ class Bench:
             raise SystemExit(f"rank {self.rank} has no edge network of {w.name}")
         need = 0
         for grad in grads:
-            info = batch.program_info(dtype, grad)
-            need += info["work_bytes"] + 2 * info["table_bytes"]
+            # room for the tuning candidates too (small_rank 9 keeps more in global memory)
+            per = [batch.program_info(dtype, grad, small_rank=sr) for sr in ((0, 9) if tune else (0,))]
+            need += max(i["work_bytes"] + 2 * i["table_bytes"] for i in per)
         engine = q.Engine(self.dev.index, arena_bytes=int(need) + (256 << 20))
         if self.tile_mode is not None:
             engine.set_tile_mode(self.tile_mode)
@@ -416,6 +421,15 @@ class Bench:
             tuned = q.autotune(engine, batch, dtype, max(grads), cache_path=autotune)
             tuned = {k: tuned[k] for k in ("small_rank", "task_terms_log2", "subtree_bytes",
                                            "cached")}
+        elif tune and batch.program_info(dtype, max(grads))["graph"]:
+            from paper_1709_03636_gb300.tuning import quick_candidates
+            t0 = time.time()
+            res = q.autotune(engine, batch, dtype, max(grads), candidates=quick_candidates())
+            tuned = {k: res[k] for k in ("small_rank", "task_terms_log2", "subtree_bytes")}
+            tuned.update(mode="quick: 6 task shapes timed on this batch, untimed setup",
+                         trials_ms={f"{t['small_rank']}/{t['task_terms_log2']}": t["ms"]
+                                    for t in res["trials"]},
+                         tuning_s=round(time.time() - t0, 1))
         for grad in grads:
             batch.prepare(engine, dtype, want_grad=grad)
         P = 2 * w.p
@@ -568,7 +582,7 @@ def run_ours(args):
         noise = (kind, float(strength))
     obs = w.graph()[:args.edges] if args.edges else None
     st = bench.setup(w, dtype, [True, False], noise=noise, obs_edges=obs,
-                     autotune=args.autotune)
+                     autotune=args.autotune, tune=args.tune == "quick")
     n_total = st["n_total"]
     grad_step, fwd_step = bench.step_fn(st, True), bench.step_fn(st, False)
 

@@ -34,11 +34,18 @@ def default_candidates(graph: bool = True):
     out = []
     for occ in (False, True):
         for sr in (9, 10, 11):
-            for tt in (15, 16, 17):
+            for tt in (15, 16, 17, 18):
                 for sb in (16384, 32768):
                     out.append(dict(DEFAULTS, small_rank=sr, task_terms_log2=tt,
                                     subtree_bytes=sb, graph_hi_occupancy=occ))
     return out
+
+
+def quick_candidates():
+    """A short list for graph programs: the rank above which tensors live in
+    global memory (9, 10) x multiply-adds per chunk task (2^16, 2^17, 2^18)."""
+    return [dict(DEFAULTS, small_rank=sr, task_terms_log2=tt)
+            for sr in (9, 10) for tt in (16, 17, 18)]
 
 
 def signature(batch, dtype: str, want_grad: bool, device_name: str) -> str:

@@ -51,15 +51,15 @@ class FakeBatch:
 def test_picks_fastest_skips_failures_and_caches(tmp_path):
     eng, batch = FakeEngine(), FakeBatch()
     times = {(sr, tt, sb): 10.0 + sr - 0.5 * tt + sb / 32768
-             for sr in (9, 10, 11) for tt in (15, 16, 17) for sb in (16384, 32768)}
+             for sr in (9, 10, 11) for tt in (15, 16, 17, 18) for sb in (16384, 32768)}
     timer = lambda: times[eng.opts] + (0.1 if eng.occ else 0.0)  # noqa: E731
     path = tmp_path / "tune.json"
     res = at.autotune(eng, batch, "c64", True, cache_path=str(path), timer=timer,
                       device_name="GB300")
-    assert (res["small_rank"], res["task_terms_log2"], res["subtree_bytes"]) == (9, 17, 16384)
+    assert (res["small_rank"], res["task_terms_log2"], res["subtree_bytes"]) == (9, 18, 16384)
     assert res["graph_hi_occupancy"] is False
     assert res["cached"] is False
-    assert eng.opts == (9, 17, 16384)          # the choice is applied last
+    assert eng.opts == (9, 18, 16384)          # the choice is applied last
     failed = [t for t in res["trials"] if t["ms"] is None]
     assert len(failed) == 2 and "arena" in failed[0]["error"]   # on both kernel builds
     table = json.loads(path.read_text())
@@ -68,7 +68,7 @@ def test_picks_fastest_skips_failures_and_caches(tmp_path):
     eng2 = FakeEngine()
     res2 = at.autotune(eng2, batch, "c64", True, cache_path=str(path),
                        timer=lambda: pytest.fail("timed a cached batch"), device_name="GB300")
-    assert res2["cached"] is True and eng2.opts == (9, 17, 16384)
+    assert res2["cached"] is True and eng2.opts == (9, 18, 16384)
 
 
 def test_signature_separates_dtype_gradient_device_and_structure():
