@@ -71,20 +71,30 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
   return make_double2(a.x + b.x, a.y + b.y);
 }
 
-// Thread 0 only.  Waits until every producer counter of `task` reaches its
-// target; false when the error flag is (or becomes) set or the bound expires.
-__device__ bool wait_for_producers(const GraphProgDev& prog, const GTask& task) {
+// Called by the team's first warp: waits until every producer counter of
+// `task` reaches its target; false when the error flag is (or becomes) set or
+// the bound expires.  Lane i polls producer counter i (32 at a time), so the
+// checks cost one memory round trip instead of one per producer; all 32 lanes
+// get the same answer.
+__device__ bool wait_for_producers_warp(const GraphProgDev& prog, const GTask& task,
+                                        uint32_t lane) {
   volatile unsigned* err = prog.counters + CTR_ERROR;
-  if (*err) return false;
+  if (__any_sync(0xffffffffu, *err != 0u)) return false;
   const unsigned long long t0 = now_ns();
-  for (uint32_t i = 0; i < task.wait_count; ++i) {
-    const WaitDev w = prog.waits[task.wait_begin + i];
-    const unsigned* c = prog.counters + ctr_index(w.counter);
+  for (uint32_t base = 0; base < task.wait_count; base += 32) {
+    const uint32_t i = base + lane;
+    const bool mine = i < task.wait_count;
+    WaitDev w{};
+    if (mine) w = prog.waits[task.wait_begin + i];
+    const unsigned* c = prog.counters + ctr_index(mine ? w.counter : 0u);
     unsigned sleep_ns = 64;   // exponential backoff, capped at 1 us
-    while (ld_acquire(c) < w.target) {
-      if (*err) return false;
-      if ((long long)(now_ns() - t0) > prog.wait_limit_ns) {
-        atomicCAS(prog.counters + CTR_ERROR, 0u, (unsigned)QTC_ERR_TIMEOUT);
+    for (;;) {
+      const bool done = !mine || ld_acquire(c) >= w.target;
+      if (__all_sync(0xffffffffu, done)) break;
+      if (__any_sync(0xffffffffu, *err != 0u)) return false;
+      const bool late = (long long)(now_ns() - t0) > prog.wait_limit_ns;
+      if (__any_sync(0xffffffffu, late)) {
+        if (lane == 0) atomicCAS(prog.counters + CTR_ERROR, 0u, (unsigned)QTC_ERR_TIMEOUT);
         return false;
       }
       __nanosleep(sleep_ns);
@@ -1315,12 +1325,16 @@ __global__ void __launch_bounds__(kGraphBlock*(kTc ? 4 : 1),
   }
 
   for (;;) {
-    if (team.tid == 0) {
-      const unsigned int t = atomicAdd(&prog.counters[CTR_QUEUE], 1u);
-      int ok = t < (unsigned)prog.n_tasks;
-      if (ok) ok = wait_for_producers(prog, prog.tasks[t]);
-      s_task[team.id] = t;
-      s_flag[team.id] = ok;
+    if (team.tid < 32) {
+      unsigned int t = 0;
+      if (team.tid == 0) t = atomicAdd(&prog.counters[CTR_QUEUE], 1u);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      bool ok = t < (unsigned)prog.n_tasks;
+      if (ok) ok = wait_for_producers_warp(prog, prog.tasks[t], team.tid);
+      if (team.tid == 0) {
+        s_task[team.id] = t;
+        s_flag[team.id] = ok;
+      }
     }
     team.sync();
     if (!s_flag[team.id]) break;
