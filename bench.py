@@ -55,7 +55,7 @@ NCU_TRAFFIC = {
     ("qaoa_p1_n50_d3", "smem_exec_kernel", "c64", True):
         (640512, "933297db19fe3c82", "profiles/smem_exec_kernel_qaoa_p1_n50_d3.md"),
     ("qaoa_p3_n60_d4", "graph_exec_kernel", "c64", True):
-        (23060459648, "af0aa91f218a49c5", "profiles/graph_exec_kernel_qaoa_p3_n60_d4.md"),
+        (23111387648, "8838fa3bffc44c32", "profiles/graph_exec_kernel_qaoa_p3_n60_d4.md"),
 }
 
 
