@@ -53,7 +53,7 @@ KERNEL_SOURCES = {
 NCU_TRAFFIC = {
     # (workload, kernel, dtype, want_grad): (bytes per launch, source hash, profile summary)
     ("qaoa_p1_n50_d3", "smem_exec_kernel", "c64", True):
-        (640512, "933297db19fe3c82", "profiles/smem_exec_kernel_qaoa_p1_n50_d3.md"),
+        (643840, "48e4649410569c71", "profiles/smem_exec_kernel_qaoa_p1_n50_d3.md"),
     ("qaoa_p3_n60_d4", "graph_exec_kernel", "c64", True):
         (23111387648, "8838fa3bffc44c32", "profiles/graph_exec_kernel_qaoa_p3_n60_d4.md"),
 }
