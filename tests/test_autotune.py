@@ -96,3 +96,21 @@ def test_task_option_ranges_are_checked():
     lib = q.lib
     assert lib.qtc_engine_set_task_options(None, 16, 32768, 1, 0) != 0
 
+
+
+def test_quick_candidates_as_the_bench_runs_them():
+    """The bench's quick tuning: small_rank 9 and 10 x 2^16, 2^17, 2^18-term
+    tasks, nothing else changed; with no cache file the fastest is applied
+    and nothing is stored."""
+    cands = at.quick_candidates()
+    assert [(c["small_rank"], c["task_terms_log2"]) for c in cands] == [
+        (9, 16), (9, 17), (9, 18), (10, 16), (10, 17), (10, 18)]
+    for c in cands:
+        assert {k: v for k, v in c.items() if k not in ("small_rank", "task_terms_log2")} == {
+            k: v for k, v in at.DEFAULTS.items() if k not in ("small_rank", "task_terms_log2")}
+    eng, batch = FakeEngine(), FakeBatch()
+    times = {(sr, tt, 32768): 5.0 + 0.1 * sr - 0.2 * tt for sr in (9, 10) for tt in (16, 17, 18)}
+    res = at.autotune(eng, batch, "c64", True, candidates=cands, timer=lambda: times[eng.opts],
+                      device_name="GB300")
+    assert (res["small_rank"], res["task_terms_log2"]) == (9, 18)
+    assert eng.opts == (9, 18, 32768) and len(res["trials"]) == 6 and res["cached"] is False
